@@ -1,0 +1,162 @@
+"""Plain, slow FP64 CPU oracle of 1-D (Core) AFD (arXiv:1711.08604).
+
+TEST INFRASTRUCTURE ONLY.  This package is imported by the test suite, by
+``__graft_entry__.smoke()`` and by the CPU-baseline leg of ``bench.py``; the
+product package ``paper_1711_08604_gb300`` never imports, links or runs it.
+It shares no code with the CUDA path.
+
+The arithmetic lives in ``afd_oracle.c`` (plain C99 complex, FP64, OpenMP over
+grid points); this module only compiles it with gcc and marshals numpy arrays.
+What each function computes, with the paper passage it follows:
+
+* ``inner``   -- the rectangle-rule inner product <G, e_a>~, Sec. 3.1 Eq. (formula1).
+* ``grid``    -- the same on the polar grid a_{s,j} = r_s exp(2 pi i j/N), Eq. (ku1)/(term81).
+* ``update``  -- the reduced-remainder (Blaschke) update of Sec. 2.
+* ``energy``  -- (1/N) sum |G(z_m)|^2, the discrete norm in the measure dt/2pi of Eq. (formula2).
+* ``decompose`` -- the greedy loop of Sec. 2 with the grid selection of Sec. 3.2
+  (Step 2) and the relative error delta of Eq. (er).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "afd_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``afd_oracle.c`` into ``liboracle.so`` (gcc -O2, OpenMP, no fast-math, no FMA contraction)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        lib.oracle_inner.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, _dp]
+        lib.oracle_grid.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
+        lib.oracle_update.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, _dp]
+        lib.oracle_energy.argtypes = [ctypes.c_int, _dp]
+        lib.oracle_energy.restype = ctypes.c_double
+        lib.oracle_decompose.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_int, _ip, ctypes.c_int,
+                                         _dp, _dp, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp]
+        lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+        _lib = lib
+        return lib
+
+
+def _cvec(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+
+
+def _rvec(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    _load().oracle_set_num_threads(int(n))
+
+
+def inner(G, a: complex) -> complex:
+    """<G, e_a>~ by the rectangle rule of Eq. (formula1)."""
+    g = _cvec(G)
+    out = np.zeros(2)
+    if _load().oracle_inner(g.size, _p(g), float(np.real(a)), float(np.imag(a)), _p(out)) != 0:
+        raise ValueError("oracle_inner: bad arguments")
+    return complex(out[0], out[1])
+
+
+def grid(G, radii) -> np.ndarray:
+    """(M, N) complex array of <G, e_{a_{s,j}}>~ over the polar grid, Eq. (term81)."""
+    g, r = _cvec(G), _rvec(radii)
+    A = np.zeros((r.size, g.size), dtype=np.complex128)
+    if _load().oracle_grid(g.size, _p(g), r.size, _p(r), _p(A)) != 0:
+        raise ValueError("oracle_grid: bad arguments")
+    return A
+
+
+def update(G, a: complex, c: complex) -> np.ndarray:
+    """G_{k+1} from G_k, a_k and c_k = <G_k, e_{a_k}> (Sec. 2)."""
+    g = _cvec(G)
+    out = np.zeros_like(g)
+    if _load().oracle_update(g.size, _p(g), float(np.real(a)), float(np.imag(a)),
+                             float(np.real(c)), float(np.imag(c)), _p(out)) != 0:
+        raise ValueError("oracle_update: bad arguments")
+    return out
+
+
+def energy(G) -> float:
+    """(1/N) sum_m |G(z_m)|^2."""
+    g = _cvec(G)
+    return float(_load().oracle_energy(g.size, _p(g)))
+
+
+def decompose(G, radii, K_max: int, energy_tol: float = 0.0, force_a1_zero: bool = False,
+              forced_idx=None, compute_grid: bool = True) -> dict:
+    """Core AFD: K_max greedy steps (or until delta <= energy_tol).
+
+    ``forced_idx`` is an optional (K_max, 2) int array of grid indices (s, j)
+    to use instead of the argmax (rows with s < 0 are free).  With
+    ``compute_grid=False`` every step must be forced and the O(M N^2) grid is
+    skipped; the coefficient then comes from ``inner`` at the forced point.
+    """
+    g, r = _cvec(G), _rvec(radii)
+    K = int(K_max)
+    fi = None
+    if forced_idx is not None:
+        fi = np.full((K, 2), -1, dtype=np.int32)
+        f = np.asarray(forced_idx, dtype=np.int32).reshape(-1, 2)
+        fi[: min(K, f.shape[0])] = f[:K]
+        fi = np.ascontiguousarray(fi)
+    a = np.zeros(K, dtype=np.complex128)
+    c = np.zeros(K, dtype=np.complex128)
+    idx = np.zeros((K, 2), dtype=np.int32)
+    own = np.zeros((K, 2), dtype=np.int32)
+    objmax = np.zeros(K)
+    obj2 = np.zeros(K)
+    objused = np.zeros(K)
+    delta = np.zeros(K + 1)
+    E = np.zeros(K + 1)
+    Gf = np.zeros_like(g)
+    steps = _load().oracle_decompose(
+        g.size, _p(g), r.size, _p(r), K, float(energy_tol), int(bool(force_a1_zero)),
+        fi.ctypes.data_as(_ip) if fi is not None else None, int(bool(compute_grid)),
+        _p(a), _p(c), idx.ctypes.data_as(_ip), own.ctypes.data_as(_ip), _p(objmax), _p(obj2),
+        _p(objused), _p(delta), _p(E), _p(Gf))
+    if steps < 0:
+        raise ValueError("oracle_decompose: bad arguments")
+    return {"steps": steps, "a": a[:steps], "coeff": c[:steps], "idx": idx[:steps],
+            "own_idx": own[:steps], "objmax": objmax[:steps], "obj2": obj2[:steps],
+            "objused": objused[:steps], "delta": delta[: steps + 1], "energy": E[: steps + 1],
+            "G_final": Gf}

@@ -1,0 +1,204 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: an exact
+identity the paper proves (the FFT route of Theorem 2.1 / Eq. (rcl)), closed
+forms of the discrete Szego-kernel inner product, the reproducing property of
+e_b, the decomposition identity Eq. (Sn) with the Takenaka-Malmquist system,
+the energy identity of Sec. 2 in its exact discrete form, brute-force argmax
+on small grids, and the relative errors printed in Tables 4 and 6.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_08604_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _fft_route(G, radii):
+    """Eq. (rcl) / Theorem 2.1: <G,e_{a_j}>~ = sqrt(1-r^2)/(N(1-r^N)) sum_l r^l c_l w^{jl},
+    c = forward DFT of the samples (Eq. (term4)), evaluated with numpy's FFT."""
+    N = G.size
+    c = np.fft.fft(G)
+    l = np.arange(N)
+    rows = []
+    for r in radii:
+        # numpy's ifft is (1/N) sum_l f_l exp(+2 pi i j l / N)
+        rows.append(np.sqrt(1.0 - r * r) / (1.0 - r ** N) * np.fft.ifft((r ** l) * c))
+    return np.array(rows)
+
+
+def _discrete_szego_inner(a, b, N):
+    """Closed form of the rectangle rule <e_b, e_a>~ on N points: summing the two
+    geometric series and folding indices mod N gives
+    sqrt(1-|a|^2) sqrt(1-|b|^2) (1 - (a conj b)^N) / ((1 - a conj b)(1 - a^N)(1 - conj(b)^N))."""
+    bc = np.conj(b)
+    return (np.sqrt(1 - abs(a) ** 2) * np.sqrt(1 - abs(b) ** 2) * (1 - (a * bc) ** N)
+            / ((1 - a * bc) * (1 - a ** N) * (1 - bc ** N)))
+
+
+@pytest.mark.parametrize("N", [8, 16, 32, 64])
+def test_direct_sum_equals_fft_route(N):
+    G = W.random_signal(N, 17 + N)
+    radii = np.array([0.0, 0.1, 0.5, 0.9, 0.99])
+    A = oracle.grid(G, radii)
+    B = _fft_route(G, radii)
+    assert np.max(np.abs(A - B)) <= 1e-13 * max(1.0, np.max(np.abs(B)))
+
+
+def test_direct_sum_equals_fft_route_workload1():
+    s = W.kernel_sum()
+    A = oracle.grid(s.G, s.radii)
+    B = _fft_route(s.G, s.radii)
+    assert np.max(np.abs(A - B)) <= 1e-12 * np.max(np.abs(B))
+
+
+@pytest.mark.parametrize("N", [8, 64, 256])
+def test_inner_matches_discrete_szego_closed_form(N):
+    rng = np.random.default_rng(5 + N)
+    for _ in range(6):
+        a = 0.97 * np.sqrt(rng.random()) * np.exp(2j * np.pi * rng.random())
+        b = 0.97 * np.sqrt(rng.random()) * np.exp(2j * np.pi * rng.random())
+        G = W.szego_sum(N, np.array([b]), np.array([1.0]))
+        got = oracle.inner(G, a)
+        want = _discrete_szego_inner(a, b, N)
+        assert abs(got - want) <= 1e-12 * max(1.0, abs(want))
+    # a = b: the discrete norm ||e_b||^2 = (1 - |b|^{2N}) / |1 - b^N|^2
+    b = 0.8 * np.exp(0.3j)
+    G = W.szego_sum(N, np.array([b]), np.array([1.0]))
+    want = (1 - abs(b) ** (2 * N)) / abs(1 - b ** N) ** 2
+    assert abs(oracle.inner(G, b) - want) <= 1e-12 * want
+    assert abs(oracle.energy(G) - want) <= 1e-12 * want
+
+
+def test_inner_at_zero_is_mean():
+    G = W.random_signal(128, 3)
+    assert abs(oracle.inner(G, 0.0) - G.mean()) <= 1e-15 * 128
+
+
+def test_reproducing_kernel_selects_b():
+    # b on the grid: radius index 25 of radii i/50 and angle index 17 of N = 256.
+    N, radii = 256, W.radii_linear(50)
+    s, j = 25, 17
+    b = radii[s] * np.exp(2j * np.pi * j / N)
+    G = W.szego_sum(N, np.array([b]), np.array([1.0]))
+    d = oracle.decompose(G, radii, 1)
+    assert tuple(d["idx"][0]) == (s, j)
+    assert abs(abs(d["coeff"][0]) - 1.0) <= 1e-13
+    assert abs(d["a"][0] - b) <= 1e-15
+    assert np.max(np.abs(d["G_final"])) <= 1e-13
+    assert d["delta"][1] <= 1e-25
+
+
+def test_constant_signal_ties_go_to_lowest_index():
+    # G = 1: <G, e_a>~ = sqrt(1-r^2)/(1 - a^N); at r = 0 all N angles tie exactly
+    # at the largest value 1, so the lowest flat index (0, 0) wins.
+    N, radii = 64, np.array([0.0, 0.2, 0.5])
+    d = oracle.decompose(np.ones(N, dtype=complex), radii, 1)
+    assert tuple(d["idx"][0]) == (0, 0)
+    assert abs(d["coeff"][0] - 1.0) <= 1e-15
+    assert np.max(np.abs(d["G_final"])) <= 1e-15
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_argmax_brute_force_small(seed):
+    N = 16
+    G = W.random_signal(N, 100 + seed)
+    radii = np.array([0.0, 0.3, 0.6, 0.85])
+    A = oracle.grid(G, radii)
+    obj = A.real ** 2 + A.imag ** 2
+    flat = int(np.argmax(obj.reshape(-1)))  # numpy returns the first maximum
+    d = oracle.decompose(G, radii, 1)
+    assert tuple(d["idx"][0]) == (flat // N, flat % N)
+    assert abs(d["coeff"][0] - A.reshape(-1)[flat]) == 0.0
+    assert d["objmax"][0] == obj.reshape(-1)[flat]
+
+
+def test_energy_identity_exact_discrete_form():
+    # E_{k+1} = ||G_k - c_k e_{a_k}||^2_N because the Blaschke factor is unimodular
+    # on the circle; with <G_k, e_a>~ = c_k and ||e_a||^2_N = (1+r^N)/(1-r^N) for
+    # a on the grid this is E_{k+1} = E_k - |c_k|^2 + |c_k|^2 2 r^N / (1 - r^N).
+    s = W.kernel_sum()
+    d = oracle.decompose(s.G, s.radii, 20)
+    E, c, a = d["energy"], d["coeff"], d["a"]
+    N = s.N
+    for k in range(d["steps"]):
+        r = abs(a[k])
+        want = E[k] - abs(c[k]) ** 2 + abs(c[k]) ** 2 * 2 * r ** N / (1 - r ** N)
+        assert abs(E[k + 1] - want) <= 1e-12 * E[0]
+
+
+def test_energy_identity_plain_form_when_rN_negligible():
+    # Sec. 2: ||G||^2 = sum_k |<G_k, e_{a_k}>|^2 + ||G_{n+1}||^2 when r_max^N <= 1e-14.
+    s = W.kernel_sum()
+    radii = np.arange(18) / 20.0  # r_max = 0.85, 0.85^256 ~ 8e-19
+    d = oracle.decompose(s.G, radii, 20)
+    lhs = d["energy"][0]
+    rhs = np.sum(np.abs(d["coeff"]) ** 2) + d["energy"][-1]
+    assert abs(lhs - rhs) <= 1e-12 * lhs
+
+
+def test_decomposition_identity_Sn():
+    # Eq. (Sn): G = sum_k c_k B_k + G_{n+1} prod_k (z - a_k)/(1 - conj(a_k) z) pointwise,
+    # B_k = e_{a_k} prod_{l<k} (z - a_l)/(1 - conj(a_l) z) (without the 1/sqrt(2 pi)
+    # factor, in the normalised measure); hence delta_n = ||G - S_n||^2_N / ||G||^2_N.
+    s = W.kernel_sum()
+    n = 8
+    d = oracle.decompose(s.G, s.radii, n)
+    z = W.sample_points(s.N)
+    S = np.zeros_like(z)
+    prod = np.ones_like(z)
+    for a, c in zip(d["a"], d["coeff"]):
+        e = np.sqrt(1 - abs(a) ** 2) / (1 - np.conj(a) * z)
+        S += c * e * prod
+        prod *= (z - a) / (1 - np.conj(a) * z)
+    resid = s.G - S
+    assert np.max(np.abs(resid - d["G_final"] * prod)) <= 1e-12 * np.max(np.abs(s.G))
+    delta = np.mean(np.abs(resid) ** 2) / np.mean(np.abs(s.G) ** 2)
+    assert abs(delta - d["delta"][n]) <= 1e-12
+
+
+def test_forced_sequence_reproduces_free_run():
+    s = W.kernel_sum(item=3)
+    free = oracle.decompose(s.G, s.radii, 6)
+    forced = oracle.decompose(s.G, s.radii, 6, forced_idx=free["idx"], compute_grid=False)
+    assert np.array_equal(free["idx"], forced["idx"])
+    assert np.array_equal(free["coeff"], forced["coeff"])
+    assert np.array_equal(free["delta"], forced["delta"])
+
+
+def test_stop_on_energy_tolerance():
+    s = W.kernel_sum(item=1)
+    full = oracle.decompose(s.G, s.radii, 10)
+    tol = full["delta"][4] * 1.0000001
+    d = oracle.decompose(s.G, s.radii, 10, energy_tol=tol)
+    assert d["steps"] == 4
+
+
+def test_bad_arguments_raise():
+    with pytest.raises(ValueError):
+        oracle.grid(np.ones(8), [0.0, 1.0])
+    with pytest.raises(ValueError):
+        oracle.decompose(np.ones(8), [0.5, 0.2], 2)
+    with pytest.raises(ValueError):
+        oracle.decompose(np.ones(8), [0.1, 0.2], 2, force_a1_zero=True)
+
+
+def _golden(name):
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, name)) if ln.strip() and not ln.startswith("#")]
+    return np.array([float(r[1]) for r in rows])
+
+
+@pytest.mark.parametrize("fname,signal,tol", [
+    ("table4_case1_delta.txt", W.paper_f1, 2e-3),
+    ("table6_case2_delta.txt", W.paper_f2, 3e-3),
+])
+def test_paper_tables_soft_pin(fname, signal, tol):
+    # Tables 4 and 6 (Sec. 4.1): delta after n steps, N = 1024, radii 0..0.8, a_1 = 0.
+    want = _golden(fname)
+    d = oracle.decompose(signal(1024), W.radii_paper(), 10, force_a1_zero=True)
+    got = d["delta"][1:11]
+    assert np.max(np.abs(got - want)) <= tol
