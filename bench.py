@@ -1,0 +1,296 @@
+#!/usr/bin/env python
+"""Throughput of FFT-accelerated Core AFD (arXiv:1711.08604) on GB300.
+
+Workload (default): one signal of N = 4096 samples (20 seeded tones with
+amplitude 1/f plus noise, positive-frequency projected), M = 200 radii i/200,
+K = 50 greedy steps, FP32 grid with FP64 guard and update.  One bench step is
+one whole decomposition (all K greedy steps: forward FFT, M inverse FFTs with
+the fused objective and argmax, FP64 guard, remainder update, energy).
+
+Metric: grid evaluations per second, M * N * K / time, with the input resident
+in device memory when the timed region starts; L2 is flushed (a 256 MiB write)
+between timed steps, outside the timed intervals.  Also reported: signals/s,
+p50/p99 latency per decomposition, end-to-end figures through the C ABI from
+pinned host memory, the grid kernel's roofline, SM clocks sampled during the
+timed region, and the CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl afd|reference]
+                  [--precision fp32|fp64]
+For N > 1 launch with torch.distributed.run; every rank decomposes its own
+copy of the workload (independent replicas, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "AFD grid evals/s (M*N*K/s)"
+UNIT = "grid_evals/s"
+N_SIG, M_RAD, K_STEPS = 4096, 200, 50
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+STEPREC_BYTES, SLOTCTL_BYTES, SLOTDEV_BYTES = 80, 40, 216
+
+
+def workload():
+    from paper_1711_08604_gb300 import workloads as W
+    return W.tones(N=N_SIG, M=M_RAD, K=K_STEPS)
+
+
+def workload_name(prec: str) -> str:
+    return (f"tones: single signal N={N_SIG}, M={M_RAD} radii i/{M_RAD}, K={K_STEPS} steps, "
+            + ("FP32 grid + FP64 guard/update" if prec == "fp32" else "FP64 plain"))
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu, self.proc, self.file = gpu, None, None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.file, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        if not self.proc or not self.file:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = [float(r[2]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(rows),
+                "reasons": reasons}
+
+
+def cpu_baseline(s, sample_steps: int = 2) -> dict:
+    """The FP64 oracle, as it stands, on the host cores: the first sample_steps
+    greedy steps of the same workload (full M x N grid each)."""
+    import oracle
+    t0 = time.perf_counter()
+    d = oracle.decompose(s.G, s.radii, sample_steps)
+    dt = time.perf_counter() - t0
+    evals = s.M * s.N * d["steps"]
+    return {"value": evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {d['steps']} of {s.K} greedy steps of the same workload "
+                      f"(direct O(M N^2) grid, {evals} grid evals, {dt:.2f} s)"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on a bounded sample of the workload per step."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    s = workload()
+    sub = s.radii[:: 8]                       # 25 of the 200 radii
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.decompose(s.G, sub, 1)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    evals = sub.size * s.N
+    value = evals * len(times) / sum(times)
+    sample = (f"one greedy step of the workload over {sub.size} of its {s.M} radii "
+              f"(every 8th), direct O(M N^2) grid")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(args.precision), "N": s.N,
+                                            "M": s.M, "K": s.K, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_afd(args):
+    import torch
+    import paper_1711_08604_gb300 as afd
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    afd._native.load()
+    s = workload()
+    prec = afd.AFD_FP32_GUARDED if args.precision == "fp32" else afd.AFD_FP64_PLAIN
+    stream = torch.cuda.Stream(device=dev)
+    plan = afd.afd_plan_create(s.N, s.radii, precision=prec, device=local, stream=stream.cuda_stream,
+                               use_graph=True)
+    K = s.K
+    Gd = torch.from_numpy(s.G).to(dev)
+    out = {"a": torch.zeros(2 * K, dtype=torch.float64, device=dev),
+           "coeff": torch.zeros(2 * K, dtype=torch.float64, device=dev),
+           "delta": torch.zeros(K + 1, dtype=torch.float64, device=dev),
+           "idx": torch.zeros(2 * K, dtype=torch.int32, device=dev)}
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    torch.cuda.synchronize()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed_loop(n, G_in, outs):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for e0, e1 in ev:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0.record(stream)
+            r = afd.afd_decompose(plan, G_in, K, 0.0, out=outs)
+            e1.record(stream)
+            assert r["steps"] == K
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+    for _ in range(args.warmup):
+        timed_loop(1, Gd, out)
+    # device-resident timed region
+    afd.afd_plan_reset_counters(plan)
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        ms = timed_loop(args.steps, Gd, out)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    launches = afd.afd_plan_counters(plan)["kernel_launches"]
+    total_ms = sum(ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    evals_per_step = s.M * s.N * K
+    value = evals_per_step * args.steps * ws / (total_ms * 1e-3)
+
+    # grid-kernel roofline: the same steps with CUDA events around every grid launch
+    afd.afd_plan_set_profiling(plan, True)
+    afd.afd_plan_reset_counters(plan)
+    prof_ms = timed_loop(args.steps, Gd, out)
+    c = afd.afd_plan_counters(plan)
+    afd.afd_plan_set_profiling(plan, False)
+    grid_avg_ms = c["grid_ms"] / max(1, c["grid_launches"])
+    logn = int(np.log2(s.N))
+    flops_per_eval = 5 * logn + 6
+    grid_flops = s.M * s.N * flops_per_eval
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clocks = clk.summary()
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    achieved_tflops = grid_flops / (grid_avg_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": f"k_grid<float,{logn}>", "achieved": achieved_tflops,
+                "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
+                "traffic": None,
+                "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                "flops_per_launch": grid_flops, "avg_launch_ms": grid_avg_ms,
+                "profiled_ms_per_step": statistics.mean(prof_ms)}
+
+    # end to end through the C ABI: pinned host input, host outputs, copies timed
+    G_pin = torch.from_numpy(s.G).pin_memory()
+    for _ in range(2):
+        timed_loop(1, G_pin, None)
+    barrier()
+    e2e_ms = timed_loop(args.steps, G_pin, None)
+    e2e_total = sum(e2e_ms)
+    if ws > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e = {"value": evals_per_step * args.steps * ws / (e2e_total * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": 16 * s.N + SLOTDEV_BYTES,
+           "d2h_bytes_per_step": STEPREC_BYTES * K + SLOTCTL_BYTES}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.precision), "N": s.N, "M": s.M, "K": K,
+                       "precision": args.precision, "parallelism": f"replicas x{ws}",
+                       "l2": "flushed (256 MiB write) between timed steps, outside the timed intervals"},
+            "signals_per_s": args.steps * ws / (total_ms * 1e-3),
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                           "min": min(ms), "max": max(ms)},
+            "wall_s": t_wall,
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "e2e": e2e,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(s)
+        print(json.dumps(line))
+    plan.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["afd", "reference"], default="afd")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_afd(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * afd.h -- C ABI of the GB300 (sm_103a) implementation of FFT-accelerated
+ * 1-D (Core) adaptive Fourier decomposition, after Gao, Ku and Qian, "Fast
+ * algorithm of adaptive Fourier series" (arXiv:1711.08604).
+ *
+ * Notation.  A signal is given by N samples G(z_m) at z_m = exp(2 pi i m / N),
+ * m = 0..N-1 (Sec. 3.1: t_m = 2 pi m / N).  The dictionary grid is
+ * a_{s,j} = r_s exp(2 pi i j / N) for M radii r_s and the same N angles
+ * (Eq. (ku1), Sec. 3.2; the paper writes r_s W^{-j}, W = exp(-2 pi i / N)).
+ * Each greedy step k picks a_k = argmax over the grid of |<G_k, e_a>~|^2
+ * (Eq. (ak) restricted to the grid, Step 2 of Sec. 3.2), with <G, e_a>~ the
+ * rectangle rule of Eq. (formula1) in the normalised measure dt / 2 pi, and
+ * replaces G_k by the reduced remainder of Sec. 2,
+ *     G_{k+1}(z) = (G_k(z) - <G_k, e_{a_k}> e_{a_k}(z)) (1 - conj(a_k) z) / (z - a_k).
+ * The relative error after k steps is delta_k = ||G - S_k||^2 / ||G||^2
+ * (Eq. (er)) = E_{k+1} / E_1 with E = (1/N) sum_m |G(z_m)|^2.
+ *
+ * Conventions for every entry point:
+ *   - Complex arrays are interleaved (re, im) doubles.
+ *   - Pointers to caller data may be host memory (pageable or pinned) or
+ *     device memory of the plan's device; the library copies as needed.  The
+ *     caller owns every buffer it passes; nothing is retained after return.
+ *   - Calls are synchronous: outputs are complete when the call returns.
+ *   - No exception or abort crosses the ABI; errors are returned as
+ *     afd_status and described by afd_last_error() (thread-local text).
+ *   - Ties in the selection go to the lowest flat index s * N + j, with the
+ *     radii in the given (ascending) order.
+ */
+#ifndef AFD_H
+#define AFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum afd_status {
+  AFD_OK = 0,
+  AFD_PENDING = 1,          /* serving: request not finished yet */
+  AFD_ERR_INVALID = -1,     /* bad argument (size, radius, pointer, option) */
+  AFD_ERR_NOMEM = -2,       /* device or host allocation failed */
+  AFD_ERR_CUDA = -3,        /* a CUDA call failed; see afd_last_error() */
+  AFD_ERR_TIMEOUT = -4,     /* a bounded wait ran out */
+  AFD_ERR_BUDGET = -5,      /* request larger than the serving memory budget */
+  AFD_ERR_NOT_FOUND = -6,   /* unknown request id */
+  AFD_ERR_NUMERIC = -7      /* non-finite objective: input holds NaN or Inf */
+} afd_status;
+
+typedef enum afd_precision {
+  /* FFTs, grid and selection in FP64; coefficient taken from the FP64 grid. */
+  AFD_FP64_PLAIN = 0,
+  /* FFTs and grid in FP32 (twiddles and powers from FP64 tables); every grid
+   * point whose FP32 objective is within guard_tau (relative) of the largest
+   * is re-evaluated by the FP64 direct sum of Eq. (formula1), which decides
+   * the selection and gives the coefficient.  Remainder and energy in FP64. */
+  AFD_FP32_GUARDED = 1
+} afd_precision;
+
+typedef struct afd_plan_opts {
+  int precision;       /* afd_precision; default AFD_FP32_GUARDED */
+  double guard_tau;    /* FP32 path: relative re-evaluation window; default 1e-4 */
+  int guard_cap;       /* FP32 path: most candidates re-evaluated per step, 1..64; default 16 */
+  int force_a1_zero;   /* 1: a_1 = 0 (needs radii[0] == 0); default 0 */
+  int device;          /* CUDA device ordinal; -1 (default): the current device */
+  void* stream;        /* cudaStream_t to run on (not the legacy default stream);
+                          NULL (default): a stream owned by the plan */
+  int use_graph;       /* 1 (default): replay the step sequence as a CUDA graph */
+} afd_plan_opts;
+
+typedef struct afd_plan afd_plan;
+typedef struct afd_batch afd_batch;
+
+/* Fills *opts with the defaults above. */
+void afd_plan_opts_default(afd_plan_opts* opts);
+
+/* Text of an afd_status value (static storage). */
+const char* afd_status_str(afd_status status);
+
+/* Description of the last error raised on the calling thread ("" if none). */
+const char* afd_last_error(void);
+
+/* Library version, "major.minor.patch" (static storage). */
+const char* afd_version(void);
+
+/*
+ * Creates a plan for signals of N samples and the radial grid radii[0..M-1]
+ * (Sec. 3.2, Step 1: the paper precomputes and stores r_s^l and the FFT
+ * twiddles; the plan holds them on the device, generated in FP64).
+ *   N      power of two, 8 <= N <= 16384 (FP32 path) or 8192 (FP64 path).
+ *   radii  host array of M ascending values in [0, 1); copied.
+ *   M      1 <= M <= 4096.
+ *   opts   NULL for defaults.
+ * On success *out owns device memory until afd_plan_destroy.  A plan is not
+ * thread-safe: use one plan per host thread.  Errors: AFD_ERR_INVALID for a
+ * bad size, radius or option; AFD_ERR_NOMEM; AFD_ERR_CUDA.
+ */
+afd_status afd_plan_create(afd_plan** out, int N, const double* radii, int M,
+                           const afd_plan_opts* opts);
+
+/* Frees the plan and its device memory.  NULL is accepted. */
+afd_status afd_plan_destroy(afd_plan* plan);
+
+/*
+ * Core AFD of one signal: up to K_max greedy steps (Sec. 2 with the grid
+ * selection of Sec. 3.2), stopping early once delta_k <= energy_tol
+ * (energy_tol = 0 runs all K_max steps).
+ *   G          2N doubles, G(z_m) interleaved; host or device pointer.
+ *   K_max      >= 1.
+ *   a_out      2*K_max doubles: a_k.                    (may be NULL)
+ *   coeff_out  2*K_max doubles: <G_k, e_{a_k}>~.        (may be NULL)
+ *   delta_out  K_max+1 doubles: delta_0 = 1, delta_k.   (may be NULL)
+ *   idx_out    2*K_max ints: grid index (s, j) of a_k.  (may be NULL)
+ *   steps_done number of steps performed.               (may be NULL)
+ * Entries past *steps_done are left untouched.  Output pointers may be host
+ * or device memory.  Returns AFD_ERR_NUMERIC (with the steps done so far) if
+ * an objective is not finite.
+ */
+afd_status afd_decompose(afd_plan* plan, const double* G, int K_max, double energy_tol,
+                         double* a_out, double* coeff_out, double* delta_out, int* idx_out,
+                         int* steps_done);
+
+/*
+ * Diagnostics of the plan's last afd_decompose (host pointers, may be NULL):
+ *   n_cand_out  K entries: FP64 guard candidates per step (0 on the FP64 path);
+ *   flags_out   K entries: bit 0 the candidate cap ended the list, bit 1 non-finite;
+ *   obj32_out   K entries: largest grid objective as computed by the grid kernel.
+ * K is the number of steps of that call.
+ */
+afd_status afd_plan_last_info(const afd_plan* plan, int* n_cand_out, int* flags_out,
+                              double* obj32_out);
+
+/*
+ * Kernel accounting of a plan since creation (or the last reset): launches of
+ * the library's kernels, and, while profiling is on, the summed device time of
+ * the grid kernel (CUDA events on the plan's stream around every grid launch;
+ * profiling turns graph replay off).  kernel_launches and grid_launches may be
+ * NULL; grid_ms is 0 unless profiling was on.
+ */
+afd_status afd_plan_set_profiling(afd_plan* plan, int on);
+afd_status afd_plan_counters(const afd_plan* plan, long long* kernel_launches,
+                             long long* grid_launches, double* grid_ms);
+afd_status afd_plan_reset_counters(afd_plan* plan);
+
+/*
+ * The CUDA stream the plan's kernels run on (cudaStream_t): opts->stream if
+ * one was given, else a stream the plan owns.  A plan-owned stream is ordered
+ * after work already queued on the legacy default stream at every call.
+ * Useful for recording CUDA events around calls.
+ */
+afd_status afd_plan_get_stream(const afd_plan* plan, void** stream);
+
+/*
+ * Batched Core AFD: n_signals independent decompositions of uneven N, run
+ * together (all signals' grid tiles of one N share a launch; the N classes
+ * run on parallel streams, and the step sequence is replayed as one CUDA
+ * graph when opts->use_graph is set).
+ *   N        host array, n_signals sizes (each as for afd_plan_create).
+ *   radii    host array of M radii shared by all signals.
+ *   K_max    steps per signal (>= 1); energy_tol as for afd_decompose.
+ * afd_batch_run takes the samples packed signal after signal (signal i starts
+ * at 2 * (N_0 + ... + N_{i-1}) doubles) and writes, for signal i and step k:
+ *   a_out[2(i K_max + k) + {0,1}], coeff_out likewise, idx_out likewise,
+ *   delta_out[i (K_max + 1) + k], steps_out[i].
+ * Any output may be NULL; pointers may be host or device memory.
+ */
+afd_status afd_batch_create(afd_batch** out, int n_signals, const int* N, const double* radii,
+                            int M, int K_max, const afd_plan_opts* opts);
+afd_status afd_batch_run(afd_batch* batch, const double* G_packed, double energy_tol,
+                         double* a_out, double* coeff_out, double* delta_out, int* idx_out,
+                         int* steps_out);
+afd_status afd_batch_counters(const afd_batch* batch, long long* kernel_launches);
+afd_status afd_batch_destroy(afd_batch* batch);
+
+/* One-shot batch: create, run and destroy. */
+afd_status afd_decompose_batch(int n_signals, const int* N, const double* radii, int M,
+                               const double* G_packed, int K_max, double energy_tol,
+                               const afd_plan_opts* opts, double* a_out, double* coeff_out,
+                               double* delta_out, int* idx_out, int* steps_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFD_H */

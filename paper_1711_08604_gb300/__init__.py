@@ -1,0 +1,261 @@
+"""GB300 (sm_103a) FFT-accelerated 1-D (Core) AFD, after arXiv:1711.08604.
+
+Thin Python binding of the C ABI in ``include/afd.h``: the functions below
+carry the C names and only marshal arguments (numpy arrays or torch tensors,
+host or CUDA) into ``lib/libafd.so``.  Every step of the decomposition runs
+in the library's CUDA kernels; importing a function that needs the library
+raises if it has not been built.
+
+Quick use::
+
+    import numpy as np, paper_1711_08604_gb300 as afd
+    plan = afd.afd_plan_create(4096, np.arange(200) / 200)
+    res = afd.afd_decompose(plan, G, K_max=50)      # G: complex128, N samples
+    res["a"], res["coeff"], res["delta"], res["idx"], res["steps"]
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native
+from ._native import PlanOpts
+
+__all__ = [
+    "AFD_FP64_PLAIN", "AFD_FP32_GUARDED", "AfdError", "PlanOpts", "afd_plan_opts_default",
+    "afd_status_str", "afd_last_error", "afd_version", "afd_plan_create", "afd_plan_destroy",
+    "afd_decompose", "afd_plan_last_info", "afd_plan_set_profiling", "afd_plan_counters",
+    "afd_plan_reset_counters", "afd_plan_get_stream", "afd_batch_create", "afd_batch_run", "afd_batch_counters",
+    "afd_batch_destroy", "afd_decompose_batch", "library_path",
+]
+
+AFD_FP64_PLAIN = 0
+AFD_FP32_GUARDED = 1
+STATUS = {0: "AFD_OK", 1: "AFD_PENDING", -1: "AFD_ERR_INVALID", -2: "AFD_ERR_NOMEM",
+          -3: "AFD_ERR_CUDA", -4: "AFD_ERR_TIMEOUT", -5: "AFD_ERR_BUDGET", -6: "AFD_ERR_NOT_FOUND",
+          -7: "AFD_ERR_NUMERIC"}
+
+
+class AfdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _native.LIB_PATH
+
+
+def _lib():
+    return _native.load()
+
+
+def _check(status: int, partial=None):
+    if status != 0 and status != 1:
+        err = AfdError(status, _lib().afd_last_error().decode())
+        err.partial = partial
+        raise err
+    return status
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _in_ptr(x, dtype=np.complex128):
+    """(pointer, keepalive) of an input array: numpy (host) or torch (host or CUDA)."""
+    if _is_torch(x):
+        import torch
+        want = torch.complex128 if dtype == np.complex128 else torch.float64
+        if x.dtype != want:
+            raise TypeError(f"expected a {want} tensor, got {x.dtype}")
+        x = x.contiguous()
+        return x.data_ptr(), x
+    a = np.ascontiguousarray(np.asarray(x, dtype=dtype))
+    return a.ctypes.data, a
+
+
+def _opts(opts=None, **kw) -> PlanOpts:
+    o = PlanOpts()
+    _lib().afd_plan_opts_default(ctypes.byref(o))
+    if opts is not None:
+        for f, _ in PlanOpts._fields_:
+            setattr(o, f, getattr(opts, f))
+    for k, v in kw.items():
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = int(getattr(v, "cuda_stream", v))
+        if k in ("force_a1_zero", "use_graph"):
+            v = int(bool(v))
+        setattr(o, k, v)
+    return o
+
+
+def afd_plan_opts_default() -> PlanOpts:
+    return _opts()
+
+
+def afd_status_str(status: int) -> str:
+    return _lib().afd_status_str(int(status)).decode()
+
+
+def afd_last_error() -> str:
+    return _lib().afd_last_error().decode()
+
+
+def afd_version() -> str:
+    return _lib().afd_version().decode()
+
+
+class Plan:
+    """Owning handle of an ``afd_plan``."""
+
+    def __init__(self, handle, N: int, M: int, opts: PlanOpts):
+        self.handle, self.N, self.M, self.opts = handle, N, M, opts
+
+    def close(self):
+        if self.handle:
+            _lib().afd_plan_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+
+class Batch:
+    """Owning handle of an ``afd_batch``."""
+
+    def __init__(self, handle, N, M: int, K_max: int):
+        self.handle, self.N, self.M, self.K_max = handle, list(N), M, K_max
+
+    def close(self):
+        if self.handle:
+            _lib().afd_batch_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+
+def afd_plan_create(N: int, radii, opts: PlanOpts | None = None, **kw) -> Plan:
+    """Plan for N samples and the given ascending radii; keyword options as in afd_plan_opts."""
+    r = np.ascontiguousarray(np.asarray(radii, dtype=np.float64))
+    o = _opts(opts, **kw)
+    h = ctypes.c_void_p()
+    _check(_lib().afd_plan_create(ctypes.byref(h), int(N), r.ctypes.data, int(r.size), ctypes.byref(o)))
+    return Plan(h, int(N), int(r.size), o)
+
+
+def afd_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def afd_decompose(plan: Plan, G, K_max: int, energy_tol: float = 0.0, out: dict | None = None) -> dict:
+    """Decompose one signal.  Returns numpy arrays a, coeff (complex), delta, idx and steps.
+
+    ``out`` may supply caller buffers (numpy or torch, host or CUDA) for keys
+    a (2K float64), coeff (2K float64), delta (K+1 float64), idx (2K int32);
+    they are then filled in place and returned as given.
+    """
+    gp, keep = _in_ptr(G)
+    K = int(K_max)
+    bufs = {"a": np.zeros(2 * K), "coeff": np.zeros(2 * K), "delta": np.zeros(K + 1),
+            "idx": np.zeros(2 * K, dtype=np.int32)}
+    if out:
+        bufs.update(out)
+    ptrs = {k: (v.data_ptr() if _is_torch(v) else v.ctypes.data) for k, v in bufs.items()}
+    steps = ctypes.c_int(0)
+    st = _lib().afd_decompose(plan.handle, gp, K, float(energy_tol), ptrs["a"], ptrs["coeff"],
+                              ptrs["delta"], ptrs["idx"], ctypes.byref(steps))
+    n = steps.value
+    res = {"steps": n}
+    if out:
+        res.update(bufs)
+    else:
+        res["a"] = bufs["a"][: 2 * n].view(np.complex128)
+        res["coeff"] = bufs["coeff"][: 2 * n].view(np.complex128)
+        res["delta"] = bufs["delta"][: n + 1]
+        res["idx"] = bufs["idx"][: 2 * n].reshape(n, 2)
+    _check(st, res)
+    return res
+
+
+def afd_plan_last_info(plan: Plan, steps: int) -> dict:
+    n_cand = np.zeros(steps, dtype=np.int32)
+    flags = np.zeros(steps, dtype=np.int32)
+    obj32 = np.zeros(steps)
+    _check(_lib().afd_plan_last_info(plan.handle, n_cand.ctypes.data, flags.ctypes.data, obj32.ctypes.data))
+    return {"n_cand": n_cand, "flags": flags, "obj32": obj32}
+
+
+def afd_plan_set_profiling(plan: Plan, on: bool) -> None:
+    _check(_lib().afd_plan_set_profiling(plan.handle, int(bool(on))))
+
+
+def afd_plan_counters(plan: Plan) -> dict:
+    kl, gl, ms = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double()
+    _check(_lib().afd_plan_counters(plan.handle, ctypes.byref(kl), ctypes.byref(gl), ctypes.byref(ms)))
+    return {"kernel_launches": kl.value, "grid_launches": gl.value, "grid_ms": ms.value}
+
+
+def afd_plan_get_stream(plan: Plan) -> int:
+    """cudaStream_t (as an int) the plan's kernels run on."""
+    sp = ctypes.c_void_p()
+    _check(_lib().afd_plan_get_stream(plan.handle, ctypes.byref(sp)))
+    return int(sp.value or 0)
+
+
+def afd_plan_reset_counters(plan: Plan) -> None:
+    _check(_lib().afd_plan_reset_counters(plan.handle))
+
+
+def afd_batch_create(N, radii, K_max: int, opts: PlanOpts | None = None, **kw) -> Batch:
+    n = np.ascontiguousarray(np.asarray(N, dtype=np.int32))
+    r = np.ascontiguousarray(np.asarray(radii, dtype=np.float64))
+    o = _opts(opts, **kw)
+    h = ctypes.c_void_p()
+    _check(_lib().afd_batch_create(ctypes.byref(h), int(n.size), n.ctypes.data, r.ctypes.data,
+                                   int(r.size), int(K_max), ctypes.byref(o)))
+    return Batch(h, n.tolist(), int(r.size), int(K_max))
+
+
+def afd_batch_run(batch: Batch, G_packed, energy_tol: float = 0.0) -> dict:
+    """Run the batch on packed samples; returns per-signal lists of arrays."""
+    gp, keep = _in_ptr(G_packed)
+    n, K = len(batch.N), batch.K_max
+    a = np.zeros(2 * n * K)
+    c = np.zeros(2 * n * K)
+    d = np.zeros(n * (K + 1))
+    ix = np.zeros(2 * n * K, dtype=np.int32)
+    steps = np.zeros(n, dtype=np.int32)
+    st = _lib().afd_batch_run(batch.handle, gp, float(energy_tol), a.ctypes.data, c.ctypes.data,
+                              d.ctypes.data, ix.ctypes.data, steps.ctypes.data)
+    res = {"steps": steps, "a": [], "coeff": [], "delta": [], "idx": []}
+    for i in range(n):
+        s = int(steps[i])
+        res["a"].append(a[2 * i * K: 2 * (i * K + s)].view(np.complex128))
+        res["coeff"].append(c[2 * i * K: 2 * (i * K + s)].view(np.complex128))
+        res["delta"].append(d[i * (K + 1): i * (K + 1) + s + 1])
+        res["idx"].append(ix[2 * i * K: 2 * (i * K + s)].reshape(s, 2))
+    _check(st, res)
+    return res
+
+
+def afd_batch_counters(batch: Batch) -> dict:
+    kl = ctypes.c_longlong()
+    _check(_lib().afd_batch_counters(batch.handle, ctypes.byref(kl)))
+    return {"kernel_launches": kl.value}
+
+
+def afd_batch_destroy(batch: Batch) -> None:
+    batch.close()
+
+
+def afd_decompose_batch(signals, radii, K_max: int, energy_tol: float = 0.0,
+                        opts: PlanOpts | None = None, **kw) -> dict:
+    """One-shot batch over a list of sample arrays (numpy complex128)."""
+    N = [int(np.asarray(g).size) for g in signals]
+    packed = np.concatenate([np.asarray(g, dtype=np.complex128) for g in signals])
+    b = afd_batch_create(N, radii, K_max, opts, **kw)
+    try:
+        return afd_batch_run(b, packed, energy_tol)
+    finally:
+        b.close()

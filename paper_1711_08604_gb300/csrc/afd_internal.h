@@ -1,0 +1,96 @@
+// Internal structures shared by the CUDA kernels and the host runtime of the
+// FFT-accelerated Core AFD library.  Not part of the public C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace afd {
+
+// Work split of the FP64 kernels: each CTA of 256 threads owns a chunk of
+// FP64_CHUNK consecutive sample points.
+constexpr int FP64_THREADS = 256;
+constexpr int FP64_CHUNK = 512;
+// Lowest-order power table length: r^l = rhi[l / RPOW_B] * rlo[l % RPOW_B].
+constexpr int RPOW_B_MAX = 64;
+constexpr int MAX_LOGN_RESIDENT = 14;  // N <= 16384: one CTA holds one FFT
+constexpr int MIN_LOGN = 3;            // N >= 8
+constexpr int MAX_CAP = 64;            // guard candidates per step, upper bound
+
+inline __host__ __device__ int chunks_of(int N) { return N > FP64_CHUNK ? N / FP64_CHUNK : 1; }
+
+// Per (N, radii) tables, owned by a plan, read-only in kernels.
+struct PlanDev {
+  int N, logN, M, B;        // B = min(RPOW_B_MAX, N); the high table has N / B entries
+  const double* radii;      // [M] ascending radii r_s in [0, 1)
+  const float2* tw32;       // [N] exp(+2 pi i k / N) rounded to FP32
+  const double2* tw64;      // [N] exp(+2 pi i k / N) in FP64 (also the sample points z_m)
+  const float* rlo32;       // [M * B]        r_s^q,        q = 0..B-1
+  const float* rhi32;       // [M * (N / B)]  r_s^(B h),    h = 0..N/B-1
+  const double* rlo64;
+  const double* rhi64;
+  const float* wsq32;       // [M] w_s^2 with w_s = sqrt(1 - r_s^2) / (1 - r_s^N)
+  const double* w64;        // [M] w_s
+  const double* sq64;       // [M] sqrt(1 - r_s^2)
+};
+
+// One greedy step's outcome, written on the device.
+struct StepRec {
+  int s, j;                 // selected grid index (radius s, angle j)
+  int n_cand;               // FP64 guard candidates evaluated (FP32 path)
+  int flags;                // bit 0: guard window saturated; bit 1: non-finite objective
+  double a_re, a_im;        // a_k = r_s exp(2 pi i j / N)
+  double c_re, c_im;        // <G_k, e_{a_k}>~
+  double obj;               // |c|^2
+  double energy;            // E_{k+1} = (1/N) sum |G_{k+1}|^2
+  double delta;             // E_{k+1} / E_1
+  double obj32;             // largest FP32 objective of the step (FP32 path)
+};
+
+// Mutable per-signal control block.
+struct SlotCtl {
+  int k;                    // greedy steps completed
+  int done;                 // set once the stop rule fires
+  int n_cand;               // candidates of the current step
+  int err;                  // sticky error bits (StepRec::flags)
+  double E1;                // initial energy
+  unsigned cnt_grid, cnt_guard, cnt_update, cnt_pad;  // last-CTA counters
+};
+
+struct Top2F { float v1, v2; int j1, j2; };
+struct Top2D { double v1, v2; int j1, j2; double2 f1, f2; };
+
+// Everything a kernel needs about one signal in flight.
+struct SlotDev {
+  PlanDev p;
+  int K_max;
+  int prec;                 // 0: FP64 plain, 1: FP32 grid + FP64 guard
+  int cap;                  // guard candidate cap
+  int force_a1_zero;
+  double tol;               // stop once delta <= tol (0: never)
+  double tau;               // guard window: obj32 >= (1 - tau) * max32
+  double2* G;               // [N] remainder G_k(z_m), FP64
+  float2* c32;              // [N] spectrum c_l / N, FP32
+  double2* c64;             // [N] spectrum c_l / N, FP64
+  void* top2;               // [M] Top2F or Top2D
+  int2* cand;               // [cap] (s, j)
+  double2* gpart;           // [cap * chunks_of(N)] guard partial sums
+  double* epart;            // [chunks_of(N)] energy partial sums
+  StepRec* rec;             // [K_max]
+  SlotCtl* ctl;
+};
+
+// Kernel launchers (afd_kernels.cu).  `ids` lists the slots of one launch, all
+// with the same logN; `n` is their number.  Each returns the launch status.
+cudaError_t launch_init(const SlotDev* slots, const int* ids, int n, int logN, cudaStream_t st);
+cudaError_t launch_grid(const SlotDev* slots, const int* ids, int n, int logN, int prec, int Mmax,
+                        cudaStream_t st);
+cudaError_t launch_guard(const SlotDev* slots, const int* ids, int n, int logN, int cap, cudaStream_t st);
+cudaError_t launch_update(const SlotDev* slots, const int* ids, int n, int logN, cudaStream_t st);
+cudaError_t launch_forward(const SlotDev* slots, const int* ids, int n, int logN, int prec,
+                           cudaStream_t st);
+// Shared memory (bytes) the grid kernel needs for this logN and precision.
+size_t grid_smem_bytes(int logN, int prec);
+size_t forward_smem_bytes(int logN, int prec);
+int grid_ffts_per_cta(int logN, int prec);
+cudaError_t configure_kernels();
+
+}  // namespace afd

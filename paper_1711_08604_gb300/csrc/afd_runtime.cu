@@ -1,0 +1,837 @@
+// Host runtime of the Core AFD library: plans, single-signal decomposition and
+// batches of uneven N.  Implements the C ABI declared in include/afd.h.
+//
+// Device memory layout.  A plan owns the tables of one (N, radii) pair: the
+// FP64 sample points / twiddles z_k = exp(2 pi i k / N) and their FP32
+// rounding, the radial power tables r_s^q and r_s^(B h) (B = min(64, N)) in
+// FP64 and FP32, and the per-radius scales.  Every signal in flight owns a
+// slot: its FP64 remainder G_k, its spectrum, the per-radius best pairs, the
+// guard candidates and partial sums, the step records and a control block.
+// A batch allocates all slots in one pooled buffer, arrays of one kind laid
+// out signal after signal, so a packed input is copied in with one memcpy.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/afd.h"
+#include "afd_internal.h"
+
+using namespace afd;
+
+// ------------------------------------------------------------------ errors --
+
+namespace {
+
+thread_local std::string g_last_error;
+
+afd_status set_error(afd_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+afd_status cuda_fail(cudaError_t e, const char* what, int line) {
+  cudaGetLastError();  // clear a non-sticky error
+  return set_error(e == cudaErrorMemoryAllocation ? AFD_ERR_NOMEM : AFD_ERR_CUDA,
+                   "%s failed (line %d): %s", what, line, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr)                                           \
+  do {                                                           \
+    cudaError_t _e = (expr);                                     \
+    if (_e != cudaSuccess) return cuda_fail(_e, #expr, __LINE__); \
+  } while (0)
+
+#define AFD_TRY(expr)                   \
+  do {                                  \
+    afd_status _s = (expr);             \
+    if (_s != AFD_OK) return _s;        \
+  } while (0)
+
+// Makes `dev` current for the scope and restores the caller's device.
+struct DeviceScope {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+std::mutex g_cfg_mu;
+bool g_configured[64] = {};
+
+afd_status ensure_configured(int dev) {
+  std::lock_guard<std::mutex> lk(g_cfg_mu);
+  if (dev < 0 || dev >= 64) return set_error(AFD_ERR_INVALID, "device ordinal %d out of range", dev);
+  if (g_configured[dev]) return AFD_OK;
+  CUDA_TRY(configure_kernels());
+  g_configured[dev] = true;
+  return AFD_OK;
+}
+
+int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+afd_status check_opts(const afd_plan_opts& o) {
+  if (o.precision != AFD_FP64_PLAIN && o.precision != AFD_FP32_GUARDED)
+    return set_error(AFD_ERR_INVALID, "precision must be AFD_FP64_PLAIN or AFD_FP32_GUARDED");
+  if (!(o.guard_tau >= 0.0 && o.guard_tau < 1.0))
+    return set_error(AFD_ERR_INVALID, "guard_tau must lie in [0, 1)");
+  if (o.guard_cap < 1 || o.guard_cap > MAX_CAP)
+    return set_error(AFD_ERR_INVALID, "guard_cap must lie in 1..%d", MAX_CAP);
+  return AFD_OK;
+}
+
+afd_status check_size(int N, int prec) {
+  if (!is_pow2(N) || N < (1 << MIN_LOGN))
+    return set_error(AFD_ERR_INVALID, "N = %d: must be a power of two >= 8", N);
+  const int maxlog = prec == AFD_FP32_GUARDED ? MAX_LOGN_RESIDENT : MAX_LOGN_RESIDENT - 1;
+  if (N > (1 << maxlog))
+    return set_error(AFD_ERR_INVALID, "N = %d: largest supported size is %d for this precision", N,
+                     1 << maxlog);
+  return AFD_OK;
+}
+
+afd_status check_radii(const double* radii, int M) {
+  if (!radii) return set_error(AFD_ERR_INVALID, "radii is NULL");
+  if (M < 1 || M > 4096) return set_error(AFD_ERR_INVALID, "M = %d: must lie in 1..4096", M);
+  for (int s = 0; s < M; ++s) {
+    if (!(radii[s] >= 0.0 && radii[s] < 1.0))
+      return set_error(AFD_ERR_INVALID, "radius %d = %g outside [0, 1)", s, radii[s]);
+    if (s > 0 && !(radii[s] > radii[s - 1]))
+      return set_error(AFD_ERR_INVALID, "radii must be strictly ascending (index %d)", s);
+  }
+  return AFD_OK;
+}
+
+// ------------------------------------------------------------------ tables --
+
+// Device tables of one (N, radii) pair, generated on the host in FP64.
+struct Tables {
+  int N = 0, M = 0;
+  std::vector<double> radii;
+  void* mem = nullptr;
+  PlanDev dev{};
+
+  ~Tables() {
+    if (mem) cudaFree(mem);
+  }
+
+  afd_status build(int N_, const double* r, int M_) {
+    N = N_;
+    M = M_;
+    radii.assign(r, r + M);
+    const int B = std::min(RPOW_B_MAX, N), H = N / B;
+    std::vector<double> tw64(2 * (size_t)N), rlo64((size_t)M * B), rhi64((size_t)M * H);
+    std::vector<float> tw32(2 * (size_t)N), rlo32((size_t)M * B), rhi32((size_t)M * H), wsq32(M);
+    std::vector<double> w64(M), sq64(M);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int k = 0; k < N; ++k) {
+      // exact values at the eighth-turn symmetry points, libm elsewhere
+      const double t = two_pi * (double)k / (double)N;
+      double c = std::cos(t), s = std::sin(t);
+      if (4 * k % N == 0) {
+        const int q = 4 * k / N;
+        c = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
+        s = (q == 1) ? 1.0 : (q == 3 ? -1.0 : 0.0);
+      }
+      tw64[2 * k] = c;
+      tw64[2 * k + 1] = s;
+      tw32[2 * k] = (float)c;
+      tw32[2 * k + 1] = (float)s;
+    }
+    for (int s = 0; s < M; ++s) {
+      const double rr = radii[s];
+      for (int q = 0; q < B; ++q) rlo64[(size_t)s * B + q] = std::pow(rr, (double)q);
+      for (int h = 0; h < H; ++h) rhi64[(size_t)s * H + h] = std::pow(rr, (double)B * h);
+      for (int q = 0; q < B; ++q) rlo32[(size_t)s * B + q] = (float)rlo64[(size_t)s * B + q];
+      for (int h = 0; h < H; ++h) rhi32[(size_t)s * H + h] = (float)rhi64[(size_t)s * H + h];
+      const double one_m_r2 = (1.0 - rr) * (1.0 + rr);
+      const double one_m_rN = 1.0 - std::pow(rr, (double)N);
+      sq64[s] = std::sqrt(one_m_r2);
+      w64[s] = sq64[s] / one_m_rN;
+      wsq32[s] = (float)(one_m_r2 / (one_m_rN * one_m_rN));
+    }
+    // one allocation, 256-byte aligned sub-arrays
+    size_t off = 0;
+    auto place = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    const size_t o_r = place(sizeof(double) * M), o_tw64 = place(16 * (size_t)N),
+                 o_tw32 = place(8 * (size_t)N), o_rlo64 = place(8 * rlo64.size()),
+                 o_rhi64 = place(8 * rhi64.size()), o_rlo32 = place(4 * rlo32.size()),
+                 o_rhi32 = place(4 * rhi32.size()), o_wsq = place(4 * (size_t)M),
+                 o_w64 = place(8 * (size_t)M), o_sq = place(8 * (size_t)M);
+    CUDA_TRY(cudaMalloc(&mem, off));
+    char* b = static_cast<char*>(mem);
+    CUDA_TRY(cudaMemcpy(b + o_r, radii.data(), 8 * (size_t)M, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_tw64, tw64.data(), 16 * (size_t)N, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_tw32, tw32.data(), 8 * (size_t)N, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_rlo64, rlo64.data(), 8 * rlo64.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_rhi64, rhi64.data(), 8 * rhi64.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_rlo32, rlo32.data(), 4 * rlo32.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_rhi32, rhi32.data(), 4 * rhi32.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_wsq, wsq32.data(), 4 * (size_t)M, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_w64, w64.data(), 8 * (size_t)M, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_sq, sq64.data(), 8 * (size_t)M, cudaMemcpyHostToDevice));
+    dev.N = N;
+    dev.logN = ilog2(N);
+    dev.M = M;
+    dev.B = B;
+    dev.radii = reinterpret_cast<const double*>(b + o_r);
+    dev.tw64 = reinterpret_cast<const double2*>(b + o_tw64);
+    dev.tw32 = reinterpret_cast<const float2*>(b + o_tw32);
+    dev.rlo64 = reinterpret_cast<const double*>(b + o_rlo64);
+    dev.rhi64 = reinterpret_cast<const double*>(b + o_rhi64);
+    dev.rlo32 = reinterpret_cast<const float*>(b + o_rlo32);
+    dev.rhi32 = reinterpret_cast<const float*>(b + o_rhi32);
+    dev.wsq32 = reinterpret_cast<const float*>(b + o_wsq);
+    dev.w64 = reinterpret_cast<const double*>(b + o_w64);
+    dev.sq64 = reinterpret_cast<const double*>(b + o_sq);
+    return AFD_OK;
+  }
+};
+
+// ------------------------------------------------------------- slot pools --
+
+// Device buffers of n signals, pooled.  Signals are grouped by logN for
+// launching; `ids_dev` holds, group after group, the slot indices.
+struct SlotPool {
+  int n = 0, K_max = 0, prec = 1, cap = 16;
+  std::vector<SlotDev> host;        // descriptors (device pointers inside)
+  std::vector<size_t> g_off;        // offset of signal i in the packed samples (doubles)
+  size_t g_total = 0;               // packed sample count (doubles)
+  void* mem = nullptr;
+  SlotDev* slots_dev = nullptr;
+  int* ids_dev = nullptr;
+  StepRec* rec_dev = nullptr;       // n * K_max, signal-major
+  SlotCtl* ctl_dev = nullptr;       // n
+  double2* G_dev = nullptr;         // packed remainders
+  StepRec* rec_host = nullptr;      // pinned mirrors
+  SlotCtl* ctl_host = nullptr;
+  struct Group { int logN, first, count, Mmax; };
+  std::vector<Group> groups;
+
+  ~SlotPool() { release(); }
+  void release() {
+    if (mem) cudaFree(mem);
+    if (rec_host) cudaFreeHost(rec_host);
+    if (ctl_host) cudaFreeHost(ctl_host);
+    mem = nullptr;
+    rec_host = nullptr;
+    ctl_host = nullptr;
+  }
+
+  // tables[i] is the plan of signal i.
+  afd_status build(const std::vector<const Tables*>& tables, int K, const afd_plan_opts& o) {
+    release();
+    n = (int)tables.size();
+    K_max = K;
+    prec = o.precision;
+    cap = prec == AFD_FP32_GUARDED ? o.guard_cap : 1;
+    // group by logN (stable: signal order within a group)
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return tables[a]->N < tables[b]->N; });
+    groups.clear();
+    for (int idx = 0; idx < n; ++idx) {
+      const int i = order[idx];
+      const int lg = ilog2(tables[i]->N);
+      if (groups.empty() || groups.back().logN != lg) groups.push_back({lg, idx, 0, 0});
+      groups.back().count++;
+      groups.back().Mmax = std::max(groups.back().Mmax, tables[i]->M);
+    }
+    // sizes
+    g_off.assign(n, 0);
+    g_total = 0;
+    for (int i = 0; i < n; ++i) {
+      g_off[i] = g_total;
+      g_total += 2 * (size_t)tables[i]->N;
+    }
+    size_t off = 0;
+    auto place = [&](size_t bytes) { size_t o2 = off; off = align_up(off + bytes); return o2; };
+    const size_t o_G = place(8 * g_total);
+    std::vector<size_t> o_c(n), o_top(n), o_cand(n), o_gp(n), o_ep(n);
+    for (int i = 0; i < n; ++i) {
+      const int N = tables[i]->N, M = tables[i]->M;
+      o_c[i] = place((prec ? 8 : 16) * (size_t)N);
+      o_top[i] = place((prec ? sizeof(Top2F) : sizeof(Top2D)) * (size_t)M);
+      o_cand[i] = place(sizeof(int2) * cap);
+      o_gp[i] = place(sizeof(double2) * cap * (size_t)chunks_of(N));
+      o_ep[i] = place(sizeof(double) * (size_t)chunks_of(N));
+    }
+    const size_t o_rec = place(sizeof(StepRec) * (size_t)n * K_max);
+    const size_t o_ctl = place(sizeof(SlotCtl) * (size_t)n);
+    const size_t o_slots = place(sizeof(SlotDev) * (size_t)n);
+    const size_t o_ids = place(sizeof(int) * (size_t)n);
+    CUDA_TRY(cudaMalloc(&mem, off));
+    CUDA_TRY(cudaMemset(mem, 0, off));
+    CUDA_TRY(cudaMallocHost((void**)&rec_host, sizeof(StepRec) * (size_t)n * K_max));
+    CUDA_TRY(cudaMallocHost((void**)&ctl_host, sizeof(SlotCtl) * (size_t)n));
+    char* b = static_cast<char*>(mem);
+    G_dev = reinterpret_cast<double2*>(b + o_G);
+    rec_dev = reinterpret_cast<StepRec*>(b + o_rec);
+    ctl_dev = reinterpret_cast<SlotCtl*>(b + o_ctl);
+    slots_dev = reinterpret_cast<SlotDev*>(b + o_slots);
+    ids_dev = reinterpret_cast<int*>(b + o_ids);
+    host.assign(n, SlotDev{});
+    for (int i = 0; i < n; ++i) {
+      SlotDev& d = host[i];
+      d.p = tables[i]->dev;
+      d.K_max = K_max;
+      d.prec = prec;
+      d.cap = cap;
+      d.force_a1_zero = o.force_a1_zero;
+      d.tol = 0.0;
+      d.tau = o.guard_tau;
+      d.G = reinterpret_cast<double2*>(b + o_G) + g_off[i] / 2;
+      d.c32 = prec ? reinterpret_cast<float2*>(b + o_c[i]) : nullptr;
+      d.c64 = prec ? nullptr : reinterpret_cast<double2*>(b + o_c[i]);
+      d.top2 = b + o_top[i];
+      d.cand = reinterpret_cast<int2*>(b + o_cand[i]);
+      d.gpart = reinterpret_cast<double2*>(b + o_gp[i]);
+      d.epart = reinterpret_cast<double*>(b + o_ep[i]);
+      d.rec = rec_dev + (size_t)i * K_max;
+      d.ctl = ctl_dev + i;
+    }
+    CUDA_TRY(cudaMemcpy(ids_dev, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    return upload(0.0, nullptr);
+  }
+
+  afd_status upload(double tol, cudaStream_t st) {
+    for (auto& d : host) d.tol = tol;
+    if (st) {
+      CUDA_TRY(cudaMemcpyAsync(slots_dev, host.data(), sizeof(SlotDev) * n, cudaMemcpyHostToDevice, st));
+    } else {
+      CUDA_TRY(cudaMemcpy(slots_dev, host.data(), sizeof(SlotDev) * n, cudaMemcpyHostToDevice));
+    }
+    return AFD_OK;
+  }
+};
+
+// Kernel launch bookkeeping.
+struct Counters {
+  long long launches = 0, grid_launches = 0;
+  double grid_ms = 0.0;
+};
+
+// Optional CUDA-event timing of the grid kernel.
+struct GridTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+  ~GridTimer() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+  afd_status pair(cudaEvent_t* a, cudaEvent_t* b) {
+    while (ev.size() < used + 2) {
+      cudaEvent_t e;
+      CUDA_TRY(cudaEventCreate(&e));
+      ev.push_back(e);
+    }
+    *a = ev[used];
+    *b = ev[used + 1];
+    used += 2;
+    return AFD_OK;
+  }
+  afd_status collect(Counters& c) {
+    for (size_t i = 0; i + 1 < used; i += 2) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      c.grid_ms += ms;
+    }
+    used = 0;
+    return AFD_OK;
+  }
+};
+
+// Enqueue the initialisation and K greedy steps of one group on stream st.
+afd_status enqueue_group(const SlotPool& pool, const SlotPool::Group& g, int K, cudaStream_t st,
+                         Counters& cnt, GridTimer* timer) {
+  const SlotDev* slots = pool.slots_dev;
+  const int* ids = pool.ids_dev + g.first;
+  const int prec = pool.prec;
+  CUDA_TRY(launch_init(slots, ids, g.count, g.logN, st));
+  CUDA_TRY(launch_forward(slots, ids, g.count, g.logN, prec, st));
+  cnt.launches += 2;
+  for (int k = 0; k < K; ++k) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timer && timer->on) {
+      AFD_TRY(timer->pair(&e0, &e1));
+      CUDA_TRY(cudaEventRecord(e0, st));
+    }
+    CUDA_TRY(launch_grid(slots, ids, g.count, g.logN, prec, g.Mmax, st));
+    if (timer && timer->on) CUDA_TRY(cudaEventRecord(e1, st));
+    cnt.grid_launches += 1;
+    cnt.launches += 1;
+    if (prec == AFD_FP32_GUARDED) {
+      CUDA_TRY(launch_guard(slots, ids, g.count, g.logN, pool.cap, st));
+      cnt.launches += 1;
+    }
+    CUDA_TRY(launch_update(slots, ids, g.count, g.logN, st));
+    cnt.launches += 1;
+    if (k + 1 < K) {
+      CUDA_TRY(launch_forward(slots, ids, g.count, g.logN, prec, st));
+      cnt.launches += 1;
+    }
+  }
+  return AFD_OK;
+}
+
+// Runs the whole K-step sequence for every group of the pool: groups on
+// their own streams (forked from and joined back to `main`).
+struct Runner {
+  cudaStream_t main = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t order = nullptr;  // orders a plan-owned stream after the legacy default stream
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int graph_K = -1;
+  long long graph_launches = 0, graph_grid_launches = 0;
+
+  ~Runner() { destroy(); }
+  void destroy() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    graph_K = -1;
+    for (auto s : side) cudaStreamDestroy(s);
+    for (auto e : join) cudaEventDestroy(e);
+    side.clear();
+    join.clear();
+    if (fork) cudaEventDestroy(fork);
+    fork = nullptr;
+    if (order) cudaEventDestroy(order);
+    order = nullptr;
+  }
+
+  // A plan-owned stream does not synchronise with the legacy default stream,
+  // so work the caller queued there (e.g. a copy producing G) is waited for.
+  afd_status order_after_default() {
+    if (!order) CUDA_TRY(cudaEventCreateWithFlags(&order, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(order, cudaStreamLegacy));
+    CUDA_TRY(cudaStreamWaitEvent(main, order, 0));
+    return AFD_OK;
+  }
+
+  afd_status prepare(size_t ngroups) {
+    if (!fork) CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    while (side.size() + 1 < ngroups) {
+      cudaStream_t s;
+      cudaEvent_t e;
+      CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      side.push_back(s);
+      join.push_back(e);
+    }
+    return AFD_OK;
+  }
+
+  afd_status enqueue(const SlotPool& pool, int K, Counters& cnt, GridTimer* timer) {
+    AFD_TRY(prepare(pool.groups.size()));
+    CUDA_TRY(cudaMemsetAsync(pool.ctl_dev, 0, sizeof(SlotCtl) * pool.n, main));
+    if (pool.groups.size() > 1) CUDA_TRY(cudaEventRecord(fork, main));
+    for (size_t gi = 0; gi < pool.groups.size(); ++gi) {
+      cudaStream_t st = gi == 0 ? main : side[gi - 1];
+      if (gi > 0) CUDA_TRY(cudaStreamWaitEvent(st, fork, 0));
+      AFD_TRY(enqueue_group(pool, pool.groups[gi], K, st, cnt, timer));
+      if (gi > 0) {
+        CUDA_TRY(cudaEventRecord(join[gi - 1], st));
+        CUDA_TRY(cudaStreamWaitEvent(main, join[gi - 1], 0));
+      }
+    }
+    return AFD_OK;
+  }
+
+  // Either replays a cached graph of the K-step sequence or launches directly.
+  afd_status run(const SlotPool& pool, int K, bool use_graph, Counters& cnt, GridTimer* timer) {
+    if (!use_graph || (timer && timer->on)) return enqueue(pool, K, cnt, timer);
+    if (graph_K != K) {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      exec = nullptr;
+      graph = nullptr;
+      Counters c2;
+      CUDA_TRY(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal));
+      afd_status st = enqueue(pool, K, c2, nullptr);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(main, &g);
+      if (st != AFD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      CUDA_TRY(e);
+      graph = g;
+      CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
+      graph_K = K;
+      graph_launches = c2.launches;
+      graph_grid_launches = c2.grid_launches;
+    }
+    CUDA_TRY(cudaGraphLaunch(exec, main));
+    cnt.launches += graph_launches;
+    cnt.grid_launches += graph_grid_launches;
+    return AFD_OK;
+  }
+};
+
+afd_status normalise_opts(const afd_plan_opts* in, afd_plan_opts& o, int& dev) {
+  afd_plan_opts_default(&o);
+  if (in) o = *in;
+  AFD_TRY(check_opts(o));
+  dev = o.device;
+  if (dev < 0) CUDA_TRY(cudaGetDevice(&dev));
+  int count = 0;
+  CUDA_TRY(cudaGetDeviceCount(&count));
+  if (dev >= count) return set_error(AFD_ERR_INVALID, "device %d not present (%d devices)", dev, count);
+  return AFD_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------- plans --
+
+struct afd_plan {
+  int device = 0;
+  afd_plan_opts opts{};
+  bool own_stream = false;
+  Tables tables;
+  SlotPool pool;
+  Runner runner;
+  Counters cnt;
+  GridTimer timer;
+  int last_steps = 0;
+  ~afd_plan() {
+    runner.destroy();
+    if (own_stream && runner.main) cudaStreamDestroy(runner.main);
+  }
+};
+
+struct afd_batch {
+  int device = 0;
+  afd_plan_opts opts{};
+  bool own_stream = false;
+  std::vector<std::unique_ptr<Tables>> tables;
+  SlotPool pool;
+  Runner runner;
+  Counters cnt;
+  std::vector<int> N;
+  ~afd_batch() {
+    runner.destroy();
+    if (own_stream && runner.main) cudaStreamDestroy(runner.main);
+  }
+};
+
+namespace {
+
+// Copy `bytes` from host memory `src` to caller memory `dst` (host or device).
+afd_status copy_out(void* dst, const void* src, size_t bytes) {
+  if (!dst || bytes == 0) return AFD_OK;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, dst) == cudaSuccess &&
+      (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+    CUDA_TRY(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+  } else {
+    cudaGetLastError();
+    std::memcpy(dst, src, bytes);
+  }
+  return AFD_OK;
+}
+
+// Gather the records of signal i (steps = its step count) into caller arrays.
+afd_status write_outputs(const SlotPool& pool, int i, int K_stride, int steps, double* a_out,
+                         double* coeff_out, double* delta_out, int* idx_out) {
+  const StepRec* r = pool.rec_host + (size_t)i * pool.K_max;
+  std::vector<double> a(2 * (size_t)steps), c(2 * (size_t)steps), d((size_t)steps + 1);
+  std::vector<int> ix(2 * (size_t)steps);
+  d[0] = 1.0;
+  for (int k = 0; k < steps; ++k) {
+    a[2 * k] = r[k].a_re;
+    a[2 * k + 1] = r[k].a_im;
+    c[2 * k] = r[k].c_re;
+    c[2 * k + 1] = r[k].c_im;
+    d[k + 1] = r[k].delta;
+    ix[2 * k] = r[k].s;
+    ix[2 * k + 1] = r[k].j;
+  }
+  const size_t base2 = 2 * (size_t)i * K_stride, based = (size_t)i * (K_stride + 1);
+  if (a_out) AFD_TRY(copy_out(a_out + base2, a.data(), 8 * a.size()));
+  if (coeff_out) AFD_TRY(copy_out(coeff_out + base2, c.data(), 8 * c.size()));
+  if (delta_out) AFD_TRY(copy_out(delta_out + based, d.data(), 8 * d.size()));
+  if (idx_out) AFD_TRY(copy_out(idx_out + base2, ix.data(), 4 * ix.size()));
+  return AFD_OK;
+}
+
+afd_status fetch_results(SlotPool& pool, cudaStream_t st) {
+  CUDA_TRY(cudaMemcpyAsync(pool.rec_host, pool.rec_dev, sizeof(StepRec) * (size_t)pool.n * pool.K_max,
+                           cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(pool.ctl_host, pool.ctl_dev, sizeof(SlotCtl) * (size_t)pool.n,
+                           cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return AFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void afd_plan_opts_default(afd_plan_opts* o) {
+  if (!o) return;
+  o->precision = AFD_FP32_GUARDED;
+  o->guard_tau = 1e-4;
+  o->guard_cap = 16;
+  o->force_a1_zero = 0;
+  o->device = -1;
+  o->stream = nullptr;
+  o->use_graph = 1;
+}
+
+const char* afd_status_str(afd_status s) {
+  switch (s) {
+    case AFD_OK: return "AFD_OK";
+    case AFD_PENDING: return "AFD_PENDING";
+    case AFD_ERR_INVALID: return "AFD_ERR_INVALID";
+    case AFD_ERR_NOMEM: return "AFD_ERR_NOMEM";
+    case AFD_ERR_CUDA: return "AFD_ERR_CUDA";
+    case AFD_ERR_TIMEOUT: return "AFD_ERR_TIMEOUT";
+    case AFD_ERR_BUDGET: return "AFD_ERR_BUDGET";
+    case AFD_ERR_NOT_FOUND: return "AFD_ERR_NOT_FOUND";
+    case AFD_ERR_NUMERIC: return "AFD_ERR_NUMERIC";
+  }
+  return "AFD_UNKNOWN_STATUS";
+}
+
+const char* afd_last_error(void) { return g_last_error.c_str(); }
+
+const char* afd_version(void) { return "0.1.0"; }
+
+afd_status afd_plan_create(afd_plan** out, int N, const double* radii, int M, const afd_plan_opts* opts) {
+  g_last_error.clear();
+  if (!out) return set_error(AFD_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  afd_plan_opts o;
+  int dev = 0;
+  AFD_TRY(normalise_opts(opts, o, dev));
+  AFD_TRY(check_size(N, o.precision));
+  AFD_TRY(check_radii(radii, M));
+  if (o.force_a1_zero && radii[0] != 0.0)
+    return set_error(AFD_ERR_INVALID, "force_a1_zero needs radii[0] == 0");
+  DeviceScope scope(dev);
+  if (!scope.ok) return set_error(AFD_ERR_CUDA, "cannot make device %d current", dev);
+  AFD_TRY(ensure_configured(dev));
+  std::unique_ptr<afd_plan> p(new (std::nothrow) afd_plan());
+  if (!p) return set_error(AFD_ERR_NOMEM, "host allocation failed");
+  p->device = dev;
+  p->opts = o;
+  if (o.stream) {
+    p->runner.main = static_cast<cudaStream_t>(o.stream);
+  } else {
+    CUDA_TRY(cudaStreamCreateWithFlags(&p->runner.main, cudaStreamNonBlocking));
+    p->own_stream = true;
+  }
+  AFD_TRY(p->tables.build(N, radii, M));
+  *out = p.release();
+  return AFD_OK;
+}
+
+afd_status afd_plan_destroy(afd_plan* plan) {
+  if (!plan) return AFD_OK;
+  DeviceScope scope(plan->device);
+  if (plan->runner.main) cudaStreamSynchronize(plan->runner.main);
+  delete plan;
+  return AFD_OK;
+}
+
+afd_status afd_decompose(afd_plan* plan, const double* G, int K_max, double energy_tol, double* a_out,
+                         double* coeff_out, double* delta_out, int* idx_out, int* steps_done) {
+  g_last_error.clear();
+  if (!plan || !G) return set_error(AFD_ERR_INVALID, "plan or G is NULL");
+  if (K_max < 1 || K_max > (1 << 20)) return set_error(AFD_ERR_INVALID, "K_max = %d out of range", K_max);
+  if (!(energy_tol >= 0.0)) return set_error(AFD_ERR_INVALID, "energy_tol must be >= 0");
+  DeviceScope scope(plan->device);
+  if (!scope.ok) return set_error(AFD_ERR_CUDA, "cannot make device %d current", plan->device);
+  SlotPool& pool = plan->pool;
+  cudaStream_t st = plan->runner.main;
+  if (pool.n != 1 || pool.K_max != K_max) {
+    CUDA_TRY(cudaStreamSynchronize(st));
+    plan->runner.destroy();
+    std::vector<const Tables*> t{&plan->tables};
+    AFD_TRY(pool.build(t, K_max, plan->opts));
+  }
+  if (plan->own_stream) AFD_TRY(plan->runner.order_after_default());
+  AFD_TRY(pool.upload(energy_tol, st));
+  CUDA_TRY(cudaMemcpyAsync(pool.G_dev, G, 16 * (size_t)plan->tables.N, cudaMemcpyDefault, st));
+  AFD_TRY(plan->runner.run(pool, K_max, plan->opts.use_graph != 0, plan->cnt, &plan->timer));
+  AFD_TRY(fetch_results(pool, st));
+  if (plan->timer.on) AFD_TRY(plan->timer.collect(plan->cnt));
+  const int steps = pool.ctl_host[0].k;
+  plan->last_steps = steps;
+  AFD_TRY(write_outputs(pool, 0, K_max, steps, a_out, coeff_out, delta_out, idx_out));
+  if (steps_done) AFD_TRY(copy_out(steps_done, &steps, sizeof(int)));
+  if (pool.ctl_host[0].err & 2) return set_error(AFD_ERR_NUMERIC, "non-finite objective at step %d", steps);
+  return AFD_OK;
+}
+
+afd_status afd_plan_last_info(const afd_plan* plan, int* n_cand_out, int* flags_out, double* obj32_out) {
+  if (!plan) return set_error(AFD_ERR_INVALID, "plan is NULL");
+  const StepRec* r = plan->pool.rec_host;
+  for (int k = 0; k < plan->last_steps && r; ++k) {
+    if (n_cand_out) n_cand_out[k] = r[k].n_cand;
+    if (flags_out) flags_out[k] = r[k].flags;
+    if (obj32_out) obj32_out[k] = r[k].obj32;
+  }
+  return AFD_OK;
+}
+
+afd_status afd_plan_set_profiling(afd_plan* plan, int on) {
+  if (!plan) return set_error(AFD_ERR_INVALID, "plan is NULL");
+  plan->timer.on = on != 0;
+  return AFD_OK;
+}
+
+afd_status afd_plan_counters(const afd_plan* plan, long long* kernel_launches, long long* grid_launches,
+                             double* grid_ms) {
+  if (!plan) return set_error(AFD_ERR_INVALID, "plan is NULL");
+  if (kernel_launches) *kernel_launches = plan->cnt.launches;
+  if (grid_launches) *grid_launches = plan->cnt.grid_launches;
+  if (grid_ms) *grid_ms = plan->cnt.grid_ms;
+  return AFD_OK;
+}
+
+afd_status afd_plan_get_stream(const afd_plan* plan, void** stream) {
+  if (!plan || !stream) return set_error(AFD_ERR_INVALID, "plan or stream is NULL");
+  *stream = plan->runner.main;
+  return AFD_OK;
+}
+
+afd_status afd_plan_reset_counters(afd_plan* plan) {
+  if (!plan) return set_error(AFD_ERR_INVALID, "plan is NULL");
+  plan->cnt = Counters{};
+  return AFD_OK;
+}
+
+// ----------------------------------------------------------------- batches --
+
+afd_status afd_batch_create(afd_batch** out, int n_signals, const int* N, const double* radii, int M,
+                            int K_max, const afd_plan_opts* opts) {
+  g_last_error.clear();
+  if (!out) return set_error(AFD_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n_signals < 1 || !N) return set_error(AFD_ERR_INVALID, "need n_signals >= 1 and N");
+  if (K_max < 1 || K_max > (1 << 20)) return set_error(AFD_ERR_INVALID, "K_max = %d out of range", K_max);
+  afd_plan_opts o;
+  int dev = 0;
+  AFD_TRY(normalise_opts(opts, o, dev));
+  AFD_TRY(check_radii(radii, M));
+  if (o.force_a1_zero && radii[0] != 0.0)
+    return set_error(AFD_ERR_INVALID, "force_a1_zero needs radii[0] == 0");
+  for (int i = 0; i < n_signals; ++i) AFD_TRY(check_size(N[i], o.precision));
+  DeviceScope scope(dev);
+  if (!scope.ok) return set_error(AFD_ERR_CUDA, "cannot make device %d current", dev);
+  AFD_TRY(ensure_configured(dev));
+  std::unique_ptr<afd_batch> b(new (std::nothrow) afd_batch());
+  if (!b) return set_error(AFD_ERR_NOMEM, "host allocation failed");
+  b->device = dev;
+  b->opts = o;
+  b->N.assign(N, N + n_signals);
+  if (o.stream) {
+    b->runner.main = static_cast<cudaStream_t>(o.stream);
+  } else {
+    CUDA_TRY(cudaStreamCreateWithFlags(&b->runner.main, cudaStreamNonBlocking));
+    b->own_stream = true;
+  }
+  std::map<int, Tables*> by_n;
+  std::vector<const Tables*> per_signal(n_signals);
+  for (int i = 0; i < n_signals; ++i) {
+    auto it = by_n.find(N[i]);
+    if (it == by_n.end()) {
+      b->tables.emplace_back(new Tables());
+      AFD_TRY(b->tables.back()->build(N[i], radii, M));
+      it = by_n.emplace(N[i], b->tables.back().get()).first;
+    }
+    per_signal[i] = it->second;
+  }
+  AFD_TRY(b->pool.build(per_signal, K_max, o));
+  *out = b.release();
+  return AFD_OK;
+}
+
+afd_status afd_batch_run(afd_batch* b, const double* G_packed, double energy_tol, double* a_out,
+                         double* coeff_out, double* delta_out, int* idx_out, int* steps_out) {
+  g_last_error.clear();
+  if (!b || !G_packed) return set_error(AFD_ERR_INVALID, "batch or G_packed is NULL");
+  if (!(energy_tol >= 0.0)) return set_error(AFD_ERR_INVALID, "energy_tol must be >= 0");
+  DeviceScope scope(b->device);
+  if (!scope.ok) return set_error(AFD_ERR_CUDA, "cannot make device %d current", b->device);
+  SlotPool& pool = b->pool;
+  cudaStream_t st = b->runner.main;
+  if (b->own_stream) AFD_TRY(b->runner.order_after_default());
+  AFD_TRY(pool.upload(energy_tol, st));
+  CUDA_TRY(cudaMemcpyAsync(pool.G_dev, G_packed, 8 * pool.g_total, cudaMemcpyDefault, st));
+  AFD_TRY(b->runner.run(pool, pool.K_max, b->opts.use_graph != 0, b->cnt, nullptr));
+  AFD_TRY(fetch_results(pool, st));
+  bool numeric = false;
+  std::vector<int> steps(pool.n);
+  for (int i = 0; i < pool.n; ++i) {
+    steps[i] = pool.ctl_host[i].k;
+    numeric |= (pool.ctl_host[i].err & 2) != 0;
+    AFD_TRY(write_outputs(pool, i, pool.K_max, steps[i], a_out, coeff_out, delta_out, idx_out));
+  }
+  if (steps_out) AFD_TRY(copy_out(steps_out, steps.data(), sizeof(int) * steps.size()));
+  if (numeric) return set_error(AFD_ERR_NUMERIC, "non-finite objective in at least one signal");
+  return AFD_OK;
+}
+
+afd_status afd_batch_counters(const afd_batch* b, long long* kernel_launches) {
+  if (!b) return set_error(AFD_ERR_INVALID, "batch is NULL");
+  if (kernel_launches) *kernel_launches = b->cnt.launches;
+  return AFD_OK;
+}
+
+afd_status afd_batch_destroy(afd_batch* b) {
+  if (!b) return AFD_OK;
+  DeviceScope scope(b->device);
+  if (b->runner.main) cudaStreamSynchronize(b->runner.main);
+  delete b;
+  return AFD_OK;
+}
+
+afd_status afd_decompose_batch(int n_signals, const int* N, const double* radii, int M,
+                               const double* G_packed, int K_max, double energy_tol,
+                               const afd_plan_opts* opts, double* a_out, double* coeff_out,
+                               double* delta_out, int* idx_out, int* steps_out) {
+  afd_batch* b = nullptr;
+  AFD_TRY(afd_batch_create(&b, n_signals, N, radii, M, K_max, opts));
+  afd_status s = afd_batch_run(b, G_packed, energy_tol, a_out, coeff_out, delta_out, idx_out, steps_out);
+  afd_batch_destroy(b);
+  return s;
+}
+
+}  // extern "C"

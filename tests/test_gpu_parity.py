@@ -1,0 +1,192 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on seeded inputs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_08604_gb300 import workloads as W
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+afd = pytest.importorskip("paper_1711_08604_gb300")
+PRECS = [afd.AFD_FP64_PLAIN, afd.AFD_FP32_GUARDED]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    afd._native.load()
+
+
+def run(G, radii, K, prec, tol=0.0, **kw):
+    plan = afd.afd_plan_create(G.size, radii, precision=prec, **kw)
+    try:
+        return afd.afd_decompose(plan, G, K, tol), plan
+    finally:
+        pass
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_workload1_kernel_sum_full_parity(prec):
+    s = W.kernel_sum()
+    res, _ = run(s.G, s.radii, s.K, prec)
+    assert res["steps"] == s.K
+    parity.check(s.G, s.radii, res, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("item", [1, 2, 3])
+def test_workload1_more_items(prec, item):
+    s = W.kernel_sum(item=item)
+    res, _ = run(s.G, s.radii, 12, prec)
+    parity.check(s.G, s.radii, res, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_reproducing_kernel(prec):
+    N, radii = 256, W.radii_linear(50)
+    b = radii[25] * np.exp(2j * np.pi * 17 / N)
+    G = W.szego_sum(N, np.array([b]), np.array([1.0]))
+    res, _ = run(G, radii, 1, prec)
+    assert tuple(res["idx"][0]) == (25, 17)
+    assert abs(abs(res["coeff"][0]) - 1.0) <= 1e-13
+    assert res["delta"][1] <= 1e-24
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N", [8, 16, 32, 64, 128, 512, 1024, 2048])
+def test_small_and_ragged_sizes(prec, N):
+    G = W.random_signal(N, 7 * N)
+    radii = np.array([0.0, 0.05, 0.3, 0.55, 0.8, 0.9, 0.97])
+    res, _ = run(G, radii, 6, prec)
+    parity.check(G, radii, res, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_single_radius_and_zero_radius_ties(prec):
+    # only r = 0: every angle ties exactly, the lowest index must win
+    N = 64
+    G = W.random_signal(N, 3)
+    res, _ = run(G, np.array([0.0]), 3, prec)
+    for k in range(3):
+        assert tuple(res["idx"][k]) == (0, 0)
+    parity.check(G, np.array([0.0]), res, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_constant_signal(prec):
+    N = 128
+    res, _ = run(np.ones(N, dtype=complex), np.array([0.0, 0.2, 0.5]), 1, prec)
+    assert tuple(res["idx"][0]) == (0, 0)
+    assert abs(res["coeff"][0] - 1.0) <= 1e-14
+    assert res["delta"][1] <= 1e-28
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_energy_tolerance_stop(prec):
+    s = W.kernel_sum(item=5)
+    full, _ = run(s.G, s.radii, 10, prec)
+    tol = float(full["delta"][5]) * 1.0001
+    res, _ = run(s.G, s.radii, 10, prec, tol=tol)
+    assert res["steps"] == 5
+    parity.check(s.G, s.radii, res, prec, energy_tol=tol)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_paper_table4_forced_a1(prec):
+    G = W.paper_f1(1024)
+    radii = W.radii_paper()
+    res, _ = run(G, radii, 10, prec, force_a1_zero=True)
+    parity.check(G, radii, res, prec, force_a1_zero=True)
+    want = np.array([float(l.split()[1]) for l in open("tests/golden/table4_case1_delta.txt")
+                     if l.strip() and not l.startswith("#")])
+    assert np.max(np.abs(res["delta"][1:11] - want)) <= 2e-3
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_workload2_tones_sampled(prec):
+    # N = 4096, M = 200, K = 50: coefficients and delta at every step through the
+    # forced oracle; full-grid selection checks at sampled steps.
+    s = W.tones()
+    res, _ = run(s.G, s.radii, s.K, prec)
+    assert res["steps"] == s.K
+    parity.check(s.G, s.radii, res, prec, full_grid=False, grid_steps=(1, 2, 50))
+
+
+def test_determinism_and_graph_equivalence():
+    s = W.tones(item=1, K=12)
+    r1, _ = run(s.G, s.radii, s.K, 1)
+    r2, _ = run(s.G, s.radii, s.K, 1)
+    r3, _ = run(s.G, s.radii, s.K, 1, use_graph=False)
+    for k in ("a", "coeff", "delta", "idx"):
+        assert np.array_equal(r1[k], r2[k])
+        assert np.array_equal(r1[k], r3[k])
+
+
+def test_plan_reuse_with_different_K():
+    s = W.kernel_sum(item=2)
+    plan = afd.afd_plan_create(s.N, s.radii)
+    a = afd.afd_decompose(plan, s.G, 4)
+    b = afd.afd_decompose(plan, s.G, 9)
+    c = afd.afd_decompose(plan, s.G, 4)
+    assert np.array_equal(a["coeff"], b["coeff"][:4])
+    assert np.array_equal(a["coeff"], c["coeff"])
+
+
+def test_device_pointers():
+    import torch
+    s = W.kernel_sum(item=4)
+    plan = afd.afd_plan_create(s.N, s.radii)
+    host = afd.afd_decompose(plan, s.G, 8)
+    Gd = torch.from_numpy(s.G).cuda()
+    out = {"a": torch.zeros(16, dtype=torch.float64, device="cuda"),
+           "coeff": torch.zeros(16, dtype=torch.float64, device="cuda"),
+           "delta": torch.zeros(9, dtype=torch.float64, device="cuda"),
+           "idx": torch.zeros(16, dtype=torch.int32, device="cuda")}
+    dev = afd.afd_decompose(plan, Gd, 8, out=out)
+    assert dev["steps"] == 8
+    assert np.array_equal(out["coeff"].cpu().numpy().view(np.complex128), host["coeff"])
+    assert np.array_equal(out["idx"].cpu().numpy().reshape(8, 2), host["idx"])
+    assert np.array_equal(out["delta"].cpu().numpy(), host["delta"])
+
+
+def test_invalid_arguments():
+    with pytest.raises(afd.AfdError) as e:
+        afd.afd_plan_create(100, [0.1, 0.2])
+    assert e.value.status == -1
+    with pytest.raises(afd.AfdError):
+        afd.afd_plan_create(64, [0.2, 0.1])
+    with pytest.raises(afd.AfdError):
+        afd.afd_plan_create(64, [0.1, 1.0])
+    with pytest.raises(afd.AfdError):
+        afd.afd_plan_create(1 << 15, [0.1])
+    with pytest.raises(afd.AfdError):
+        afd.afd_plan_create(16384, [0.1], precision=0)
+    with pytest.raises(afd.AfdError):
+        afd.afd_plan_create(64, [0.1], guard_cap=0)
+    with pytest.raises(afd.AfdError):
+        afd.afd_plan_create(64, [0.1, 0.2], force_a1_zero=True)
+    plan = afd.afd_plan_create(64, [0.0, 0.5])
+    with pytest.raises(afd.AfdError):
+        afd.afd_decompose(plan, np.ones(64, complex), 0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_zero_signal(prec):
+    res, _ = run(np.zeros(64, dtype=complex), np.array([0.0, 0.5]), 2, prec)
+    assert res["steps"] == 2
+    assert tuple(res["idx"][0]) == (0, 0)
+    assert np.all(res["coeff"] == 0)
+    assert np.all(res["delta"][1:] == 0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_nan_input_reports_numeric_error(prec):
+    G = W.random_signal(64, 1)
+    G[5] = np.nan
+    plan = afd.afd_plan_create(64, np.array([0.0, 0.5]), precision=prec)
+    with pytest.raises(afd.AfdError) as e:
+        afd.afd_decompose(plan, G, 3)
+    assert e.value.status == -7
