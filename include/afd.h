@@ -179,6 +179,37 @@ afd_status afd_decompose_batch(int n_signals, const int* N, const double* radii,
                                const afd_plan_opts* opts, double* a_out, double* coeff_out,
                                double* delta_out, int* idx_out, int* steps_out);
 
+/*
+ * Allocation-free FP64 inner products (the paper has no counterpart: this is
+ * an interface addition for callers that cannot allocate device memory).
+ *
+ * out[p] = <G, e_{a_p}>~ = sqrt(1-|a_p|^2)/N * sum_m G(z_m) / (1 - a_p conj(z_m))
+ * for n_points arbitrary points a_p of the open unit disc, by the same FP64
+ * rectangle rule the FP32 path uses to re-evaluate its selection candidates.
+ * Some callers cannot call cudaMalloc: work being recorded into a CUDA graph
+ * (allocation is not allowed during stream capture and can synchronise the
+ * device), latency-critical loops, and hosts that give the library a fixed
+ * pre-reserved memory pool.  This entry point allocates nothing: its scratch
+ * (partial sums and a completion counter) is a static device array of
+ * 128 KiB + 256 B that every GPU loading the library holds until the process
+ * exits.
+ *   G       2N doubles (interleaved complex), device memory; 1 <= N <= AFD_NOALLOC_MAX_N.
+ *   points  2*n_points doubles, device memory; 1 <= n_points <= AFD_NOALLOC_MAX_POINTS.
+ *   out     2*n_points doubles, device memory.
+ *   stream  cudaStream_t to run on (NULL: the legacy default stream).
+ * Asynchronous: the result is ready when the stream reaches that point.
+ * Sizes beyond the limits, NULL or host (unmapped) pointers return
+ * AFD_ERR_INVALID with a message in afd_last_error().  The first call on a
+ * device looks up the scratch array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (different
+ * streams or host threads) race and must be serialised by the caller.
+ */
+#define AFD_NOALLOC_MAX_N 65536
+#define AFD_NOALLOC_MAX_POINTS 64
+afd_status afd_inner_products_noalloc(const double* G, int N, const double* points, int n_points,
+                                      double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

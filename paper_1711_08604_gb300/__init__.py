@@ -27,7 +27,7 @@ __all__ = [
     "afd_status_str", "afd_last_error", "afd_version", "afd_plan_create", "afd_plan_destroy",
     "afd_decompose", "afd_plan_last_info", "afd_plan_set_profiling", "afd_plan_counters",
     "afd_plan_reset_counters", "afd_plan_get_stream", "afd_batch_create", "afd_batch_run", "afd_batch_counters",
-    "afd_batch_destroy", "afd_decompose_batch", "library_path",
+    "afd_batch_destroy", "afd_decompose_batch", "afd_inner_products_noalloc", "library_path",
 ]
 
 AFD_FP64_PLAIN = 0
@@ -259,3 +259,18 @@ def afd_decompose_batch(signals, radii, K_max: int, energy_tol: float = 0.0,
         return afd_batch_run(b, packed, energy_tol)
     finally:
         b.close()
+
+
+def afd_inner_products_noalloc(G, points, out=None, stream=None):
+    """<G, e_a>~ at each point of ``points`` (torch CUDA complex128 tensors), FP64,
+    without any device allocation by the library (its scratch is a static device
+    array).  ``out`` (complex128, same device, len(points)) is filled and returned.
+    Asynchronous on ``stream`` (a torch stream or cudaStream_t int; default: the
+    legacy default stream)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(points)
+    s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(_lib().afd_inner_products_noalloc(G.data_ptr(), int(G.numel()), points.data_ptr(),
+                                             int(points.numel()), out.data_ptr(), s or None))
+    return out

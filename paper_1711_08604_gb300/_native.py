@@ -44,6 +44,7 @@ SIGNATURES = {
     "afd_batch_destroy": (c_int, [c_void_p]),
     "afd_decompose_batch": (c_int, [c_int, c_void_p, c_void_p, c_int, c_void_p, c_int, c_double,
                                     P(PlanOpts), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "afd_inner_products_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
 }
 
 _lib = None

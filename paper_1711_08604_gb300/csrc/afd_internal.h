@@ -92,5 +92,7 @@ size_t grid_smem_bytes(int logN, int prec);
 size_t forward_smem_bytes(int logN, int prec);
 int grid_ffts_per_cta(int logN, int prec);
 cudaError_t configure_kernels();
+// Sets the text afd_last_error() returns on the calling thread.
+void set_last_error_text(const char* text);
 
 }  // namespace afd

@@ -516,6 +516,8 @@ afd_status normalise_opts(const afd_plan_opts* in, afd_plan_opts& o, int& dev) {
 
 }  // namespace
 
+void afd::set_last_error_text(const char* text) { g_last_error = text ? text : ""; }
+
 // ------------------------------------------------------------------- plans --
 
 struct afd_plan {
