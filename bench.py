@@ -44,6 +44,28 @@ FP32_LANES_PER_SM = 128
 STEPREC_BYTES, SLOTCTL_BYTES, SLOTDEV_BYTES = 80, 40, 216
 
 
+def kernel_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("afd_kernels.cu", "afd_fft.cuh", "afd_internal.h"):
+        with open(os.path.join(ROOT, "paper_1711_08604_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the kernel sources changed since that capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("kernel_sources_sha256_16") != kernel_sources_hash():
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
 def workload():
     from paper_1711_08604_gb300 import workloads as W
     return W.tones(N=N_SIG, M=M_RAD, K=K_STEPS)
@@ -213,13 +235,18 @@ def run_afd(args):
     evals_per_step = s.M * s.N * K
     value = evals_per_step * args.steps * ws / (total_ms * 1e-3)
 
-    # grid-kernel roofline: the same steps with CUDA events around every grid launch
+    # Per-kernel device times: the same K steps again, with CUDA events recorded
+    # between consecutive kernels inside the replayed graph (event-record nodes
+    # on the plan's stream).
     afd.afd_plan_set_profiling(plan, True)
+    timed_loop(1, Gd, out)
     afd.afd_plan_reset_counters(plan)
-    prof_ms = timed_loop(args.steps, Gd, out)
-    c = afd.afd_plan_counters(plan)
+    ms_prof = timed_loop(args.steps, Gd, out)
+    ktimes = afd.afd_plan_kernel_times(plan)
     afd.afd_plan_set_profiling(plan, False)
-    grid_avg_ms = c["grid_ms"] / max(1, c["grid_launches"])
+
+    grid_ms, grid_n = ktimes["grid"]
+    grid_avg_ms = grid_ms / max(1, grid_n)
     logn = int(np.log2(s.N))
     flops_per_eval = 5 * logn + 6
     grid_flops = s.M * s.N * flops_per_eval
@@ -230,10 +257,15 @@ def run_afd(args):
     achieved_tflops = grid_flops / (grid_avg_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": f"k_grid<float,{logn}>", "achieved": achieved_tflops,
                 "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
-                "traffic": None,
+                "traffic": ncu_traffic(f"k_grid<float,{logn}>"),
+                "traffic_note": "dram read+write bytes per launch, one cold-cache ncu capture "
+                                "(profiles/k_grid_f32_tones_N4096_M200.md); null if the kernel changed since",
                 "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
                 "flops_per_launch": grid_flops, "avg_launch_ms": grid_avg_ms,
-                "profiled_ms_per_step": statistics.mean(prof_ms)}
+                "flops_per_eval": f"5*log2(N)+6 = {flops_per_eval}"}
+    prof_total = sum(ms_prof)
+    kernel_us = {k: {"launches": n, "avg_us": 1e3 * t / max(1, n), "share": t / max(prof_total, 1e-9)}
+                 for k, (t, n) in ktimes.items()}
 
     # end to end through the C ABI: pinned host input, host outputs, copies timed
     G_pin = torch.from_numpy(s.G).pin_memory()
@@ -262,6 +294,9 @@ def run_afd(args):
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                            "min": min(ms), "max": max(ms)},
             "wall_s": t_wall,
+            "kernels": kernel_us,
+            "kernels_note": "device time per kernel from CUDA events inside the replayed graph, "
+                            "a second pass of the same steps; share = fraction of that pass",
             "gpu_launches": int(launches),
             "roofline": roofline,
             "e2e": e2e,

@@ -133,14 +133,20 @@ afd_status afd_plan_last_info(const afd_plan* plan, int* n_cand_out, int* flags_
 
 /*
  * Kernel accounting of a plan since creation (or the last reset): launches of
- * the library's kernels, and, while profiling is on, the summed device time of
- * the grid kernel (CUDA events on the plan's stream around every grid launch;
- * profiling turns graph replay off).  kernel_launches and grid_launches may be
- * NULL; grid_ms is 0 unless profiling was on.
+ * the library's kernels and, while profiling is on, summed device times.
+ * Profiling records CUDA events on the plan's stream between consecutive
+ * kernels of the step sequence (inside the CUDA graph when graphs are used,
+ * as event-record nodes), so the times are those of the kernels as they run
+ * in the sequence; each profiled call synchronises once more to read them.
+ * afd_plan_counters: all launches, grid-kernel launches and grid-kernel ms.
+ * afd_plan_kernel_times: ms[4] and launches[4] per kernel kind, in the order
+ * grid, guard, update, forward (initialisation launches are not included).
+ * Any output pointer may be NULL.
  */
 afd_status afd_plan_set_profiling(afd_plan* plan, int on);
 afd_status afd_plan_counters(const afd_plan* plan, long long* kernel_launches,
                              long long* grid_launches, double* grid_ms);
+afd_status afd_plan_kernel_times(const afd_plan* plan, double* ms, long long* launches);
 afd_status afd_plan_reset_counters(afd_plan* plan);
 
 /*
@@ -178,6 +184,59 @@ afd_status afd_decompose_batch(int n_signals, const int* N, const double* radii,
                                const double* G_packed, int K_max, double energy_tol,
                                const afd_plan_opts* opts, double* a_out, double* coeff_out,
                                double* delta_out, int* idx_out, int* steps_out);
+
+/*
+ * Serving: continuous batching of independent decompositions.
+ *
+ * A server owns a worker thread and one CUDA stream.  Requests of any N
+ * (as for afd_plan_create) and their own radii, step limit and energy
+ * tolerance are queued by afd_serve_submit (any host thread; the samples are
+ * copied at submission).  The worker admits queued requests oldest first into
+ * device slots while the memory budget allows (slot buffers and the plan
+ * tables of each distinct (N, radii) count against it), then repeatedly runs
+ * one greedy step for every admitted request at once (launches grouped by N),
+ * retires the requests whose stop rule fired and admits waiting ones, so
+ * requests that arrive while others run share the device.  Each request gets
+ * the same result as afd_decompose with the server's options would give it
+ * alone.
+ *   mem_budget_bytes  device memory the server may hold (>= 1 MiB).
+ *   opts              precision, guard and device options as for plans
+ *                     (use_graph is ignored); NULL for defaults.
+ * afd_serve_submit: AFD_ERR_BUDGET if the request alone cannot fit the
+ *   budget; req_id receives the id.  G may be host or device memory.
+ * afd_serve_poll: AFD_PENDING while the request runs; otherwise fills *out
+ *   (may be NULL) and forgets the request, returning its status (AFD_OK,
+ *   AFD_ERR_NUMERIC, AFD_ERR_CUDA ...).  AFD_ERR_NOT_FOUND for unknown ids.
+ * afd_serve_wait: as poll, blocking up to timeout_s seconds (AFD_ERR_TIMEOUT).
+ * afd_serve_destroy: stops the worker; unfinished requests are dropped.
+ */
+typedef struct afd_server afd_server;
+
+typedef struct afd_result {
+  int K_cap;          /* in: capacity (steps) of the caller's arrays below */
+  double* a;          /* out, host, 2*K_cap (may be NULL) */
+  double* coeff;      /* out, host, 2*K_cap (may be NULL) */
+  double* delta;      /* out, host, K_cap+1 (may be NULL) */
+  int* idx;           /* out, host, 2*K_cap (may be NULL) */
+  int steps;          /* out: steps performed */
+  int status;         /* out: afd_status of the request */
+  double latency_ms;  /* out: submission to completion */
+} afd_result;
+
+typedef struct afd_serve_stats {
+  unsigned long long submitted, completed, failed, ticks;
+  long long kernel_launches;
+  int queued, active;
+  size_t bytes_reserved, bytes_in_use;
+} afd_serve_stats;
+
+afd_status afd_serve_create(afd_server** out, size_t mem_budget_bytes, const afd_plan_opts* opts);
+afd_status afd_serve_submit(afd_server* server, int N, const double* radii, int M, const double* G,
+                            int K_max, double energy_tol, uint64_t* req_id);
+afd_status afd_serve_poll(afd_server* server, uint64_t req_id, afd_result* out);
+afd_status afd_serve_wait(afd_server* server, uint64_t req_id, double timeout_s, afd_result* out);
+afd_status afd_serve_get_stats(afd_server* server, afd_serve_stats* out);
+afd_status afd_serve_destroy(afd_server* server);
 
 /*
  * Allocation-free FP64 inner products (the paper has no counterpart: this is

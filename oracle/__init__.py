@@ -10,6 +10,7 @@ grid points); this module only compiles it with gcc and marshals numpy arrays.
 What each function computes, with the paper passage it follows:
 
 * ``inner``   -- the rectangle-rule inner product <G, e_a>~, Sec. 3.1 Eq. (formula1).
+* ``inner_many`` -- the same at a list of points.
 * ``grid``    -- the same on the polar grid a_{s,j} = r_s exp(2 pi i j/N), Eq. (ku1)/(term81).
 * ``update``  -- the reduced-remainder (Blaschke) update of Sec. 2.
 * ``energy``  -- (1/N) sum |G(z_m)|^2, the discrete norm in the measure dt/2pi of Eq. (formula2).
@@ -55,6 +56,7 @@ def _load():
         lib = ctypes.CDLL(build())
         lib.oracle_inner.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, _dp]
         lib.oracle_grid.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
+        lib.oracle_inner_many.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
         lib.oracle_update.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, _dp]
         lib.oracle_energy.argtypes = [ctypes.c_int, _dp]
@@ -95,6 +97,15 @@ def inner(G, a: complex) -> complex:
     if _load().oracle_inner(g.size, _p(g), float(np.real(a)), float(np.imag(a)), _p(out)) != 0:
         raise ValueError("oracle_inner: bad arguments")
     return complex(out[0], out[1])
+
+
+def inner_many(G, points) -> np.ndarray:
+    """<G, e_a>~ at each of the given points (Eq. (formula1))."""
+    g, pts = _cvec(G), _cvec(points)
+    out = np.zeros_like(pts)
+    if _load().oracle_inner_many(g.size, _p(g), pts.size, _p(pts), _p(out)) != 0:
+        raise ValueError("oracle_inner_many: bad arguments")
+    return out
 
 
 def grid(G, radii) -> np.ndarray:

@@ -102,6 +102,27 @@ int oracle_inner(int N, const double* G, double a_re, double a_im, double* out) 
   return 0;
 }
 
+/* out[p] = <G, e_{a_p}>~ for n arbitrary points a_p (interleaved complex), by
+ * the rectangle rule of Eq. (formula1); OpenMP over points. */
+int oracle_inner_many(int N, const double* G, int n, const double* points, double* out) {
+  if (N <= 0 || n <= 0 || !G || !points || !out) return -1;
+  for (int p = 0; p < n; ++p) {
+    cplx a = points[2 * p] + I * points[2 * p + 1];
+    if (creal(a * conj(a)) >= 1.0) return -1;
+  }
+  cplx* z = make_points(N);
+  if (!z) return -1;
+#pragma omp parallel for schedule(static)
+  for (int p = 0; p < n; ++p) {
+    cplx a = points[2 * p] + I * points[2 * p + 1];
+    cplx v = inner_with_table(N, (const cplx*)G, z, a);
+    out[2 * p] = creal(v);
+    out[2 * p + 1] = cimag(v);
+  }
+  free(z);
+  return 0;
+}
+
 /* A[s*N + j] = <G, e_{a_{s,j}}>~ for the whole M x N grid (Step 1 of the
  * algorithm, evaluated directly as in Eq. (term81)).  A is 2*M*N doubles. */
 int oracle_grid(int N, const double* G, int M, const double* radii, double* A) {

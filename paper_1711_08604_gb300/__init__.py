@@ -26,8 +26,10 @@ __all__ = [
     "AFD_FP64_PLAIN", "AFD_FP32_GUARDED", "AfdError", "PlanOpts", "afd_plan_opts_default",
     "afd_status_str", "afd_last_error", "afd_version", "afd_plan_create", "afd_plan_destroy",
     "afd_decompose", "afd_plan_last_info", "afd_plan_set_profiling", "afd_plan_counters",
-    "afd_plan_reset_counters", "afd_plan_get_stream", "afd_batch_create", "afd_batch_run", "afd_batch_counters",
-    "afd_batch_destroy", "afd_decompose_batch", "afd_inner_products_noalloc", "library_path",
+    "afd_plan_reset_counters", "afd_plan_get_stream", "afd_plan_kernel_times", "afd_batch_create", "afd_batch_run", "afd_batch_counters",
+    "afd_batch_destroy", "afd_decompose_batch", "afd_serve_create", "afd_serve_submit",
+    "afd_serve_poll", "afd_serve_wait", "afd_serve_get_stats", "afd_serve_destroy",
+    "afd_inner_products_noalloc", "library_path",
 ]
 
 AFD_FP64_PLAIN = 0
@@ -196,6 +198,17 @@ def afd_plan_counters(plan: Plan) -> dict:
     return {"kernel_launches": kl.value, "grid_launches": gl.value, "grid_ms": ms.value}
 
 
+KERNEL_KINDS = ("grid", "guard", "update", "forward")
+
+
+def afd_plan_kernel_times(plan: Plan) -> dict:
+    """Per kernel kind: {"grid": (ms, launches), ...} accumulated while profiling."""
+    ms = np.zeros(4)
+    n = np.zeros(4, dtype=np.int64)
+    _check(_lib().afd_plan_kernel_times(plan.handle, ms.ctypes.data, n.ctypes.data))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
 def afd_plan_get_stream(plan: Plan) -> int:
     """cudaStream_t (as an int) the plan's kernels run on."""
     sp = ctypes.c_void_p()
@@ -259,6 +272,82 @@ def afd_decompose_batch(signals, radii, K_max: int, energy_tol: float = 0.0,
         return afd_batch_run(b, packed, energy_tol)
     finally:
         b.close()
+
+
+class Server:
+    """Owning handle of an ``afd_server``."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            _lib().afd_serve_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+
+def afd_serve_create(mem_budget_bytes: int, opts: PlanOpts | None = None, **kw) -> Server:
+    """Serving engine with a device memory budget (continuous batching)."""
+    o = _opts(opts, **kw)
+    h = ctypes.c_void_p()
+    _check(_lib().afd_serve_create(ctypes.byref(h), int(mem_budget_bytes), ctypes.byref(o)))
+    return Server(h)
+
+
+def afd_serve_submit(server: Server, G, radii, K_max: int, energy_tol: float = 0.0) -> int:
+    gp, keep = _in_ptr(G)
+    r = np.ascontiguousarray(np.asarray(radii, dtype=np.float64))
+    n = int(G.numel()) if _is_torch(G) else int(np.asarray(G).size)
+    rid = ctypes.c_uint64()
+    _check(_lib().afd_serve_submit(server.handle, n, r.ctypes.data, int(r.size), gp, int(K_max),
+                                   float(energy_tol), ctypes.byref(rid)))
+    return int(rid.value)
+
+
+def _result_buffers(K_cap: int):
+    a, c = np.zeros(2 * K_cap), np.zeros(2 * K_cap)
+    d, ix = np.zeros(K_cap + 1), np.zeros(2 * K_cap, dtype=np.int32)
+    res = _native.Result(K_cap, a.ctypes.data, c.ctypes.data, d.ctypes.data, ix.ctypes.data, 0, 0, 0.0)
+    return res, (a, c, d, ix)
+
+
+def _result_dict(res, bufs) -> dict:
+    a, c, d, ix = bufs
+    n = res.steps
+    return {"steps": n, "status": res.status, "latency_ms": res.latency_ms,
+            "a": a[: 2 * n].view(np.complex128), "coeff": c[: 2 * n].view(np.complex128),
+            "delta": d[: n + 1], "idx": ix[: 2 * n].reshape(n, 2)}
+
+
+def afd_serve_poll(server: Server, req_id: int, K_cap: int = 4096):
+    """None while the request runs; its result dict once finished (then forgotten)."""
+    res, bufs = _result_buffers(K_cap)
+    st = _lib().afd_serve_poll(server.handle, int(req_id), ctypes.byref(res))
+    if st == 1:
+        return None
+    out = _result_dict(res, bufs)
+    _check(st, out)
+    return out
+
+
+def afd_serve_wait(server: Server, req_id: int, timeout_s: float = 60.0, K_cap: int = 4096) -> dict:
+    res, bufs = _result_buffers(K_cap)
+    st = _lib().afd_serve_wait(server.handle, int(req_id), float(timeout_s), ctypes.byref(res))
+    out = _result_dict(res, bufs)
+    _check(st, out)
+    return out
+
+
+def afd_serve_get_stats(server: Server) -> dict:
+    s = _native.ServeStats()
+    _check(_lib().afd_serve_get_stats(server.handle, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in _native.ServeStats._fields_}
+
+
+def afd_serve_destroy(server: Server) -> None:
+    server.close()
 
 
 def afd_inner_products_noalloc(G, points, out=None, stream=None):

@@ -22,6 +22,18 @@ class PlanOpts(ctypes.Structure):
                 ("use_graph", c_int)]
 
 
+class Result(ctypes.Structure):
+    _fields_ = [("K_cap", c_int), ("a", c_void_p), ("coeff", c_void_p), ("delta", c_void_p),
+                ("idx", c_void_p), ("steps", c_int), ("status", c_int), ("latency_ms", c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_ulonglong), ("completed", ctypes.c_ulonglong),
+                ("failed", ctypes.c_ulonglong), ("ticks", ctypes.c_ulonglong),
+                ("kernel_launches", c_ll), ("queued", c_int), ("active", c_int),
+                ("bytes_reserved", c_size_t), ("bytes_in_use", c_size_t)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "afd_plan_opts_default": (None, [P(PlanOpts)]),
@@ -36,6 +48,7 @@ SIGNATURES = {
     "afd_plan_set_profiling": (c_int, [c_void_p, c_int]),
     "afd_plan_counters": (c_int, [c_void_p, P(c_ll), P(c_ll), P(c_double)]),
     "afd_plan_reset_counters": (c_int, [c_void_p]),
+    "afd_plan_kernel_times": (c_int, [c_void_p, c_void_p, c_void_p]),
     "afd_plan_get_stream": (c_int, [c_void_p, P(c_void_p)]),
     "afd_batch_create": (c_int, [P(c_void_p), c_int, c_void_p, c_void_p, c_int, c_int, P(PlanOpts)]),
     "afd_batch_run": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -44,6 +57,12 @@ SIGNATURES = {
     "afd_batch_destroy": (c_int, [c_void_p]),
     "afd_decompose_batch": (c_int, [c_int, c_void_p, c_void_p, c_int, c_void_p, c_int, c_double,
                                     P(PlanOpts), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "afd_serve_create": (c_int, [P(c_void_p), c_size_t, P(PlanOpts)]),
+    "afd_serve_submit": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_double, P(c_u64)]),
+    "afd_serve_poll": (c_int, [c_void_p, c_u64, P(Result)]),
+    "afd_serve_wait": (c_int, [c_void_p, c_u64, c_double, P(Result)]),
+    "afd_serve_get_stats": (c_int, [c_void_p, P(ServeStats)]),
+    "afd_serve_destroy": (c_int, [c_void_p]),
     "afd_inner_products_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
 }
 

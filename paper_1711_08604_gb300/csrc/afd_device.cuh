@@ -1,0 +1,366 @@
+// Device helpers shared by the kernel translation units: best-pair
+// reductions, deterministic block sums, last-CTA detection, programmatic
+// dependent launch, and the selection of Step 2 (Sec. 3.2) run by the last CTA
+// of a signal's grid launch.
+#pragma once
+#include <climits>
+#include <cstdint>
+
+#include "afd_internal.h"
+
+namespace afd {
+
+
+__device__ __forceinline__ bool better_f(float va, int ja, float vb, int jb) {
+  return va > vb || (va == vb && ja < jb);
+}
+__device__ __forceinline__ bool better_d(double va, int ja, double vb, int jb) {
+  return va > vb || (va == vb && ja < jb);
+}
+
+struct Best2F {
+  float v1, v2;
+  int j1, j2;
+  __device__ __forceinline__ void init() { v1 = v2 = -1.0f; j1 = j2 = INT_MAX; }
+  __device__ __forceinline__ void insert(float v, int j) {
+    if (better_f(v, j, v1, j1)) { v2 = v1; j2 = j1; v1 = v; j1 = j; }
+    else if (better_f(v, j, v2, j2)) { v2 = v; j2 = j; }
+  }
+  __device__ __forceinline__ void merge(const Best2F& o) {
+    if (better_f(o.v1, o.j1, v1, j1)) {
+      if (better_f(v1, j1, o.v2, o.j2)) { v2 = v1; j2 = j1; } else { v2 = o.v2; j2 = o.j2; }
+      v1 = o.v1; j1 = o.j1;
+    } else if (better_f(o.v1, o.j1, v2, j2)) {
+      v2 = o.v1; j2 = o.j1;
+    }
+  }
+  __device__ __forceinline__ Best2F shfl(int off) const {
+    Best2F r;
+    r.v1 = __shfl_xor_sync(0xffffffffu, v1, off);
+    r.v2 = __shfl_xor_sync(0xffffffffu, v2, off);
+    r.j1 = __shfl_xor_sync(0xffffffffu, j1, off);
+    r.j2 = __shfl_xor_sync(0xffffffffu, j2, off);
+    return r;
+  }
+};
+
+struct Best1D {
+  double v;
+  int j;
+  double2 f;
+  __device__ __forceinline__ void init() { v = -1.0; j = INT_MAX; f = make_double2(0.0, 0.0); }
+  __device__ __forceinline__ void insert(double vv, int jj, double2 ff) {
+    if (better_d(vv, jj, v, j)) { v = vv; j = jj; f = ff; }
+  }
+  __device__ __forceinline__ void merge(const Best1D& o) { insert(o.v, o.j, o.f); }
+  __device__ __forceinline__ Best1D shfl(int off) const {
+    Best1D r;
+    r.v = __shfl_xor_sync(0xffffffffu, v, off);
+    r.j = __shfl_xor_sync(0xffffffffu, j, off);
+    r.f.x = __shfl_xor_sync(0xffffffffu, f.x, off);
+    r.f.y = __shfl_xor_sync(0xffffffffu, f.y, off);
+    return r;
+  }
+};
+
+// Reduce B over each group of TPF consecutive threads; the group's thread
+// t == 0 ends with the result.  All threads of the CTA must call it.
+template <int TPF, class B>
+__device__ __forceinline__ void group_reduce(B& b, B* red) {
+  constexpr int W = TPF < 32 ? TPF : 32;
+#pragma unroll
+  for (int off = W / 2; off > 0; off >>= 1) b.merge(b.shfl(off));
+  if constexpr (TPF > 32) {
+    constexpr int WPG = TPF / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = b;
+    __syncthreads();
+    if (lane == 0 && (warp % WPG) == 0) {
+#pragma unroll 1
+      for (int w = 1; w < WPG; ++w) b.merge(red[warp + w]);
+    }
+  }
+}
+
+// Deterministic FP64 block sum (fixed shuffle tree, warps added in order).
+// Result valid in thread 0.
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double x, double* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll 1
+    for (int w = 0; w < THREADS / 32; ++w) s += red[w];
+  }
+  return s;
+}
+
+// Block-wide best (v, flat) over all threads; every thread gets the result.
+template <int THREADS>
+__device__ __forceinline__ void block_best_f(float& v, int& f, float* sv, int* sf) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    float ov = __shfl_xor_sync(0xffffffffu, v, off);
+    int of = __shfl_xor_sync(0xffffffffu, f, off);
+    if (better_f(ov, of, v, f)) { v = ov; f = of; }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) { sv[warp] = v; sf[warp] = f; }
+  __syncthreads();
+  v = sv[0];
+  f = sf[0];
+#pragma unroll 1
+  for (int w = 1; w < THREADS / 32; ++w)
+    if (better_f(sv[w], sf[w], v, f)) { v = sv[w]; f = sf[w]; }
+}
+
+// Last-CTA detection: returns true in every thread of the CTA that is the
+// last of `target` CTAs to arrive on *counter, and resets the counter.
+__device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned target, int* s_flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(counter, 1u);
+    *s_flag = (prev == target - 1u);
+    if (*s_flag) *counter = 0u;
+  }
+  __syncthreads();
+  const bool last = *s_flag != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+__device__ __forceinline__ int ld_done(const SlotCtl* c) { return *((volatile const int*)&c->done); }
+
+// Programmatic dependent launch: the step kernels are launched so that the
+// next kernel in the stream may be scheduled while this one runs.  Each kernel
+// lets its dependents launch at entry and waits for its own predecessor to
+// complete (with its memory visible) before reading anything it produced.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Candidates of the FP32 path: every grid point whose FP32 objective is at
+// least thr, ordered best first (value, then lowest flat index s N + j); the
+// first cap of them go to out[].  Reads the best pairs top[0 .. M sub), sub
+// entries per radius.  Every thread of the CTA must call it; every thread gets
+// n (candidates kept) and count (points at or above thr).  Deterministic: the
+// same inputs give the same list in any CTA.
+template <int THREADS>
+__device__ void select_core(const Top2F* top, int M, int N, int sub, float thr, int cap, int2* out, int* n_out,
+                            int* count_out) {
+  constexpr int LIST = 1024;
+  __shared__ float s_v[LIST];
+  __shared__ int s_f[LIST];
+  __shared__ int s_count;
+  __shared__ float sv[32];
+  __shared__ int sf[32];
+  __syncthreads();
+  if (threadIdx.x == 0) s_count = 0;
+  __syncthreads();
+  for (int r = threadIdx.x; r < M * sub; r += THREADS) {
+    const int s = r / sub;
+    const int4 raw = __ldcg(reinterpret_cast<const int4*>(top) + r);  // v1, v2, j1, j2
+    const float v1 = __int_as_float(raw.x), v2 = __int_as_float(raw.y);
+    if (v1 >= thr && raw.z != INT_MAX) {
+      const int i = atomicAdd(&s_count, 1);
+      if (i < LIST) { s_v[i] = v1; s_f[i] = s * N + raw.z; }
+    }
+    if (v2 >= thr && raw.w != INT_MAX) {
+      const int i = atomicAdd(&s_count, 1);
+      if (i < LIST) { s_v[i] = v2; s_f[i] = s * N + raw.w; }
+    }
+  }
+  __syncthreads();
+  const int count = s_count;
+  int n;
+  if (count <= LIST) {
+    // rank of each entry = number of better entries; ranks are distinct
+    for (int i = threadIdx.x; i < count; i += THREADS) {
+      const float v = s_v[i];
+      const int f = s_f[i];
+      int rank = 0;
+      for (int q = 0; q < count; ++q) rank += better_f(s_v[q], s_f[q], v, f) ? 1 : 0;
+      if (rank < cap) out[rank] = make_int2(f / N, f % N);
+    }
+    n = min(count, cap);
+  } else {
+    // a plateau wider than the list (degenerate input): pick the best cap one
+    // at a time, each strictly worse than the previous pick
+    float last_v = __int_as_float(0x7f800000);
+    int last_f = -1;
+    for (n = 0; n < cap; ++n) {
+      float bv = -1.0f;
+      int bf = INT_MAX;
+      for (int e = threadIdx.x; e < 2 * M * sub; e += THREADS) {
+        const int r = e >> 1, s = r / sub;
+        const float v = (e & 1) ? __ldcg(&top[r].v2) : __ldcg(&top[r].v1);
+        const int j = (e & 1) ? __ldcg(&top[r].j2) : __ldcg(&top[r].j1);
+        if (j == INT_MAX || !(v >= thr)) continue;
+        const int f = s * N + j;
+        if (better_f(last_v, last_f, v, f) && better_f(v, f, bv, bf)) { bv = v; bf = f; }
+      }
+      block_best_f<THREADS>(bv, bf, sv, sf);
+      if (bf == INT_MAX) break;
+      if (threadIdx.x == 0) out[n] = make_int2(bf / N, bf % N);
+      last_v = bv;
+      last_f = bf;
+    }
+  }
+  __syncthreads();
+  *n_out = n;
+  *count_out = count;
+}
+
+// FP32 selection in the last CTA of a signal's grid launch: every grid point
+// whose FP32 objective is within the relative window tau of the step's largest
+// one (known from the atomicMax each CTA made) becomes a candidate for the
+// FP64 guard, at most cap of them, best first.
+template <int THREADS>
+__device__ void select_candidates_f32(const SlotDev& sd, int k, int sub = 1) {
+  SlotCtl* ctl = sd.ctl;
+  StepRec& rec = sd.rec[k];
+  const float vmax = __uint_as_float(__ldcg(&ctl->vmax_bits));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->vmax_bits = 0u;  // ready for the next step
+    rec.obj32 = vmax;
+    rec.flags = 0;
+  }
+  if (sd.force_a1_zero && k == 0) {
+    if (threadIdx.x == 0) {
+      sd.cand[0] = make_int2(0, 0);
+      ctl->n_cand = 1;
+    }
+    return;
+  }
+  const float thr = vmax - vmax * (float)sd.tau;
+  int n, count;
+  select_core<THREADS>(reinterpret_cast<const Top2F*>(sd.top2), sd.p.M, sd.p.N, sub, thr, sd.cap, sd.cand, &n,
+                       &count);
+  if (threadIdx.x == 0) {
+    ctl->n_cand = n;
+    if (count > sd.cap) rec.flags = 1;
+  }
+}
+
+// ---------------------------------------------------- FP64 guard and update --
+
+// One term of the guard's rectangle rule for the candidate (s, j) at sample m:
+// G(z_m) K_s[(j - m) mod N], K_s[d] = 1 / (1 - r_s w^d).
+__device__ __forceinline__ void guard_term(const SlotDev& sd, int s, int j, int m, double2 g, double& ar,
+                                           double& ai) {
+  const int N = sd.p.N;
+  const double2 k = __ldg(&sd.p.K64[(size_t)s * N + ((j - m) & (N - 1))]);
+  ar = fma(g.x, k.x, -g.y * k.y);
+  ai = fma(g.x, k.y, g.y * k.x);
+}
+
+// Fixed-order sum over the first FP64_THREADS threads (warps 0..3) of (x, y):
+// a shuffle tree inside each warp, then the warps in order.  Every thread of
+// the CTA must call it; thread 0 gets the total.
+__device__ __forceinline__ double2 sum_fp64_group(double x, double y, double* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, off);
+    y += __shfl_xor_sync(0xffffffffu, y, off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0 && warp < FP64_THREADS / 32) {
+    red[2 * warp] = x;
+    red[2 * warp + 1] = y;
+  }
+  __syncthreads();
+  double tx = 0.0, ty = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < FP64_THREADS / 32; ++w) {
+      tx += red[2 * w];
+      ty += red[2 * w + 1];
+    }
+  }
+  return make_double2(tx, ty);
+}
+
+// Reduced-remainder update of Sec. 2 at z_m for a = r_s w^j and
+// c' = c sqrt(1 - r_s^2):  G_{k+1}(z_m) = (G_k(z_m) u - c') / (z_m - a) with
+// u = 1 - conj(a) z_m = 1 - r_s w^d, d = (m - j) mod N.  Because
+// z_m - a = z_m conj(u), the division is (...) conj(z_m) conj(K_s[d]).
+__device__ __forceinline__ double2 update_point(const SlotDev& sd, int m, int s, int j, double r, double cr,
+                                                double ci, double2 g) {
+  const int N = sd.p.N;
+  const int d = (m - j) & (N - 1);
+  const double2 w = __ldg(&sd.p.tw64[d]);
+  const double2 z = __ldg(&sd.p.tw64[m]);
+  const double2 kd = __ldg(&sd.p.K64[(size_t)s * N + d]);
+  const double ur = fma(-r, w.x, 1.0), ui = -r * w.y;
+  const double xr = fma(g.x, ur, fma(-g.y, ui, -cr));
+  const double xi = fma(g.x, ui, fma(g.y, ur, -ci));
+  const double yr = fma(xr, kd.x, xi * kd.y);  // (x) conj(K)
+  const double yi = fma(xi, kd.x, -xr * kd.y);
+  return make_double2(fma(yr, z.x, yi * z.y), fma(yi, z.x, -yr * z.y));  // (y) conj(z)
+}
+
+// FP64 selection: global best of the per-radius maxima; writes the step record.
+template <int THREADS>
+__device__ void select_best_f64(const SlotDev& sd, int k, Best1D* red) {
+  const int M = sd.p.M, N = sd.p.N;
+  const Top2D* top = reinterpret_cast<const Top2D*>(sd.top2);
+  Best1D b;
+  b.init();
+  if (sd.force_a1_zero && k == 0) {
+    if (threadIdx.x == 0) {
+      b.v = __ldcg(&top[0].v1);
+      b.j = 0;  // radius 0: every angle ties, j1 == 0
+      b.f.x = __ldcg(&top[0].f1.x);
+      b.f.y = __ldcg(&top[0].f1.y);
+    }
+  } else {
+    for (int s = threadIdx.x; s < M; s += THREADS) {
+      const int j = __ldcg(&top[s].j1);
+      if (j == INT_MAX) continue;
+      double2 f;
+      f.x = __ldcg(&top[s].f1.x);
+      f.y = __ldcg(&top[s].f1.y);
+      b.insert(__ldcg(&top[s].v1), s * N + j, f);
+    }
+    group_reduce<THREADS>(b, red);
+  }
+  if (threadIdx.x == 0) {
+    StepRec& r = sd.rec[k];
+    if (b.j == INT_MAX || !(b.v >= 0.0) || b.v > 1.79e308) {
+      r.flags = 2;
+      sd.ctl->err |= 2;
+      sd.ctl->done = 1;
+      r.s = -1;
+      r.j = -1;
+      return;
+    }
+    const int s = b.j / N, j = b.j % N;
+    const double w = sd.p.w64[s];
+    const double rr = sd.p.radii[s];
+    const double2 z = sd.p.tw64[j];
+    r.s = s;
+    r.j = j;
+    r.n_cand = 0;
+    r.flags = 0;
+    r.a_re = rr * z.x;
+    r.a_im = rr * z.y;
+    r.c_re = w * b.f.x;
+    r.c_im = w * b.f.y;
+    r.obj = r.c_re * r.c_re + r.c_im * r.c_im;
+    r.obj32 = b.v;
+  }
+}
+
+
+}  // namespace afd

@@ -11,8 +11,8 @@
 // global memory and the last pass may consume its outputs from registers,
 // leaving (passes - 1) shared-memory round trips.
 //
-// Radix schedule: one short pass of 2^(LOGN mod 4) first (if LOGN is not a
-// multiple of 4), then radix-16 passes.  Shared memory is padded with one
+// Radix schedule (FftSchedule): one short pass of 2^(LOGN mod 4) first (if
+// LOGN is not a multiple of 4), then radix-16 passes.  Shared memory is padded with one
 // element per 16 (index i -> i + i/16), which makes the strided stores of the
 // first passes bank-conflict free.
 //
@@ -89,6 +89,34 @@ __device__ __forceinline__ void dft(V2<T>* v) {
 
 __device__ __forceinline__ int smem_pad(int i) { return i + (i >> 4); }
 
+// Radix schedule of a 2^logn transform, shared by device code and the host
+// code that builds the twiddle and power tables: pass 0 has radix
+// 2^(logn mod 4) when logn is not a multiple of 4, every other pass radix 16.
+struct FftSchedule {
+  static __host__ __device__ constexpr int npass(int logn) { return logn / 4 + (logn % 4 ? 1 : 0); }
+  static __host__ __device__ constexpr int radix(int logn, int p) {
+    return (p == 0 && logn % 4) ? (1 << (logn % 4)) : 16;
+  }
+  // length of the sub-transforms that pass p combines
+  static __host__ __device__ constexpr int ns(int logn, int p) {
+    int n = 1;
+    for (int i = 0; i < p; ++i) n *= radix(logn, i);
+    return n;
+  }
+  // Stage twiddle table: pass p >= 1 owns (radix - 1) * ns entries at tw_off,
+  // entry (q - 1) * ns + k holding exp(2 pi i q k / (ns * radix)), so that a
+  // warp's consecutive butterflies read consecutive entries.
+  static __host__ __device__ constexpr int tw_off(int logn, int p) {
+    int o = 0;
+    for (int i = 1; i < p; ++i) o += (radix(logn, i) - 1) * ns(logn, i);
+    return o;
+  }
+  static __host__ __device__ constexpr int tw_size(int logn) { return tw_off(logn, npass(logn)); }
+  // Power table split: r^l = lo[l mod B] * hi[l / B] with B = N / radix(0),
+  // so the pass-0 inputs of one thread share lo and differ only in hi.
+  static __host__ __device__ constexpr int pow_b(int logn) { return (1 << logn) / radix(logn, 0); }
+};
+
 // Compile-time shape of one transform.
 template <typename T, int LOGN>
 struct FftShape {
@@ -96,31 +124,27 @@ struct FftShape {
   // Points per thread: 16 (32 for FP32 at N = 16384 to keep 512 threads).
   static constexpr int P = LOGN < 4 ? N : ((sizeof(T) == 4 && LOGN >= 14) ? 32 : 16);
   static constexpr int TPF = N / P;                    // threads per transform
-  static constexpr int REM = LOGN % 4;                 // bits of the short first pass
-  static constexpr int NPASS = LOGN / 4 + (REM ? 1 : 0);
+  static constexpr int NPASS = FftSchedule::npass(LOGN);
   static constexpr int SMEM = N + N / 16 + 1;          // padded elements per transform
-  static __host__ __device__ constexpr int radix(int p) { return (p == 0 && REM) ? (1 << REM) : 16; }
-  static __host__ __device__ constexpr int ns(int p) {
-    int n = 1;
-    for (int i = 0; i < p; ++i) n *= radix(i);
-    return n;
-  }
+  static __host__ __device__ constexpr int radix(int p) { return FftSchedule::radix(LOGN, p); }
+  static __host__ __device__ constexpr int ns(int p) { return FftSchedule::ns(LOGN, p); }
 };
 
 // Twiddles of pass PASS applied to the thread's butterflies, then the DFTs.
+// tw is the stage twiddle table of FftSchedule.
 template <typename T, int LOGN, int DIR, int PASS>
 __device__ __forceinline__ void fft_pass(V2<T>* v, int t, const V2<T>* __restrict__ tw) {
   using S = FftShape<T, LOGN>;
   constexpr int R = S::radix(PASS), NS = S::ns(PASS), NB = S::P / R;
+  constexpr int OFF = FftSchedule::tw_off(LOGN, PASS);
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     if constexpr (NS > 1) {
       const int b = t + i * S::TPF;
       const int k = b & (NS - 1);
-      constexpr int STRIDE = S::N / (NS * R);
 #pragma unroll
       for (int q = 1; q < R; ++q) {
-        const V2<T> w = __ldg(&tw[q * k * STRIDE]);
+        const V2<T> w = __ldg(&tw[OFF + (q - 1) * NS + k]);
         v[i * R + q] = DIR > 0 ? cmul<T>(v[i * R + q], w) : cmulc<T>(v[i * R + q], w);
       }
     }

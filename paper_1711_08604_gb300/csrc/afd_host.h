@@ -1,0 +1,71 @@
+// Host-side helpers shared by the library's translation units (plans,
+// batches, serving).  Not part of the public C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/afd.h"
+#include "afd_internal.h"
+
+#define CUDA_TRY(expr)                                                  \
+  do {                                                                  \
+    cudaError_t _e = (expr);                                            \
+    if (_e != cudaSuccess) return ::afd::cuda_fail(_e, #expr, __LINE__); \
+  } while (0)
+
+#define AFD_TRY(expr)            \
+  do {                           \
+    afd_status _s = (expr);      \
+    if (_s != AFD_OK) return _s; \
+  } while (0)
+
+namespace afd {
+
+// Error text of the calling thread (afd_last_error).
+afd_status set_error(afd_status st, const char* fmt, ...);
+void clear_last_error();
+const char* last_error_text();
+afd_status cuda_fail(cudaError_t e, const char* what, int line);
+
+afd_status ensure_configured(int dev);  // kernel attributes, once per device
+int ilog2(int n);
+bool is_pow2(int n);
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+afd_status check_opts(const afd_plan_opts& o);
+afd_status check_size(int N, int prec, bool allow_two_pass = false);
+afd_status check_radii(const double* radii, int M);
+// opts (NULL: defaults) validated into o; dev = the device to use.
+afd_status normalise_opts(const afd_plan_opts* in, afd_plan_opts& o, int& dev);
+
+// Makes `dev` current for the scope and restores the caller's device.
+struct DeviceScope {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Device tables of one (N, radii) pair (see afd_runtime.cu).
+struct Tables {
+  int N = 0, M = 0;
+  std::vector<double> radii;
+  void* mem = nullptr;
+  size_t bytes = 0;
+  PlanDev dev{};
+  Tables() = default;
+  Tables(const Tables&) = delete;
+  Tables& operator=(const Tables&) = delete;
+  ~Tables();
+  afd_status build(int N, const double* radii, int M);
+  static size_t bytes_for(int N, int M);  // device bytes build() allocates
+};
+
+}  // namespace afd

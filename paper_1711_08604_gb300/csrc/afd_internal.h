@@ -5,13 +5,16 @@
 
 namespace afd {
 
-// Work split of the FP64 kernels: each CTA of 256 threads owns a chunk of
-// FP64_CHUNK consecutive sample points.
-constexpr int FP64_THREADS = 256;
-constexpr int FP64_CHUNK = 512;
-// Lowest-order power table length: r^l = rhi[l / RPOW_B] * rlo[l % RPOW_B].
-constexpr int RPOW_B_MAX = 64;
+// Work split of the FP64 kernels (guard, update, energy): each CTA of
+// FP64_THREADS threads owns FP64_CHUNK consecutive sample points, one per
+// thread, so one signal's FP64 work spreads over N / 128 SMs.  GB300 issues
+// FP64 at about 1/70 of its FP32 rate, so FP64 work is spread wide.  The split
+// depends on N only, which keeps results identical alone and in a batch.
+constexpr int FP64_THREADS = 128;
+constexpr int FP64_CHUNK = 128;
+constexpr int GUARD_PAR = 4;           // candidates in flight per guard launch
 constexpr int MAX_LOGN_RESIDENT = 14;  // N <= 16384: one CTA holds one FFT
+constexpr int TWO_PASS_LOGN = 16;      // N = 65536: two-pass FFT through HBM (plans only)
 constexpr int MIN_LOGN = 3;            // N >= 8
 constexpr int MAX_CAP = 64;            // guard candidates per step, upper bound
 
@@ -19,10 +22,11 @@ inline __host__ __device__ int chunks_of(int N) { return N > FP64_CHUNK ? N / FP
 
 // Per (N, radii) tables, owned by a plan, read-only in kernels.
 struct PlanDev {
-  int N, logN, M, B;        // B = min(RPOW_B_MAX, N); the high table has N / B entries
+  int N, logN, M, B;        // B = FftSchedule::pow_b(logN); the high power table has N / B entries
   const double* radii;      // [M] ascending radii r_s in [0, 1)
-  const float2* tw32;       // [N] exp(+2 pi i k / N) rounded to FP32
   const double2* tw64;      // [N] exp(+2 pi i k / N) in FP64 (also the sample points z_m)
+  const float2* st32;       // [FftSchedule::tw_size] FFT stage twiddles, FP32
+  const double2* st64;      // the same in FP64
   const float* rlo32;       // [M * B]        r_s^q,        q = 0..B-1
   const float* rhi32;       // [M * (N / B)]  r_s^(B h),    h = 0..N/B-1
   const double* rlo64;
@@ -30,13 +34,16 @@ struct PlanDev {
   const float* wsq32;       // [M] w_s^2 with w_s = sqrt(1 - r_s^2) / (1 - r_s^N)
   const double* w64;        // [M] w_s
   const double* sq64;       // [M] sqrt(1 - r_s^2)
+  const double2* K64;       // [M * N] 1 / (1 - r_s exp(2 pi i d / N)), FP64
+  const float2* tw32n;      // [N] exp(+2 pi i k / N) in FP32 (two-pass path only)
 };
 
 // One greedy step's outcome, written on the device.
 struct StepRec {
   int s, j;                 // selected grid index (radius s, angle j)
   int n_cand;               // FP64 guard candidates evaluated (FP32 path)
-  int flags;                // bit 0: guard window saturated; bit 1: non-finite objective
+  int flags;                // bit 0: more points in the guard window than the cap; bit 1: non-finite
+                            // objective; bit 2: a bounded wait ran out
   double a_re, a_im;        // a_k = r_s exp(2 pi i j / N)
   double c_re, c_im;        // <G_k, e_{a_k}>~
   double obj;               // |c|^2
@@ -52,7 +59,10 @@ struct SlotCtl {
   int n_cand;               // candidates of the current step
   int err;                  // sticky error bits (StepRec::flags)
   double E1;                // initial energy
-  unsigned cnt_grid, cnt_guard, cnt_update, cnt_pad;  // last-CTA counters
+  unsigned cnt_grid, cnt_guard, cnt_update;  // last-CTA counters
+  unsigned vmax_bits;       // FP32 path: bits of the step's largest objective (atomicMax)
+  unsigned bar_count, bar_gen;  // persistent kernel: grid barrier
+  unsigned vmax2[2];        // persistent kernel: vmax_bits of even / odd steps
 };
 
 struct Top2F { float v1, v2; int j1, j2; };
@@ -68,7 +78,9 @@ struct SlotDev {
   double tol;               // stop once delta <= tol (0: never)
   double tau;               // guard window: obj32 >= (1 - tau) * max32
   double2* G;               // [N] remainder G_k(z_m), FP64
+  float2* g32;              // [N] G_k(z_m) / N rounded to FP32 (input of the FP32 forward FFT)
   float2* c32;              // [N] spectrum c_l / N, FP32
+  float2* X;                // two-pass path: [M * N] pass-1 output, X_s[j2][l1]
   double2* c64;             // [N] spectrum c_l / N, FP64
   void* top2;               // [M] Top2F or Top2D
   int2* cand;               // [cap] (s, j)
@@ -83,10 +95,15 @@ struct SlotDev {
 cudaError_t launch_init(const SlotDev* slots, const int* ids, int n, int logN, cudaStream_t st);
 cudaError_t launch_grid(const SlotDev* slots, const int* ids, int n, int logN, int prec, int Mmax,
                         cudaStream_t st);
+// Whole FP32-path decomposition of slot 0 in one cooperative launch (after
+// launch_init); logN <= MAX_LOGN_RESIDENT.
+cudaError_t launch_persistent(const SlotDev* slots, int logN, int M, cudaStream_t st);
 cudaError_t launch_guard(const SlotDev* slots, const int* ids, int n, int logN, int cap, cudaStream_t st);
 cudaError_t launch_update(const SlotDev* slots, const int* ids, int n, int logN, cudaStream_t st);
 cudaError_t launch_forward(const SlotDev* slots, const int* ids, int n, int logN, int prec,
                            cudaStream_t st);
+// Fills K[s * N + d] = 1 / (1 - r_s exp(2 pi i d / N)) for a plan.
+cudaError_t launch_kernel_table(const double* radii, int M, int N, double2* K, cudaStream_t st);
 // Shared memory (bytes) the grid kernel needs for this logN and precision.
 size_t grid_smem_bytes(int logN, int prec);
 size_t forward_smem_bytes(int logN, int prec);

@@ -24,140 +24,12 @@
 #include <climits>
 #include <cstdint>
 
+#include "afd_device.cuh"
 #include "afd_fft.cuh"
+#include "afd_fft2.h"
 #include "afd_internal.h"
 
 namespace afd {
-
-// ---------------------------------------------------------------- helpers --
-
-__device__ __forceinline__ bool better_f(float va, int ja, float vb, int jb) {
-  return va > vb || (va == vb && ja < jb);
-}
-__device__ __forceinline__ bool better_d(double va, int ja, double vb, int jb) {
-  return va > vb || (va == vb && ja < jb);
-}
-
-struct Best2F {
-  float v1, v2;
-  int j1, j2;
-  __device__ __forceinline__ void init() { v1 = v2 = -1.0f; j1 = j2 = INT_MAX; }
-  __device__ __forceinline__ void insert(float v, int j) {
-    if (better_f(v, j, v1, j1)) { v2 = v1; j2 = j1; v1 = v; j1 = j; }
-    else if (better_f(v, j, v2, j2)) { v2 = v; j2 = j; }
-  }
-  __device__ __forceinline__ void merge(const Best2F& o) {
-    if (better_f(o.v1, o.j1, v1, j1)) {
-      if (better_f(v1, j1, o.v2, o.j2)) { v2 = v1; j2 = j1; } else { v2 = o.v2; j2 = o.j2; }
-      v1 = o.v1; j1 = o.j1;
-    } else if (better_f(o.v1, o.j1, v2, j2)) {
-      v2 = o.v1; j2 = o.j1;
-    }
-  }
-  __device__ __forceinline__ Best2F shfl(int off) const {
-    Best2F r;
-    r.v1 = __shfl_xor_sync(0xffffffffu, v1, off);
-    r.v2 = __shfl_xor_sync(0xffffffffu, v2, off);
-    r.j1 = __shfl_xor_sync(0xffffffffu, j1, off);
-    r.j2 = __shfl_xor_sync(0xffffffffu, j2, off);
-    return r;
-  }
-};
-
-struct Best1D {
-  double v;
-  int j;
-  double2 f;
-  __device__ __forceinline__ void init() { v = -1.0; j = INT_MAX; f = make_double2(0.0, 0.0); }
-  __device__ __forceinline__ void insert(double vv, int jj, double2 ff) {
-    if (better_d(vv, jj, v, j)) { v = vv; j = jj; f = ff; }
-  }
-  __device__ __forceinline__ void merge(const Best1D& o) { insert(o.v, o.j, o.f); }
-  __device__ __forceinline__ Best1D shfl(int off) const {
-    Best1D r;
-    r.v = __shfl_xor_sync(0xffffffffu, v, off);
-    r.j = __shfl_xor_sync(0xffffffffu, j, off);
-    r.f.x = __shfl_xor_sync(0xffffffffu, f.x, off);
-    r.f.y = __shfl_xor_sync(0xffffffffu, f.y, off);
-    return r;
-  }
-};
-
-// Reduce B over each group of TPF consecutive threads; the group's thread
-// t == 0 ends with the result.  All threads of the CTA must call it.
-template <int TPF, class B>
-__device__ __forceinline__ void group_reduce(B& b, B* red) {
-  constexpr int W = TPF < 32 ? TPF : 32;
-#pragma unroll
-  for (int off = W / 2; off > 0; off >>= 1) b.merge(b.shfl(off));
-  if constexpr (TPF > 32) {
-    constexpr int WPG = TPF / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[warp] = b;
-    __syncthreads();
-    if (lane == 0 && (warp % WPG) == 0) {
-#pragma unroll 1
-      for (int w = 1; w < WPG; ++w) b.merge(red[warp + w]);
-    }
-  }
-}
-
-// Deterministic FP64 block sum (fixed shuffle tree, warps added in order).
-// Result valid in thread 0.
-template <int THREADS>
-__device__ __forceinline__ double block_sum(double x, double* red) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = x;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0) {
-#pragma unroll 1
-    for (int w = 0; w < THREADS / 32; ++w) s += red[w];
-  }
-  return s;
-}
-
-// Block-wide best (v, flat) over all threads; every thread gets the result.
-template <int THREADS>
-__device__ __forceinline__ void block_best_f(float& v, int& f, float* sv, int* sf) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    float ov = __shfl_xor_sync(0xffffffffu, v, off);
-    int of = __shfl_xor_sync(0xffffffffu, f, off);
-    if (better_f(ov, of, v, f)) { v = ov; f = of; }
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) { sv[warp] = v; sf[warp] = f; }
-  __syncthreads();
-  v = sv[0];
-  f = sf[0];
-#pragma unroll 1
-  for (int w = 1; w < THREADS / 32; ++w)
-    if (better_f(sv[w], sf[w], v, f)) { v = sv[w]; f = sf[w]; }
-}
-
-// Last-CTA detection: returns true in every thread of the CTA that is the
-// last of `target` CTAs to arrive on *counter, and resets the counter.
-__device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned target, int* s_flag) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned prev = atomicAdd(counter, 1u);
-    *s_flag = (prev == target - 1u);
-    if (*s_flag) *counter = 0u;
-  }
-  __syncthreads();
-  const bool last = *s_flag != 0;
-  if (last) __threadfence();
-  return last;
-}
-
-__device__ __forceinline__ int ld_done(const SlotCtl* c) { return *((volatile const int*)&c->done); }
 
 // ------------------------------------------------------------ grid kernel --
 
@@ -168,109 +40,6 @@ struct GridCfg {
   static constexpr int THREADS = S::TPF * FPC;
 };
 
-// FP32 selection in the last CTA of a signal: list the grid points whose
-// objective is within tau of the largest one, best first, at most cap.
-template <int THREADS>
-__device__ void select_candidates_f32(const SlotDev& sd, int k) {
-  __shared__ float sv[32];
-  __shared__ int sf[32];
-  const int M = sd.p.M, N = sd.p.N;
-  const Top2F* top = reinterpret_cast<const Top2F*>(sd.top2);
-  SlotCtl* ctl = sd.ctl;
-  if (sd.force_a1_zero && k == 0) {
-    if (threadIdx.x == 0) {
-      sd.cand[0] = make_int2(0, 0);
-      ctl->n_cand = 1;
-      sd.rec[k].obj32 = __ldcg(&top[0].v1);
-    }
-    return;
-  }
-  float last_v = __int_as_float(0x7f800000);  // +inf: nothing chosen yet
-  int last_f = -1;
-  float thr = 0.0f;
-  int n = 0;
-#pragma unroll 1
-  for (; n < sd.cap; ++n) {
-    float bv = -1.0f;
-    int bf = INT_MAX;
-    for (int e = threadIdx.x; e < 2 * M; e += THREADS) {
-      const int s = e >> 1;
-      const float v = (e & 1) ? __ldcg(&top[s].v2) : __ldcg(&top[s].v1);
-      const int j = (e & 1) ? __ldcg(&top[s].j2) : __ldcg(&top[s].j1);
-      if (j == INT_MAX) continue;
-      const int f = s * N + j;
-      // strictly worse than the last pick, better than the current best
-      if (better_f(last_v, last_f, v, f) && better_f(v, f, bv, bf)) { bv = v; bf = f; }
-    }
-    block_best_f<THREADS>(bv, bf, sv, sf);
-    if (n == 0) {
-      if (!(bv >= 0.0f) || bv == __int_as_float(0x7f800000)) break;  // nothing finite
-      thr = bv - bv * (float)sd.tau;
-      if (threadIdx.x == 0) sd.rec[k].obj32 = bv;
-    }
-    if (bf == INT_MAX || !(bv >= thr)) break;
-    if (threadIdx.x == 0) sd.cand[n] = make_int2(bf / N, bf % N);
-    last_v = bv;
-    last_f = bf;
-  }
-  if (threadIdx.x == 0) {
-    ctl->n_cand = n;
-    if (n == sd.cap) ctl->err |= 1;  // the cap, not the window, ended the list
-  }
-}
-
-// FP64 selection: global best of the per-radius maxima; writes the step record.
-template <int THREADS>
-__device__ void select_best_f64(const SlotDev& sd, int k, Best1D* red) {
-  const int M = sd.p.M, N = sd.p.N;
-  const Top2D* top = reinterpret_cast<const Top2D*>(sd.top2);
-  Best1D b;
-  b.init();
-  if (sd.force_a1_zero && k == 0) {
-    if (threadIdx.x == 0) {
-      b.v = __ldcg(&top[0].v1);
-      b.j = 0;  // radius 0: every angle ties, j1 == 0
-      b.f.x = __ldcg(&top[0].f1.x);
-      b.f.y = __ldcg(&top[0].f1.y);
-    }
-  } else {
-    for (int s = threadIdx.x; s < M; s += THREADS) {
-      const int j = __ldcg(&top[s].j1);
-      if (j == INT_MAX) continue;
-      double2 f;
-      f.x = __ldcg(&top[s].f1.x);
-      f.y = __ldcg(&top[s].f1.y);
-      b.insert(__ldcg(&top[s].v1), s * N + j, f);
-    }
-    group_reduce<THREADS>(b, red);
-  }
-  if (threadIdx.x == 0) {
-    StepRec& r = sd.rec[k];
-    if (b.j == INT_MAX || !(b.v >= 0.0) || b.v > 1.79e308) {
-      r.flags = 2;
-      sd.ctl->err |= 2;
-      sd.ctl->done = 1;
-      r.s = -1;
-      r.j = -1;
-      return;
-    }
-    const int s = b.j / N, j = b.j % N;
-    const double w = sd.p.w64[s];
-    const double rr = sd.p.radii[s];
-    const double2 z = sd.p.tw64[j];
-    r.s = s;
-    r.j = j;
-    r.n_cand = 0;
-    r.flags = 0;
-    r.a_re = rr * z.x;
-    r.a_im = rr * z.y;
-    r.c_re = w * b.f.x;
-    r.c_im = w * b.f.y;
-    r.obj = r.c_re * r.c_re + r.c_im * r.c_im;
-    r.obj32 = b.v;
-  }
-}
-
 template <typename T, int LOGN>
 __global__ void __launch_bounds__(GridCfg<T, LOGN>::THREADS)
 k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
@@ -279,8 +48,8 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
   constexpr int N = S::N, P = S::P, TPF = S::TPF, FPC = C::FPC, THREADS = C::THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_last;
+  pdl_launch_dependents();
   const SlotDev& sd = slots[ids[blockIdx.y]];
-  if (ld_done(sd.ctl)) return;
 
   const int g = threadIdx.x / TPF, t = threadIdx.x % TPF;
   const int s = blockIdx.x * FPC + g;
@@ -288,33 +57,48 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
   const bool active = s < M;
   V2<T>* buf = reinterpret_cast<V2<T>*>(smem_raw) + g * S::SMEM;
 
-  // Pass-0 input f(l) = r_s^l c_l / N, read straight from the spectrum.
+  // Pass-0 input f(l) = r_s^l c_l / N, read straight from the spectrum.  The
+  // thread's inputs are l = b + q B (q < R0) with B = N / R0, so
+  // r_s^l = lo[b] * hi[q] with one lo value per butterfly.
+  constexpr int R0 = S::radix(0), B = FftSchedule::pow_b(LOGN), NB0 = P / R0;
   V2<T> v[P];
   const V2<T>* tw;
-  if constexpr (sizeof(T) == 4) tw = sd.p.tw32; else tw = sd.p.tw64;
+  if constexpr (sizeof(T) == 4) tw = sd.p.st32; else tw = sd.p.st64;
   if (active) {
-    const int B = sd.p.B;
-    const int lb = 31 - __clz(B);
     const T* lo;
     const T* hi;
     const V2<T>* c;
     if constexpr (sizeof(T) == 4) {
       lo = sd.p.rlo32 + (size_t)s * B;
-      hi = sd.p.rhi32 + (size_t)s * (N >> lb);
+      hi = sd.p.rhi32 + (size_t)s * R0;
       c = sd.c32;
     } else {
       lo = sd.p.rlo64 + (size_t)s * B;
-      hi = sd.p.rhi64 + (size_t)s * (N >> lb);
+      hi = sd.p.rhi64 + (size_t)s * R0;
       c = sd.c64;
     }
+    // the power tables are constant: fetch them before waiting for the
+    // kernel that produced the spectrum
+    T h[R0], lb[NB0];
 #pragma unroll
-    for (int e = 0; e < P; ++e) {
-      const int l = fft_in_index<T, LOGN>(t, e);
-      const T rp = __ldg(&hi[l >> lb]) * __ldg(&lo[l & (B - 1)]);
-      const V2<T> x = __ldg(&c[l]);
-      v[e] = mk2<T>(x.x * rp, x.y * rp);
+    for (int q = 0; q < R0; ++q) h[q] = __ldg(&hi[q]);
+#pragma unroll
+    for (int i = 0; i < NB0; ++i) lb[i] = __ldg(&lo[t + i * TPF]);
+    pdl_wait();
+    if (ld_done(sd.ctl)) return;
+#pragma unroll
+    for (int i = 0; i < NB0; ++i) {
+      const int b = t + i * TPF;
+#pragma unroll
+      for (int q = 0; q < R0; ++q) {
+        const T rp = lb[i] * h[q];
+        const V2<T> x = c[b + q * B];
+        v[i * R0 + q] = mk2<T>(x.x * rp, x.y * rp);
+      }
     }
   } else {
+    pdl_wait();
+    if (ld_done(sd.ctl)) return;
 #pragma unroll
     for (int e = 0; e < P; ++e) v[e] = mk2<T>((T)0, (T)0);
   }
@@ -337,6 +121,8 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
       o.j1 = b.j1;
       o.j2 = b.j2;
       reinterpret_cast<Top2F*>(sd.top2)[s] = o;
+      // objectives are >= 0, so their bit patterns order like the values
+      if (o.v1 >= 0.0f && o.v1 <= 3.402823466e38f) atomicMax(&sd.ctl->vmax_bits, __float_as_uint(o.v1));
     }
     if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
     select_candidates_f32<THREADS>(sd, sd.ctl->k);
@@ -366,56 +152,64 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
 
 // ----------------------------------------------------------- guard kernel --
 
-// <G, e_a>~ partial sums over one chunk of samples for candidate a = r w^j:
-// sum_m G(z_m) / (1 - r w^{j-m}), the kernel written as
-// (1 - r cos + i r sin) / ((1 - r cos)^2 + (r sin)^2) to avoid cancellation.
+// Deterministic sum of `count` partials (double2) by one warp: lane q adds
+// partials q, q + 32, ... in order, then a fixed shuffle tree.  Lane 0 gets
+// the total.
+__device__ __forceinline__ double2 warp_sum_partials(const double2* part, int count) {
+  const int lane = threadIdx.x & 31;
+  double x = 0.0, y = 0.0;
+  for (int q = lane; q < count; q += 32) {
+    const double2 v = __ldcg(&part[q]);
+    x += v.x;
+    y += v.y;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, off);
+    y += __shfl_xor_sync(0xffffffffu, y, off);
+  }
+  return make_double2(x, y);
+}
+
+// FP64 re-evaluation of the FP32 path's candidates by the rectangle rule of
+// Eq. (formula1): for a = r_s w^j,
+//   <G, e_a>~ = sqrt(1 - r_s^2)/N sum_m G(z_m) K_s[(j - m) mod N],
+// K_s[d] = 1 / (1 - r_s w^d) from the plan.  CTA (c0, p) adds chunk p of the
+// candidates c0, c0 + GUARD_PAR, ...; the last CTA totals each candidate and
+// picks the largest |.|^2 (ties: lowest flat index s N + j).
 __global__ void __launch_bounds__(FP64_THREADS)
-k_guard(const SlotDev* __restrict__ slots, const int* __restrict__ ids, int cap) {
-  __shared__ double red[FP64_THREADS / 32];
+k_guard(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
+  __shared__ double red[2 * (FP64_THREADS / 32)];
+  __shared__ double s_re[MAX_CAP], s_im[MAX_CAP];
   __shared__ int s_last;
+  pdl_launch_dependents();
   const SlotDev& sd = slots[ids[blockIdx.y]];
   SlotCtl* ctl = sd.ctl;
+  pdl_wait();
   if (ld_done(ctl)) return;
   const int N = sd.p.N;
   const int Pg = chunks_of(N);
-  const int cidx = blockIdx.x / Pg, p = blockIdx.x % Pg;
+  const int c0 = blockIdx.x / Pg, p = blockIdx.x % Pg;
   const int n_cand = ctl->n_cand;
-  if (cidx < n_cand) {
-    const int2 cj = sd.cand[cidx];
-    const double r = sd.p.radii[cj.x];
-    const int j = cj.y;
-    const int m0 = p * (N / Pg), m1 = m0 + N / Pg;
+  const int m = p * FP64_CHUNK + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double2 g = make_double2(0.0, 0.0);
+  if (m < N && c0 < n_cand) g = sd.G[m];
+  for (int c = c0; c < n_cand; c += GUARD_PAR) {
+    const int2 cj = sd.cand[c];
     double ar = 0.0, ai = 0.0;
-    for (int m = m0 + threadIdx.x; m < m1; m += FP64_THREADS) {
-      const double2 w = __ldg(&sd.p.tw64[(j - m) & (N - 1)]);
-      const double u = fma(-r, w.x, 1.0);
-      const double vv = r * w.y;
-      const double inv = 1.0 / fma(u, u, vv * vv);
-      const double kr = u * inv, ki = vv * inv;
-      const double2 gm = sd.G[m];
-      ar = fma(gm.x, kr, fma(-gm.y, ki, ar));
-      ai = fma(gm.x, ki, fma(gm.y, kr, ai));
-    }
-    const double sr = block_sum<FP64_THREADS>(ar, red);
-    const double si = block_sum<FP64_THREADS>(ai, red);
-    if (threadIdx.x == 0) sd.gpart[cidx * Pg + p] = make_double2(sr, si);
+    if (m < N) guard_term(sd, cj.x, cj.y, m, g, ar, ai);
+    const double2 tot = sum_fp64_group(ar, ai, red);
+    if (threadIdx.x == 0) sd.gpart[c * Pg + p] = tot;
   }
   if (!arrive_last(&ctl->cnt_guard, gridDim.x, &s_last)) return;
-  // Candidate c's partial sums are added in chunk order by thread c.
-  __shared__ double s_re[MAX_CAP], s_im[MAX_CAP], s_v[MAX_CAP];
-  if (threadIdx.x < n_cand) {
-    const int c = threadIdx.x;
-    const int2 cj = sd.cand[c];
-    double sr = 0.0, si = 0.0;
-    for (int q = 0; q < Pg; ++q) {
-      const double2 pp = __ldcg(&sd.gpart[c * Pg + q]);
-      sr += pp.x;
-      si += pp.y;
+  for (int c = warp; c < n_cand; c += FP64_THREADS / 32) {
+    const double2 tot = warp_sum_partials(sd.gpart + c * Pg, Pg);
+    if (lane == 0) {
+      const double sc = sd.p.sq64[sd.cand[c].x] / (double)N;
+      s_re[c] = sc * tot.x;
+      s_im[c] = sc * tot.y;
     }
-    const double sc = sd.p.sq64[cj.x] / (double)N;
-    s_re[c] = sc * sr;
-    s_im[c] = sc * si;
-    s_v[c] = s_re[c] * s_re[c] + s_im[c] * s_im[c];
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -425,7 +219,7 @@ k_guard(const SlotDev* __restrict__ slots, const int* __restrict__ ids, int cap)
   double bv = -1.0, bre = 0.0, bim = 0.0;
   for (int c = 0; c < n_cand; ++c) {
     const int2 cj = sd.cand[c];
-    const double v = s_v[c];
+    const double v = s_re[c] * s_re[c] + s_im[c] * s_im[c];
     const int f = cj.x * N + cj.y, bf = bs * N + bj;
     if (bs < 0 || v > bv || (v == bv && f < bf)) {
       bs = cj.x; bj = cj.y; bv = v; bre = s_re[c]; bim = s_im[c];
@@ -434,7 +228,7 @@ k_guard(const SlotDev* __restrict__ slots, const int* __restrict__ ids, int cap)
   if (bs < 0 || !(bv <= 1.79e308)) {
     rec.s = -1;
     rec.j = -1;
-    rec.flags = 2;
+    rec.flags |= 2;
     ctl->err |= 2;
     ctl->done = 1;
     return;
@@ -444,7 +238,6 @@ k_guard(const SlotDev* __restrict__ slots, const int* __restrict__ ids, int cap)
   rec.s = bs;
   rec.j = bj;
   rec.n_cand = n_cand;
-  rec.flags = ctl->err & 1;
   rec.a_re = rr * z.x;
   rec.a_im = rr * z.y;
   rec.c_re = bre;
@@ -454,57 +247,53 @@ k_guard(const SlotDev* __restrict__ slots, const int* __restrict__ ids, int cap)
 
 // ---------------------------------------------------------- update kernel --
 
+// Reduced-remainder update of Sec. 2 at z_m, a = r_s w^j, c' = c sqrt(1-r_s^2):
+//   G_{k+1}(z_m) = (G_k(z_m) u - c') / (z_m - a),   u = 1 - conj(a) z_m = 1 - r_s w^d,
+// d = (m - j) mod N.  Because z_m - a = z_m conj(u), the division is
+// (...) conj(z_m) conj(K_s[d]) with the plan's K_s[d] = 1 / (1 - r_s w^d).
+// Also accumulates the energy and, on the FP32 path, writes G_{k+1}/N in FP32
+// for the next forward FFT.  INIT: energy (E_1) and FP32 copy of G_1 only.
 template <bool INIT>
 __global__ void __launch_bounds__(FP64_THREADS)
 k_update(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
-  __shared__ double red[FP64_THREADS / 32];
+  __shared__ double red[2 * (FP64_THREADS / 32)];
   __shared__ int s_last;
+  pdl_launch_dependents();
   const SlotDev& sd = slots[ids[blockIdx.y]];
   SlotCtl* ctl = sd.ctl;
+  pdl_wait();
   if (ld_done(ctl)) return;
   const int N = sd.p.N;
   const int Pu = chunks_of(N);
   const int p = blockIdx.x;
-  const int m0 = p * (N / Pu), m1 = m0 + N / Pu;
+  const int m = p * FP64_CHUNK + threadIdx.x;
   const int k = ctl->k;
   double e = 0.0;
-  if constexpr (INIT) {
-    for (int m = m0 + threadIdx.x; m < m1; m += FP64_THREADS) {
-      const double2 g = sd.G[m];
-      e = fma(g.x, g.x, fma(g.y, g.y, e));
+  if (m < N) {
+    double2 g = sd.G[m];
+    if constexpr (!INIT) {
+      const StepRec& rec = sd.rec[k];
+      const int s = rec.s;
+      const double na = sd.p.sq64[s];
+      g = update_point(sd, m, s, rec.j, sd.p.radii[s], rec.c_re * na, rec.c_im * na, g);
+      sd.G[m] = g;
     }
-  } else {
-    const StepRec& rec = sd.rec[k];
-    const double ar = rec.a_re, ai = rec.a_im;
-    const double na = sd.p.sq64[rec.s];  // sqrt(1 - |a|^2) with |a| = r_s
-    const double cr = rec.c_re * na, ci = rec.c_im * na;
-    for (int m = m0 + threadIdx.x; m < m1; m += FP64_THREADS) {
-      const double2 z = __ldg(&sd.p.tw64[m]);
-      const double2 g = sd.G[m];
-      // u = 1 - conj(a) z
-      const double ur = fma(-ar, z.x, fma(-ai, z.y, 1.0));
-      const double ui = fma(ai, z.x, -ar * z.y);
-      // numerator G u - c sqrt(1-|a|^2)
-      const double nr = fma(g.x, ur, fma(-g.y, ui, -cr));
-      const double ni = fma(g.x, ui, fma(g.y, ur, -ci));
-      // divide by d = z - a
-      const double dr = z.x - ar, di = z.y - ai;
-      const double inv = 1.0 / fma(dr, dr, di * di);
-      const double gr = fma(nr, dr, ni * di) * inv;
-      const double gi = fma(ni, dr, -nr * di) * inv;
-      sd.G[m] = make_double2(gr, gi);
-      e = fma(gr, gr, fma(gi, gi, e));
+    e = fma(g.x, g.x, g.y * g.y);
+    if (sd.prec) {
+      const double inv_n = 1.0 / (double)N;  // exact: N is a power of two
+      sd.g32[m] = make_float2((float)(g.x * inv_n), (float)(g.y * inv_n));
     }
   }
-  const double es = block_sum<FP64_THREADS>(e, red);
+  const double es = sum_fp64_group(e, 0.0, red).x;
   if (threadIdx.x == 0) sd.epart[p] = es;
   if (!arrive_last(&ctl->cnt_update, gridDim.x, &s_last)) return;
-  __shared__ double s_part[FP64_THREADS];
-  for (int q = threadIdx.x; q < Pu; q += FP64_THREADS) s_part[q] = __ldcg(&sd.epart[q]);
-  __syncthreads();
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x >= 32) return;
+  // energy partials: lane q adds q, q + 32, ... in order, then a fixed tree
   double E = 0.0;
-  for (int q = 0; q < Pu; ++q) E += s_part[q];
+  for (int q = threadIdx.x; q < Pu; q += 32) E += __ldcg(&sd.epart[q]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) E += __shfl_xor_sync(0xffffffffu, E, off);
+  if (threadIdx.x != 0) return;
   E /= (double)N;
   if constexpr (INIT) {
     ctl->E1 = E;
@@ -520,35 +309,337 @@ k_update(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
 
 // --------------------------------------------------------- forward kernel --
 
+// c_l / N = (1/N) sum_m G(z_m) w^{-ml} (Eq. (term4)); FP32 path from the FP32
+// copy the update wrote, FP64 path from G itself.
 template <typename T, int LOGN>
 __global__ void __launch_bounds__(FftShape<T, LOGN>::TPF)
 k_forward(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
   using S = FftShape<T, LOGN>;
   constexpr int P = S::P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_launch_dependents();
   const SlotDev& sd = slots[ids[blockIdx.x]];
+  pdl_wait();
   if (ld_done(sd.ctl)) return;
   const int t = threadIdx.x;
   V2<T>* buf = reinterpret_cast<V2<T>*>(smem_raw);
-  const double scale = 1.0 / (double)S::N;  // exact: N is a power of two
   V2<T> v[P];
-#pragma unroll
-  for (int e = 0; e < P; ++e) {
-    const double2 g = sd.G[fft_in_index<T, LOGN>(t, e)];
-    v[e] = mk2<T>((T)(g.x * scale), (T)(g.y * scale));
-  }
   const V2<T>* tw;
-  if constexpr (sizeof(T) == 4) tw = sd.p.tw32; else tw = sd.p.tw64;
-  fft_run<T, LOGN, -1>(v, t, buf, tw);
   V2<T>* c;
-  if constexpr (sizeof(T) == 4) c = sd.c32; else c = sd.c64;
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int e = 0; e < P; ++e) v[e] = sd.g32[fft_in_index<T, LOGN>(t, e)];
+    tw = sd.p.st32;
+    c = sd.c32;
+  } else {
+    const double inv_n = 1.0 / (double)S::N;
+#pragma unroll
+    for (int e = 0; e < P; ++e) {
+      const double2 g = sd.G[fft_in_index<T, LOGN>(t, e)];
+      v[e] = mk2<T>(g.x * inv_n, g.y * inv_n);
+    }
+    tw = sd.p.st64;
+    c = sd.c64;
+  }
+  fft_run<T, LOGN, -1>(v, t, buf, tw);
 #pragma unroll
   for (int e = 0; e < P; ++e) c[fft_out_index<T, LOGN>(t, e)] = v[e];
+}
+
+// -------------------------------------------------------- plan K table --
+
+// K[s N + d] = 1 / (1 - r_s w^d), w = exp(2 pi i / N), written as
+// (p + i q) / (p^2 + q^2) with p = 1 - r cos = (1 - r) + 2 r sin^2(pi d / N)
+// (no cancellation as r -> 1 and d -> 0) and q = r sin(2 pi d / N).
+__global__ void __launch_bounds__(256)
+k_kernel_table(const double* __restrict__ radii, int N, double2* __restrict__ K) {
+  const int d = blockIdx.x * 256 + threadIdx.x;
+  const int s = blockIdx.y;
+  if (d >= N) return;
+  const double r = radii[s];
+  double sn, cs;
+  sincospi(2.0 * (double)d / (double)N, &sn, &cs);
+  const double sh = sinpi((double)d / (double)N);
+  const double pr = (1.0 - r) + 2.0 * r * sh * sh;
+  const double qi = r * sn;
+  const double inv = 1.0 / fma(pr, pr, qi * qi);
+  K[(size_t)s * N + d] = make_double2(pr * inv, qi * inv);
+}
+
+// ------------------------------------------------------ persistent kernel --
+
+constexpr long kBarrierLimit = 1L << 25;  // polls (with a short sleep) before a barrier gives up
+
+// Grid-wide barrier of a cooperative launch (all CTAs are co-resident).
+// Bounded: a CTA that polls kBarrierLimit times flags a timeout (error bit 2)
+// and every CTA then leaves the kernel.  False in every thread when it must.
+__device__ __forceinline__ bool grid_barrier(SlotCtl* ctl, unsigned nblocks, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &ctl->bar_gen;
+    const unsigned g0 = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&ctl->bar_count, 1u) == nblocks - 1u) {
+      ctl->bar_count = 0u;
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      long it = 0;
+      while (*gen == g0) {
+        if (++it > kBarrierLimit) {
+          atomicOr(&ctl->err, 4);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (*((volatile int*)&ctl->err) & 4) ok = 0;
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// All K greedy steps of one FP32-path signal in one launch.  Per step:
+//   A  each CTA: forward FFT of G_k from its FP32 copy (the same arithmetic as
+//      k_forward), then its radii's inverse FFTs with the objective and best
+//      pairs (as k_grid) -- barrier --
+//   B  each CTA: the candidate list (the same in every CTA), then its share of
+//      the guard's partial sums -- barrier --
+//   C  each CTA: the winner from the partial sums (the same in every CTA), then
+//      its share of the remainder update and energy partials -- barrier --
+//   D  each CTA: the energy, delta and the stop rule (the same in every CTA).
+// Every reduction uses the work split and order of the separate kernels, so
+// results are bitwise those of the multi-kernel sequence.
+template <int LOGN>
+__global__ void __launch_bounds__(GridCfg<float, LOGN>::THREADS)
+k_persistent(const SlotDev* __restrict__ slots) {
+  using S = FftShape<float, LOGN>;
+  using C = GridCfg<float, LOGN>;
+  constexpr int N = S::N, P = S::P, TPF = S::TPF, FPC = C::FPC, THREADS = C::THREADS;
+  constexpr int R0 = S::radix(0), B = FftSchedule::pow_b(LOGN), NB0 = P / R0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Best2F red2[32];
+  __shared__ double red[2 * (FP64_THREADS / 32)];
+  __shared__ int2 s_cand[MAX_CAP];
+  __shared__ double s_re[MAX_CAP], s_im[MAX_CAP];
+  __shared__ int s_ok, s_ps, s_pj;
+  __shared__ double s_pre, s_pim, s_pv, s_E;
+
+  const SlotDev& sd = slots[0];
+  SlotCtl* ctl = sd.ctl;
+  const int M = sd.p.M;
+  const int n_tiles = (M + FPC - 1) / FPC;
+  const int Pc = chunks_of(N);
+  const unsigned nb = gridDim.x;
+  const bool cta0 = blockIdx.x == 0;
+  const int g = threadIdx.x / TPF, t = threadIdx.x % TPF;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* buf = reinterpret_cast<float2*>(smem_raw) + g * S::SMEM;
+  Top2F* top = reinterpret_cast<Top2F*>(sd.top2);
+
+  for (int k = 0; k < sd.K_max; ++k) {
+    // ---------------------------------------------------------------- A --
+    for (int tile = blockIdx.x; tile < n_tiles; tile += nb) {
+      const int s = tile * FPC + g;
+      const bool active = s < M;
+      float2 v[P];
+#pragma unroll
+      for (int e = 0; e < P; ++e) v[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
+      fft_run<float, LOGN, -1>(v, t, buf, sd.p.st32);
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < P; ++e) buf[smem_pad(fft_out_index<float, LOGN>(t, e))] = v[e];
+      __syncthreads();
+      if (active) {
+        const float* lo = sd.p.rlo32 + (size_t)s * B;
+        const float* hi = sd.p.rhi32 + (size_t)s * R0;
+        float h[R0];
+#pragma unroll
+        for (int q = 0; q < R0; ++q) h[q] = __ldg(&hi[q]);
+#pragma unroll
+        for (int i = 0; i < NB0; ++i) {
+          const int b = t + i * TPF;
+          const float lb = __ldg(&lo[b]);
+#pragma unroll
+          for (int q = 0; q < R0; ++q) {
+            const float rp = lb * h[q];
+            const float2 x = buf[smem_pad(b + q * B)];
+            v[i * R0 + q] = make_float2(x.x * rp, x.y * rp);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < P; ++e) v[e] = make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      fft_run<float, LOGN, +1>(v, t, buf, sd.p.st32);
+      Best2F b;
+      b.init();
+#pragma unroll
+      for (int e = 0; e < P; ++e) b.insert(v[e].x * v[e].x + v[e].y * v[e].y, fft_out_index<float, LOGN>(t, e));
+      group_reduce<TPF>(b, red2);
+      if (t == 0 && active) {
+        const float w2 = sd.p.wsq32[s];
+        Top2F o;
+        o.v1 = b.v1 * w2;
+        o.v2 = b.v2 * w2;
+        o.j1 = b.j1;
+        o.j2 = b.j2;
+        top[s] = o;
+        if (o.v1 >= 0.0f && o.v1 <= 3.402823466e38f) atomicMax(&ctl->vmax2[k & 1], __float_as_uint(o.v1));
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(ctl, nb, &s_ok)) return;
+
+    // ---------------------------------------------------------------- B --
+    const float vmax = __uint_as_float(__ldcg(&ctl->vmax2[k & 1]));
+    int n = 1, count = 1;
+    if (sd.force_a1_zero && k == 0) {
+      if (threadIdx.x == 0) s_cand[0] = make_int2(0, 0);
+      __syncthreads();
+    } else {
+      select_core<THREADS>(top, M, N, 1, vmax - vmax * (float)sd.tau, sd.cap, s_cand, &n, &count);
+    }
+    if (cta0 && threadIdx.x == 0) {
+      ctl->vmax2[(k + 1) & 1] = 0u;  // the next step's accumulator
+      StepRec& rec = sd.rec[k];
+      rec.obj32 = vmax;
+      rec.flags = count > sd.cap ? 1 : 0;
+      ctl->n_cand = n;
+      for (int c = 0; c < n; ++c) sd.cand[c] = s_cand[c];
+    }
+    for (int it = blockIdx.x; it < n * Pc; it += nb) {
+      const int c = it / Pc, p = it % Pc;
+      const int m = p * FP64_CHUNK + threadIdx.x;
+      double ar = 0.0, ai = 0.0;
+      if (threadIdx.x < FP64_THREADS && m < N) guard_term(sd, s_cand[c].x, s_cand[c].y, m, sd.G[m], ar, ai);
+      const double2 tot = sum_fp64_group(ar, ai, red);
+      if (threadIdx.x == 0) sd.gpart[c * Pc + p] = tot;
+    }
+    if (!grid_barrier(ctl, nb, &s_ok)) return;
+
+    // ---------------------------------------------------------------- C --
+    for (int c = warp; c < n; c += THREADS / 32) {
+      const double2 tot = warp_sum_partials(sd.gpart + c * Pc, Pc);
+      if (lane == 0) {
+        const double sc = sd.p.sq64[s_cand[c].x] / (double)N;
+        s_re[c] = sc * tot.x;
+        s_im[c] = sc * tot.y;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int bs = -1, bj = -1;
+      double bv = -1.0, bre = 0.0, bim = 0.0;
+      for (int c = 0; c < n; ++c) {
+        const int2 cj = s_cand[c];
+        const double v = s_re[c] * s_re[c] + s_im[c] * s_im[c];
+        const int f = cj.x * N + cj.y, bf = bs * N + bj;
+        if (bs < 0 || v > bv || (v == bv && f < bf)) {
+          bs = cj.x; bj = cj.y; bv = v; bre = s_re[c]; bim = s_im[c];
+        }
+      }
+      if (bs >= 0 && !(bv <= 1.79e308)) bs = -1;
+      s_ps = bs;
+      s_pj = bj;
+      s_pre = bre;
+      s_pim = bim;
+      s_pv = bv;
+    }
+    __syncthreads();
+    const int ps = s_ps, pj = s_pj;
+    if (ps < 0) {
+      if (cta0 && threadIdx.x == 0) {
+        StepRec& rec = sd.rec[k];
+        rec.s = -1;
+        rec.j = -1;
+        rec.flags |= 2;
+        ctl->err |= 2;
+        ctl->done = 1;
+      }
+      return;
+    }
+    if (cta0 && threadIdx.x == 0) {
+      StepRec& rec = sd.rec[k];
+      const double rr = sd.p.radii[ps];
+      const double2 z = sd.p.tw64[pj];
+      rec.s = ps;
+      rec.j = pj;
+      rec.n_cand = n;
+      rec.a_re = rr * z.x;
+      rec.a_im = rr * z.y;
+      rec.c_re = s_pre;
+      rec.c_im = s_pim;
+      rec.obj = s_pv;
+    }
+    {
+      const double na = sd.p.sq64[ps];
+      const double r = sd.p.radii[ps], cr = s_pre * na, ci = s_pim * na;
+      const double inv_n = 1.0 / (double)N;  // exact: N is a power of two
+      for (int p = blockIdx.x; p < Pc; p += nb) {
+        const int m = p * FP64_CHUNK + threadIdx.x;
+        double e = 0.0;
+        if (threadIdx.x < FP64_THREADS && m < N) {
+          const double2 gn = update_point(sd, m, ps, pj, r, cr, ci, sd.G[m]);
+          sd.G[m] = gn;
+          e = fma(gn.x, gn.x, gn.y * gn.y);
+          sd.g32[m] = make_float2((float)(gn.x * inv_n), (float)(gn.y * inv_n));
+        }
+        const double es = sum_fp64_group(e, 0.0, red).x;
+        if (threadIdx.x == 0) sd.epart[p] = es;
+      }
+    }
+    if (!grid_barrier(ctl, nb, &s_ok)) return;
+
+    // ---------------------------------------------------------------- D --
+    if (threadIdx.x < 32) {
+      double E = 0.0;
+      for (int q = threadIdx.x; q < Pc; q += 32) E += __ldcg(&sd.epart[q]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) E += __shfl_xor_sync(0xffffffffu, E, off);
+      if (threadIdx.x == 0) s_E = E / (double)N;
+    }
+    __syncthreads();
+    const double E = s_E;
+    const double E1 = __ldcg(&ctl->E1);
+    const double delta = E1 > 0.0 ? E / E1 : 0.0;
+    const bool stop = k + 1 >= sd.K_max || (sd.tol > 0.0 && delta <= sd.tol);
+    if (cta0 && threadIdx.x == 0) {
+      StepRec& rec = sd.rec[k];
+      rec.energy = E;
+      rec.delta = delta;
+      ctl->k = k + 1;
+      if (stop) ctl->done = 1;
+    }
+    if (stop) return;
+  }
 }
 
 // --------------------------------------------------------------- launchers --
 
 namespace {
+
+// Launch with programmatic stream serialisation (see pdl_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 template <typename T, int LOGN>
 size_t grid_smem() {
@@ -565,14 +656,13 @@ template <typename T, int LOGN>
 cudaError_t grid_launch(const SlotDev* slots, const int* ids, int n, int Mmax, cudaStream_t st) {
   using C = GridCfg<T, LOGN>;
   dim3 grid((Mmax + C::FPC - 1) / C::FPC, n);
-  k_grid<T, LOGN><<<grid, C::THREADS, grid_smem<T, LOGN>(), st>>>(slots, ids);
-  return cudaGetLastError();
+  return launch_pdl(k_grid<T, LOGN>, grid, dim3(C::THREADS), grid_smem<T, LOGN>(), st, slots, ids);
 }
 
 template <typename T, int LOGN>
 cudaError_t fwd_launch(const SlotDev* slots, const int* ids, int n, cudaStream_t st) {
-  k_forward<T, LOGN><<<n, FftShape<T, LOGN>::TPF, fwd_smem<T, LOGN>(), st>>>(slots, ids);
-  return cudaGetLastError();
+  return launch_pdl(k_forward<T, LOGN>, dim3(n), dim3(FftShape<T, LOGN>::TPF), fwd_smem<T, LOGN>(), st,
+                    slots, ids);
 }
 
 template <typename T, int LOGN>
@@ -580,6 +670,11 @@ cudaError_t set_attrs() {
   cudaError_t e = cudaFuncSetAttribute(k_grid<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)grid_smem<T, LOGN>());
   if (e != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 4) {
+    e = cudaFuncSetAttribute(k_persistent<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)grid_smem<T, LOGN>());
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(k_forward<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)fwd_smem<T, LOGN>());
 }
@@ -595,7 +690,8 @@ cudaError_t configure_kernels() {
   if ((e = set_attrs<double, L>()) != cudaSuccess) return e;
   AFD_FOR_EACH_LOGN(X)
 #undef X
-  return set_attrs<float, 14>();
+  if ((e = set_attrs<float, 14>()) != cudaSuccess) return e;
+  return fft2_configure();
 }
 
 size_t grid_smem_bytes(int logN, int prec) {
@@ -660,25 +756,72 @@ cudaError_t launch_forward(const SlotDev* slots, const int* ids, int n, int logN
   }
 }
 
+namespace {
+int g_persist_blocks[MAX_LOGN_RESIDENT + 1] = {};  // co-resident CTAs per logN (0: not yet known)
+
+template <int LOGN>
+cudaError_t persistent_launch(const SlotDev* slots, int M, cudaStream_t st) {
+  using C = GridCfg<float, LOGN>;
+  const size_t smem = grid_smem<float, LOGN>();
+  if (!g_persist_blocks[LOGN]) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<LOGN>, C::THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    g_persist_blocks[LOGN] = per_sm * sms;
+  }
+  const int n_tiles = (M + C::FPC - 1) / C::FPC;
+  int blocks = n_tiles > chunks_of(1 << LOGN) ? n_tiles : chunks_of(1 << LOGN);
+  if (blocks > g_persist_blocks[LOGN]) blocks = g_persist_blocks[LOGN];
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(C::THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_persistent<LOGN>, slots);
+}
+}  // namespace
+
+cudaError_t launch_persistent(const SlotDev* slots, int logN, int M, cudaStream_t st) {
+  switch (logN) {
+#define X(L) case L: return persistent_launch<L>(slots, M, st);
+    AFD_FOR_EACH_LOGN(X)
+#undef X
+    case 14: return persistent_launch<14>(slots, M, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_guard(const SlotDev* slots, const int* ids, int n, int logN, int cap, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  dim3 grid(cap * chunks_of(1 << logN), n);
-  k_guard<<<grid, FP64_THREADS, 0, st>>>(slots, ids, cap);
+  dim3 grid((cap < GUARD_PAR ? cap : GUARD_PAR) * chunks_of(1 << logN), n);
+  return launch_pdl(k_guard, grid, dim3(FP64_THREADS), 0, st, slots, ids);
+}
+
+cudaError_t launch_kernel_table(const double* radii, int M, int N, double2* K, cudaStream_t st) {
+  dim3 grid((N + 255) / 256, M);
+  k_kernel_table<<<grid, 256, 0, st>>>(radii, N, K);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(const SlotDev* slots, const int* ids, int n, int logN, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   dim3 grid(chunks_of(1 << logN), n);
-  k_update<false><<<grid, FP64_THREADS, 0, st>>>(slots, ids);
-  return cudaGetLastError();
+  return launch_pdl(k_update<false>, grid, dim3(FP64_THREADS), 0, st, slots, ids);
 }
 
 cudaError_t launch_init(const SlotDev* slots, const int* ids, int n, int logN, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   dim3 grid(chunks_of(1 << logN), n);
-  k_update<true><<<grid, FP64_THREADS, 0, st>>>(slots, ids);
-  return cudaGetLastError();
+  return launch_pdl(k_update<true>, grid, dim3(FP64_THREADS), 0, st, slots, ids);
 }
 
 }  // namespace afd

@@ -24,15 +24,22 @@
 #include <vector>
 
 #include "../../include/afd.h"
+#include "afd_fft.cuh"
+#include "afd_fft2.h"
+#include "afd_host.h"
 #include "afd_internal.h"
 
 using namespace afd;
 
 // ------------------------------------------------------------------ errors --
 
-namespace {
+namespace afd {
 
+namespace {
 thread_local std::string g_last_error;
+std::mutex g_cfg_mu;
+bool g_configured[64] = {};
+}  // namespace
 
 afd_status set_error(afd_status st, const char* fmt, ...) {
   char buf[512];
@@ -44,40 +51,15 @@ afd_status set_error(afd_status st, const char* fmt, ...) {
   return st;
 }
 
+void set_last_error_text(const char* text) { g_last_error = text ? text : ""; }
+void clear_last_error() { g_last_error.clear(); }
+const char* last_error_text() { return g_last_error.c_str(); }
+
 afd_status cuda_fail(cudaError_t e, const char* what, int line) {
   cudaGetLastError();  // clear a non-sticky error
   return set_error(e == cudaErrorMemoryAllocation ? AFD_ERR_NOMEM : AFD_ERR_CUDA,
                    "%s failed (line %d): %s", what, line, cudaGetErrorString(e));
 }
-
-#define CUDA_TRY(expr)                                           \
-  do {                                                           \
-    cudaError_t _e = (expr);                                     \
-    if (_e != cudaSuccess) return cuda_fail(_e, #expr, __LINE__); \
-  } while (0)
-
-#define AFD_TRY(expr)                   \
-  do {                                  \
-    afd_status _s = (expr);             \
-    if (_s != AFD_OK) return _s;        \
-  } while (0)
-
-// Makes `dev` current for the scope and restores the caller's device.
-struct DeviceScope {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceScope(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceScope() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-std::mutex g_cfg_mu;
-bool g_configured[64] = {};
 
 afd_status ensure_configured(int dev) {
   std::lock_guard<std::mutex> lk(g_cfg_mu);
@@ -96,8 +78,6 @@ int ilog2(int n) {
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
-size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
-
 afd_status check_opts(const afd_plan_opts& o) {
   if (o.precision != AFD_FP64_PLAIN && o.precision != AFD_FP32_GUARDED)
     return set_error(AFD_ERR_INVALID, "precision must be AFD_FP64_PLAIN or AFD_FP32_GUARDED");
@@ -108,9 +88,10 @@ afd_status check_opts(const afd_plan_opts& o) {
   return AFD_OK;
 }
 
-afd_status check_size(int N, int prec) {
+afd_status check_size(int N, int prec, bool allow_two_pass) {
   if (!is_pow2(N) || N < (1 << MIN_LOGN))
     return set_error(AFD_ERR_INVALID, "N = %d: must be a power of two >= 8", N);
+  if (allow_two_pass && prec == AFD_FP32_GUARDED && N == (1 << TWO_PASS_LOGN)) return AFD_OK;
   const int maxlog = prec == AFD_FP32_GUARDED ? MAX_LOGN_RESIDENT : MAX_LOGN_RESIDENT - 1;
   if (N > (1 << maxlog))
     return set_error(AFD_ERR_INVALID, "N = %d: largest supported size is %d for this precision", N,
@@ -130,41 +111,79 @@ afd_status check_radii(const double* radii, int M) {
   return AFD_OK;
 }
 
+afd_status normalise_opts(const afd_plan_opts* in, afd_plan_opts& o, int& dev) {
+  afd_plan_opts_default(&o);
+  if (in) o = *in;
+  AFD_TRY(check_opts(o));
+  dev = o.device;
+  if (dev < 0) CUDA_TRY(cudaGetDevice(&dev));
+  int count = 0;
+  CUDA_TRY(cudaGetDeviceCount(&count));
+  if (dev >= count) return set_error(AFD_ERR_INVALID, "device %d not present (%d devices)", dev, count);
+  return AFD_OK;
+}
+
 // ------------------------------------------------------------------ tables --
 
-// Device tables of one (N, radii) pair, generated on the host in FP64.
-struct Tables {
-  int N = 0, M = 0;
-  std::vector<double> radii;
-  void* mem = nullptr;
-  PlanDev dev{};
+Tables::~Tables() {
+  if (mem) cudaFree(mem);
+}
 
-  ~Tables() {
-    if (mem) cudaFree(mem);
-  }
+size_t Tables::bytes_for(int N, int M) {
+  const int logN = ilog2(N);
+  const bool two_pass = logN > MAX_LOGN_RESIDENT;
+  const int B = two_pass ? 256 : FftSchedule::pow_b(logN), H = N / B;
+  const size_t tws = (size_t)std::max(FftSchedule::tw_size(two_pass ? 8 : logN), 1);
+  size_t off = 0;
+  for (size_t b : {sizeof(double) * M, 16 * (size_t)N, 16 * tws, 8 * tws, 8 * (size_t)M * B, 8 * (size_t)M * H,
+                   4 * (size_t)M * B, 4 * (size_t)M * H, 4 * (size_t)M, 8 * (size_t)M, 8 * (size_t)M,
+                   16 * (size_t)M * N, two_pass ? 8 * (size_t)N : 0})
+    off = align_up(off + b);
+  return off;
+}
 
-  afd_status build(int N_, const double* r, int M_) {
+afd_status Tables::build(int N_, const double* r, int M_) {
     N = N_;
     M = M_;
     radii.assign(r, r + M);
-    const int B = std::min(RPOW_B_MAX, N), H = N / B;
-    std::vector<double> tw64(2 * (size_t)N), rlo64((size_t)M * B), rhi64((size_t)M * H);
-    std::vector<float> tw32(2 * (size_t)N), rlo32((size_t)M * B), rhi32((size_t)M * H), wsq32(M);
+    const int logN = ilog2(N);
+    const bool two_pass = logN > MAX_LOGN_RESIDENT;
+    // the two-pass path splits r^l at 256 and runs 256-point sub-transforms
+    const int B = two_pass ? 256 : FftSchedule::pow_b(logN), H = N / B;
+    const int slog = two_pass ? 8 : logN;  // log2 of the transforms the stage twiddles serve
+    const int TWS = FftSchedule::tw_size(slog);
+    std::vector<double> tw64(2 * (size_t)N), st64(2 * (size_t)std::max(TWS, 1)),
+        rlo64((size_t)M * B), rhi64((size_t)M * H);
+    std::vector<float> st32(2 * (size_t)std::max(TWS, 1)), rlo32((size_t)M * B), rhi32((size_t)M * H),
+        wsq32(M);
     std::vector<double> w64(M), sq64(M);
     const double two_pi = 6.283185307179586476925286766559;
     for (int k = 0; k < N; ++k) {
-      // exact values at the eighth-turn symmetry points, libm elsewhere
+      // exact values at the quarter turns, libm elsewhere
       const double t = two_pi * (double)k / (double)N;
-      double c = std::cos(t), s = std::sin(t);
-      if (4 * k % N == 0) {
-        const int q = 4 * k / N;
+      double c = std::cos(t), sn = std::sin(t);
+      if (4 * (long)k % N == 0) {
+        const int q = (int)(4 * (long)k / N);
         c = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
-        s = (q == 1) ? 1.0 : (q == 3 ? -1.0 : 0.0);
+        sn = (q == 1) ? 1.0 : (q == 3 ? -1.0 : 0.0);
       }
       tw64[2 * k] = c;
-      tw64[2 * k + 1] = s;
-      tw32[2 * k] = (float)c;
-      tw32[2 * k + 1] = (float)s;
+      tw64[2 * k + 1] = sn;
+    }
+    // FFT stage twiddles of 2^slog-point transforms: pass p, input q, class k
+    // -> exp(2 pi i q k / (ns R)) = w^(q k stride), w = exp(2 pi i / N)
+    for (int p = 1; p < FftSchedule::npass(slog); ++p) {
+      const int R = FftSchedule::radix(slog, p), NS = FftSchedule::ns(slog, p);
+      const int off = FftSchedule::tw_off(slog, p), stride = N / (NS * R);
+      for (int q = 1; q < R; ++q)
+        for (int k = 0; k < NS; ++k) {
+          const size_t e = (size_t)off + (size_t)(q - 1) * NS + k;
+          const size_t src = (size_t)q * k * stride;
+          st64[2 * e] = tw64[2 * src];
+          st64[2 * e + 1] = tw64[2 * src + 1];
+          st32[2 * e] = (float)tw64[2 * src];
+          st32[2 * e + 1] = (float)tw64[2 * src + 1];
+        }
     }
     for (int s = 0; s < M; ++s) {
       const double rr = radii[s];
@@ -178,19 +197,22 @@ struct Tables {
       w64[s] = sq64[s] / one_m_rN;
       wsq32[s] = (float)(one_m_r2 / (one_m_rN * one_m_rN));
     }
-    // one allocation, 256-byte aligned sub-arrays
+    // one allocation, 256-byte aligned sub-arrays (sizes as in Tables::bytes_for)
     size_t off = 0;
     auto place = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
     const size_t o_r = place(sizeof(double) * M), o_tw64 = place(16 * (size_t)N),
-                 o_tw32 = place(8 * (size_t)N), o_rlo64 = place(8 * rlo64.size()),
-                 o_rhi64 = place(8 * rhi64.size()), o_rlo32 = place(4 * rlo32.size()),
-                 o_rhi32 = place(4 * rhi32.size()), o_wsq = place(4 * (size_t)M),
-                 o_w64 = place(8 * (size_t)M), o_sq = place(8 * (size_t)M);
+                 o_st64 = place(8 * st64.size()), o_st32 = place(4 * st32.size()),
+                 o_rlo64 = place(8 * rlo64.size()), o_rhi64 = place(8 * rhi64.size()),
+                 o_rlo32 = place(4 * rlo32.size()), o_rhi32 = place(4 * rhi32.size()),
+                 o_wsq = place(4 * (size_t)M), o_w64 = place(8 * (size_t)M), o_sq = place(8 * (size_t)M),
+                 o_K = place(16 * (size_t)M * N), o_tw32n = place(two_pass ? 8 * (size_t)N : 0);
     CUDA_TRY(cudaMalloc(&mem, off));
+    bytes = off;
     char* b = static_cast<char*>(mem);
     CUDA_TRY(cudaMemcpy(b + o_r, radii.data(), 8 * (size_t)M, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b + o_tw64, tw64.data(), 16 * (size_t)N, cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(b + o_tw32, tw32.data(), 8 * (size_t)N, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_st64, st64.data(), 8 * st64.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_st32, st32.data(), 4 * st32.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b + o_rlo64, rlo64.data(), 8 * rlo64.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b + o_rhi64, rhi64.data(), 8 * rhi64.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b + o_rlo32, rlo32.data(), 4 * rlo32.size(), cudaMemcpyHostToDevice));
@@ -199,12 +221,13 @@ struct Tables {
     CUDA_TRY(cudaMemcpy(b + o_w64, w64.data(), 8 * (size_t)M, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b + o_sq, sq64.data(), 8 * (size_t)M, cudaMemcpyHostToDevice));
     dev.N = N;
-    dev.logN = ilog2(N);
+    dev.logN = logN;
     dev.M = M;
     dev.B = B;
     dev.radii = reinterpret_cast<const double*>(b + o_r);
     dev.tw64 = reinterpret_cast<const double2*>(b + o_tw64);
-    dev.tw32 = reinterpret_cast<const float2*>(b + o_tw32);
+    dev.st64 = reinterpret_cast<const double2*>(b + o_st64);
+    dev.st32 = reinterpret_cast<const float2*>(b + o_st32);
     dev.rlo64 = reinterpret_cast<const double*>(b + o_rlo64);
     dev.rhi64 = reinterpret_cast<const double*>(b + o_rhi64);
     dev.rlo32 = reinterpret_cast<const float*>(b + o_rlo32);
@@ -212,9 +235,22 @@ struct Tables {
     dev.wsq32 = reinterpret_cast<const float*>(b + o_wsq);
     dev.w64 = reinterpret_cast<const double*>(b + o_w64);
     dev.sq64 = reinterpret_cast<const double*>(b + o_sq);
+    dev.K64 = reinterpret_cast<const double2*>(b + o_K);
+    dev.tw32n = nullptr;
+    if (two_pass) {
+      std::vector<float> tw32n(2 * (size_t)N);
+      for (size_t i = 0; i < 2 * (size_t)N; ++i) tw32n[i] = (float)tw64[i];
+      CUDA_TRY(cudaMemcpy(b + o_tw32n, tw32n.data(), 8 * (size_t)N, cudaMemcpyHostToDevice));
+      dev.tw32n = reinterpret_cast<const float2*>(b + o_tw32n);
+    }
+    CUDA_TRY(launch_kernel_table(dev.radii, M, N, reinterpret_cast<double2*>(b + o_K), nullptr));
+    CUDA_TRY(cudaDeviceSynchronize());
     return AFD_OK;
-  }
-};
+}
+
+}  // namespace afd
+
+namespace {
 
 // ------------------------------------------------------------- slot pools --
 
@@ -235,6 +271,7 @@ struct SlotPool {
   SlotCtl* ctl_host = nullptr;
   struct Group { int logN, first, count, Mmax; };
   std::vector<Group> groups;
+  std::vector<Fft2Maps> maps;       // TMA descriptors of two-pass slots (N = 65536)
 
   ~SlotPool() { release(); }
   void release() {
@@ -276,11 +313,15 @@ struct SlotPool {
     size_t off = 0;
     auto place = [&](size_t bytes) { size_t o2 = off; off = align_up(off + bytes); return o2; };
     const size_t o_G = place(8 * g_total);
-    std::vector<size_t> o_c(n), o_top(n), o_cand(n), o_gp(n), o_ep(n);
+    std::vector<size_t> o_c(n), o_g32(n), o_top(n), o_cand(n), o_gp(n), o_ep(n), o_X(n);
     for (int i = 0; i < n; ++i) {
       const int N = tables[i]->N, M = tables[i]->M;
+      const bool two_pass = ilog2(N) == TWO_PASS_LOGN;
       o_c[i] = place((prec ? 8 : 16) * (size_t)N);
-      o_top[i] = place((prec ? sizeof(Top2F) : sizeof(Top2D)) * (size_t)M);
+      o_g32[i] = place(prec ? 8 * (size_t)N : 0);
+      o_X[i] = place(two_pass ? 8 * (size_t)M * N : 0);
+      // two-pass: one best pair per (radius, 16-row block of pass 2)
+      o_top[i] = place((prec ? sizeof(Top2F) : sizeof(Top2D)) * (size_t)M * (two_pass ? 16 : 1));
       o_cand[i] = place(sizeof(int2) * cap);
       o_gp[i] = place(sizeof(double2) * cap * (size_t)chunks_of(N));
       o_ep[i] = place(sizeof(double) * (size_t)chunks_of(N));
@@ -311,6 +352,8 @@ struct SlotPool {
       d.tau = o.guard_tau;
       d.G = reinterpret_cast<double2*>(b + o_G) + g_off[i] / 2;
       d.c32 = prec ? reinterpret_cast<float2*>(b + o_c[i]) : nullptr;
+      d.g32 = prec ? reinterpret_cast<float2*>(b + o_g32[i]) : nullptr;
+      d.X = ilog2(tables[i]->N) == TWO_PASS_LOGN ? reinterpret_cast<float2*>(b + o_X[i]) : nullptr;
       d.c64 = prec ? nullptr : reinterpret_cast<double2*>(b + o_c[i]);
       d.top2 = b + o_top[i];
       d.cand = reinterpret_cast<int2*>(b + o_cand[i]);
@@ -320,6 +363,12 @@ struct SlotPool {
       d.ctl = ctl_dev + i;
     }
     CUDA_TRY(cudaMemcpy(ids_dev, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    maps.assign(n, Fft2Maps{});
+    for (int i = 0; i < n; ++i) {
+      if (!host[i].X) continue;
+      const int r = fft2_make_maps(&maps[i], host[i].c32, host[i].g32, host[i].X, tables[i]->M);
+      if (r) return set_error(AFD_ERR_CUDA, "tensor map encoding failed (driver status %d)", r);
+    }
     return upload(0.0, nullptr);
   }
 
@@ -334,70 +383,97 @@ struct SlotPool {
   }
 };
 
-// Kernel launch bookkeeping.
+// Kernel launch bookkeeping.  Kernel kinds: 0 grid, 1 guard, 2 update,
+// 3 forward (4 = initialisation, not timed).
+constexpr int KINDS = 4;
 struct Counters {
-  long long launches = 0, grid_launches = 0;
-  double grid_ms = 0.0;
+  long long launches = 0;
+  long long n[KINDS] = {};
+  double ms[KINDS] = {};
 };
 
-// Optional CUDA-event timing of the grid kernel.
-struct GridTimer {
+// Optional CUDA-event timing of every kernel of the step sequence.  Events are
+// recorded between consecutive kernels on their stream; under stream capture
+// they become event-record nodes of the graph, so a replayed graph is timed
+// as it runs.
+struct StepTimer {
   bool on = false;
   std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;  // kind of the kernel that ends at event i; -1 opens a sequence
   size_t used = 0;
-  ~GridTimer() {
+  ~StepTimer() {
     for (auto e : ev) cudaEventDestroy(e);
   }
-  afd_status pair(cudaEvent_t* a, cudaEvent_t* b) {
-    while (ev.size() < used + 2) {
+  afd_status mark(cudaStream_t st, int k) {
+    if (!on) return AFD_OK;
+    if (ev.size() <= used) {
       cudaEvent_t e;
       CUDA_TRY(cudaEventCreate(&e));
       ev.push_back(e);
+      kind.push_back(k);
     }
-    *a = ev[used];
-    *b = ev[used + 1];
-    used += 2;
+    kind[used] = k;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusActive) {
+      CUDA_TRY(cudaEventRecordWithFlags(ev[used], st, cudaEventRecordExternal));
+    } else {
+      CUDA_TRY(cudaEventRecord(ev[used], st));
+    }
+    ++used;
     return AFD_OK;
   }
-  afd_status collect(Counters& c) {
-    for (size_t i = 0; i + 1 < used; i += 2) {
+  // Events of the last run (or of the captured graph) after the stream has
+  // been synchronised.
+  afd_status collect(Counters& c, size_t count) {
+    for (size_t i = 1; i < count; ++i) {
+      if (kind[i] < 0 || kind[i] >= KINDS) continue;
       float ms = 0.f;
-      CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
-      c.grid_ms += ms;
+      CUDA_TRY(cudaEventElapsedTime(&ms, ev[i - 1], ev[i]));
+      c.ms[kind[i]] += ms;
     }
-    used = 0;
     return AFD_OK;
   }
 };
 
 // Enqueue the initialisation and K greedy steps of one group on stream st.
 afd_status enqueue_group(const SlotPool& pool, const SlotPool::Group& g, int K, cudaStream_t st,
-                         Counters& cnt, GridTimer* timer) {
+                         Counters& cnt, StepTimer* timer) {
   const SlotDev* slots = pool.slots_dev;
   const int* ids = pool.ids_dev + g.first;
   const int prec = pool.prec;
+  const bool t = timer && timer->on;
+  // the two-pass path (N = 65536) serves single-signal plans: slot 0
+  const bool two_pass = g.logN == TWO_PASS_LOGN;
+  if (two_pass && (g.count != 1 || pool.n != 1)) return set_error(AFD_ERR_INVALID, "N = 65536 needs its own plan");
+  const int per = two_pass ? 2 : 1;  // launches per transform stage
   CUDA_TRY(launch_init(slots, ids, g.count, g.logN, st));
-  CUDA_TRY(launch_forward(slots, ids, g.count, g.logN, prec, st));
-  cnt.launches += 2;
+  if (two_pass) CUDA_TRY(launch_forward2(slots, pool.maps[0], st));
+  else CUDA_TRY(launch_forward(slots, ids, g.count, g.logN, prec, st));
+  cnt.launches += 1 + per;
+  if (t) AFD_TRY(timer->mark(st, -1));
   for (int k = 0; k < K; ++k) {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (timer && timer->on) {
-      AFD_TRY(timer->pair(&e0, &e1));
-      CUDA_TRY(cudaEventRecord(e0, st));
-    }
-    CUDA_TRY(launch_grid(slots, ids, g.count, g.logN, prec, g.Mmax, st));
-    if (timer && timer->on) CUDA_TRY(cudaEventRecord(e1, st));
-    cnt.grid_launches += 1;
-    cnt.launches += 1;
+    if (two_pass) CUDA_TRY(launch_grid2(slots, pool.maps[0], g.Mmax, st));
+    else CUDA_TRY(launch_grid(slots, ids, g.count, g.logN, prec, g.Mmax, st));
+    if (t) AFD_TRY(timer->mark(st, 0));
+    cnt.n[0] += per;
+    cnt.launches += per;
     if (prec == AFD_FP32_GUARDED) {
       CUDA_TRY(launch_guard(slots, ids, g.count, g.logN, pool.cap, st));
+      if (t) AFD_TRY(timer->mark(st, 1));
+      cnt.n[1] += 1;
       cnt.launches += 1;
     }
     CUDA_TRY(launch_update(slots, ids, g.count, g.logN, st));
+    if (t) AFD_TRY(timer->mark(st, 2));
+    cnt.n[2] += 1;
     cnt.launches += 1;
     if (k + 1 < K) {
-      CUDA_TRY(launch_forward(slots, ids, g.count, g.logN, prec, st));
-      cnt.launches += 1;
+      if (two_pass) CUDA_TRY(launch_forward2(slots, pool.maps[0], st));
+      else CUDA_TRY(launch_forward(slots, ids, g.count, g.logN, prec, st));
+      if (t) AFD_TRY(timer->mark(st, 3));
+      cnt.n[3] += per;
+      cnt.launches += per;
     }
   }
   return AFD_OK;
@@ -414,7 +490,9 @@ struct Runner {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   int graph_K = -1;
-  long long graph_launches = 0, graph_grid_launches = 0;
+  bool graph_timed = false;
+  size_t graph_events = 0;
+  Counters graph_cnt;  // launches of one replay
 
   ~Runner() { destroy(); }
   void destroy() {
@@ -455,8 +533,9 @@ struct Runner {
     return AFD_OK;
   }
 
-  afd_status enqueue(const SlotPool& pool, int K, Counters& cnt, GridTimer* timer) {
+  afd_status enqueue(const SlotPool& pool, int K, Counters& cnt, StepTimer* timer) {
     AFD_TRY(prepare(pool.groups.size()));
+    if (timer) timer->used = 0;
     CUDA_TRY(cudaMemsetAsync(pool.ctl_dev, 0, sizeof(SlotCtl) * pool.n, main));
     if (pool.groups.size() > 1) CUDA_TRY(cudaEventRecord(fork, main));
     for (size_t gi = 0; gi < pool.groups.size(); ++gi) {
@@ -471,17 +550,27 @@ struct Runner {
     return AFD_OK;
   }
 
-  // Either replays a cached graph of the K-step sequence or launches directly.
-  afd_status run(const SlotPool& pool, int K, bool use_graph, Counters& cnt, GridTimer* timer) {
-    if (!use_graph || (timer && timer->on)) return enqueue(pool, K, cnt, timer);
-    if (graph_K != K) {
+  // Either replays a cached graph of the K-step sequence or launches directly;
+  // with the timer on, per-kernel device times of this run are added to cnt.
+  afd_status run(const SlotPool& pool, int K, bool use_graph, Counters& cnt, StepTimer* timer) {
+    const bool timed = timer && timer->on;
+    if (!use_graph) {
+      AFD_TRY(enqueue(pool, K, cnt, timer));
+      if (timed) {
+        CUDA_TRY(cudaStreamSynchronize(main));
+        AFD_TRY(timer->collect(cnt, timer->used));
+      }
+      return AFD_OK;
+    }
+    if (graph_K != K || graph_timed != timed) {
       if (exec) cudaGraphExecDestroy(exec);
       if (graph) cudaGraphDestroy(graph);
       exec = nullptr;
       graph = nullptr;
+      graph_K = -1;
       Counters c2;
       CUDA_TRY(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal));
-      afd_status st = enqueue(pool, K, c2, nullptr);
+      afd_status st = enqueue(pool, K, c2, timer);
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamEndCapture(main, &g);
       if (st != AFD_OK) {
@@ -492,31 +581,22 @@ struct Runner {
       graph = g;
       CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
       graph_K = K;
-      graph_launches = c2.launches;
-      graph_grid_launches = c2.grid_launches;
+      graph_timed = timed;
+      graph_events = timed ? timer->used : 0;
+      graph_cnt = c2;
     }
     CUDA_TRY(cudaGraphLaunch(exec, main));
-    cnt.launches += graph_launches;
-    cnt.grid_launches += graph_grid_launches;
+    cnt.launches += graph_cnt.launches;
+    for (int i = 0; i < KINDS; ++i) cnt.n[i] += graph_cnt.n[i];
+    if (timed) {
+      CUDA_TRY(cudaStreamSynchronize(main));
+      AFD_TRY(timer->collect(cnt, graph_events));
+    }
     return AFD_OK;
   }
 };
 
-afd_status normalise_opts(const afd_plan_opts* in, afd_plan_opts& o, int& dev) {
-  afd_plan_opts_default(&o);
-  if (in) o = *in;
-  AFD_TRY(check_opts(o));
-  dev = o.device;
-  if (dev < 0) CUDA_TRY(cudaGetDevice(&dev));
-  int count = 0;
-  CUDA_TRY(cudaGetDeviceCount(&count));
-  if (dev >= count) return set_error(AFD_ERR_INVALID, "device %d not present (%d devices)", dev, count);
-  return AFD_OK;
-}
-
 }  // namespace
-
-void afd::set_last_error_text(const char* text) { g_last_error = text ? text : ""; }
 
 // ------------------------------------------------------------------- plans --
 
@@ -528,7 +608,7 @@ struct afd_plan {
   SlotPool pool;
   Runner runner;
   Counters cnt;
-  GridTimer timer;
+  StepTimer timer;
   int last_steps = 0;
   ~afd_plan() {
     runner.destroy();
@@ -630,18 +710,18 @@ const char* afd_status_str(afd_status s) {
   return "AFD_UNKNOWN_STATUS";
 }
 
-const char* afd_last_error(void) { return g_last_error.c_str(); }
+const char* afd_last_error(void) { return last_error_text(); }
 
 const char* afd_version(void) { return "0.1.0"; }
 
 afd_status afd_plan_create(afd_plan** out, int N, const double* radii, int M, const afd_plan_opts* opts) {
-  g_last_error.clear();
+  clear_last_error();
   if (!out) return set_error(AFD_ERR_INVALID, "out is NULL");
   *out = nullptr;
   afd_plan_opts o;
   int dev = 0;
   AFD_TRY(normalise_opts(opts, o, dev));
-  AFD_TRY(check_size(N, o.precision));
+  AFD_TRY(check_size(N, o.precision, true));
   AFD_TRY(check_radii(radii, M));
   if (o.force_a1_zero && radii[0] != 0.0)
     return set_error(AFD_ERR_INVALID, "force_a1_zero needs radii[0] == 0");
@@ -673,7 +753,7 @@ afd_status afd_plan_destroy(afd_plan* plan) {
 
 afd_status afd_decompose(afd_plan* plan, const double* G, int K_max, double energy_tol, double* a_out,
                          double* coeff_out, double* delta_out, int* idx_out, int* steps_done) {
-  g_last_error.clear();
+  clear_last_error();
   if (!plan || !G) return set_error(AFD_ERR_INVALID, "plan or G is NULL");
   if (K_max < 1 || K_max > (1 << 20)) return set_error(AFD_ERR_INVALID, "K_max = %d out of range", K_max);
   if (!(energy_tol >= 0.0)) return set_error(AFD_ERR_INVALID, "energy_tol must be >= 0");
@@ -692,7 +772,6 @@ afd_status afd_decompose(afd_plan* plan, const double* G, int K_max, double ener
   CUDA_TRY(cudaMemcpyAsync(pool.G_dev, G, 16 * (size_t)plan->tables.N, cudaMemcpyDefault, st));
   AFD_TRY(plan->runner.run(pool, K_max, plan->opts.use_graph != 0, plan->cnt, &plan->timer));
   AFD_TRY(fetch_results(pool, st));
-  if (plan->timer.on) AFD_TRY(plan->timer.collect(plan->cnt));
   const int steps = pool.ctl_host[0].k;
   plan->last_steps = steps;
   AFD_TRY(write_outputs(pool, 0, K_max, steps, a_out, coeff_out, delta_out, idx_out));
@@ -722,8 +801,17 @@ afd_status afd_plan_counters(const afd_plan* plan, long long* kernel_launches, l
                              double* grid_ms) {
   if (!plan) return set_error(AFD_ERR_INVALID, "plan is NULL");
   if (kernel_launches) *kernel_launches = plan->cnt.launches;
-  if (grid_launches) *grid_launches = plan->cnt.grid_launches;
-  if (grid_ms) *grid_ms = plan->cnt.grid_ms;
+  if (grid_launches) *grid_launches = plan->cnt.n[0];
+  if (grid_ms) *grid_ms = plan->cnt.ms[0];
+  return AFD_OK;
+}
+
+afd_status afd_plan_kernel_times(const afd_plan* plan, double* ms, long long* launches) {
+  if (!plan) return set_error(AFD_ERR_INVALID, "plan is NULL");
+  for (int i = 0; i < KINDS; ++i) {
+    if (ms) ms[i] = plan->cnt.ms[i];
+    if (launches) launches[i] = plan->cnt.n[i];
+  }
   return AFD_OK;
 }
 
@@ -743,7 +831,7 @@ afd_status afd_plan_reset_counters(afd_plan* plan) {
 
 afd_status afd_batch_create(afd_batch** out, int n_signals, const int* N, const double* radii, int M,
                             int K_max, const afd_plan_opts* opts) {
-  g_last_error.clear();
+  clear_last_error();
   if (!out) return set_error(AFD_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (n_signals < 1 || !N) return set_error(AFD_ERR_INVALID, "need n_signals >= 1 and N");
@@ -787,7 +875,7 @@ afd_status afd_batch_create(afd_batch** out, int n_signals, const int* N, const 
 
 afd_status afd_batch_run(afd_batch* b, const double* G_packed, double energy_tol, double* a_out,
                          double* coeff_out, double* delta_out, int* idx_out, int* steps_out) {
-  g_last_error.clear();
+  clear_last_error();
   if (!b || !G_packed) return set_error(AFD_ERR_INVALID, "batch or G_packed is NULL");
   if (!(energy_tol >= 0.0)) return set_error(AFD_ERR_INVALID, "energy_tol must be >= 0");
   DeviceScope scope(b->device);

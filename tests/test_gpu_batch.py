@@ -1,0 +1,100 @@
+"""Batched decompositions of uneven N through the C ABI (afd_batch_*)."""
+import numpy as np
+import pytest
+
+from paper_1711_08604_gb300 import workloads as W
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+afd = pytest.importorskip("paper_1711_08604_gb300")
+PRECS = [afd.AFD_FP64_PLAIN, afd.AFD_FP32_GUARDED]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    afd._native.load()
+
+
+def small_batch(n=12, Ns=(256, 512, 1024, 2048, 4096, 8192), seed=0):
+    sigs = []
+    for i in range(n):
+        N = Ns[i % len(Ns)]
+        sigs.append(W.random_signal(N, 500 + seed + i) if i % 3 == 0
+                    else W.szego_sum(N, 0.9 * np.exp(2j * np.pi * np.array([0.1 * i, 0.37 + 0.05 * i])),
+                                     np.array([1.0, 0.5j])))
+    return sigs
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_equals_single_signal_runs(prec):
+    sigs = small_batch()
+    radii = W.radii_linear(30)
+    K = 8
+    res = afd.afd_decompose_batch(sigs, radii, K, precision=prec)
+    for i, G in enumerate(sigs):
+        plan = afd.afd_plan_create(G.size, radii, precision=prec)
+        one = afd.afd_decompose(plan, G, K)
+        plan.close()
+        assert res["steps"][i] == one["steps"]
+        for key in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(res[key][i], one[key]), (i, key)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_parity_with_oracle(prec):
+    sigs = small_batch(n=6, Ns=(64, 256, 1024), seed=9)
+    radii = W.radii_linear(20)
+    res = afd.afd_decompose_batch(sigs, radii, 6, precision=prec)
+    for i, G in enumerate(sigs):
+        r = {k: res[k][i] for k in ("a", "coeff", "delta", "idx")}
+        r["steps"] = int(res["steps"][i])
+        parity.check(G, radii, r, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_per_signal_energy_stop(prec):
+    sigs = small_batch(n=6, Ns=(512, 1024), seed=3)
+    radii = W.radii_linear(25)
+    full = afd.afd_decompose_batch(sigs, radii, 10, precision=prec)
+    tol = float(np.median([d[4] for d in full["delta"]]))
+    res = afd.afd_decompose_batch(sigs, radii, 10, energy_tol=tol, precision=prec)
+    for i in range(len(sigs)):
+        d = full["delta"][i][1:]
+        first = int(np.argmax(d <= tol)) + 1 if np.any(d <= tol) else 10
+        assert res["steps"][i] == first
+        assert np.array_equal(res["coeff"][i], full["coeff"][i][:first])
+
+
+def test_batch_reuse_and_counters():
+    sigs = small_batch(n=5, Ns=(1024, 2048))
+    radii = W.radii_linear(16)
+    b = afd.afd_batch_create([g.size for g in sigs], radii, 5)
+    packed = np.concatenate(sigs)
+    r1 = afd.afd_batch_run(b, packed)
+    r2 = afd.afd_batch_run(b, packed)
+    assert afd.afd_batch_counters(b)["kernel_launches"] > 0
+    b.close()
+    for i in range(len(sigs)):
+        assert np.array_equal(r1["coeff"][i], r2["coeff"][i])
+
+
+def test_workload3_full_batch_sampled_parity():
+    # 1024 signals, N in {1024..8192}, M = 100, K = 30, FP32 grid + FP64 guard
+    sigs = W.batch()
+    G = [s.G for s in sigs]
+    radii = sigs[0].radii
+    res = afd.afd_decompose_batch(G, radii, 30)
+    assert np.all(res["steps"] == 30)
+    by_n = {}
+    for i, s in enumerate(sigs):
+        by_n.setdefault(s.N, i)
+    for N, i in sorted(by_n.items()):
+        r = {k: res[k][i] for k in ("a", "coeff", "delta", "idx")}
+        r["steps"] = 30
+        # every step through the forced oracle; full-grid selection at step 1
+        # for the two smallest sizes (the oracle grid is O(M N^2))
+        parity.check(sigs[i].G, radii, r, 1, full_grid=False, grid_steps=(1,) if N <= 2048 else ())

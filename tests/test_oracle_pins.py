@@ -74,6 +74,21 @@ def test_inner_matches_discrete_szego_closed_form(N):
     assert abs(oracle.energy(G) - want) <= 1e-12 * want
 
 
+def test_inner_many_matches_closed_form_and_grid():
+    N = 64
+    rng = np.random.default_rng(8)
+    b = 0.8 * np.exp(0.7j)
+    G = W.szego_sum(N, np.array([b]), np.array([1.0]))
+    pts = 0.95 * np.sqrt(rng.random(9)) * np.exp(2j * np.pi * rng.random(9))
+    got = oracle.inner_many(G, pts)
+    want = np.array([_discrete_szego_inner(a, b, N) for a in pts])
+    assert np.max(np.abs(got - want)) <= 1e-12
+    radii = np.array([0.3, 0.7])
+    A = oracle.grid(G, radii)
+    on_grid = np.array([r * np.exp(2j * np.pi * j / N) for r in radii for j in range(N)])
+    assert np.max(np.abs(oracle.inner_many(G, on_grid) - A.reshape(-1))) <= 1e-13
+
+
 def test_inner_at_zero_is_mean():
     G = W.random_signal(128, 3)
     assert abs(oracle.inner(G, 0.0) - G.mean()) <= 1e-15 * 128
