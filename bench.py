@@ -129,6 +129,22 @@ class ClockSampler:
                 "reasons": reasons}
 
 
+def aggregate(local_ms: float, local_units: float, world_size: int):
+    """Whole-job time and units over the ranks of an independent-replica run:
+    the slowest rank's time (MAX) and the units of all ranks (SUM).  With one
+    rank, the local figures."""
+    if world_size <= 1:
+        return local_ms, local_units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([local_units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def cpu_baseline(s, sample_steps: int = 2) -> dict:
     """The FP64 oracle, as it stands, on the host cores: the first sample_steps
     greedy steps of the same workload (full M x N grid each)."""
@@ -140,6 +156,117 @@ def cpu_baseline(s, sample_steps: int = 2) -> dict:
     return {"value": evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"first {d['steps']} of {s.K} greedy steps of the same workload "
                       f"(direct O(M N^2) grid, {evals} grid evals, {dt:.2f} s)"}
+
+
+def bench_batch(afd, torch, dev, reps: int = 3) -> dict:
+    """Workload 3: 1024 signals of uneven N in {1024..8192}, M = 100, K = 30, one
+    batch (per-N launches on parallel streams, replayed as one CUDA graph)."""
+    from paper_1711_08604_gb300 import workloads as W
+    sigs = W.batch()
+    N = [x.N for x in sigs]
+    packed = torch.from_numpy(np.concatenate([x.G for x in sigs])).to(dev)
+    b = afd.afd_batch_create(N, sigs[0].radii, 30)
+    afd.afd_batch_run(b, packed)  # warm-up (graph capture)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        r = afd.afd_batch_run(b, packed)
+        times.append(time.perf_counter() - t0)
+    b.close()
+    evals = sum(int(x.M) * x.N * int(st) for x, st in zip(sigs, r["steps"]))
+    t = min(times)
+    return {"workload": "batch: 1024 signals, N in {1024,2048,4096,8192}, M=100, K=30, FP32+FP64 guard",
+            "grid_evals_per_s": evals / t, "signals_per_s": len(sigs) / t, "s_per_batch": t,
+            "timing": "host wall clock around afd_batch_run (device-resident input), best of %d" % reps}
+
+
+def bench_serve(afd, duration: float = 3.0, fp64_sample: int = 40) -> dict:
+    """Workload 4: Poisson arrivals at 2000 req/s; N in {512..16384}, M = 128,
+    stop at delta <= 1e-4 or K = 64; 40 GB admission budget.  Latency is
+    submission to completion.  The same requests with N <= 8192 (a sample) are
+    also run one by one through FP64-plain plans for the signals/s comparison."""
+    import threading
+    from paper_1711_08604_gb300 import workloads as W
+    reqs = W.serving_requests(duration=duration)
+    srv = afd.afd_serve_create(40 << 30)
+    # warm the plan cache so table building is not inside the measurement
+    warm = {}
+    for _, x in reqs:
+        warm.setdefault(x.N, x)
+    for x in warm.values():
+        afd.afd_serve_wait(srv, afd.afd_serve_submit(srv, x.G, x.radii, 2, 0.0), 120.0)
+    ids = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submit():
+        for i, (t, x) in enumerate(reqs):
+            while time.perf_counter() - t0 < t:
+                time.sleep(0.0002)
+            ids[i] = afd.afd_serve_submit(srv, x.G, x.radii, x.K, x.tol)
+
+    th = threading.Thread(target=submit)
+    th.start()
+    th.join()
+    outs = [afd.afd_serve_wait(srv, i, 600.0) for i in ids]
+    t_all = time.perf_counter() - t0
+    st = afd.afd_serve_get_stats(srv)
+    # capacity: the same requests all submitted at once
+    t2 = time.perf_counter()
+    ids2 = [afd.afd_serve_submit(srv, x.G, x.radii, x.K, x.tol) for _, x in reqs]
+    for i in ids2:
+        afd.afd_serve_wait(srv, i, 600.0)
+    capacity = len(reqs) / (time.perf_counter() - t2)
+    srv.close()
+    lat = np.array([o["latency_ms"] for o in outs])
+    evals = sum(x.M * x.N * o["steps"] for (_, x), o in zip(reqs, outs))
+    served = len(reqs) / t_all
+    # plain FP64 single-signal path, requests one after another
+    sample = [x for _, x in reqs if x.N <= 8192][:fp64_sample]
+    plans = {}
+    t1 = time.perf_counter()
+    for x in sample:
+        if x.N not in plans:
+            plans[x.N] = afd.afd_plan_create(x.N, x.radii, precision=afd.AFD_FP64_PLAIN)
+            afd.afd_decompose(plans[x.N], x.G, 2, 0.0)
+    t1 = time.perf_counter()
+    for x in sample:
+        afd.afd_decompose(plans[x.N], x.G, x.K, x.tol)
+    fp64_rate = len(sample) / (time.perf_counter() - t1)
+    for p in plans.values():
+        p.close()
+    return {"workload": f"serving: Poisson 2000 req/s for {duration:g} s, N in 512..16384, M=128, "
+                        "delta<=1e-4 or K=64, 40 GB budget",
+            "requests": len(reqs), "signals_per_s": served, "grid_evals_per_s": evals / t_all,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "ticks": st["ticks"], "kernel_launches": st["kernel_launches"],
+            "capacity_signals_per_s": capacity,
+            "fp64_plain_single_signal_per_s": fp64_rate,
+            "capacity_vs_fp64_plain": capacity / fp64_rate,
+            "fp64_plain_sample": f"{len(sample)} of the same requests with N <= 8192, one plan per N",
+            "note": "served signals/s is bounded by the offered 2000 req/s; capacity: all requests "
+                    "submitted at once (FP32+FP64-guarded continuous batching)"}
+
+
+def bench_paper_sweep(afd, reps: int = 20) -> dict:
+    """The N-sweep of Table 9 (Sec. 4.2): f1 on N = 128..4096 points, radii
+    0, 0.1, ..., 0.8, 10 steps (a_1 = 0 imposed, as Tables 4 and 6 read);
+    milliseconds per decomposition, FP32 + FP64 guard.  The paper's Matlab
+    times on one CPU thread are context, not a target."""
+    from paper_1711_08604_gb300 import workloads as W
+    out = {}
+    for N in (128, 256, 512, 1024, 2048, 4096):
+        G = W.paper_f1(N)
+        plan = afd.afd_plan_create(N, W.radii_paper(), force_a1_zero=True)
+        afd.afd_decompose(plan, G, 10)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            afd.afd_decompose(plan, G, 10)
+        out[str(N)] = 1e3 * (time.perf_counter() - t0) / reps
+        plan.close()
+    return {"workload": "Table 9 sweep: f1, radii 0..0.8, 10 steps", "ms_per_decomposition": out,
+            "timing": f"host wall clock per afd_decompose call (host input and outputs), mean of {reps}"}
 
 
 def run_reference(args):
@@ -227,13 +354,9 @@ def run_afd(args):
         barrier()
         t_wall = time.perf_counter() - t_wall
     launches = afd.afd_plan_counters(plan)["kernel_launches"]
-    total_ms = sum(ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     evals_per_step = s.M * s.N * K
-    value = evals_per_step * args.steps * ws / (total_ms * 1e-3)
+    total_ms, total_evals = aggregate(sum(ms), evals_per_step * args.steps, ws)
+    value = total_evals / (total_ms * 1e-3)
 
     # Per-kernel device times: the same K steps again, with CUDA events recorded
     # between consecutive kernels inside the replayed graph (event-record nodes
@@ -243,26 +366,36 @@ def run_afd(args):
     afd.afd_plan_reset_counters(plan)
     ms_prof = timed_loop(args.steps, Gd, out)
     ktimes = afd.afd_plan_kernel_times(plan)
+    phases = afd.afd_plan_phase_cycles(plan)
     afd.afd_plan_set_profiling(plan, False)
 
-    grid_ms, grid_n = ktimes["grid"]
-    grid_avg_ms = grid_ms / max(1, grid_n)
     logn = int(np.log2(s.N))
     flops_per_eval = 5 * logn + 6
-    grid_flops = s.M * s.N * flops_per_eval
+    if ktimes["persistent"][1] > 0:
+        # one cooperative launch per decomposition: all K steps' grid evaluations
+        kname = f"k_persistent<{logn}>"
+        k_ms, k_n = ktimes["persistent"]
+        evals_per_launch = s.M * s.N * K
+    else:
+        kname = f"k_grid<float,{logn}>"
+        k_ms, k_n = ktimes["grid"]
+        evals_per_launch = s.M * s.N
+    avg_ms = k_ms / max(1, k_n)
+    flops_per_launch = evals_per_launch * flops_per_eval
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clocks = clk.summary()
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
-    achieved_tflops = grid_flops / (grid_avg_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": f"k_grid<float,{logn}>", "achieved": achieved_tflops,
+    achieved_tflops = flops_per_launch / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved_tflops,
                 "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
-                "traffic": ncu_traffic(f"k_grid<float,{logn}>"),
-                "traffic_note": "dram read+write bytes per launch, one cold-cache ncu capture "
-                                "(profiles/k_grid_f32_tones_N4096_M200.md); null if the kernel changed since",
+                "traffic": ncu_traffic(kname),
+                "traffic_note": "dram read+write bytes per launch from one cold-cache ncu capture "
+                                "(profiles/); null if the kernel changed since",
                 "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
-                "flops_per_launch": grid_flops, "avg_launch_ms": grid_avg_ms,
-                "flops_per_eval": f"5*log2(N)+6 = {flops_per_eval}"}
+                "grid_evals_per_launch": evals_per_launch,
+                "flops_per_eval": f"5*log2(N)+6 = {flops_per_eval}",
+                "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_ms}
     prof_total = sum(ms_prof)
     kernel_us = {k: {"launches": n, "avg_us": 1e3 * t / max(1, n), "share": t / max(prof_total, 1e-9)}
                  for k, (t, n) in ktimes.items()}
@@ -273,12 +406,8 @@ def run_afd(args):
         timed_loop(1, G_pin, None)
     barrier()
     e2e_ms = timed_loop(args.steps, G_pin, None)
-    e2e_total = sum(e2e_ms)
-    if ws > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e = {"value": evals_per_step * args.steps * ws / (e2e_total * 1e-3), "unit": UNIT,
+    e2e_total, e2e_evals = aggregate(sum(e2e_ms), evals_per_step * args.steps, ws)
+    e2e = {"value": e2e_evals / (e2e_total * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": 16 * s.N + SLOTDEV_BYTES,
            "d2h_bytes_per_step": STEPREC_BYTES * K + SLOTCTL_BYTES}
 
@@ -290,11 +419,12 @@ def run_afd(args):
             "config": {"workload": workload_name(args.precision), "N": s.N, "M": s.M, "K": K,
                        "precision": args.precision, "parallelism": f"replicas x{ws}",
                        "l2": "flushed (256 MiB write) between timed steps, outside the timed intervals"},
-            "signals_per_s": args.steps * ws / (total_ms * 1e-3),
+            "signals_per_s": total_evals / evals_per_step / (total_ms * 1e-3),
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                            "min": min(ms), "max": max(ms)},
             "wall_s": t_wall,
             "kernels": kernel_us,
+            "persistent_phase_cycles_per_step": phases,
             "kernels_note": "device time per kernel from CUDA events inside the replayed graph, "
                             "a second pass of the same steps; share = fraction of that pass",
             "gpu_launches": int(launches),
@@ -304,6 +434,10 @@ def run_afd(args):
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(s)
+        if not args.no_extra:
+            line["other_workloads"] = {"batch": bench_batch(afd, torch, dev),
+                                       "serving": bench_serve(afd, args.serve_seconds),
+                                       "paper_table9": bench_paper_sweep(afd)}
         print(json.dumps(line))
     plan.close()
     if ws > 1:
@@ -319,6 +453,8 @@ def main():
     ap.add_argument("--impl", choices=["afd", "reference"], default="afd")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batch and serving workloads")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -67,6 +67,10 @@ typedef struct afd_plan_opts {
   void* stream;        /* cudaStream_t to run on (not the legacy default stream);
                           NULL (default): a stream owned by the plan */
   int use_graph;       /* 1 (default): replay the step sequence as a CUDA graph */
+  int persistent;      /* 1 (default): a single-signal FP32-path decomposition with N <= 4096
+                          runs as one persistent cooperative kernel (bounded grid barriers
+                          between the phases of a step); 0: one launch per kernel per step.
+                          Results are identical either way.  Batches and serving ignore it. */
 } afd_plan_opts;
 
 typedef struct afd_plan afd_plan;
@@ -139,14 +143,24 @@ afd_status afd_plan_last_info(const afd_plan* plan, int* n_cand_out, int* flags_
  * as event-record nodes), so the times are those of the kernels as they run
  * in the sequence; each profiled call synchronises once more to read them.
  * afd_plan_counters: all launches, grid-kernel launches and grid-kernel ms.
- * afd_plan_kernel_times: ms[4] and launches[4] per kernel kind, in the order
- * grid, guard, update, forward (initialisation launches are not included).
+ * afd_plan_kernel_times: ms[5] and launches[5] per kernel kind, in the order
+ * grid, guard, update, forward, persistent (the whole-decomposition kernel;
+ * initialisation launches are not included).
  * Any output pointer may be NULL.
  */
 afd_status afd_plan_set_profiling(afd_plan* plan, int on);
 afd_status afd_plan_counters(const afd_plan* plan, long long* kernel_launches,
                              long long* grid_launches, double* grid_ms);
 afd_status afd_plan_kernel_times(const afd_plan* plan, double* ms, long long* launches);
+
+/*
+ * Phase breakdown of the persistent kernel while profiling is on: average SM
+ * clock cycles per greedy step, measured by the kernel's first CTA, in the
+ * order: transforms and best pairs (A), wait at barrier 1, candidates and
+ * guard sums (B), barrier 2, winner and remainder update (C), barrier 3,
+ * energy and stop rule (D).  steps: greedy steps averaged over.
+ */
+afd_status afd_plan_phase_cycles(const afd_plan* plan, double* avg_cycles, long long* steps);
 afd_status afd_plan_reset_counters(afd_plan* plan);
 
 /*
@@ -184,6 +198,21 @@ afd_status afd_decompose_batch(int n_signals, const int* N, const double* radii,
                                const double* G_packed, int K_max, double energy_tol,
                                const afd_plan_opts* opts, double* a_out, double* coeff_out,
                                double* delta_out, int* idx_out, int* steps_out);
+
+/*
+ * Partial sums of the expansion, Eq. (Sn) (Sec. 2):
+ *   S_n(z_m) = sum_{k=1..n} coeff_k B_k(z_m),
+ *   B_k(z) = sqrt(1-|a_k|^2)/(1 - conj(a_k) z) prod_{l<k} (z - a_l)/(1 - conj(a_l) z),
+ * at the N points z_m = exp(2 pi i m / N), in FP64 (normalised measure: no
+ * 1/sqrt(2 pi) factor).  With the a_k and coefficients afd_decompose returned,
+ * ||G - S_n||^2 / ||G||^2 (discrete norms) equals delta_n.
+ *   a, coeff  2n doubles each (interleaved complex); host or device memory.
+ *   all_prefixes  0: S_out holds S_n (2N doubles); 1: S_out holds S_1..S_n,
+ *                 one after another (2 N n doubles).
+ * Synchronous; allocates device staging for host pointers.
+ */
+afd_status afd_synthesize(int N, const double* a, const double* coeff, int n, int all_prefixes,
+                          double* S_out);
 
 /*
  * Serving: continuous batching of independent decompositions.

@@ -26,8 +26,8 @@ __all__ = [
     "AFD_FP64_PLAIN", "AFD_FP32_GUARDED", "AfdError", "PlanOpts", "afd_plan_opts_default",
     "afd_status_str", "afd_last_error", "afd_version", "afd_plan_create", "afd_plan_destroy",
     "afd_decompose", "afd_plan_last_info", "afd_plan_set_profiling", "afd_plan_counters",
-    "afd_plan_reset_counters", "afd_plan_get_stream", "afd_plan_kernel_times", "afd_batch_create", "afd_batch_run", "afd_batch_counters",
-    "afd_batch_destroy", "afd_decompose_batch", "afd_serve_create", "afd_serve_submit",
+    "afd_plan_reset_counters", "afd_plan_get_stream", "afd_plan_kernel_times", "afd_plan_phase_cycles", "afd_batch_create", "afd_batch_run", "afd_batch_counters",
+    "afd_batch_destroy", "afd_decompose_batch", "afd_synthesize", "afd_serve_create", "afd_serve_submit",
     "afd_serve_poll", "afd_serve_wait", "afd_serve_get_stats", "afd_serve_destroy",
     "afd_inner_products_noalloc", "library_path",
 ]
@@ -87,7 +87,7 @@ def _opts(opts=None, **kw) -> PlanOpts:
     for k, v in kw.items():
         if k == "stream" and v is not None and not isinstance(v, int):
             v = int(getattr(v, "cuda_stream", v))
-        if k in ("force_a1_zero", "use_graph"):
+        if k in ("force_a1_zero", "use_graph", "persistent"):
             v = int(bool(v))
         setattr(o, k, v)
     return o
@@ -198,15 +198,28 @@ def afd_plan_counters(plan: Plan) -> dict:
     return {"kernel_launches": kl.value, "grid_launches": gl.value, "grid_ms": ms.value}
 
 
-KERNEL_KINDS = ("grid", "guard", "update", "forward")
+KERNEL_KINDS = ("grid", "guard", "update", "forward", "persistent")
 
 
 def afd_plan_kernel_times(plan: Plan) -> dict:
     """Per kernel kind: {"grid": (ms, launches), ...} accumulated while profiling."""
-    ms = np.zeros(4)
-    n = np.zeros(4, dtype=np.int64)
+    ms = np.zeros(len(KERNEL_KINDS))
+    n = np.zeros(len(KERNEL_KINDS), dtype=np.int64)
     _check(_lib().afd_plan_kernel_times(plan.handle, ms.ctypes.data, n.ctypes.data))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+PHASES = ("transforms", "barrier1", "guard", "barrier2", "update", "barrier3", "energy")
+
+
+def afd_plan_phase_cycles(plan: Plan) -> dict:
+    """Average SM cycles per greedy step of each persistent-kernel phase (profiling on)."""
+    v = np.zeros(len(PHASES))
+    n = ctypes.c_longlong()
+    _check(_lib().afd_plan_phase_cycles(plan.handle, v.ctypes.data, ctypes.byref(n)))
+    out = {k: float(v[i]) for i, k in enumerate(PHASES)}
+    out["steps"] = n.value
+    return out
 
 
 def afd_plan_get_stream(plan: Plan) -> int:
@@ -272,6 +285,17 @@ def afd_decompose_batch(signals, radii, K_max: int, energy_tol: float = 0.0,
         return afd_batch_run(b, packed, energy_tol)
     finally:
         b.close()
+
+
+def afd_synthesize(N: int, a, coeff, all_prefixes: bool = False) -> np.ndarray:
+    """S_n (or S_1..S_n as rows) on the N sample points from a_k and coefficients."""
+    av = np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+    cv = np.ascontiguousarray(np.asarray(coeff, dtype=np.complex128))
+    n = int(av.size)
+    out = np.zeros((n if all_prefixes else 1) * int(N), dtype=np.complex128)
+    _check(_lib().afd_synthesize(int(N), av.ctypes.data, cv.ctypes.data, n, int(bool(all_prefixes)),
+                                 out.ctypes.data))
+    return out.reshape(n, int(N)) if all_prefixes else out
 
 
 class Server:

@@ -19,7 +19,7 @@ P = ctypes.POINTER
 class PlanOpts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("guard_tau", c_double), ("guard_cap", c_int),
                 ("force_a1_zero", c_int), ("device", c_int), ("stream", c_void_p),
-                ("use_graph", c_int)]
+                ("use_graph", c_int), ("persistent", c_int)]
 
 
 class Result(ctypes.Structure):
@@ -49,6 +49,7 @@ SIGNATURES = {
     "afd_plan_counters": (c_int, [c_void_p, P(c_ll), P(c_ll), P(c_double)]),
     "afd_plan_reset_counters": (c_int, [c_void_p]),
     "afd_plan_kernel_times": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "afd_plan_phase_cycles": (c_int, [c_void_p, c_void_p, P(c_ll)]),
     "afd_plan_get_stream": (c_int, [c_void_p, P(c_void_p)]),
     "afd_batch_create": (c_int, [P(c_void_p), c_int, c_void_p, c_void_p, c_int, c_int, P(PlanOpts)]),
     "afd_batch_run": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -57,6 +58,7 @@ SIGNATURES = {
     "afd_batch_destroy": (c_int, [c_void_p]),
     "afd_decompose_batch": (c_int, [c_int, c_void_p, c_void_p, c_int, c_void_p, c_int, c_double,
                                     P(PlanOpts), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "afd_synthesize": (c_int, [c_int, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "afd_serve_create": (c_int, [P(c_void_p), c_size_t, P(PlanOpts)]),
     "afd_serve_submit": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_double, P(c_u64)]),
     "afd_serve_poll": (c_int, [c_void_p, c_u64, P(Result)]),

@@ -131,8 +131,9 @@ struct FftShape {
 };
 
 // Twiddles of pass PASS applied to the thread's butterflies, then the DFTs.
-// tw is the stage twiddle table of FftSchedule.
-template <typename T, int LOGN, int DIR, int PASS>
+// tw is the stage twiddle table of FftSchedule, in global memory (read through
+// the read-only cache) or, with TW_SMEM, in shared memory.
+template <typename T, int LOGN, int DIR, int PASS, bool TW_SMEM = false>
 __device__ __forceinline__ void fft_pass(V2<T>* v, int t, const V2<T>* __restrict__ tw) {
   using S = FftShape<T, LOGN>;
   constexpr int R = S::radix(PASS), NS = S::ns(PASS), NB = S::P / R;
@@ -144,7 +145,7 @@ __device__ __forceinline__ void fft_pass(V2<T>* v, int t, const V2<T>* __restric
       const int k = b & (NS - 1);
 #pragma unroll
       for (int q = 1; q < R; ++q) {
-        const V2<T> w = __ldg(&tw[OFF + (q - 1) * NS + k]);
+        const V2<T> w = TW_SMEM ? tw[OFF + (q - 1) * NS + k] : __ldg(&tw[OFF + (q - 1) * NS + k]);
         v[i * R + q] = DIR > 0 ? cmul<T>(v[i * R + q], w) : cmulc<T>(v[i * R + q], w);
       }
     }
@@ -202,16 +203,16 @@ __device__ __forceinline__ int fft_out_index(int t, int e) {
 // Runs passes PASS..NPASS-1; v holds the inputs of pass PASS.  Every thread of
 // the CTA must call this (it contains __syncthreads), including threads whose
 // transform is idle.
-template <typename T, int LOGN, int DIR, int PASS = 0>
+template <typename T, int LOGN, int DIR, int PASS = 0, bool TW_SMEM = false>
 __device__ __forceinline__ void fft_run(V2<T>* v, int t, V2<T>* buf, const V2<T>* __restrict__ tw) {
   using S = FftShape<T, LOGN>;
-  fft_pass<T, LOGN, DIR, PASS>(v, t, tw);
+  fft_pass<T, LOGN, DIR, PASS, TW_SMEM>(v, t, tw);
   if constexpr (PASS + 1 < S::NPASS) {
     fft_store<T, LOGN, PASS>(v, t, buf);
     __syncthreads();
     fft_load<T, LOGN, PASS + 1>(v, t, buf);
     __syncthreads();
-    fft_run<T, LOGN, DIR, PASS + 1>(v, t, buf, tw);
+    fft_run<T, LOGN, DIR, PASS + 1, TW_SMEM>(v, t, buf, tw);
   }
 }
 

@@ -15,6 +15,7 @@ constexpr int FP64_CHUNK = 128;
 constexpr int GUARD_PAR = 4;           // candidates in flight per guard launch
 constexpr int MAX_LOGN_RESIDENT = 14;  // N <= 16384: one CTA holds one FFT
 constexpr int TWO_PASS_LOGN = 16;      // N = 65536: two-pass FFT through HBM (plans only)
+constexpr int PERSISTENT_MAX_LOGN = 12;  // persistent single-signal kernel up to N = 4096
 constexpr int MIN_LOGN = 3;            // N >= 8
 constexpr int MAX_CAP = 64;            // guard candidates per step, upper bound
 
@@ -88,6 +89,7 @@ struct SlotDev {
   double* epart;            // [chunks_of(N)] energy partial sums
   StepRec* rec;             // [K_max]
   SlotCtl* ctl;
+  long long* phase_clk;     // persistent kernel, optional: 8 SM-clock stamps per step (CTA 0)
 };
 
 // Kernel launchers (afd_kernels.cu).  `ids` lists the slots of one launch, all

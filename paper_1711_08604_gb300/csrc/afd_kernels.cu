@@ -370,29 +370,32 @@ k_kernel_table(const double* __restrict__ radii, int N, double2* __restrict__ K)
 
 constexpr long kBarrierLimit = 1L << 25;  // polls (with a short sleep) before a barrier gives up
 
-// Grid-wide barrier of a cooperative launch (all CTAs are co-resident).
-// Bounded: a CTA that polls kBarrierLimit times flags a timeout (error bit 2)
-// and every CTA then leaves the kernel.  False in every thread when it must.
-__device__ __forceinline__ bool grid_barrier(SlotCtl* ctl, unsigned nblocks, int* s_ok) {
+// Grid-wide barrier of a cooperative launch (all CTAs are co-resident).  The
+// arrival counter only grows during a launch (the host zeroes it before), so
+// barrier number e of the launch is passed when it reaches nblocks * (e + 1):
+// one atomic per CTA and a poll, no reset.  Bounded: a CTA that polls
+// kBarrierLimit times flags a timeout (error bit 2), and every CTA that sees
+// the flag leaves.  False in every thread when the kernel must stop.
+__device__ __forceinline__ bool grid_barrier(SlotCtl* ctl, unsigned target, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = &ctl->bar_gen;
-    const unsigned g0 = *gen;
-    __threadfence();
     int ok = 1;
-    if (atomicAdd(&ctl->bar_count, 1u) == nblocks - 1u) {
-      ctl->bar_count = 0u;
-      __threadfence();
-      atomicAdd(&ctl->bar_gen, 1u);
-    } else {
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
+    if (arrived < target) {
+      volatile unsigned* cnt = &ctl->bar_count;
       long it = 0;
-      while (*gen == g0) {
+      while (*cnt < target) {
         if (++it > kBarrierLimit) {
           atomicOr(&ctl->err, 4);
           ok = 0;
           break;
         }
-        __nanosleep(32);
+        if ((it & 1023) == 0 && (*((volatile int*)&ctl->err) & 4)) {  // another CTA gave up
+          ok = 0;
+          break;
+        }
+        __nanosleep(20);
       }
     }
     __threadfence();
@@ -403,25 +406,29 @@ __device__ __forceinline__ bool grid_barrier(SlotCtl* ctl, unsigned nblocks, int
   return *s_ok != 0;
 }
 
-// All K greedy steps of one FP32-path signal in one launch.  Per step:
-//   A  each CTA: forward FFT of G_k from its FP32 copy (the same arithmetic as
-//      k_forward), then its radii's inverse FFTs with the objective and best
-//      pairs (as k_grid) -- barrier --
+// All greedy steps of one FP32-path signal in one launch.  Per step:
+//   A  each CTA: forward FFT of G_k from its FP32 copy (the arithmetic of
+//      k_forward), its radii's inverse FFTs with the objective and best pairs
+//      (as k_grid) -- barrier --
 //   B  each CTA: the candidate list (the same in every CTA), then its share of
 //      the guard's partial sums -- barrier --
-//   C  each CTA: the winner from the partial sums (the same in every CTA), then
-//      its share of the remainder update and energy partials -- barrier --
-//   D  each CTA: the energy, delta and the stop rule (the same in every CTA).
-// Every reduction uses the work split and order of the separate kernels, so
-// results are bitwise those of the multi-kernel sequence.
+//   C  each CTA: the winner from the partial sums (the same in every CTA), its
+//      share of the remainder update and energy partials -- barrier --
+// and, at the top of the next step, the energy, delta and stop rule (the same
+// in every CTA; their loads overlap those of G_{k+1}).  Inputs of B and C that
+// do not depend on the step's outcome (G, z_m) are fetched early.  Every
+// reduction uses the work split and order of the separate kernels, so results
+// are bitwise those of the multi-kernel sequence.
 template <int LOGN>
-__global__ void __launch_bounds__(GridCfg<float, LOGN>::THREADS)
+__global__ void __launch_bounds__(GridCfg<float, LOGN>::THREADS, 2)
 k_persistent(const SlotDev* __restrict__ slots) {
   using S = FftShape<float, LOGN>;
   using C = GridCfg<float, LOGN>;
   constexpr int N = S::N, P = S::P, TPF = S::TPF, FPC = C::FPC, THREADS = C::THREADS;
   constexpr int R0 = S::radix(0), B = FftSchedule::pow_b(LOGN), NB0 = P / R0;
+  constexpr int TWS = FftSchedule::tw_size(LOGN) > 0 ? FftSchedule::tw_size(LOGN) : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float2 s_tw[TWS];  // stage twiddles for the kernel's lifetime
   __shared__ Best2F red2[32];
   __shared__ double red[2 * (FP64_THREADS / 32)];
   __shared__ int2 s_cand[MAX_CAP];
@@ -435,38 +442,99 @@ k_persistent(const SlotDev* __restrict__ slots) {
   const int n_tiles = (M + FPC - 1) / FPC;
   const int Pc = chunks_of(N);
   const unsigned nb = gridDim.x;
+  unsigned epoch = 0;  // barriers passed so far
   const bool cta0 = blockIdx.x == 0;
   const int g = threadIdx.x / TPF, t = threadIdx.x % TPF;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float2* buf = reinterpret_cast<float2*>(smem_raw) + g * S::SMEM;
   Top2F* top = reinterpret_cast<Top2F*>(sd.top2);
+  long long* clk = (cta0 && threadIdx.x == 0) ? sd.phase_clk : nullptr;
+  for (int i = threadIdx.x; i < FftSchedule::tw_size(LOGN); i += THREADS) s_tw[i] = sd.p.st32[i];
+  // the radial powers of this CTA's first tile stay in registers across steps
+  const int s_first = blockIdx.x * FPC + g;
+  float h0[R0], lb0[NB0];
+  if (s_first < M) {
+#pragma unroll
+    for (int q = 0; q < R0; ++q) h0[q] = __ldg(&sd.p.rhi32[(size_t)s_first * R0 + q]);
+#pragma unroll
+    for (int i = 0; i < NB0; ++i) lb0[i] = __ldg(&sd.p.rlo32[(size_t)s_first * B + t + i * TPF]);
+  }
+  // this CTA's usual guard chunk and update chunk (128 samples each)
+  const int m_guard = (int)(blockIdx.x % (unsigned)Pc) * FP64_CHUNK + threadIdx.x;
+  const int m_upd = (int)blockIdx.x * FP64_CHUNK + threadIdx.x;
+  const bool own_guard = threadIdx.x < FP64_THREADS && m_guard < N;
+  const bool own_upd = threadIdx.x < FP64_THREADS && (int)blockIdx.x < Pc && m_upd < N;
+  __syncthreads();
 
-  for (int k = 0; k < sd.K_max; ++k) {
+  for (int k = 0;; ++k) {
+    if (clk && k < sd.K_max) clk[8 * k + 0] = clock64();
+    // inputs of this step that no later phase of it changes
+    float2 vin[P];
+    if (k < sd.K_max) {
+#pragma unroll
+      for (int e = 0; e < P; ++e) vin[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
+    }
+    const double2 g_guard = own_guard ? sd.G[m_guard] : make_double2(0.0, 0.0);
+    const double2 g_upd = own_upd ? sd.G[m_upd] : make_double2(0.0, 0.0);
+    // ------------------------------------------- energy and stop of step k-1 --
+    if (k > 0) {
+      if (threadIdx.x < 32) {
+        double E = 0.0;
+        for (int q = threadIdx.x; q < Pc; q += 32) E += __ldcg(&sd.epart[q]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) E += __shfl_xor_sync(0xffffffffu, E, off);
+        if (threadIdx.x == 0) s_E = E / (double)N;
+      }
+      __syncthreads();
+      const double E = s_E;
+      const double E1 = __ldcg(&ctl->E1);
+      const double delta = E1 > 0.0 ? E / E1 : 0.0;
+      const bool stop = k >= sd.K_max || (sd.tol > 0.0 && delta <= sd.tol);
+      if (cta0 && threadIdx.x == 0) {
+        StepRec& rec = sd.rec[k - 1];
+        rec.energy = E;
+        rec.delta = delta;
+        ctl->k = k;
+        if (stop) ctl->done = 1;
+      }
+      if (stop) return;
+    }
     // ---------------------------------------------------------------- A --
     for (int tile = blockIdx.x; tile < n_tiles; tile += nb) {
       const int s = tile * FPC + g;
       const bool active = s < M;
       float2 v[P];
+      if (tile == (int)blockIdx.x) {
 #pragma unroll
-      for (int e = 0; e < P; ++e) v[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
-      fft_run<float, LOGN, -1>(v, t, buf, sd.p.st32);
+        for (int e = 0; e < P; ++e) v[e] = vin[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < P; ++e) v[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
+      }
+      fft_run<float, LOGN, -1, 0, true>(v, t, buf, s_tw);
       __syncthreads();
 #pragma unroll
       for (int e = 0; e < P; ++e) buf[smem_pad(fft_out_index<float, LOGN>(t, e))] = v[e];
       __syncthreads();
       if (active) {
-        const float* lo = sd.p.rlo32 + (size_t)s * B;
-        const float* hi = sd.p.rhi32 + (size_t)s * R0;
-        float h[R0];
+        float h[R0], lb[NB0];
+        if (tile == (int)blockIdx.x) {
 #pragma unroll
-        for (int q = 0; q < R0; ++q) h[q] = __ldg(&hi[q]);
+          for (int q = 0; q < R0; ++q) h[q] = h0[q];
+#pragma unroll
+          for (int i = 0; i < NB0; ++i) lb[i] = lb0[i];
+        } else {
+#pragma unroll
+          for (int q = 0; q < R0; ++q) h[q] = __ldg(&sd.p.rhi32[(size_t)s * R0 + q]);
+#pragma unroll
+          for (int i = 0; i < NB0; ++i) lb[i] = __ldg(&sd.p.rlo32[(size_t)s * B + t + i * TPF]);
+        }
 #pragma unroll
         for (int i = 0; i < NB0; ++i) {
           const int b = t + i * TPF;
-          const float lb = __ldg(&lo[b]);
 #pragma unroll
           for (int q = 0; q < R0; ++q) {
-            const float rp = lb * h[q];
+            const float rp = lb[i] * h[q];
             const float2 x = buf[smem_pad(b + q * B)];
             v[i * R0 + q] = make_float2(x.x * rp, x.y * rp);
           }
@@ -476,7 +544,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
         for (int e = 0; e < P; ++e) v[e] = make_float2(0.f, 0.f);
       }
       __syncthreads();
-      fft_run<float, LOGN, +1>(v, t, buf, sd.p.st32);
+      fft_run<float, LOGN, +1, 0, true>(v, t, buf, s_tw);
       Best2F b;
       b.init();
 #pragma unroll
@@ -494,7 +562,9 @@ k_persistent(const SlotDev* __restrict__ slots) {
       }
       __syncthreads();
     }
-    if (!grid_barrier(ctl, nb, &s_ok)) return;
+    if (clk) clk[8 * k + 1] = clock64();
+    if (!grid_barrier(ctl, nb * ++epoch, &s_ok)) return;
+    if (clk) clk[8 * k + 2] = clock64();
 
     // ---------------------------------------------------------------- B --
     const float vmax = __uint_as_float(__ldcg(&ctl->vmax2[k & 1]));
@@ -517,11 +587,14 @@ k_persistent(const SlotDev* __restrict__ slots) {
       const int c = it / Pc, p = it % Pc;
       const int m = p * FP64_CHUNK + threadIdx.x;
       double ar = 0.0, ai = 0.0;
-      if (threadIdx.x < FP64_THREADS && m < N) guard_term(sd, s_cand[c].x, s_cand[c].y, m, sd.G[m], ar, ai);
+      if (threadIdx.x < FP64_THREADS && m < N)
+        guard_term(sd, s_cand[c].x, s_cand[c].y, m, m == m_guard ? g_guard : sd.G[m], ar, ai);
       const double2 tot = sum_fp64_group(ar, ai, red);
       if (threadIdx.x == 0) sd.gpart[c * Pc + p] = tot;
     }
-    if (!grid_barrier(ctl, nb, &s_ok)) return;
+    if (clk) clk[8 * k + 3] = clock64();
+    if (!grid_barrier(ctl, nb * ++epoch, &s_ok)) return;
+    if (clk) clk[8 * k + 4] = clock64();
 
     // ---------------------------------------------------------------- C --
     for (int c = warp; c < n; c += THREADS / 32) {
@@ -585,7 +658,8 @@ k_persistent(const SlotDev* __restrict__ slots) {
         const int m = p * FP64_CHUNK + threadIdx.x;
         double e = 0.0;
         if (threadIdx.x < FP64_THREADS && m < N) {
-          const double2 gn = update_point(sd, m, ps, pj, r, cr, ci, sd.G[m]);
+          const bool mine = m == m_upd && own_upd;
+          const double2 gn = update_point(sd, m, ps, pj, r, cr, ci, mine ? g_upd : sd.G[m]);
           sd.G[m] = gn;
           e = fma(gn.x, gn.x, gn.y * gn.y);
           sd.g32[m] = make_float2((float)(gn.x * inv_n), (float)(gn.y * inv_n));
@@ -594,29 +668,12 @@ k_persistent(const SlotDev* __restrict__ slots) {
         if (threadIdx.x == 0) sd.epart[p] = es;
       }
     }
-    if (!grid_barrier(ctl, nb, &s_ok)) return;
-
-    // ---------------------------------------------------------------- D --
-    if (threadIdx.x < 32) {
-      double E = 0.0;
-      for (int q = threadIdx.x; q < Pc; q += 32) E += __ldcg(&sd.epart[q]);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) E += __shfl_xor_sync(0xffffffffu, E, off);
-      if (threadIdx.x == 0) s_E = E / (double)N;
+    if (clk) clk[8 * k + 5] = clock64();
+    if (!grid_barrier(ctl, nb * ++epoch, &s_ok)) return;
+    if (clk) {
+      clk[8 * k + 6] = clock64();
+      clk[8 * k + 7] = clk[8 * k + 6];  // the energy phase is timed inside the next step's stamps
     }
-    __syncthreads();
-    const double E = s_E;
-    const double E1 = __ldcg(&ctl->E1);
-    const double delta = E1 > 0.0 ? E / E1 : 0.0;
-    const bool stop = k + 1 >= sd.K_max || (sd.tol > 0.0 && delta <= sd.tol);
-    if (cta0 && threadIdx.x == 0) {
-      StepRec& rec = sd.rec[k];
-      rec.energy = E;
-      rec.delta = delta;
-      ctl->k = k + 1;
-      if (stop) ctl->done = 1;
-    }
-    if (stop) return;
   }
 }
 
@@ -670,7 +727,7 @@ cudaError_t set_attrs() {
   cudaError_t e = cudaFuncSetAttribute(k_grid<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)grid_smem<T, LOGN>());
   if (e != cudaSuccess) return e;
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4 && LOGN <= PERSISTENT_MAX_LOGN) {
     e = cudaFuncSetAttribute(k_persistent<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)grid_smem<T, LOGN>());
     if (e != cudaSuccess) return e;
@@ -757,7 +814,7 @@ cudaError_t launch_forward(const SlotDev* slots, const int* ids, int n, int logN
 }
 
 namespace {
-int g_persist_blocks[MAX_LOGN_RESIDENT + 1] = {};  // co-resident CTAs per logN (0: not yet known)
+int g_persist_blocks[PERSISTENT_MAX_LOGN + 1] = {};  // co-resident CTAs per logN (0: not yet known)
 
 template <int LOGN>
 cudaError_t persistent_launch(const SlotDev* slots, int M, cudaStream_t st) {
@@ -793,9 +850,8 @@ cudaError_t persistent_launch(const SlotDev* slots, int M, cudaStream_t st) {
 cudaError_t launch_persistent(const SlotDev* slots, int logN, int M, cudaStream_t st) {
   switch (logN) {
 #define X(L) case L: return persistent_launch<L>(slots, M, st);
-    AFD_FOR_EACH_LOGN(X)
+    X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
 #undef X
-    case 14: return persistent_launch<14>(slots, M, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -272,6 +272,7 @@ struct SlotPool {
   struct Group { int logN, first, count, Mmax; };
   std::vector<Group> groups;
   std::vector<Fft2Maps> maps;       // TMA descriptors of two-pass slots (N = 65536)
+  bool persistent = false;          // single FP32 slot: one persistent launch per decomposition
 
   ~SlotPool() { release(); }
   void release() {
@@ -289,6 +290,7 @@ struct SlotPool {
     n = (int)tables.size();
     K_max = K;
     prec = o.precision;
+    persistent = o.persistent != 0;
     cap = prec == AFD_FP32_GUARDED ? o.guard_cap : 1;
     // group by logN (stable: signal order within a group)
     std::vector<int> order(n);
@@ -384,8 +386,8 @@ struct SlotPool {
 };
 
 // Kernel launch bookkeeping.  Kernel kinds: 0 grid, 1 guard, 2 update,
-// 3 forward (4 = initialisation, not timed).
-constexpr int KINDS = 4;
+// 3 forward, 4 persistent (initialisation is not timed).
+constexpr int KINDS = 5;  // + 4: the persistent whole-decomposition kernel
 struct Counters {
   long long launches = 0;
   long long n[KINDS] = {};
@@ -447,6 +449,15 @@ afd_status enqueue_group(const SlotPool& pool, const SlotPool::Group& g, int K, 
   const bool two_pass = g.logN == TWO_PASS_LOGN;
   if (two_pass && (g.count != 1 || pool.n != 1)) return set_error(AFD_ERR_INVALID, "N = 65536 needs its own plan");
   const int per = two_pass ? 2 : 1;  // launches per transform stage
+  if (pool.persistent && pool.n == 1 && prec == AFD_FP32_GUARDED && g.logN <= PERSISTENT_MAX_LOGN) {
+    CUDA_TRY(launch_init(slots, ids, g.count, g.logN, st));
+    if (t) AFD_TRY(timer->mark(st, -1));
+    CUDA_TRY(launch_persistent(slots, g.logN, g.Mmax, st));
+    if (t) AFD_TRY(timer->mark(st, 4));
+    cnt.n[4] += 1;
+    cnt.launches += 2;
+    return AFD_OK;
+  }
   CUDA_TRY(launch_init(slots, ids, g.count, g.logN, st));
   if (two_pass) CUDA_TRY(launch_forward2(slots, pool.maps[0], st));
   else CUDA_TRY(launch_forward(slots, ids, g.count, g.logN, prec, st));
@@ -610,9 +621,14 @@ struct afd_plan {
   Counters cnt;
   StepTimer timer;
   int last_steps = 0;
+  long long* phase_dev = nullptr;  // persistent kernel phase stamps while profiling
+  int phase_cap = 0;
+  double phase_sum[7] = {};
+  long long phase_steps = 0;
   ~afd_plan() {
     runner.destroy();
     if (own_stream && runner.main) cudaStreamDestroy(runner.main);
+    if (phase_dev) cudaFree(phase_dev);
   }
 };
 
@@ -693,6 +709,7 @@ void afd_plan_opts_default(afd_plan_opts* o) {
   o->device = -1;
   o->stream = nullptr;
   o->use_graph = 1;
+  o->persistent = 1;
 }
 
 const char* afd_status_str(afd_status s) {
@@ -768,12 +785,29 @@ afd_status afd_decompose(afd_plan* plan, const double* G, int K_max, double ener
     AFD_TRY(pool.build(t, K_max, plan->opts));
   }
   if (plan->own_stream) AFD_TRY(plan->runner.order_after_default());
+  const bool stamps = plan->timer.on && pool.persistent && plan->opts.precision == AFD_FP32_GUARDED &&
+                      plan->tables.N <= (1 << PERSISTENT_MAX_LOGN);
+  if (stamps && plan->phase_cap < K_max) {
+    if (plan->phase_dev) cudaFree(plan->phase_dev);
+    plan->phase_dev = nullptr;
+    plan->phase_cap = 0;
+    CUDA_TRY(cudaMalloc(&plan->phase_dev, sizeof(long long) * 8 * (size_t)K_max));
+    plan->phase_cap = K_max;
+  }
+  pool.host[0].phase_clk = stamps ? plan->phase_dev : nullptr;
   AFD_TRY(pool.upload(energy_tol, st));
   CUDA_TRY(cudaMemcpyAsync(pool.G_dev, G, 16 * (size_t)plan->tables.N, cudaMemcpyDefault, st));
   AFD_TRY(plan->runner.run(pool, K_max, plan->opts.use_graph != 0, plan->cnt, &plan->timer));
   AFD_TRY(fetch_results(pool, st));
   const int steps = pool.ctl_host[0].k;
   plan->last_steps = steps;
+  if (stamps && steps > 0) {
+    std::vector<long long> c(8 * (size_t)steps);
+    CUDA_TRY(cudaMemcpy(c.data(), plan->phase_dev, sizeof(long long) * c.size(), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < steps; ++k)
+      for (int i = 0; i < 7; ++i) plan->phase_sum[i] += (double)(c[8 * k + i + 1] - c[8 * k + i]);
+    plan->phase_steps += steps;
+  }
   AFD_TRY(write_outputs(pool, 0, K_max, steps, a_out, coeff_out, delta_out, idx_out));
   if (steps_done) AFD_TRY(copy_out(steps_done, &steps, sizeof(int)));
   if (pool.ctl_host[0].err & 2) return set_error(AFD_ERR_NUMERIC, "non-finite objective at step %d", steps);
@@ -815,6 +849,14 @@ afd_status afd_plan_kernel_times(const afd_plan* plan, double* ms, long long* la
   return AFD_OK;
 }
 
+afd_status afd_plan_phase_cycles(const afd_plan* plan, double* avg_cycles, long long* steps) {
+  if (!plan) return set_error(AFD_ERR_INVALID, "plan is NULL");
+  for (int i = 0; i < 7 && avg_cycles; ++i)
+    avg_cycles[i] = plan->phase_steps ? plan->phase_sum[i] / (double)plan->phase_steps : 0.0;
+  if (steps) *steps = plan->phase_steps;
+  return AFD_OK;
+}
+
 afd_status afd_plan_get_stream(const afd_plan* plan, void** stream) {
   if (!plan || !stream) return set_error(AFD_ERR_INVALID, "plan or stream is NULL");
   *stream = plan->runner.main;
@@ -824,6 +866,8 @@ afd_status afd_plan_get_stream(const afd_plan* plan, void** stream) {
 afd_status afd_plan_reset_counters(afd_plan* plan) {
   if (!plan) return set_error(AFD_ERR_INVALID, "plan is NULL");
   plan->cnt = Counters{};
+  for (double& v : plan->phase_sum) v = 0.0;
+  plan->phase_steps = 0;
   return AFD_OK;
 }
 
@@ -869,6 +913,7 @@ afd_status afd_batch_create(afd_batch** out, int n_signals, const int* N, const 
     per_signal[i] = it->second;
   }
   AFD_TRY(b->pool.build(per_signal, K_max, o));
+  b->pool.persistent = false;  // batches use the per-kernel launches
   *out = b.release();
   return AFD_OK;
 }

@@ -190,3 +190,72 @@ def test_nan_input_reports_numeric_error(prec):
     with pytest.raises(afd.AfdError) as e:
         afd.afd_decompose(plan, G, 3)
     assert e.value.status == -7
+
+
+@pytest.mark.parametrize("N", [256, 1024, 4096])
+def test_persistent_kernel_equals_kernel_sequence(N):
+    # one cooperative launch per decomposition vs one launch per kernel per
+    # step: the same arithmetic in the same order, so bitwise equal results
+    s = W.tones(item=3, N=N, M=40, K=12) if N >= 1024 else W.kernel_sum(item=3, N=N, M=40, K=12)
+    a, _ = run(s.G, s.radii, s.K, 1, persistent=True)
+    b, _ = run(s.G, s.radii, s.K, 1, persistent=False)
+    for k in ("a", "coeff", "delta", "idx"):
+        assert np.array_equal(a[k], b[k]), k
+    tol = float(a["delta"][6]) * 1.0000001
+    c, _ = run(s.G, s.radii, s.K, 1, tol=tol, persistent=True)
+    assert c["steps"] == 6 and np.array_equal(c["coeff"], a["coeff"][:6])
+
+
+def test_persistent_kernel_profiled():
+    s = W.tones(item=4, K=8)
+    plan = afd.afd_plan_create(s.N, s.radii)
+    afd.afd_plan_set_profiling(plan, True)
+    r = afd.afd_decompose(plan, s.G, s.K)
+    kt = afd.afd_plan_kernel_times(plan)
+    assert r["steps"] == s.K
+    assert kt["persistent"][1] == 1 and kt["persistent"][0] > 0
+    parity.check(s.G, s.radii, r, 1, full_grid=False, grid_steps=(1,))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_synthesis_recovers_energy_curve(prec):
+    # Eq. (Sn): G - S_n = G_{n+1} times a unimodular Blaschke product on the
+    # circle, so ||G - S_n||^2 / ||G||^2 = delta_n for every n
+    s = W.kernel_sum(item=7)
+    res, _ = run(s.G, s.radii, 10, prec)
+    S = afd.afd_synthesize(s.N, res["a"], res["coeff"], all_prefixes=True)
+    E1 = np.mean(np.abs(s.G) ** 2)
+    for n in range(1, 11):
+        d = np.mean(np.abs(s.G - S[n - 1]) ** 2) / E1
+        assert abs(d - res["delta"][n]) <= 1e-12 + 1e-10 * res["delta"][n]
+    # against the expansion written out with numpy
+    z = W.sample_points(s.N)
+    Sn = np.zeros_like(z)
+    prod = np.ones_like(z)
+    for a, c in zip(res["a"], res["coeff"]):
+        Sn += c * np.sqrt(1 - abs(a) ** 2) / (1 - np.conj(a) * z) * prod
+        prod *= (z - a) / (1 - np.conj(a) * z)
+    assert np.max(np.abs(S[-1] - Sn)) <= 1e-12 * np.max(np.abs(s.G))
+    last = afd.afd_synthesize(s.N, res["a"], res["coeff"])
+    assert np.array_equal(last, S[-1])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_paper_table6_forced_a1(prec):
+    G = W.paper_f2(1024)
+    radii = W.radii_paper()
+    res, _ = run(G, radii, 10, prec, force_a1_zero=True)
+    parity.check(G, radii, res, prec, force_a1_zero=True)
+    want = np.array([float(l.split()[1]) for l in open("tests/golden/table6_case2_delta.txt")
+                     if l.strip() and not l.startswith("#")])
+    assert np.max(np.abs(res["delta"][1:11] - want)) <= 3e-3
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N", [128, 256, 512, 1024, 2048, 4096])
+def test_paper_table9_sweep(prec, N):
+    # the N-sweep of Table 9: f1 sampled on N points, radii 0..0.8, 10 steps
+    G = W.paper_f1(N)
+    radii = W.radii_paper()
+    res, _ = run(G, radii, 10, prec, force_a1_zero=True)
+    parity.check(G, radii, res, prec, force_a1_zero=True)
