@@ -41,7 +41,7 @@ UNIT = "grid_evals/s"
 N_SIG, M_RAD, K_STEPS = 4096, 200, 50
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
-STEPREC_BYTES, SLOTCTL_BYTES, SLOTDEV_BYTES = 80, 40, 216
+STEPREC_BYTES, SLOTCTL_BYTES, SLOTDEV_BYTES = 80, 64, 296  # StepRec, SlotCtl, SlotDev
 
 
 def kernel_sources_hash() -> str:
@@ -455,11 +455,23 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and serving workloads")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--workload", choices=["main", "batch", "serve", "sweep"], default="main",
+                    help="main: the contract line; batch / serve / sweep: only that workload's figures "
+                         "(for profiling), printed as one JSON object")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "main":
+        import torch
+        import paper_1711_08604_gb300 as afd
+        afd._native.load()
+        dev = torch.device("cuda", 0)
+        fn = {"batch": lambda: bench_batch(afd, torch, dev), "serve": lambda: bench_serve(afd, args.serve_seconds),
+              "sweep": lambda: bench_paper_sweep(afd)}[args.workload]
+        print(json.dumps(fn()))
+        return 0
     return run_afd(args)
 
 

@@ -92,7 +92,13 @@ const char* afd_version(void);
  * Creates a plan for signals of N samples and the radial grid radii[0..M-1]
  * (Sec. 3.2, Step 1: the paper precomputes and stores r_s^l and the FFT
  * twiddles; the plan holds them on the device, generated in FP64).
- *   N      power of two, 8 <= N <= 16384 (FP32 path) or 8192 (FP64 path).
+ *   N      a power of two, 8 <= N <= 16384 (FP32 path) or 8192 (FP64 path),
+ *          or N = 65536 (FP32 path, single-signal plans only);
+ *          or N = 2^a 3^b 5^c >= 9 that is not a power of two, N <= 12800
+ *          (FP32 path) or 6400 (FP64 path): the remark of Sec. 3.1 that the
+ *          radix-2 split of Theorem 2.1 extends to N = p^K, taken here as
+ *          mixed radices 2, 3, 4, 5, 8 and 16.  Not persistent; not served
+ *          by afd_serve_* (power-of-two sizes only there).
  *   radii  host array of M ascending values in [0, 1); copied.
  *   M      1 <= M <= 4096.
  *   opts   NULL for defaults.
@@ -124,6 +130,24 @@ afd_status afd_plan_destroy(afd_plan* plan);
 afd_status afd_decompose(afd_plan* plan, const double* G, int K_max, double energy_tol,
                          double* a_out, double* coeff_out, double* delta_out, int* idx_out,
                          int* steps_done);
+
+/*
+ * Checkpoint and resume.  As afd_decompose, but starting from a remainder:
+ *   G       2N doubles: G itself (E1_in = 0) or a remainder G_{k+1} returned by
+ *           an earlier call (E1_in = that call's E_1).
+ *   E1_in   0: a fresh start (E_1 = energy of G, a_1 = 0 imposed if the plan
+ *           asks for it); > 0: the reference energy of the original signal,
+ *           so delta keeps its meaning across calls (delta_out[0] = E(G)/E1_in).
+ *   G_final 2N doubles (host or device, may be NULL): the remainder after the
+ *           last step, i.e. the state to resume from.
+ *   E1_out  (may be NULL): the E_1 used.
+ * A decomposition split into calls this way gives bitwise the results of one
+ * call (the state between greedy steps is exactly G_{k+1} and E_1).  The step
+ * records of each call are numbered from 0.
+ */
+afd_status afd_decompose_from(afd_plan* plan, const double* G, double E1_in, int K_max, double energy_tol,
+                              double* a_out, double* coeff_out, double* delta_out, int* idx_out,
+                              int* steps_done, double* G_final, double* E1_out);
 
 /*
  * Diagnostics of the plan's last afd_decompose (host pointers, may be NULL):

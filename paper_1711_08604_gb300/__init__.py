@@ -25,7 +25,7 @@ from ._native import PlanOpts
 __all__ = [
     "AFD_FP64_PLAIN", "AFD_FP32_GUARDED", "AfdError", "PlanOpts", "afd_plan_opts_default",
     "afd_status_str", "afd_last_error", "afd_version", "afd_plan_create", "afd_plan_destroy",
-    "afd_decompose", "afd_plan_last_info", "afd_plan_set_profiling", "afd_plan_counters",
+    "afd_decompose", "afd_decompose_from", "afd_plan_last_info", "afd_plan_set_profiling", "afd_plan_counters",
     "afd_plan_reset_counters", "afd_plan_get_stream", "afd_plan_kernel_times", "afd_plan_phase_cycles", "afd_batch_create", "afd_batch_run", "afd_batch_counters",
     "afd_batch_destroy", "afd_decompose_batch", "afd_synthesize", "afd_serve_create", "afd_serve_submit",
     "afd_serve_poll", "afd_serve_wait", "afd_serve_get_stats", "afd_serve_destroy",
@@ -176,6 +176,27 @@ def afd_decompose(plan: Plan, G, K_max: int, energy_tol: float = 0.0, out: dict 
         res["coeff"] = bufs["coeff"][: 2 * n].view(np.complex128)
         res["delta"] = bufs["delta"][: n + 1]
         res["idx"] = bufs["idx"][: 2 * n].reshape(n, 2)
+    _check(st, res)
+    return res
+
+
+def afd_decompose_from(plan: Plan, G, K_max: int, energy_tol: float = 0.0, E1: float = 0.0) -> dict:
+    """Resumable decomposition: start from G (E1 = 0) or from a remainder returned
+    earlier (E1 = that run's E_1).  The result dict adds "G_final" (the remainder
+    to resume from) and "E1"."""
+    gp, keep = _in_ptr(G)
+    K = int(K_max)
+    n_pts = int(G.numel()) if _is_torch(G) else int(np.asarray(G).size)
+    a, c = np.zeros(2 * K), np.zeros(2 * K)
+    d, ix = np.zeros(K + 1), np.zeros(2 * K, dtype=np.int32)
+    gf = np.zeros(n_pts, dtype=np.complex128)
+    steps, e1 = ctypes.c_int(0), ctypes.c_double(0.0)
+    st = _lib().afd_decompose_from(plan.handle, gp, float(E1), K, float(energy_tol), a.ctypes.data,
+                                   c.ctypes.data, d.ctypes.data, ix.ctypes.data, ctypes.byref(steps),
+                                   gf.ctypes.data, ctypes.byref(e1))
+    n = steps.value
+    res = {"steps": n, "a": a[: 2 * n].view(np.complex128), "coeff": c[: 2 * n].view(np.complex128),
+           "delta": d[: n + 1], "idx": ix[: 2 * n].reshape(n, 2), "G_final": gf, "E1": e1.value}
     _check(st, res)
     return res
 

@@ -44,6 +44,8 @@ SIGNATURES = {
     "afd_plan_destroy": (c_int, [c_void_p]),
     "afd_decompose": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_void_p]),
+    "afd_decompose_from": (c_int, [c_void_p, c_void_p, c_double, c_int, c_double, c_void_p, c_void_p,
+                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "afd_plan_last_info": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "afd_plan_set_profiling": (c_int, [c_void_p, c_int]),
     "afd_plan_counters": (c_int, [c_void_p, P(c_ll), P(c_ll), P(c_double)]),

@@ -259,7 +259,7 @@ __device__ void select_candidates_f32(const SlotDev& sd, int k, int sub = 1) {
 __device__ __forceinline__ void guard_term(const SlotDev& sd, int s, int j, int m, double2 g, double& ar,
                                            double& ai) {
   const int N = sd.p.N;
-  const double2 k = __ldg(&sd.p.K64[(size_t)s * N + ((j - m) & (N - 1))]);
+  const double2 k = __ldg(&sd.p.K64[(size_t)s * N + wrap_mod(j - m, N)]);
   ar = fma(g.x, k.x, -g.y * k.y);
   ai = fma(g.x, k.y, g.y * k.x);
 }
@@ -298,7 +298,7 @@ __device__ __forceinline__ double2 sum_fp64_group(double x, double y, double* re
 __device__ __forceinline__ double2 update_point(const SlotDev& sd, int m, int s, int j, double r, double cr,
                                                 double ci, double2 g) {
   const int N = sd.p.N;
-  const int d = (m - j) & (N - 1);
+  const int d = wrap_mod(m - j, N);
   const double2 w = __ldg(&sd.p.tw64[d]);
   const double2 z = __ldg(&sd.p.tw64[m]);
   const double2 kd = __ldg(&sd.p.K64[(size_t)s * N + d]);

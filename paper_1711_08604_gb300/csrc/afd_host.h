@@ -34,7 +34,7 @@ bool is_pow2(int n);
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 afd_status check_opts(const afd_plan_opts& o);
-afd_status check_size(int N, int prec, bool allow_two_pass = false);
+afd_status check_size(int N, int prec, bool allow_two_pass = false, bool allow_mixed = false);
 afd_status check_radii(const double* radii, int M);
 // opts (NULL: defaults) validated into o; dev = the device to use.
 afd_status normalise_opts(const afd_plan_opts* in, afd_plan_opts& o, int& dev);

@@ -19,7 +19,31 @@ constexpr int PERSISTENT_MAX_LOGN = 12;  // persistent single-signal kernel up t
 constexpr int MIN_LOGN = 3;            // N >= 8
 constexpr int MAX_CAP = 64;            // guard candidates per step, upper bound
 
-inline __host__ __device__ int chunks_of(int N) { return N > FP64_CHUNK ? N / FP64_CHUNK : 1; }
+inline __host__ __device__ int chunks_of(int N) { return (N + FP64_CHUNK - 1) / FP64_CHUNK; }
+// (x mod N) for x in (-N, 2N); N need not be a power of two
+inline __host__ __device__ int wrap_mod(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
+constexpr int MIXED_MAX_PASSES = 24;
+// Largest shared-memory footprint (two ping-pong buffers of N points) of the
+// mixed-radix kernels: N <= 12800 in FP32, N <= 6400 in FP64.
+constexpr int MIXED_MAX_SMEM = 204800;
+
+// Radix schedule of the mixed-radix Stockham transform of length
+// N = 2^a 3^b 5^c: radix-16 passes, one pass of 8, 4 or 2 for the rest of the
+// power of two, then radix-3 and radix-5 passes.  Returns the number of passes
+// written to radix[], or -1 if N has another prime factor or needs more than
+// MIXED_MAX_PASSES passes.
+template <typename I>
+inline __host__ __device__ int mixed_schedule(int N, I* radix) {
+  if (N < 2) return -1;
+  int n = N, np = 0;
+  while (n % 16 == 0 && np < MIXED_MAX_PASSES) { radix[np++] = 16; n /= 16; }
+  if (n % 8 == 0 && np < MIXED_MAX_PASSES) { radix[np++] = 8; n /= 8; }
+  else if (n % 4 == 0 && np < MIXED_MAX_PASSES) { radix[np++] = 4; n /= 4; }
+  else if (n % 2 == 0 && np < MIXED_MAX_PASSES) { radix[np++] = 2; n /= 2; }
+  while (n % 3 == 0 && np < MIXED_MAX_PASSES) { radix[np++] = 3; n /= 3; }
+  while (n % 5 == 0 && np < MIXED_MAX_PASSES) { radix[np++] = 5; n /= 5; }
+  return n == 1 ? np : -1;
+}
 
 // Per (N, radii) tables, owned by a plan, read-only in kernels.
 struct PlanDev {
@@ -36,7 +60,10 @@ struct PlanDev {
   const double* w64;        // [M] w_s
   const double* sq64;       // [M] sqrt(1 - r_s^2)
   const double2* K64;       // [M * N] 1 / (1 - r_s exp(2 pi i d / N)), FP64
-  const float2* tw32n;      // [N] exp(+2 pi i k / N) in FP32 (two-pass path only)
+  const float2* tw32n;      // [N] exp(+2 pi i k / N) in FP32 (two-pass and mixed-radix paths)
+  double inv_n;             // 1 / N (exact for powers of two)
+  int mix_npass;            // mixed-radix path (N not a power of two): passes and radices
+  unsigned char mix_radix[MIXED_MAX_PASSES];
 };
 
 // One greedy step's outcome, written on the device.
@@ -64,6 +91,7 @@ struct SlotCtl {
   unsigned vmax_bits;       // FP32 path: bits of the step's largest objective (atomicMax)
   unsigned bar_count, bar_gen;  // persistent kernel: grid barrier
   unsigned vmax2[2];        // persistent kernel: vmax_bits of even / odd steps
+  double Estart;            // energy of the remainder the call started from
 };
 
 struct Top2F { float v1, v2; int j1, j2; };
@@ -78,6 +106,7 @@ struct SlotDev {
   int force_a1_zero;
   double tol;               // stop once delta <= tol (0: never)
   double tau;               // guard window: obj32 >= (1 - tau) * max32
+  double E1_given;          // > 0: reference energy E_1 of a resumed decomposition
   double2* G;               // [N] remainder G_k(z_m), FP64
   float2* g32;              // [N] G_k(z_m) / N rounded to FP32 (input of the FP32 forward FFT)
   float2* c32;              // [N] spectrum c_l / N, FP32
@@ -91,17 +120,27 @@ struct SlotDev {
   SlotCtl* ctl;
   long long* phase_clk;     // persistent kernel, optional: 8 SM-clock stamps per step (CTA 0)
 };
+// Host-visible layout sizes (the bench reports per-step transfer bytes from them).
+static_assert(sizeof(StepRec) == 80, "StepRec layout");
+static_assert(sizeof(SlotCtl) == 64, "SlotCtl layout");
+static_assert(sizeof(SlotDev) == 296, "SlotDev layout");
 
 // Kernel launchers (afd_kernels.cu).  `ids` lists the slots of one launch, all
 // with the same logN; `n` is their number.  Each returns the launch status.
-cudaError_t launch_init(const SlotDev* slots, const int* ids, int n, int logN, cudaStream_t st);
+cudaError_t launch_init(const SlotDev* slots, const int* ids, int n, int N, cudaStream_t st);
 cudaError_t launch_grid(const SlotDev* slots, const int* ids, int n, int logN, int prec, int Mmax,
                         cudaStream_t st);
 // Whole FP32-path decomposition of slot 0 in one cooperative launch (after
 // launch_init); logN <= MAX_LOGN_RESIDENT.
 cudaError_t launch_persistent(const SlotDev* slots, int logN, int M, cudaStream_t st);
-cudaError_t launch_guard(const SlotDev* slots, const int* ids, int n, int logN, int cap, cudaStream_t st);
-cudaError_t launch_update(const SlotDev* slots, const int* ids, int n, int logN, cudaStream_t st);
+cudaError_t launch_guard(const SlotDev* slots, const int* ids, int n, int N, int cap, cudaStream_t st);
+cudaError_t launch_update(const SlotDev* slots, const int* ids, int n, int N, cudaStream_t st);
+// Mixed-radix path (afd_mixed.cu): N = 2^a 3^b 5^c, not a power of two.
+cudaError_t launch_grid_mixed(const SlotDev* slots, const int* ids, int n, int N, int prec, int Mmax,
+                              cudaStream_t st);
+cudaError_t launch_forward_mixed(const SlotDev* slots, const int* ids, int n, int N, int prec, cudaStream_t st);
+cudaError_t mixed_configure();
+size_t mixed_smem_bytes(int N, int prec);
 cudaError_t launch_forward(const SlotDev* slots, const int* ids, int n, int logN, int prec,
                            cudaStream_t st);
 // Fills K[s * N + d] = 1 / (1 - r_s exp(2 pi i d / N)) for a plan.

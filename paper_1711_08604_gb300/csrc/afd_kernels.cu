@@ -252,7 +252,8 @@ k_guard(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
 // d = (m - j) mod N.  Because z_m - a = z_m conj(u), the division is
 // (...) conj(z_m) conj(K_s[d]) with the plan's K_s[d] = 1 / (1 - r_s w^d).
 // Also accumulates the energy and, on the FP32 path, writes G_{k+1}/N in FP32
-// for the next forward FFT.  INIT: energy (E_1) and FP32 copy of G_1 only.
+// for the next forward FFT.  INIT: energy and FP32 copy of the starting
+// remainder only; E_1 is that energy unless a resumed call supplies it.
 template <bool INIT>
 __global__ void __launch_bounds__(FP64_THREADS)
 k_update(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
@@ -279,10 +280,7 @@ k_update(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
       sd.G[m] = g;
     }
     e = fma(g.x, g.x, g.y * g.y);
-    if (sd.prec) {
-      const double inv_n = 1.0 / (double)N;  // exact: N is a power of two
-      sd.g32[m] = make_float2((float)(g.x * inv_n), (float)(g.y * inv_n));
-    }
+    if (sd.prec) sd.g32[m] = make_float2((float)(g.x * sd.p.inv_n), (float)(g.y * sd.p.inv_n));
   }
   const double es = sum_fp64_group(e, 0.0, red).x;
   if (threadIdx.x == 0) sd.epart[p] = es;
@@ -296,7 +294,8 @@ k_update(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
   if (threadIdx.x != 0) return;
   E /= (double)N;
   if constexpr (INIT) {
-    ctl->E1 = E;
+    ctl->Estart = E;
+    ctl->E1 = sd.E1_given > 0.0 ? sd.E1_given : E;
   } else {
     StepRec& rec = sd.rec[k];
     const double delta = ctl->E1 > 0.0 ? E / ctl->E1 : 0.0;
@@ -748,6 +747,7 @@ cudaError_t configure_kernels() {
   AFD_FOR_EACH_LOGN(X)
 #undef X
   if ((e = set_attrs<float, 14>()) != cudaSuccess) return e;
+  if ((e = mixed_configure()) != cudaSuccess) return e;
   return fft2_configure();
 }
 
@@ -856,9 +856,9 @@ cudaError_t launch_persistent(const SlotDev* slots, int logN, int M, cudaStream_
   }
 }
 
-cudaError_t launch_guard(const SlotDev* slots, const int* ids, int n, int logN, int cap, cudaStream_t st) {
+cudaError_t launch_guard(const SlotDev* slots, const int* ids, int n, int N, int cap, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  dim3 grid((cap < GUARD_PAR ? cap : GUARD_PAR) * chunks_of(1 << logN), n);
+  dim3 grid((cap < GUARD_PAR ? cap : GUARD_PAR) * chunks_of(N), n);
   return launch_pdl(k_guard, grid, dim3(FP64_THREADS), 0, st, slots, ids);
 }
 
@@ -868,15 +868,15 @@ cudaError_t launch_kernel_table(const double* radii, int M, int N, double2* K, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_update(const SlotDev* slots, const int* ids, int n, int logN, cudaStream_t st) {
+cudaError_t launch_update(const SlotDev* slots, const int* ids, int n, int N, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  dim3 grid(chunks_of(1 << logN), n);
+  dim3 grid(chunks_of(N), n);
   return launch_pdl(k_update<false>, grid, dim3(FP64_THREADS), 0, st, slots, ids);
 }
 
-cudaError_t launch_init(const SlotDev* slots, const int* ids, int n, int logN, cudaStream_t st) {
+cudaError_t launch_init(const SlotDev* slots, const int* ids, int n, int N, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  dim3 grid(chunks_of(1 << logN), n);
+  dim3 grid(chunks_of(N), n);
   return launch_pdl(k_update<true>, grid, dim3(FP64_THREADS), 0, st, slots, ids);
 }
 

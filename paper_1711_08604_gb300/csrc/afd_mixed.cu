@@ -1,0 +1,306 @@
+// Grid and forward kernels for N = 2^a 3^b 5^c that is not a power of two.
+//
+// The paper's fast route (Eq. (rcl), Theorem 2.1, Sec. 3.1) splits the sum
+// over l by the factors of N; its closing remark on N = p^K notes that the
+// same split works for any radix p.  Here the transform is a mixed-radix
+// Stockham FFT with radices 16, 8, 4, 2, 3 and 5 (mixed_schedule): pass p of
+// radix R over sub-transforms of length Ns reads x[b + q N/R] (q < R) for
+// butterfly b, multiplies input q by w^(dir q (b mod Ns) N/(Ns R)) with
+// w = exp(2 pi i / N), does an R-point DFT and writes output q to
+// ((b - b mod Ns) R + b mod Ns + q Ns); after the last pass the values are in
+// natural order.  Pass 0 reads its inputs straight from global memory and the
+// last pass hands its outputs to the caller from registers; the passes in
+// between ping-pong between two shared-memory buffers of N points.
+//
+// k_grid_mixed  one CTA per (radius, signal): f(l) = r_s^l c_l / N, inverse
+//               transform, objective w_s^2 |F_s(j)|^2, the per-radius best
+//               pair(s) and, in the last CTA of the signal, the selection of
+//               Step 2 -- the same contract as k_grid.
+// k_forward_mixed  one CTA per signal: c_l / N = (1/N) sum_m G(z_m) w^{-ml}.
+// The FP64 guard and update kernels are shared with the power-of-two path
+// (they index the sample points modulo N).
+#include <climits>
+#include <cstdint>
+
+#include "../../include/afd.h"
+#include "afd_device.cuh"
+#include "afd_fft.cuh"
+#include "afd_internal.h"
+
+namespace afd {
+
+namespace {
+
+constexpr int MX_THREADS = 256;
+
+// X_k = sum_{q<3} v_q exp(DIR 2 pi i q k / 3)
+template <int DIR, typename T>
+__device__ __forceinline__ void dft3(V2<T>* v) {
+  const T h = (T)0.86602540378443864676;  // sin(2 pi / 3)
+  const V2<T> a = v[0], t1 = cadd<T>(v[1], v[2]), d = csub<T>(v[1], v[2]);
+  const V2<T> m = mk2<T>(a.x - (T)0.5 * t1.x, a.y - (T)0.5 * t1.y);
+  // DIR i h d
+  const V2<T> r = DIR > 0 ? mk2<T>(-h * d.y, h * d.x) : mk2<T>(h * d.y, -h * d.x);
+  v[0] = cadd<T>(a, t1);
+  v[1] = cadd<T>(m, r);
+  v[2] = csub<T>(m, r);
+}
+
+// X_k = sum_{q<5} v_q exp(DIR 2 pi i q k / 5), from the symmetric pairs
+// t1 = v1 + v4, t2 = v2 + v3, t3 = v1 - v4, t4 = v2 - v3.
+template <int DIR, typename T>
+__device__ __forceinline__ void dft5(V2<T>* v) {
+  const T c1 = (T)0.30901699437494742410;   // cos(2 pi / 5)
+  const T c2 = (T)-0.80901699437494742410;  // cos(4 pi / 5)
+  const T s1 = (T)0.95105651629515357212;   // sin(2 pi / 5)
+  const T s2 = (T)0.58778525229247312917;   // sin(4 pi / 5)
+  const V2<T> v0 = v[0];
+  const V2<T> t1 = cadd<T>(v[1], v[4]), t2 = cadd<T>(v[2], v[3]);
+  const V2<T> t3 = csub<T>(v[1], v[4]), t4 = csub<T>(v[2], v[3]);
+  const V2<T> A = mk2<T>(v0.x + c1 * t1.x + c2 * t2.x, v0.y + c1 * t1.y + c2 * t2.y);
+  const V2<T> C = mk2<T>(v0.x + c2 * t1.x + c1 * t2.x, v0.y + c2 * t1.y + c1 * t2.y);
+  // P = s1 t3 + s2 t4, Q = s2 t3 - s1 t4; the odd parts are DIR i P and DIR i Q
+  const V2<T> P = mk2<T>(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+  const V2<T> Q = mk2<T>(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+  const V2<T> iP = DIR > 0 ? mk2<T>(-P.y, P.x) : mk2<T>(P.y, -P.x);
+  const V2<T> iQ = DIR > 0 ? mk2<T>(-Q.y, Q.x) : mk2<T>(Q.y, -Q.x);
+  v[0] = cadd<T>(v0, cadd<T>(t1, t2));
+  v[1] = cadd<T>(A, iP);
+  v[2] = cadd<T>(C, iQ);
+  v[3] = csub<T>(C, iQ);
+  v[4] = csub<T>(A, iP);
+}
+
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft_any(V2<T>* v) {
+  if constexpr (R == 3) dft3<DIR, T>(v);
+  else if constexpr (R == 5) dft5<DIR, T>(v);
+  else dft<R, DIR, T>(v);
+}
+
+// One Stockham pass of radix R; src(b, q, N/R) is input q of butterfly b,
+// dst(i, value) takes output i.
+template <typename T, int R, int DIR, class Src, class Dst>
+__device__ __forceinline__ void mx_pass(int N, int Ns, const V2<T>* __restrict__ tw, Src& src, Dst& dst) {
+  const int NR = N / R, step = N / (Ns * R);
+  for (int b = threadIdx.x; b < NR; b += MX_THREADS) {
+    const int k = b % Ns;
+    V2<T> v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = src(b, q, NR);
+    if (k != 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        const V2<T> w = __ldg(&tw[q * k * step]);  // q k step < N
+        v[q] = DIR > 0 ? cmul<T>(v[q], w) : cmulc<T>(v[q], w);
+      }
+    }
+    dft_any<R, DIR, T>(v);
+    const int base = (b - k) * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) dst(base + q * Ns, v[q]);
+  }
+}
+
+template <typename T, int DIR, class Src, class Dst>
+__device__ __forceinline__ void mx_pass_any(int R, int N, int Ns, const V2<T>* __restrict__ tw, Src& src,
+                                            Dst& dst) {
+  switch (R) {
+    case 16: mx_pass<T, 16, DIR>(N, Ns, tw, src, dst); break;
+    case 8: mx_pass<T, 8, DIR>(N, Ns, tw, src, dst); break;
+    case 4: mx_pass<T, 4, DIR>(N, Ns, tw, src, dst); break;
+    case 2: mx_pass<T, 2, DIR>(N, Ns, tw, src, dst); break;
+    case 3: mx_pass<T, 3, DIR>(N, Ns, tw, src, dst); break;
+    default: mx_pass<T, 5, DIR>(N, Ns, tw, src, dst); break;
+  }
+}
+
+// The whole transform (at least two passes): first(b, q, N/R0) supplies pass
+// 0's inputs, last(i, value) consumes the natural-order outputs.  buf holds
+// 2 N points.  Every thread of the CTA must call it.
+template <typename T, int DIR, class First, class Last>
+__device__ void mx_run(const PlanDev& p, V2<T>* buf, const V2<T>* __restrict__ tw, First& first, Last& last) {
+  const int N = p.N, np = p.mix_npass;
+  V2<T>* cur = buf;
+  V2<T>* nxt = buf + N;
+  auto to_cur = [&](int i, V2<T> x) { cur[i] = x; };
+  mx_pass_any<T, DIR>(p.mix_radix[0], N, 1, tw, first, to_cur);
+  int Ns = p.mix_radix[0];
+  for (int ps = 1; ps < np; ++ps) {
+    __syncthreads();
+    const int R = p.mix_radix[ps];
+    auto from_cur = [&](int b, int q, int NR) { return cur[b + q * NR]; };
+    if (ps + 1 < np) {
+      auto to_nxt = [&](int i, V2<T> x) { nxt[i] = x; };
+      mx_pass_any<T, DIR>(R, N, Ns, tw, from_cur, to_nxt);
+      V2<T>* t = cur;
+      cur = nxt;
+      nxt = t;
+    } else {
+      mx_pass_any<T, DIR>(R, N, Ns, tw, from_cur, last);
+    }
+    Ns *= R;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ const V2<T>* mx_twiddles(const PlanDev& p) {
+  if constexpr (sizeof(T) == 4) return p.tw32n; else return p.tw64;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MX_THREADS)
+k_grid_mixed(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_last;
+  pdl_launch_dependents();
+  const SlotDev& sd = slots[ids[blockIdx.y]];
+  const int s = blockIdx.x;
+  const int M = sd.p.M;
+  const bool active = s < M;
+  pdl_wait();
+  if (ld_done(sd.ctl)) return;
+  V2<T>* buf = reinterpret_cast<V2<T>*>(smem_raw);
+  if constexpr (sizeof(T) == 4) {
+    __shared__ Best2F red[32];
+    Best2F best;
+    best.init();
+    if (active) {
+      // f(l) = r_s^l c_l / N with r_s^l = lo[l mod B] hi[l div B], B = N / R0:
+      // input q of butterfly b of pass 0 is l = b + q B
+      const int B = sd.p.B, R0 = sd.p.mix_radix[0];
+      const float* lo = sd.p.rlo32 + (size_t)s * B;
+      const float* hi = sd.p.rhi32 + (size_t)s * R0;
+      const float2* c = sd.c32;
+      auto first = [&](int b, int q, int NR) {
+        const float rp = __ldg(&lo[b]) * __ldg(&hi[q]);
+        const float2 x = __ldcg(&c[b + q * NR]);
+        return make_float2(x.x * rp, x.y * rp);
+      };
+      auto last = [&](int i, float2 x) { best.insert(x.x * x.x + x.y * x.y, i); };
+      mx_run<float, +1>(sd.p, buf, mx_twiddles<float>(sd.p), first, last);
+    }
+    group_reduce<MX_THREADS>(best, red);
+    if (threadIdx.x == 0 && active) {
+      const float w2 = sd.p.wsq32[s];
+      Top2F o;
+      o.v1 = best.v1 * w2;
+      o.v2 = best.v2 * w2;
+      o.j1 = best.j1;
+      o.j2 = best.j2;
+      reinterpret_cast<Top2F*>(sd.top2)[s] = o;
+      if (o.v1 >= 0.0f && o.v1 <= 3.402823466e38f) atomicMax(&sd.ctl->vmax_bits, __float_as_uint(o.v1));
+    }
+    if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
+    select_candidates_f32<MX_THREADS>(sd, sd.ctl->k);
+  } else {
+    __shared__ Best1D red[32];
+    Best1D best;
+    best.init();
+    if (active) {
+      const int B = sd.p.B, R0 = sd.p.mix_radix[0];
+      const double* lo = sd.p.rlo64 + (size_t)s * B;
+      const double* hi = sd.p.rhi64 + (size_t)s * R0;
+      const double2* c = sd.c64;
+      auto first = [&](int b, int q, int NR) {
+        const double rp = __ldg(&lo[b]) * __ldg(&hi[q]);
+        const double2 x = __ldcg(&c[b + q * NR]);
+        return make_double2(x.x * rp, x.y * rp);
+      };
+      auto last = [&](int i, double2 x) { best.insert(x.x * x.x + x.y * x.y, i, x); };
+      mx_run<double, +1>(sd.p, buf, mx_twiddles<double>(sd.p), first, last);
+    }
+    group_reduce<MX_THREADS>(best, red);
+    if (threadIdx.x == 0 && active) {
+      const double w = sd.p.w64[s];
+      Top2D o;
+      o.v1 = best.v * (w * w);
+      o.j1 = best.j;
+      o.f1 = best.f;
+      o.v2 = -1.0;
+      o.j2 = INT_MAX;
+      o.f2 = make_double2(0.0, 0.0);
+      reinterpret_cast<Top2D*>(sd.top2)[s] = o;
+    }
+    if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
+    __syncthreads();
+    select_best_f64<MX_THREADS>(sd, sd.ctl->k, red);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MX_THREADS)
+k_forward_mixed(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_launch_dependents();
+  const SlotDev& sd = slots[ids[blockIdx.x]];
+  pdl_wait();
+  if (ld_done(sd.ctl)) return;
+  V2<T>* buf = reinterpret_cast<V2<T>*>(smem_raw);
+  if constexpr (sizeof(T) == 4) {
+    const float2* g = sd.g32;  // G / N in FP32, written by the update
+    float2* c = sd.c32;
+    auto first = [&](int b, int q, int NR) { return __ldcg(&g[b + q * NR]); };
+    auto last = [&](int i, float2 x) { c[i] = x; };
+    mx_run<float, -1>(sd.p, buf, mx_twiddles<float>(sd.p), first, last);
+  } else {
+    const double2* G = sd.G;
+    double2* c = sd.c64;
+    const double n = (double)sd.p.N;
+    auto first = [&](int b, int q, int NR) {
+      const double2 x = __ldcg(&G[b + q * NR]);
+      return make_double2(x.x / n, x.y / n);
+    };
+    auto last = [&](int i, double2 x) { c[i] = x; };
+    mx_run<double, -1>(sd.p, buf, mx_twiddles<double>(sd.p), first, last);
+  }
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl_mx(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(MX_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+}  // namespace
+
+size_t mixed_smem_bytes(int N, int prec) { return 2 * (size_t)N * (prec == AFD_FP32_GUARDED ? 8 : 16); }
+
+cudaError_t launch_grid_mixed(const SlotDev* slots, const int* ids, int n, int N, int prec, int Mmax,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const dim3 grid(Mmax, n);
+  const size_t smem = mixed_smem_bytes(N, prec);
+  if (prec == AFD_FP32_GUARDED) return launch_pdl_mx(k_grid_mixed<float>, grid, smem, st, slots, ids);
+  return launch_pdl_mx(k_grid_mixed<double>, grid, smem, st, slots, ids);
+}
+
+cudaError_t launch_forward_mixed(const SlotDev* slots, const int* ids, int n, int N, int prec, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const size_t smem = mixed_smem_bytes(N, prec);
+  if (prec == AFD_FP32_GUARDED) return launch_pdl_mx(k_forward_mixed<float>, dim3(n), smem, st, slots, ids);
+  return launch_pdl_mx(k_forward_mixed<double>, dim3(n), smem, st, slots, ids);
+}
+
+cudaError_t mixed_configure() {
+  cudaError_t e;
+  const int smem = MIXED_MAX_SMEM;
+  if ((e = cudaFuncSetAttribute(k_grid_mixed<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_grid_mixed<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_forward_mixed<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+    return e;
+  return cudaFuncSetAttribute(k_forward_mixed<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+}  // namespace afd

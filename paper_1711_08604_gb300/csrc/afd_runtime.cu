@@ -88,9 +88,21 @@ afd_status check_opts(const afd_plan_opts& o) {
   return AFD_OK;
 }
 
-afd_status check_size(int N, int prec, bool allow_two_pass) {
+afd_status check_size(int N, int prec, bool allow_two_pass, bool allow_mixed) {
+  if (allow_mixed && !is_pow2(N) && N >= (1 << MIN_LOGN)) {
+    int radix[MIXED_MAX_PASSES];
+    if (mixed_schedule(N, radix) < 2)
+      return set_error(AFD_ERR_INVALID, "N = %d: must be a power of two or a product of powers of 2, 3 and 5", N);
+    if (mixed_smem_bytes(N, prec) > (size_t)MIXED_MAX_SMEM)
+      return set_error(AFD_ERR_INVALID, "N = %d: largest mixed-radix size is %d for this precision", N,
+                       (int)(MIXED_MAX_SMEM / (prec == AFD_FP32_GUARDED ? 16 : 32)));
+    return AFD_OK;
+  }
   if (!is_pow2(N) || N < (1 << MIN_LOGN))
-    return set_error(AFD_ERR_INVALID, "N = %d: must be a power of two >= 8", N);
+    return set_error(AFD_ERR_INVALID,
+                     allow_mixed ? "N = %d: must be >= 8 and a power of two or a product of powers of 2, 3 and 5"
+                                 : "N = %d: must be a power of two >= 8",
+                     N);
   if (allow_two_pass && prec == AFD_FP32_GUARDED && N == (1 << TWO_PASS_LOGN)) return AFD_OK;
   const int maxlog = prec == AFD_FP32_GUARDED ? MAX_LOGN_RESIDENT : MAX_LOGN_RESIDENT - 1;
   if (N > (1 << maxlog))
@@ -129,15 +141,36 @@ Tables::~Tables() {
   if (mem) cudaFree(mem);
 }
 
+// Shape of a plan's tables: the power-table split r^l = lo[l mod B] hi[l div B]
+// (B = N / first radix), the stage-twiddle size of the power-of-two FFTs, and
+// whether the FP32 twiddles w^k of all N points are needed (two-pass and
+// mixed-radix transforms).
+struct TableShape {
+  int logN, B, H, tws;
+  bool two_pass, mixed;
+  int mix_npass;
+  int mix_radix[MIXED_MAX_PASSES];
+  explicit TableShape(int N) {
+    mixed = !is_pow2(N);
+    logN = mixed ? -1 : ilog2(N);
+    two_pass = !mixed && logN > MAX_LOGN_RESIDENT;
+    mix_npass = mixed ? mixed_schedule(N, mix_radix) : 0;
+    if (mixed) B = N / mix_radix[0];
+    else B = two_pass ? 256 : FftSchedule::pow_b(logN);
+    H = N / B;
+    tws = mixed ? 1 : std::max(FftSchedule::tw_size(two_pass ? 8 : logN), 1);
+  }
+  bool tw32n() const { return two_pass || mixed; }
+};
+
 size_t Tables::bytes_for(int N, int M) {
-  const int logN = ilog2(N);
-  const bool two_pass = logN > MAX_LOGN_RESIDENT;
-  const int B = two_pass ? 256 : FftSchedule::pow_b(logN), H = N / B;
-  const size_t tws = (size_t)std::max(FftSchedule::tw_size(two_pass ? 8 : logN), 1);
+  const TableShape sh(N);
+  const int B = sh.B, H = sh.H;
+  const size_t tws = (size_t)sh.tws;
   size_t off = 0;
   for (size_t b : {sizeof(double) * M, 16 * (size_t)N, 16 * tws, 8 * tws, 8 * (size_t)M * B, 8 * (size_t)M * H,
                    4 * (size_t)M * B, 4 * (size_t)M * H, 4 * (size_t)M, 8 * (size_t)M, 8 * (size_t)M,
-                   16 * (size_t)M * N, two_pass ? 8 * (size_t)N : 0})
+                   16 * (size_t)M * N, sh.tw32n() ? 8 * (size_t)N : 0})
     off = align_up(off + b);
   return off;
 }
@@ -146,12 +179,13 @@ afd_status Tables::build(int N_, const double* r, int M_) {
     N = N_;
     M = M_;
     radii.assign(r, r + M);
-    const int logN = ilog2(N);
-    const bool two_pass = logN > MAX_LOGN_RESIDENT;
+    const TableShape sh(N);
+    const int logN = sh.logN;
+    const bool two_pass = sh.two_pass;
     // the two-pass path splits r^l at 256 and runs 256-point sub-transforms
-    const int B = two_pass ? 256 : FftSchedule::pow_b(logN), H = N / B;
+    const int B = sh.B, H = sh.H;
     const int slog = two_pass ? 8 : logN;  // log2 of the transforms the stage twiddles serve
-    const int TWS = FftSchedule::tw_size(slog);
+    const int TWS = sh.mixed ? 0 : FftSchedule::tw_size(slog);
     std::vector<double> tw64(2 * (size_t)N), st64(2 * (size_t)std::max(TWS, 1)),
         rlo64((size_t)M * B), rhi64((size_t)M * H);
     std::vector<float> st32(2 * (size_t)std::max(TWS, 1)), rlo32((size_t)M * B), rhi32((size_t)M * H),
@@ -172,7 +206,7 @@ afd_status Tables::build(int N_, const double* r, int M_) {
     }
     // FFT stage twiddles of 2^slog-point transforms: pass p, input q, class k
     // -> exp(2 pi i q k / (ns R)) = w^(q k stride), w = exp(2 pi i / N)
-    for (int p = 1; p < FftSchedule::npass(slog); ++p) {
+    for (int p = 1; !sh.mixed && p < FftSchedule::npass(slog); ++p) {
       const int R = FftSchedule::radix(slog, p), NS = FftSchedule::ns(slog, p);
       const int off = FftSchedule::tw_off(slog, p), stride = N / (NS * R);
       for (int q = 1; q < R; ++q)
@@ -205,7 +239,7 @@ afd_status Tables::build(int N_, const double* r, int M_) {
                  o_rlo64 = place(8 * rlo64.size()), o_rhi64 = place(8 * rhi64.size()),
                  o_rlo32 = place(4 * rlo32.size()), o_rhi32 = place(4 * rhi32.size()),
                  o_wsq = place(4 * (size_t)M), o_w64 = place(8 * (size_t)M), o_sq = place(8 * (size_t)M),
-                 o_K = place(16 * (size_t)M * N), o_tw32n = place(two_pass ? 8 * (size_t)N : 0);
+                 o_K = place(16 * (size_t)M * N), o_tw32n = place(sh.tw32n() ? 8 * (size_t)N : 0);
     CUDA_TRY(cudaMalloc(&mem, off));
     bytes = off;
     char* b = static_cast<char*>(mem);
@@ -237,7 +271,10 @@ afd_status Tables::build(int N_, const double* r, int M_) {
     dev.sq64 = reinterpret_cast<const double*>(b + o_sq);
     dev.K64 = reinterpret_cast<const double2*>(b + o_K);
     dev.tw32n = nullptr;
-    if (two_pass) {
+    dev.inv_n = 1.0 / (double)N;
+    dev.mix_npass = sh.mix_npass;
+    for (int i = 0; i < MIXED_MAX_PASSES; ++i) dev.mix_radix[i] = i < sh.mix_npass ? sh.mix_radix[i] : 0;
+    if (sh.tw32n()) {
       std::vector<float> tw32n(2 * (size_t)N);
       for (size_t i = 0; i < 2 * (size_t)N; ++i) tw32n[i] = (float)tw64[i];
       CUDA_TRY(cudaMemcpy(b + o_tw32n, tw32n.data(), 8 * (size_t)N, cudaMemcpyHostToDevice));
@@ -269,7 +306,7 @@ struct SlotPool {
   double2* G_dev = nullptr;         // packed remainders
   StepRec* rec_host = nullptr;      // pinned mirrors
   SlotCtl* ctl_host = nullptr;
-  struct Group { int logN, first, count, Mmax; };
+  struct Group { int N, logN, first, count, Mmax; };  // logN = -1: mixed-radix N
   std::vector<Group> groups;
   std::vector<Fft2Maps> maps;       // TMA descriptors of two-pass slots (N = 65536)
   bool persistent = false;          // single FP32 slot: one persistent launch per decomposition
@@ -292,7 +329,7 @@ struct SlotPool {
     prec = o.precision;
     persistent = o.persistent != 0;
     cap = prec == AFD_FP32_GUARDED ? o.guard_cap : 1;
-    // group by logN (stable: signal order within a group)
+    // group by N (stable: signal order within a group)
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
@@ -300,8 +337,8 @@ struct SlotPool {
     groups.clear();
     for (int idx = 0; idx < n; ++idx) {
       const int i = order[idx];
-      const int lg = ilog2(tables[i]->N);
-      if (groups.empty() || groups.back().logN != lg) groups.push_back({lg, idx, 0, 0});
+      const int Ni = tables[i]->N;
+      if (groups.empty() || groups.back().N != Ni) groups.push_back({Ni, is_pow2(Ni) ? ilog2(Ni) : -1, idx, 0, 0});
       groups.back().count++;
       groups.back().Mmax = std::max(groups.back().Mmax, tables[i]->M);
     }
@@ -318,7 +355,7 @@ struct SlotPool {
     std::vector<size_t> o_c(n), o_g32(n), o_top(n), o_cand(n), o_gp(n), o_ep(n), o_X(n);
     for (int i = 0; i < n; ++i) {
       const int N = tables[i]->N, M = tables[i]->M;
-      const bool two_pass = ilog2(N) == TWO_PASS_LOGN;
+      const bool two_pass = N == (1 << TWO_PASS_LOGN);
       o_c[i] = place((prec ? 8 : 16) * (size_t)N);
       o_g32[i] = place(prec ? 8 * (size_t)N : 0);
       o_X[i] = place(two_pass ? 8 * (size_t)M * N : 0);
@@ -355,7 +392,7 @@ struct SlotPool {
       d.G = reinterpret_cast<double2*>(b + o_G) + g_off[i] / 2;
       d.c32 = prec ? reinterpret_cast<float2*>(b + o_c[i]) : nullptr;
       d.g32 = prec ? reinterpret_cast<float2*>(b + o_g32[i]) : nullptr;
-      d.X = ilog2(tables[i]->N) == TWO_PASS_LOGN ? reinterpret_cast<float2*>(b + o_X[i]) : nullptr;
+      d.X = tables[i]->N == (1 << TWO_PASS_LOGN) ? reinterpret_cast<float2*>(b + o_X[i]) : nullptr;
       d.c64 = prec ? nullptr : reinterpret_cast<double2*>(b + o_c[i]);
       d.top2 = b + o_top[i];
       d.cand = reinterpret_cast<int2*>(b + o_cand[i]);
@@ -447,10 +484,11 @@ afd_status enqueue_group(const SlotPool& pool, const SlotPool::Group& g, int K, 
   const bool t = timer && timer->on;
   // the two-pass path (N = 65536) serves single-signal plans: slot 0
   const bool two_pass = g.logN == TWO_PASS_LOGN;
+  const bool mixed = g.logN < 0;
   if (two_pass && (g.count != 1 || pool.n != 1)) return set_error(AFD_ERR_INVALID, "N = 65536 needs its own plan");
   const int per = two_pass ? 2 : 1;  // launches per transform stage
-  if (pool.persistent && pool.n == 1 && prec == AFD_FP32_GUARDED && g.logN <= PERSISTENT_MAX_LOGN) {
-    CUDA_TRY(launch_init(slots, ids, g.count, g.logN, st));
+  if (pool.persistent && pool.n == 1 && prec == AFD_FP32_GUARDED && !mixed && g.logN <= PERSISTENT_MAX_LOGN) {
+    CUDA_TRY(launch_init(slots, ids, g.count, g.N, st));
     if (t) AFD_TRY(timer->mark(st, -1));
     CUDA_TRY(launch_persistent(slots, g.logN, g.Mmax, st));
     if (t) AFD_TRY(timer->mark(st, 4));
@@ -458,30 +496,34 @@ afd_status enqueue_group(const SlotPool& pool, const SlotPool::Group& g, int K, 
     cnt.launches += 2;
     return AFD_OK;
   }
-  CUDA_TRY(launch_init(slots, ids, g.count, g.logN, st));
-  if (two_pass) CUDA_TRY(launch_forward2(slots, pool.maps[0], st));
-  else CUDA_TRY(launch_forward(slots, ids, g.count, g.logN, prec, st));
+  auto forward = [&]() -> cudaError_t {
+    if (two_pass) return launch_forward2(slots, pool.maps[0], st);
+    if (mixed) return launch_forward_mixed(slots, ids, g.count, g.N, prec, st);
+    return launch_forward(slots, ids, g.count, g.logN, prec, st);
+  };
+  CUDA_TRY(launch_init(slots, ids, g.count, g.N, st));
+  CUDA_TRY(forward());
   cnt.launches += 1 + per;
   if (t) AFD_TRY(timer->mark(st, -1));
   for (int k = 0; k < K; ++k) {
     if (two_pass) CUDA_TRY(launch_grid2(slots, pool.maps[0], g.Mmax, st));
+    else if (mixed) CUDA_TRY(launch_grid_mixed(slots, ids, g.count, g.N, prec, g.Mmax, st));
     else CUDA_TRY(launch_grid(slots, ids, g.count, g.logN, prec, g.Mmax, st));
     if (t) AFD_TRY(timer->mark(st, 0));
     cnt.n[0] += per;
     cnt.launches += per;
     if (prec == AFD_FP32_GUARDED) {
-      CUDA_TRY(launch_guard(slots, ids, g.count, g.logN, pool.cap, st));
+      CUDA_TRY(launch_guard(slots, ids, g.count, g.N, pool.cap, st));
       if (t) AFD_TRY(timer->mark(st, 1));
       cnt.n[1] += 1;
       cnt.launches += 1;
     }
-    CUDA_TRY(launch_update(slots, ids, g.count, g.logN, st));
+    CUDA_TRY(launch_update(slots, ids, g.count, g.N, st));
     if (t) AFD_TRY(timer->mark(st, 2));
     cnt.n[2] += 1;
     cnt.launches += 1;
     if (k + 1 < K) {
-      if (two_pass) CUDA_TRY(launch_forward2(slots, pool.maps[0], st));
-      else CUDA_TRY(launch_forward(slots, ids, g.count, g.logN, prec, st));
+      CUDA_TRY(forward());
       if (t) AFD_TRY(timer->mark(st, 3));
       cnt.n[3] += per;
       cnt.launches += per;
@@ -669,7 +711,9 @@ afd_status write_outputs(const SlotPool& pool, int i, int K_stride, int steps, d
   const StepRec* r = pool.rec_host + (size_t)i * pool.K_max;
   std::vector<double> a(2 * (size_t)steps), c(2 * (size_t)steps), d((size_t)steps + 1);
   std::vector<int> ix(2 * (size_t)steps);
-  d[0] = 1.0;
+  const SlotCtl& ctl = pool.ctl_host[i];
+  // delta_0: 1 for a fresh start, E(start) / E_1 for a resumed one
+  d[0] = (ctl.E1 > 0.0 && ctl.Estart != ctl.E1) ? ctl.Estart / ctl.E1 : 1.0;
   for (int k = 0; k < steps; ++k) {
     a[2 * k] = r[k].a_re;
     a[2 * k + 1] = r[k].a_im;
@@ -738,7 +782,7 @@ afd_status afd_plan_create(afd_plan** out, int N, const double* radii, int M, co
   afd_plan_opts o;
   int dev = 0;
   AFD_TRY(normalise_opts(opts, o, dev));
-  AFD_TRY(check_size(N, o.precision, true));
+  AFD_TRY(check_size(N, o.precision, true, true));
   AFD_TRY(check_radii(radii, M));
   if (o.force_a1_zero && radii[0] != 0.0)
     return set_error(AFD_ERR_INVALID, "force_a1_zero needs radii[0] == 0");
@@ -768,10 +812,12 @@ afd_status afd_plan_destroy(afd_plan* plan) {
   return AFD_OK;
 }
 
-afd_status afd_decompose(afd_plan* plan, const double* G, int K_max, double energy_tol, double* a_out,
-                         double* coeff_out, double* delta_out, int* idx_out, int* steps_done) {
+afd_status afd_decompose_from(afd_plan* plan, const double* G, double E1_in, int K_max, double energy_tol,
+                              double* a_out, double* coeff_out, double* delta_out, int* idx_out,
+                              int* steps_done, double* G_final, double* E1_out) {
   clear_last_error();
   if (!plan || !G) return set_error(AFD_ERR_INVALID, "plan or G is NULL");
+  if (!(E1_in >= 0.0) || std::isinf(E1_in)) return set_error(AFD_ERR_INVALID, "E1 must be finite and >= 0");
   if (K_max < 1 || K_max > (1 << 20)) return set_error(AFD_ERR_INVALID, "K_max = %d out of range", K_max);
   if (!(energy_tol >= 0.0)) return set_error(AFD_ERR_INVALID, "energy_tol must be >= 0");
   DeviceScope scope(plan->device);
@@ -795,6 +841,8 @@ afd_status afd_decompose(afd_plan* plan, const double* G, int K_max, double ener
     plan->phase_cap = K_max;
   }
   pool.host[0].phase_clk = stamps ? plan->phase_dev : nullptr;
+  pool.host[0].E1_given = E1_in;
+  pool.host[0].force_a1_zero = (plan->opts.force_a1_zero && E1_in == 0.0) ? 1 : 0;
   AFD_TRY(pool.upload(energy_tol, st));
   CUDA_TRY(cudaMemcpyAsync(pool.G_dev, G, 16 * (size_t)plan->tables.N, cudaMemcpyDefault, st));
   AFD_TRY(plan->runner.run(pool, K_max, plan->opts.use_graph != 0, plan->cnt, &plan->timer));
@@ -810,8 +858,16 @@ afd_status afd_decompose(afd_plan* plan, const double* G, int K_max, double ener
   }
   AFD_TRY(write_outputs(pool, 0, K_max, steps, a_out, coeff_out, delta_out, idx_out));
   if (steps_done) AFD_TRY(copy_out(steps_done, &steps, sizeof(int)));
+  if (E1_out) AFD_TRY(copy_out(E1_out, &pool.ctl_host[0].E1, sizeof(double)));
+  if (G_final) CUDA_TRY(cudaMemcpy(G_final, pool.G_dev, 16 * (size_t)plan->tables.N, cudaMemcpyDefault));
   if (pool.ctl_host[0].err & 2) return set_error(AFD_ERR_NUMERIC, "non-finite objective at step %d", steps);
   return AFD_OK;
+}
+
+afd_status afd_decompose(afd_plan* plan, const double* G, int K_max, double energy_tol, double* a_out,
+                         double* coeff_out, double* delta_out, int* idx_out, int* steps_done) {
+  return afd_decompose_from(plan, G, 0.0, K_max, energy_tol, a_out, coeff_out, delta_out, idx_out, steps_done,
+                            nullptr, nullptr);
 }
 
 afd_status afd_plan_last_info(const afd_plan* plan, int* n_cand_out, int* flags_out, double* obj32_out) {
@@ -886,7 +942,7 @@ afd_status afd_batch_create(afd_batch** out, int n_signals, const int* N, const 
   AFD_TRY(check_radii(radii, M));
   if (o.force_a1_zero && radii[0] != 0.0)
     return set_error(AFD_ERR_INVALID, "force_a1_zero needs radii[0] == 0");
-  for (int i = 0; i < n_signals; ++i) AFD_TRY(check_size(N[i], o.precision));
+  for (int i = 0; i < n_signals; ++i) AFD_TRY(check_size(N[i], o.precision, false, true));
   DeviceScope scope(dev);
   if (!scope.ok) return set_error(AFD_ERR_CUDA, "cannot make device %d current", dev);
   AFD_TRY(ensure_configured(dev));

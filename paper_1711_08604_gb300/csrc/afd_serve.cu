@@ -334,17 +334,17 @@ struct afd_server {
       if (all[l].empty()) continue;
       const int nf = (int)fresh[l].size(), na = (int)all[l].size();
       if (nf) {
-        CUDA_TRY(launch_init(slots_dev, ids_dev + off_fresh[l], nf, l, stream));
+        CUDA_TRY(launch_init(slots_dev, ids_dev + off_fresh[l], nf, 1 << l, stream));
         CUDA_TRY(launch_forward(slots_dev, ids_dev + off_fresh[l], nf, l, prec, stream));
         launches += 2;
       }
       const int* ids = ids_dev + off_all[l];
       CUDA_TRY(launch_grid(slots_dev, ids, na, l, prec, Mmax[l], stream));
       if (prec == AFD_FP32_GUARDED) {
-        CUDA_TRY(launch_guard(slots_dev, ids, na, l, opts.guard_cap, stream));
+        CUDA_TRY(launch_guard(slots_dev, ids, na, 1 << l, opts.guard_cap, stream));
         ++launches;
       }
-      CUDA_TRY(launch_update(slots_dev, ids, na, l, stream));
+      CUDA_TRY(launch_update(slots_dev, ids, na, 1 << l, stream));
       CUDA_TRY(launch_forward(slots_dev, ids, na, l, prec, stream));
       launches += 3;
     }

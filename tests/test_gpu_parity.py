@@ -154,7 +154,7 @@ def test_device_pointers():
 
 def test_invalid_arguments():
     with pytest.raises(afd.AfdError) as e:
-        afd.afd_plan_create(100, [0.1, 0.2])
+        afd.afd_plan_create(112, [0.1, 0.2])  # 7 * 16: neither 2^a nor 2^a 3^b 5^c
     assert e.value.status == -1
     with pytest.raises(afd.AfdError):
         afd.afd_plan_create(64, [0.2, 0.1])
@@ -259,3 +259,25 @@ def test_paper_table9_sweep(prec, N):
     radii = W.radii_paper()
     res, _ = run(G, radii, 10, prec, force_a1_zero=True)
     parity.check(G, radii, res, prec, force_a1_zero=True)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("persistent", [True, False])
+def test_checkpoint_resume_is_bitwise(prec, persistent):
+    # a decomposition split into two calls (the state between calls is the
+    # remainder and E_1) equals one call
+    s = W.tones(item=5, K=30)
+    plan = afd.afd_plan_create(s.N, s.radii, precision=prec, persistent=persistent)
+    full = afd.afd_decompose_from(plan, s.G, 30)
+    p1 = afd.afd_decompose_from(plan, s.G, 12)
+    p2 = afd.afd_decompose_from(plan, p1["G_final"], 18, E1=p1["E1"])
+    plan.close()
+    assert p1["E1"] == full["E1"] and p2["E1"] == full["E1"]
+    for key in ("a", "coeff", "idx"):
+        assert np.array_equal(np.concatenate([p1[key], p2[key]]), full[key]), key
+    assert np.array_equal(p1["delta"], full["delta"][:13])
+    assert np.array_equal(p2["delta"], full["delta"][12:])
+    assert np.array_equal(p2["G_final"], full["G_final"])
+    # the remainder is the oracle's G_{k+1} to FP64 rounding
+    ora = oracle.decompose(s.G, s.radii, 12, forced_idx=p1["idx"], compute_grid=False)
+    assert np.max(np.abs(p1["G_final"] - ora["G_final"])) <= 1e-10 * np.max(np.abs(s.G))
