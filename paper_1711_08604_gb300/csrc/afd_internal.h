@@ -23,6 +23,9 @@ inline __host__ __device__ int chunks_of(int N) { return (N + FP64_CHUNK - 1) / 
 // (x mod N) for x in (-N, 2N); N need not be a power of two
 inline __host__ __device__ int wrap_mod(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
 constexpr int MIXED_MAX_PASSES = 24;
+// Grid-barrier counter of the persistent kernel: its own 128-byte line,
+// zeroed before a launch.
+constexpr int BAR_BYTES = 128;
 // Largest shared-memory footprint (two ping-pong buffers of N points) of the
 // mixed-radix kernels: N <= 12800 in FP32, N <= 6400 in FP64.
 constexpr int MIXED_MAX_SMEM = 204800;
@@ -114,16 +117,17 @@ struct SlotDev {
   double2* c64;             // [N] spectrum c_l / N, FP64
   void* top2;               // [M] Top2F or Top2D
   int2* cand;               // [cap] (s, j)
-  double2* gpart;           // [cap * chunks_of(N)] guard partial sums
-  double* epart;            // [chunks_of(N)] energy partial sums
+  double2* gpart;           // [cap * chunks_of(N)] guard partial sums (x4: persistent, per warp)
+  double* epart;            // [chunks_of(N)] energy partial sums (persistent: x4 per warp, x K_max steps)
   StepRec* rec;             // [K_max]
   SlotCtl* ctl;
   long long* phase_clk;     // persistent kernel, optional: 8 SM-clock stamps per step (CTA 0)
+  unsigned* bar;            // persistent kernel: grid-barrier arrival counter (own 128-byte line)
 };
 // Host-visible layout sizes (the bench reports per-step transfer bytes from them).
 static_assert(sizeof(StepRec) == 80, "StepRec layout");
 static_assert(sizeof(SlotCtl) == 64, "SlotCtl layout");
-static_assert(sizeof(SlotDev) == 296, "SlotDev layout");
+static_assert(sizeof(SlotDev) == 304, "SlotDev layout");
 
 // Kernel launchers (afd_kernels.cu).  `ids` lists the slots of one launch, all
 // with the same logN; `n` is their number.  Each returns the launch status.

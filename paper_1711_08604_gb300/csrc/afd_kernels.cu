@@ -367,37 +367,43 @@ k_kernel_table(const double* __restrict__ radii, int N, double2* __restrict__ K)
 
 // ------------------------------------------------------ persistent kernel --
 
-constexpr long kBarrierLimit = 1L << 25;  // polls (with a short sleep) before a barrier gives up
+constexpr long kBarrierLimit = 1L << 24;  // polls before a barrier gives up (seconds)
+
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 
 // Grid-wide barrier of a cooperative launch (all CTAs are co-resident).  The
 // arrival counter only grows during a launch (the host zeroes it before), so
-// barrier number e of the launch is passed when it reaches nblocks * (e + 1):
-// one atomic per CTA and a poll, no reset.  Bounded: a CTA that polls
-// kBarrierLimit times flags a timeout (error bit 2), and every CTA that sees
-// the flag leaves.  False in every thread when the kernel must stop.
-__device__ __forceinline__ bool grid_barrier(SlotCtl* ctl, unsigned target, int* s_ok) {
+// barrier number e of the launch is passed once it reaches nblocks * (e + 1):
+// one reduction per CTA and a poll, no reset.  Thread 0 publishes its CTA's
+// writes with a release fence before arriving and acquires the others' once
+// the count is reached.  Bounded: a CTA that polls kBarrierLimit times flags a
+// timeout (error bit 2), and every CTA that sees the flag leaves.  False in
+// every thread when the kernel must stop.
+__device__ __forceinline__ bool grid_barrier(const SlotDev& sd, unsigned target, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    SlotCtl* ctl = sd.ctl;
+    unsigned* bar = sd.bar;
     int ok = 1;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
-    if (arrived < target) {
-      volatile unsigned* cnt = &ctl->bar_count;
-      long it = 0;
-      while (*cnt < target) {
-        if (++it > kBarrierLimit) {
-          atomicOr(&ctl->err, 4);
-          ok = 0;
-          break;
-        }
-        if ((it & 1023) == 0 && (*((volatile int*)&ctl->err) & 4)) {  // another CTA gave up
-          ok = 0;
-          break;
-        }
-        __nanosleep(20);
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    for (long it = 1; ld_relaxed_gpu(bar) < target; ++it) {
+      if (it > kBarrierLimit) {
+        atomicOr(&ctl->err, 4);
+        ok = 0;
+        break;
       }
+      if ((it & 255) == 0 && (*((volatile int*)&ctl->err) & 4)) {  // another CTA gave up
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
     }
-    __threadfence();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     if (*((volatile int*)&ctl->err) & 4) ok = 0;
     *s_ok = ok;
   }
@@ -409,15 +415,16 @@ __device__ __forceinline__ bool grid_barrier(SlotCtl* ctl, unsigned target, int*
 //   A  each CTA: forward FFT of G_k from its FP32 copy (the arithmetic of
 //      k_forward), its radii's inverse FFTs with the objective and best pairs
 //      (as k_grid) -- barrier --
-//   B  each CTA: the candidate list (the same in every CTA), then its share of
-//      the guard's partial sums -- barrier --
-//   C  each CTA: the winner from the partial sums (the same in every CTA), its
-//      share of the remainder update and energy partials -- barrier --
+//   B  each CTA: the candidate list (the same in every CTA), then warp-sized
+//      items (one candidate, 32 samples) of the guard's sums -- barrier --
+//   C  each CTA: the winner from the partial sums (the same in every CTA),
+//      warp-sized items of the remainder update and energy -- barrier --
 // and, at the top of the next step, the energy, delta and stop rule (the same
-// in every CTA; their loads overlap those of G_{k+1}).  Inputs of B and C that
-// do not depend on the step's outcome (G, z_m) are fetched early.  Every
-// reduction uses the work split and order of the separate kernels, so results
-// are bitwise those of the multi-kernel sequence.
+// in every CTA).  FP64 throughput per SM is low, so the guard and update work
+// goes out in 32-sample items over all CTAs, warp 0 of every CTA first.  Each
+// item keeps its warp's shuffle-tree sum, and the consumers add the four warp
+// sums of a 128-sample chunk in warp order, then the chunks as the separate
+// kernels do: results are bitwise those of the multi-kernel sequence.
 template <int LOGN>
 __global__ void __launch_bounds__(GridCfg<float, LOGN>::THREADS, 2)
 k_persistent(const SlotDev* __restrict__ slots) {
@@ -429,13 +436,19 @@ k_persistent(const SlotDev* __restrict__ slots) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float2 s_tw[TWS];  // stage twiddles for the kernel's lifetime
   __shared__ Best2F red2[32];
-  __shared__ double red[2 * (FP64_THREADS / 32)];
   __shared__ int2 s_cand[MAX_CAP];
-  __shared__ double s_re[MAX_CAP], s_im[MAX_CAP];
-  __shared__ int s_ok, s_ps, s_pj;
+  __shared__ double s_re[MAX_CAP], s_im[MAX_CAP], s_v[MAX_CAP];
+  __shared__ double s_rad[MAX_CAP], s_sq[MAX_CAP];  // radius and sqrt(1 - r^2) of each candidate
+  __shared__ int s_ok, s_pc, s_ps, s_pj;
   __shared__ double s_pre, s_pim, s_pv, s_E;
 
-  const SlotDev& sd = slots[0];
+  // the descriptor lives in shared memory for the kernel's lifetime: its
+  // fields are read after every grid barrier
+  __shared__ SlotDev s_sd;
+  for (int i = threadIdx.x; i < (int)(sizeof(SlotDev) / 8); i += THREADS)
+    reinterpret_cast<unsigned long long*>(&s_sd)[i] = reinterpret_cast<const unsigned long long*>(slots)[i];
+  __syncthreads();
+  const SlotDev& sd = s_sd;
   SlotCtl* ctl = sd.ctl;
   const int M = sd.p.M;
   const int n_tiles = (M + FPC - 1) / FPC;
@@ -458,46 +471,100 @@ k_persistent(const SlotDev* __restrict__ slots) {
 #pragma unroll
     for (int i = 0; i < NB0; ++i) lb0[i] = __ldg(&sd.p.rlo32[(size_t)s_first * B + t + i * TPF]);
   }
-  // this CTA's usual guard chunk and update chunk (128 samples each)
-  const int m_guard = (int)(blockIdx.x % (unsigned)Pc) * FP64_CHUNK + threadIdx.x;
-  const int m_upd = (int)blockIdx.x * FP64_CHUNK + threadIdx.x;
-  const bool own_guard = threadIdx.x < FP64_THREADS && m_guard < N;
-  const bool own_upd = threadIdx.x < FP64_THREADS && (int)blockIdx.x < Pc && m_upd < N;
+  // warp-sized FP64 items: W per candidate (guard) and W for the update, four
+  // per 128-sample chunk; global warp gw takes items gw, gw + nw, ...
+  constexpr int WPC = FP64_CHUNK / 32;
+  const int W = WPC * Pc;
+  const int nw = (int)nb * (THREADS / 32);
+  const int gw = warp * (int)nb + (int)blockIdx.x;
+  // the warp's first update item keeps its samples G(z_m) in registers: the
+  // same lane updates the same sample at every step
+  const int m_own = gw < W ? gw * 32 + lane : -1;
+  double2 g_own = make_double2(0.0, 0.0);
+  if (m_own >= 0 && m_own < N) g_own = sd.G[m_own];
   __syncthreads();
 
+  // Energy of the remainder after step kk, E = (1/N) sum |G|^2, from that
+  // step's warp partials in the chunk and lane order of k_update.  Called by a
+  // whole warp; every lane gets E.
+  auto energy_of = [&](int kk) -> double {
+    double E = 0.0;
+    for (int q = lane; q < Pc; q += 32) {
+      double ch = 0.0;  // chunk q: its four warp sums in warp order
+#pragma unroll
+      for (int w = 0; w < WPC; ++w) ch += __ldcg(&sd.epart[(size_t)kk * W + q * WPC + w]);
+      E += ch;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) E += __shfl_xor_sync(0xffffffffu, E, off);
+    return E * sd.p.inv_n;  // exact: N is a power of two
+  };
+  // With an energy tolerance, step kk's delta decides at once whether to stop
+  // (the same decision in every CTA).  Returns true when the decomposition stops.
+  auto finish_step = [&](int kk) -> bool {
+    if (threadIdx.x < 32) {
+      const double E = energy_of(kk);
+      if (threadIdx.x == 0) s_E = E;
+    }
+    __syncthreads();
+    const double E = s_E;
+    const double E1 = __ldcg(&ctl->E1);
+    const double delta = E1 > 0.0 ? E / E1 : 0.0;
+    const bool stop = kk + 1 >= sd.K_max || delta <= sd.tol;
+    if (cta0 && threadIdx.x == 0) {
+      StepRec& rec = sd.rec[kk];
+      rec.energy = E;
+      rec.delta = delta;
+      ctl->k = kk + 1;
+      if (stop) ctl->done = 1;
+    }
+    return stop;
+  };
+  // Without a tolerance nothing waits for the energies: after the last step,
+  // one warp per step (over all CTAs) writes energy and delta.
+  auto finish_all = [&](int steps) {
+    const double E1 = __ldcg(&ctl->E1);
+    for (int kk = gw; kk < steps; kk += nw) {
+      const double E = energy_of(kk);
+      if (lane == 0) {
+        StepRec& rec = sd.rec[kk];
+        rec.energy = E;
+        rec.delta = E1 > 0.0 ? E / E1 : 0.0;
+      }
+    }
+    if (cta0 && threadIdx.x == 0) {
+      ctl->k = steps;
+      ctl->done = 1;
+    }
+  };
+  // Energy partial of each of the warp's update items of step kk: a shuffle
+  // tree over its 32 samples of the new remainder.
+  auto energy_items = [&](int kk) {
+    for (int i = gw; i < W; i += nw) {
+      const int m = i * 32 + lane;
+      double e = 0.0;
+      if (m < N) {
+        const double2 g2 = m == m_own ? g_own : sd.G[m];
+        e = fma(g2.x, g2.x, g2.y * g2.y);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+      if (lane == 0) sd.epart[(size_t)kk * W + i] = e;
+    }
+  };
+
   for (int k = 0;; ++k) {
-    if (clk && k < sd.K_max) clk[8 * k + 0] = clock64();
+    if (k >= sd.K_max) {
+      // after the last step's update (its energy partials are written)
+      if (sd.tol > 0.0) finish_step(k - 1);
+      else finish_all(k);
+      return;
+    }
+    if (clk) clk[8 * k + 0] = clock64();
     // inputs of this step that no later phase of it changes
     float2 vin[P];
-    if (k < sd.K_max) {
 #pragma unroll
-      for (int e = 0; e < P; ++e) vin[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
-    }
-    const double2 g_guard = own_guard ? sd.G[m_guard] : make_double2(0.0, 0.0);
-    const double2 g_upd = own_upd ? sd.G[m_upd] : make_double2(0.0, 0.0);
-    // ------------------------------------------- energy and stop of step k-1 --
-    if (k > 0) {
-      if (threadIdx.x < 32) {
-        double E = 0.0;
-        for (int q = threadIdx.x; q < Pc; q += 32) E += __ldcg(&sd.epart[q]);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) E += __shfl_xor_sync(0xffffffffu, E, off);
-        if (threadIdx.x == 0) s_E = E / (double)N;
-      }
-      __syncthreads();
-      const double E = s_E;
-      const double E1 = __ldcg(&ctl->E1);
-      const double delta = E1 > 0.0 ? E / E1 : 0.0;
-      const bool stop = k >= sd.K_max || (sd.tol > 0.0 && delta <= sd.tol);
-      if (cta0 && threadIdx.x == 0) {
-        StepRec& rec = sd.rec[k - 1];
-        rec.energy = E;
-        rec.delta = delta;
-        ctl->k = k;
-        if (stop) ctl->done = 1;
-      }
-      if (stop) return;
-    }
+    for (int e = 0; e < P; ++e) vin[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
     // ---------------------------------------------------------------- A --
     for (int tile = blockIdx.x; tile < n_tiles; tile += nb) {
       const int s = tile * FPC + g;
@@ -511,10 +578,15 @@ k_persistent(const SlotDev* __restrict__ slots) {
         for (int e = 0; e < P; ++e) v[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
       }
       fft_run<float, LOGN, -1, 0, true>(v, t, buf, s_tw);
-      __syncthreads();
+      // The forward transform leaves c_l, l = t + TPF e, in register e (its
+      // last pass is one full-width butterfly per thread); the inverse
+      // transform's pass 0 wants l = t + i TPF + q B = t + TPF (i + q NB0) in
+      // register i R0 + q.  The spectrum therefore stays in registers.
+      static_assert(LOGN < 4 || (P == 16 && S::radix(S::NPASS - 1) == 16 && S::ns(S::NPASS - 1) == TPF),
+                    "forward outputs t + TPF e");
+      float2 vf[P];
 #pragma unroll
-      for (int e = 0; e < P; ++e) buf[smem_pad(fft_out_index<float, LOGN>(t, e))] = v[e];
-      __syncthreads();
+      for (int e = 0; e < P; ++e) vf[e] = v[e];
       if (active) {
         float h[R0], lb[NB0];
         if (tile == (int)blockIdx.x) {
@@ -530,11 +602,10 @@ k_persistent(const SlotDev* __restrict__ slots) {
         }
 #pragma unroll
         for (int i = 0; i < NB0; ++i) {
-          const int b = t + i * TPF;
 #pragma unroll
           for (int q = 0; q < R0; ++q) {
             const float rp = lb[i] * h[q];
-            const float2 x = buf[smem_pad(b + q * B)];
+            const float2 x = vf[i + q * NB0];
             v[i * R0 + q] = make_float2(x.x * rp, x.y * rp);
           }
         }
@@ -542,7 +613,6 @@ k_persistent(const SlotDev* __restrict__ slots) {
 #pragma unroll
         for (int e = 0; e < P; ++e) v[e] = make_float2(0.f, 0.f);
       }
-      __syncthreads();
       fft_run<float, LOGN, +1, 0, true>(v, t, buf, s_tw);
       Best2F b;
       b.init();
@@ -561,11 +631,22 @@ k_persistent(const SlotDev* __restrict__ slots) {
       }
       __syncthreads();
     }
+    // energy partials of step k-1, left out of its update phase so that the
+    // FFTs above did not wait for them
+    if (k > 0) energy_items(k - 1);
     if (clk) clk[8 * k + 1] = clock64();
-    if (!grid_barrier(ctl, nb * ++epoch, &s_ok)) return;
+    if (!grid_barrier(sd, nb * ++epoch, &s_ok)) return;
     if (clk) clk[8 * k + 2] = clock64();
+    // step k-1 is complete: with a tolerance, its energy, delta and the stop
+    // rule (the FFTs of step k ran speculatively; nothing of step k is
+    // recorded before this)
+    if (k > 0 && sd.tol > 0.0 && finish_step(k - 1)) return;
 
     // ---------------------------------------------------------------- B --
+    // G at the warp's first guard item (the item index modulo W does not
+    // depend on the candidates), fetched while the candidates are selected
+    const int m_g0 = (gw % W) * 32 + lane;
+    const double2 g_g0 = m_g0 < N ? sd.G[m_g0] : make_double2(0.0, 0.0);
     const float vmax = __uint_as_float(__ldcg(&ctl->vmax2[k & 1]));
     int n = 1, count = 1;
     if (sd.force_a1_zero && k == 0) {
@@ -582,41 +663,68 @@ k_persistent(const SlotDev* __restrict__ slots) {
       ctl->n_cand = n;
       for (int c = 0; c < n; ++c) sd.cand[c] = s_cand[c];
     }
-    for (int it = blockIdx.x; it < n * Pc; it += nb) {
-      const int c = it / Pc, p = it % Pc;
-      const int m = p * FP64_CHUNK + threadIdx.x;
+    for (int it = gw; it < n * W; it += nw) {
+      const int c = it / W, i = it % W;
+      const int m = i * 32 + lane;
       double ar = 0.0, ai = 0.0;
-      if (threadIdx.x < FP64_THREADS && m < N)
-        guard_term(sd, s_cand[c].x, s_cand[c].y, m, m == m_guard ? g_guard : sd.G[m], ar, ai);
-      const double2 tot = sum_fp64_group(ar, ai, red);
-      if (threadIdx.x == 0) sd.gpart[c * Pc + p] = tot;
+      if (m < N) guard_term(sd, s_cand[c].x, s_cand[c].y, m, m == m_g0 ? g_g0 : sd.G[m], ar, ai);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, off);
+        ai += __shfl_xor_sync(0xffffffffu, ai, off);
+      }
+      if (lane == 0) sd.gpart[it] = make_double2(ar, ai);
     }
     if (clk) clk[8 * k + 3] = clock64();
-    if (!grid_barrier(ctl, nb * ++epoch, &s_ok)) return;
+    if (!grid_barrier(sd, nb * ++epoch, &s_ok)) return;
     if (clk) clk[8 * k + 4] = clock64();
 
     // ---------------------------------------------------------------- C --
+    if (threadIdx.x < n) {
+      s_rad[threadIdx.x] = sd.p.radii[s_cand[threadIdx.x].x];
+      s_sq[threadIdx.x] = sd.p.sq64[s_cand[threadIdx.x].x];
+    }
     for (int c = warp; c < n; c += THREADS / 32) {
-      const double2 tot = warp_sum_partials(sd.gpart + c * Pc, Pc);
+      double x = 0.0, y = 0.0;
+      for (int q = lane; q < Pc; q += 32) {
+        double cx = 0.0, cy = 0.0;  // chunk q: its four warp sums in warp order
+#pragma unroll
+        for (int w = 0; w < WPC; ++w) {
+          const double2 v = __ldcg(&sd.gpart[c * W + q * WPC + w]);
+          cx += v.x;
+          cy += v.y;
+        }
+        x += cx;
+        y += cy;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, off);
+        y += __shfl_xor_sync(0xffffffffu, y, off);
+      }
+      const double2 tot = make_double2(x, y);
       if (lane == 0) {
-        const double sc = sd.p.sq64[s_cand[c].x] / (double)N;
-        s_re[c] = sc * tot.x;
-        s_im[c] = sc * tot.y;
+        const double sc = sd.p.sq64[s_cand[c].x] * sd.p.inv_n;  // exact scaling: N is a power of two
+        const double re = sc * tot.x, im = sc * tot.y;
+        s_re[c] = re;
+        s_im[c] = im;
+        s_v[c] = re * re + im * im;
       }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      int bs = -1, bj = -1;
+      int bc = -1, bs = -1, bj = -1;
       double bv = -1.0, bre = 0.0, bim = 0.0;
       for (int c = 0; c < n; ++c) {
         const int2 cj = s_cand[c];
-        const double v = s_re[c] * s_re[c] + s_im[c] * s_im[c];
+        const double v = s_v[c];
         const int f = cj.x * N + cj.y, bf = bs * N + bj;
         if (bs < 0 || v > bv || (v == bv && f < bf)) {
-          bs = cj.x; bj = cj.y; bv = v; bre = s_re[c]; bim = s_im[c];
+          bc = c; bs = cj.x; bj = cj.y; bv = v; bre = s_re[c]; bim = s_im[c];
         }
       }
       if (bs >= 0 && !(bv <= 1.79e308)) bs = -1;
+      s_pc = bc;
       s_ps = bs;
       s_pj = bj;
       s_pre = bre;
@@ -632,13 +740,18 @@ k_persistent(const SlotDev* __restrict__ slots) {
         rec.j = -1;
         rec.flags |= 2;
         ctl->err |= 2;
-        ctl->done = 1;
+      }
+      if (sd.tol > 0.0) {
+        if (cta0 && threadIdx.x == 0) ctl->done = 1;
+      } else {
+        finish_all(k);  // the energies of the steps done
       }
       return;
     }
-    if (cta0 && threadIdx.x == 0) {
+    // the step record, by the last CTA (the update items start at CTA 0)
+    if (blockIdx.x == nb - 1 && threadIdx.x == 0) {
       StepRec& rec = sd.rec[k];
-      const double rr = sd.p.radii[ps];
+      const double rr = s_rad[s_pc];
       const double2 z = sd.p.tw64[pj];
       rec.s = ps;
       rec.j = pj;
@@ -650,25 +763,24 @@ k_persistent(const SlotDev* __restrict__ slots) {
       rec.obj = s_pv;
     }
     {
-      const double na = sd.p.sq64[ps];
-      const double r = sd.p.radii[ps], cr = s_pre * na, ci = s_pim * na;
-      const double inv_n = 1.0 / (double)N;  // exact: N is a power of two
-      for (int p = blockIdx.x; p < Pc; p += nb) {
-        const int m = p * FP64_CHUNK + threadIdx.x;
-        double e = 0.0;
-        if (threadIdx.x < FP64_THREADS && m < N) {
-          const bool mine = m == m_upd && own_upd;
-          const double2 gn = update_point(sd, m, ps, pj, r, cr, ci, mine ? g_upd : sd.G[m]);
+      const double na = s_sq[s_pc];
+      const double r = s_rad[s_pc], cr = s_pre * na, ci = s_pim * na;
+      const double inv_n = sd.p.inv_n;
+      for (int i = gw; i < W; i += nw) {
+        const int m = i * 32 + lane;
+        if (m < N) {
+          const double2 gn = update_point(sd, m, ps, pj, r, cr, ci, m == m_own ? g_own : sd.G[m]);
+          if (m == m_own) g_own = gn;
           sd.G[m] = gn;
-          e = fma(gn.x, gn.x, gn.y * gn.y);
           sd.g32[m] = make_float2((float)(gn.x * inv_n), (float)(gn.y * inv_n));
         }
-        const double es = sum_fp64_group(e, 0.0, red).x;
-        if (threadIdx.x == 0) sd.epart[p] = es;
       }
+      // the energy partials: now after the last step, else during the next
+      // step's FFTs
+      if (k + 1 >= sd.K_max) energy_items(k);
     }
     if (clk) clk[8 * k + 5] = clock64();
-    if (!grid_barrier(ctl, nb * ++epoch, &s_ok)) return;
+    if (!grid_barrier(sd, nb * ++epoch, &s_ok)) return;
     if (clk) {
       clk[8 * k + 6] = clock64();
       clk[8 * k + 7] = clk[8 * k + 6];  // the energy phase is timed inside the next step's stamps

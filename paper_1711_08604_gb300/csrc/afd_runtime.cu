@@ -303,6 +303,7 @@ struct SlotPool {
   int* ids_dev = nullptr;
   StepRec* rec_dev = nullptr;       // n * K_max, signal-major
   SlotCtl* ctl_dev = nullptr;       // n
+  size_t ctl_bytes = 0;             // control blocks and barrier counters
   double2* G_dev = nullptr;         // packed remainders
   StepRec* rec_host = nullptr;      // pinned mirrors
   SlotCtl* ctl_host = nullptr;
@@ -362,11 +363,17 @@ struct SlotPool {
       // two-pass: one best pair per (radius, 16-row block of pass 2)
       o_top[i] = place((prec ? sizeof(Top2F) : sizeof(Top2D)) * (size_t)M * (two_pass ? 16 : 1));
       o_cand[i] = place(sizeof(int2) * cap);
-      o_gp[i] = place(sizeof(double2) * cap * (size_t)chunks_of(N));
-      o_ep[i] = place(sizeof(double) * (size_t)chunks_of(N));
+      // the persistent kernel keeps one partial per 32-sample warp item, and
+      // its energy partials for every step
+      const size_t parts = (size_t)chunks_of(N) * (persistent ? FP64_CHUNK / 32 : 1);
+      o_gp[i] = place(sizeof(double2) * cap * parts);
+      o_ep[i] = place(sizeof(double) * parts * (persistent ? (size_t)K_max : 1));
     }
     const size_t o_rec = place(sizeof(StepRec) * (size_t)n * K_max);
-    const size_t o_ctl = place(sizeof(SlotCtl) * (size_t)n);
+    // control blocks, then (persistent plans) the grid-barrier counters; one
+    // memset per run clears both
+    ctl_bytes = align_up(sizeof(SlotCtl) * (size_t)n) + (persistent ? BAR_BYTES : 0);
+    const size_t o_ctl = place(ctl_bytes);
     const size_t o_slots = place(sizeof(SlotDev) * (size_t)n);
     const size_t o_ids = place(sizeof(int) * (size_t)n);
     CUDA_TRY(cudaMalloc(&mem, off));
@@ -400,6 +407,7 @@ struct SlotPool {
       d.epart = reinterpret_cast<double*>(b + o_ep[i]);
       d.rec = rec_dev + (size_t)i * K_max;
       d.ctl = ctl_dev + i;
+      d.bar = persistent ? reinterpret_cast<unsigned*>(b + o_ctl + align_up(sizeof(SlotCtl) * (size_t)n)) : nullptr;
     }
     CUDA_TRY(cudaMemcpy(ids_dev, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     maps.assign(n, Fft2Maps{});
@@ -589,7 +597,7 @@ struct Runner {
   afd_status enqueue(const SlotPool& pool, int K, Counters& cnt, StepTimer* timer) {
     AFD_TRY(prepare(pool.groups.size()));
     if (timer) timer->used = 0;
-    CUDA_TRY(cudaMemsetAsync(pool.ctl_dev, 0, sizeof(SlotCtl) * pool.n, main));
+    CUDA_TRY(cudaMemsetAsync(pool.ctl_dev, 0, pool.ctl_bytes, main));
     if (pool.groups.size() > 1) CUDA_TRY(cudaEventRecord(fork, main));
     for (size_t gi = 0; gi < pool.groups.size(); ++gi) {
       cudaStream_t st = gi == 0 ? main : side[gi - 1];
