@@ -175,10 +175,80 @@ def bench_batch(afd, torch, dev, reps: int = 3) -> dict:
         times.append(time.perf_counter() - t0)
     b.close()
     evals = sum(int(x.M) * x.N * int(st) for x, st in zip(sigs, r["steps"]))
+    flops = sum(int(x.M) * x.N * int(st) * (5 * int(np.log2(x.N)) + 6) for x, st in zip(sigs, r["steps"]))
     t = min(times)
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     return {"workload": "batch: 1024 signals, N in {1024,2048,4096,8192}, M=100, K=30, FP32+FP64 guard",
             "grid_evals_per_s": evals / t, "signals_per_s": len(sigs) / t, "s_per_batch": t,
-            "timing": "host wall clock around afd_batch_run (device-resident input), best of %d" % reps}
+            "timing": "host wall clock around afd_batch_run (device-resident input), best of %d" % reps,
+            "grid_fp32_tflops": flops / t / 1e12,
+            "grid_fp32_frac_of_peak": flops / t / 1e12 / peak,
+            "fp32_note": "grid flops (5 log2 N + 6 per grid evaluation) over the whole batch time, "
+                         "FP64 guard/update and forward FFTs included in the time; peak derived: "
+                         f"{sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x 2070 MHz"}
+
+
+def hbm_peak_gbs() -> tuple:
+    """Measured HBM copy bandwidth of this GPU pool (MEASURED_PEAKS.json), else
+    the fallback figure of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json: STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (earlier GB300 copy measurement)"
+
+
+def bench_chirp(afd, torch, dev, reps: int = 3) -> dict:
+    """Workload 5: one decomposition of N = 65536 (two-pass HBM-staged FFT),
+    M = 1000 radii i/1000, K = 100.  Grid evals/s over the whole decomposition,
+    and the two-pass grid stage against HBM bandwidth: pass 1 writes and pass 2
+    reads the M x N FP32 intermediate, 16 M N bytes per step."""
+    from paper_1711_08604_gb300 import workloads as W
+    s = W.chirp()
+    stream = torch.cuda.Stream(device=dev)
+    plan = afd.afd_plan_create(s.N, s.radii, device=dev.index, stream=stream.cuda_stream, use_graph=True)
+    Gd = torch.from_numpy(s.G).to(dev)
+    K = s.K
+    out = {"a": torch.zeros(2 * K, dtype=torch.float64, device=dev),
+           "coeff": torch.zeros(2 * K, dtype=torch.float64, device=dev),
+           "delta": torch.zeros(K + 1, dtype=torch.float64, device=dev),
+           "idx": torch.zeros(2 * K, dtype=torch.int32, device=dev)}
+
+    def once():
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = afd.afd_decompose(plan, Gd, K, 0.0, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert r["steps"] == K
+        return e0.elapsed_time(e1)
+
+    once()
+    ms = min(once() for _ in range(reps))
+    afd.afd_plan_set_profiling(plan, True)
+    once()
+    afd.afd_plan_reset_counters(plan)
+    once()
+    kt = afd.afd_plan_kernel_times(plan)
+    afd.afd_plan_set_profiling(plan, False)
+    plan.close()
+    grid_ms, grid_launches = kt["grid"]
+    steps = grid_launches // 2  # pass 1 + pass 2 per step
+    bytes_per_step = 16 * s.M * s.N
+    gbs = bytes_per_step * steps / (grid_ms * 1e-3) / 1e9 if grid_ms > 0 else 0.0
+    peak, src = hbm_peak_gbs()
+    return {"workload": "large: N=65536 two-pass FFT, M=1000 radii i/1000, K=100, FP32 grid + FP64 guard/update",
+            "ms_per_decomposition": ms, "grid_evals_per_s": s.M * s.N * K / (ms * 1e-3),
+            "timing": "CUDA events around afd_decompose (device-resident input), best of %d" % reps,
+            "kernels_ms": {k: {"launches": n, "total_ms": t} for k, (t, n) in kt.items()},
+            "roofline_two_pass_grid": {"bound": "hbm", "kernel": "k_grid2_pass1 + k_grid2_pass2",
+                                       "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                       "peak_source": src,
+                                       "bytes_per_step": bytes_per_step,
+                                       "bytes_note": "pass-1 write + pass-2 read of the M x N FP32 "
+                                                     "intermediate; the spectrum and tables are L2-resident",
+                                       "ms_per_step": grid_ms / max(1, steps)}}
 
 
 def bench_serve(afd, duration: float = 3.0, fp64_sample: int = 40) -> dict:
@@ -436,6 +506,7 @@ def run_afd(args):
             line["cpu_baseline"] = cpu_baseline(s)
         if not args.no_extra:
             line["other_workloads"] = {"batch": bench_batch(afd, torch, dev),
+                                       "large_two_pass": bench_chirp(afd, torch, dev),
                                        "serving": bench_serve(afd, args.serve_seconds),
                                        "paper_table9": bench_paper_sweep(afd)}
         print(json.dumps(line))
@@ -455,7 +526,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and serving workloads")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
-    ap.add_argument("--workload", choices=["main", "batch", "serve", "sweep"], default="main",
+    ap.add_argument("--workload", choices=["main", "batch", "serve", "sweep", "large"], default="main",
                     help="main: the contract line; batch / serve / sweep: only that workload's figures "
                          "(for profiling), printed as one JSON object")
     args = ap.parse_args()
@@ -469,7 +540,7 @@ def main():
         afd._native.load()
         dev = torch.device("cuda", 0)
         fn = {"batch": lambda: bench_batch(afd, torch, dev), "serve": lambda: bench_serve(afd, args.serve_seconds),
-              "sweep": lambda: bench_paper_sweep(afd)}[args.workload]
+              "sweep": lambda: bench_paper_sweep(afd), "large": lambda: bench_chirp(afd, torch, dev)}[args.workload]
         print(json.dumps(fn()))
         return 0
     return run_afd(args)

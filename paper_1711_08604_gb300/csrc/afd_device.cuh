@@ -26,6 +26,15 @@ struct Best2F {
     if (better_f(v, j, v1, j1)) { v2 = v1; j2 = j1; v1 = v; j1 = j; }
     else if (better_f(v, j, v2, j2)) { v2 = v; j2 = j; }
   }
+  // For values offered in increasing index order: the index exceeds every
+  // index held, so a tie keeps the held (lower) one and plain comparisons do.
+  __device__ __forceinline__ void push_ascending(float v, int j) {
+    const bool p1 = v > v1, p2 = v > v2;
+    v2 = p1 ? v1 : (p2 ? v : v2);
+    j2 = p1 ? j1 : (p2 ? j : j2);
+    v1 = p1 ? v : v1;
+    j1 = p1 ? j : j1;
+  }
   __device__ __forceinline__ void merge(const Best2F& o) {
     if (better_f(o.v1, o.j1, v1, j1)) {
       if (better_f(v1, j1, o.v2, o.j2)) { v2 = v1; j2 = j1; } else { v2 = o.v2; j2 = o.j2; }
@@ -51,6 +60,12 @@ struct Best1D {
   __device__ __forceinline__ void init() { v = -1.0; j = INT_MAX; f = make_double2(0.0, 0.0); }
   __device__ __forceinline__ void insert(double vv, int jj, double2 ff) {
     if (better_d(vv, jj, v, j)) { v = vv; j = jj; f = ff; }
+  }
+  __device__ __forceinline__ void push_ascending(double vv, int jj, double2 ff) {
+    const bool p = vv > v;
+    v = p ? vv : v;
+    j = p ? jj : j;
+    f = p ? ff : f;
   }
   __device__ __forceinline__ void merge(const Best1D& o) { insert(o.v, o.j, o.f); }
   __device__ __forceinline__ Best1D shfl(int off) const {
@@ -122,11 +137,13 @@ __device__ __forceinline__ void block_best_f(float& v, int& f, float* sv, int* s
 }
 
 // Last-CTA detection: returns true in every thread of the CTA that is the
-// last of `target` CTAs to arrive on *counter, and resets the counter.
+// last of `target` CTAs to arrive on *counter, and resets the counter.  Every
+// write the last CTA reads must come from thread 0 or be followed by a
+// __threadfence() in the thread that made it.
 __device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned target, int* s_flag) {
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     unsigned prev = atomicAdd(counter, 1u);
     *s_flag = (prev == target - 1u);
     if (*s_flag) *counter = 0u;

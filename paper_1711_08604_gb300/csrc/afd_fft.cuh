@@ -200,6 +200,15 @@ __device__ __forceinline__ int fft_out_index(int t, int e) {
   return (b - k) * R + k + (e % R) * NS;
 }
 
+// Register slot of the u-th smallest output index of a thread after the last
+// pass; that index is t + TPF u.
+template <typename T, int LOGN>
+__host__ __device__ constexpr int fft_out_slot(int u) {
+  using S = FftShape<T, LOGN>;
+  constexpr int R = S::radix(S::NPASS - 1), NB = S::P / R;
+  return (u % NB) * R + u / NB;
+}
+
 // Runs passes PASS..NPASS-1; v holds the inputs of pass PASS.  Every thread of
 // the CTA must call this (it contains __syncthreads), including threads whose
 // transform is idle.

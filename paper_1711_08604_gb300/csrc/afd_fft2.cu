@@ -6,21 +6,31 @@
 // w = exp(DIR 2 pi i / N).  This is the splitting of Theorem 2.1 (Sec. 3.1)
 // taken with a radix of 256 instead of 2: pass 1 does the 256 inner sums
 // (length-256 transforms over l2) and the twiddle w^{j2 l1}; pass 2 the outer
-// length-256 transforms over l1.
-//
-// Pass 1: a CTA takes 16 consecutive columns l1 of f (one radius s): a TMA
-// load of a {16 l1 x 256 l2} tile (128-byte rows, 128B swizzle), the spectrum
-// times r_s^l = r_s^{l1} r_s^{256 l2} in registers, 16 transforms of 256
-// points, the twiddle, and a TMA store of the tile X_s[j2][l1] (X is stored
-// transposed so that pass 2 reads whole rows).
-// Pass 2: a CTA takes 16 rows j2 of X_s: a TMA load of {256 l1 x 16 j2}, 16
-// transforms of 256 points, then either the objective w_s^2 |F_s(j)|^2 with
-// the CTA's best two (grid mode) or, for the forward transform of G, a TMA
-// store of c_j (forward mode).  X holds 512 KiB per radius: 2 x 512 KiB of
+// length-256 transforms over l1.  X holds 512 KiB per radius: 2 x 512 KiB of
 // HBM traffic per radius per step, the dominant memory stream.
 //
+// Grid step (inverse transforms of r_s^l c_l, all radii), two persistent,
+// pipelined kernels:
+//   k_grid2_pass1  CTA = (column block a of 16 columns l1, a set of radii).  One
+//                  TMA load of the spectrum tile {16 l1 x 256 l2} (128-byte
+//                  rows, 128B swizzle), kept for all its radii; per radius the
+//                  tile times r_s^l = r_s^{l1} r_s^{256 l2}, 16 transforms of
+//                  256 points, the twiddle (held in registers: it does not
+//                  depend on the radius), and an asynchronous TMA store of
+//                  X_s[j2][l1] (X is stored transposed so that pass 2 reads
+//                  whole rows) from one of two buffers, so that the store of
+//                  one radius overlaps the transforms of the next.
+//   k_grid2_pass2  CTA = a strided set of (radius, block of 16 rows j2) items;
+//                  a two-stage ring of TMA loads {256 l1 x 16 j2} keeps the
+//                  next item's load in flight during the current item's 16
+//                  transforms of 256 points, objective w_s^2 |F_s(j)|^2 and
+//                  best two.  The last CTA selects the candidates.
+// Forward transform of G (one per step, 16 CTAs): k_fwd2_pass1/2, one tile per
+// CTA, ending with a TMA store of c_j.
+//
 // mbarrier waits are bounded: a load that does not arrive within the limit
-// sets error bit 2 of the signal (AFD_ERR_TIMEOUT at the host) and stops it.
+// sets error bit 2 of the signal (AFD_ERR_TIMEOUT at the host) and stops it;
+// the CTA waits (bounded) for its other copies before it leaves.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -42,6 +52,13 @@ constexpr int kThreads = 256;          // 16 transforms per CTA
 constexpr int kTileElems = 16 * 256;   // one TMA tile of float2
 constexpr int kTileBytes = kTileElems * 8;
 constexpr size_t kSmemBytes = 1024 + kTileBytes + sizeof(float2) * 16 * S8::SMEM;
+// grid passes: an FFT exchange buffer of 16 padded transforms, also used as
+// pass 1's output tile (1 KiB multiple, for the 128B-swizzled TMA store)
+constexpr int kScratchBytes = 35 * 1024;
+static_assert(sizeof(float2) * 16 * S8::SMEM <= (size_t)kScratchBytes && kTileBytes <= kScratchBytes,
+              "scratch holds the transforms and the tile");
+constexpr size_t kP1Smem = 1024 + kTileBytes + 2 * (size_t)kScratchBytes;
+constexpr size_t kP2Smem = 1024 + 2 * (size_t)kTileBytes + kScratchBytes;
 constexpr long kWaitLimit = 1L << 22;  // mbarrier polls before giving up
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -91,6 +108,18 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int 
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Asynchronous TMA store, committed as its own bulk group (thread 0 only).
+__device__ __forceinline__ void tma_store_2d_async(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+               ::"l"(map), "r"(x), "r"(y), "r"(smem_u32(src))
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// At most one of this thread's bulk stores still reading shared memory.
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// All of this thread's bulk stores complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Element (row y, column x) of a {16 x 256} tile with 128-byte rows under the
 // 128B swizzle: the 16-byte chunk index is XOR-ed with (y mod 8).
 __device__ __forceinline__ int swz16(int y, int x) { return y * 16 + ((((x >> 1) ^ (y & 7))) << 1) + (x & 1); }
@@ -100,178 +129,269 @@ __device__ __forceinline__ float2* align1024(unsigned char* p) {
   return reinterpret_cast<float2*>(p + ((1024u - (a & 1023u)) & 1023u));
 }
 
-// The tile's TMA load, with a bounded wait; false (after flagging the signal)
-// when it did not arrive.
+// Bounded wait of the whole CTA for phase `parity` of bar: thread 0 polls and
+// the outcome is shared, so every thread takes the same branch; the others
+// then observe the completed phase themselves (it is already complete).
+__device__ bool cta_wait(uint64_t* bar, unsigned parity, int* s_flag) {
+  if (threadIdx.x == 0) *s_flag = mbar_wait_bounded(bar, parity) ? 1 : 0;
+  __syncthreads();
+  const bool ok = *s_flag != 0;
+  if (ok) mbar_wait_bounded(bar, parity);
+  return ok;
+}
+
+// The tile's TMA load, with a bounded wait; false in every thread (after
+// flagging the signal) when it did not arrive.
 __device__ bool load_tile(float2* tile, const CUtensorMap* map, int x, int y, uint64_t* bar, SlotCtl* ctl) {
+  __shared__ int s_flag;
   if (threadIdx.x == 0) {
     mbar_expect_tx(bar, kTileBytes);
     tma_load_2d(tile, map, x, y, bar);
   }
-  if (mbar_wait_bounded(bar, 0)) return true;
+  if (cta_wait(bar, 0, &s_flag)) return true;
   if (threadIdx.x == 0) {
     atomicOr(&ctl->err, 4);
     ctl->done = 1;
+    mbar_wait_bounded(bar, 0);  // give a late copy a last chance to land before the CTA exits
   }
-  mbar_wait_bounded(bar, 0);  // give a late copy a last chance to land before the CTA exits
   return false;
 }
 
-__device__ __forceinline__ bool better2(float va, int ja, float vb, int jb) {
-  return va > vb || (va == vb && ja < jb);
-}
+
 
 }  // namespace
 
-// MODE 0: grid (inverse transform of r_s^l c_l, one radius per blockIdx.y);
-// MODE 1: forward transform of G / N.
-template <int MODE>
+// Forward transform of G / N, pass 1: one tile of 16 columns per CTA.
 __global__ void __launch_bounds__(kThreads)
-k_fft2_pass1(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Maps maps) {
+k_fwd2_pass1(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Maps maps) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ alignas(8) uint64_t bar;
   pdl_launch_dependents();
   const SlotDev& sd = slots[0];
   float2* tile = align1024(smem_raw);
   float2* fbuf = tile + kTileElems;
-  const int a = blockIdx.x, s = blockIdx.y;
+  const int a = blockIdx.x;
   const int g = threadIdx.x >> 4, t = threadIdx.x & 15;
   const int l1 = 16 * a + g;
-  float lo = 1.f, h[16];
-  if constexpr (MODE == 0) {
-    lo = __ldg(&sd.p.rlo32[s * 256 + l1]);
-#pragma unroll
-    for (int q = 0; q < 16; ++q) h[q] = __ldg(&sd.p.rhi32[s * 256 + t + 16 * q]);
-  }
   if (threadIdx.x == 0) mbar_init(&bar);
   __syncthreads();
   pdl_wait();
   if (ld_done(sd.ctl)) return;
-  if (!load_tile(tile, MODE == 0 ? &maps.c : &maps.g, 16 * a, 0, &bar, sd.ctl)) return;
+  if (!load_tile(tile, &maps.g, 16 * a, 0, &bar, sd.ctl)) return;
 
   float2 v[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const float2 x = tile[swz16(t + 16 * q, g)];  // l2 = t + 16 q
-    if constexpr (MODE == 0) {
-      const float rp = lo * h[q];
-      v[q] = make_float2(x.x * rp, x.y * rp);
-    } else {
-      v[q] = x;
-    }
-  }
-  fft_run<float, L8, MODE == 0 ? 1 : -1>(v, t, fbuf + g * S8::SMEM, sd.p.st32);
-  // twiddle w^{j2 l1} and the transposed tile X[j2][l1]
+  for (int q = 0; q < 16; ++q) v[q] = tile[swz16(t + 16 * q, g)];  // l2 = t + 16 q
+  fft_run<float, L8, -1>(v, t, fbuf + g * S8::SMEM, sd.p.st32);
+  // twiddle w^{-j2 l1} and the transposed tile X[j2][l1]
 #pragma unroll
   for (int e = 0; e < 16; ++e) {
     const int j2 = fft_out_index<float, L8>(t, e);
     const float2 w = __ldg(&sd.p.tw32n[j2 * l1]);
-    tile[swz16(j2, g)] = MODE == 0 ? cmul<float>(v[e], w) : cmulc<float>(v[e], w);
+    tile[swz16(j2, g)] = cmulc<float>(v[e], w);
   }
   fence_proxy_async();
   __syncthreads();
-  if (threadIdx.x == 0) tma_store_2d(&maps.xs, 16 * a, MODE == 0 ? s * 256 : 0, tile);
+  if (threadIdx.x == 0) tma_store_2d(&maps.xs, 16 * a, 0, tile);
 }
 
-template <int MODE>
+// Forward transform, pass 2: 16 rows j2 per CTA, c_j (j = j2 + 256 j1) stored
+// through a {16 j2 x 256 j1} tile.
 __global__ void __launch_bounds__(kThreads)
-k_fft2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Maps maps) {
+k_fwd2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Maps maps) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ alignas(8) uint64_t bar;
-  __shared__ float rv1[16], rv2[16];
-  __shared__ int rj1[16], rj2[16];
-  __shared__ int s_last;
   pdl_launch_dependents();
   const SlotDev& sd = slots[0];
   float2* tile = align1024(smem_raw);
   float2* fbuf = tile + kTileElems;
-  const int b = blockIdx.x, s = blockIdx.y;
+  const int b = blockIdx.x;
   const int g = threadIdx.x >> 4, t = threadIdx.x & 15;
-  const int j2 = 16 * b + g;
   if (threadIdx.x == 0) mbar_init(&bar);
   __syncthreads();
   pdl_wait();
   if (ld_done(sd.ctl)) return;
-  if (!load_tile(tile, &maps.xl, 0, (MODE == 0 ? s * 256 : 0) + 16 * b, &bar, sd.ctl)) return;
+  if (!load_tile(tile, &maps.xl, 0, 16 * b, &bar, sd.ctl)) return;
 
   float2 v[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = tile[g * 256 + t + 16 * q];  // row j2, l1 = t + 16 q
-  fft_run<float, L8, MODE == 0 ? 1 : -1>(v, t, fbuf + g * S8::SMEM, sd.p.st32);
-
-  if constexpr (MODE == 1) {
-    // c_j for j = j2 + 256 j1, through a {16 j2 x 256 j1} tile
+  fft_run<float, L8, -1>(v, t, fbuf + g * S8::SMEM, sd.p.st32);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) tile[swz16(fft_out_index<float, L8>(t, e), g)] = v[e];
+  for (int e = 0; e < 16; ++e) tile[swz16(fft_out_index<float, L8>(t, e), g)] = v[e];
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) tma_store_2d(&maps.c, 16 * b, 0, tile);
+}
+
+// Grid pass 1 (see the file comment).  gridDim.x = 16 R: CTA (a, r) takes
+// column block a and radii r, r + R, ...
+__global__ void __launch_bounds__(kThreads)
+k_grid2_pass1(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Maps maps) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ alignas(8) uint64_t bar;
+  pdl_launch_dependents();
+  const SlotDev& sd = slots[0];
+  float2* ctile = align1024(smem_raw);
+  float2* obuf = ctile + kTileElems;
+  const int R = gridDim.x / 16;
+  const int a = blockIdx.x % 16, r0 = blockIdx.x / 16;
+  const int g = threadIdx.x >> 4, t = threadIdx.x & 15;
+  const int l1 = 16 * a + g;
+  // w^{j2 l1} for this thread's outputs j2 = t + 16 e, as w^{t l1} w^{16 e l1}
+  // (the second from the 4096-entry table after w^k): the same for all radii
+  float2 tw[16];
+  {
+    const float2 base = __ldg(&sd.p.tw32n[t * l1]);
+    const float2* t4k = sd.p.tw32n + 65536;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) tw[e] = cmul<float>(base, __ldg(&t4k[(e * l1) & 4095]));
+  }
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
+  pdl_wait();
+  if (ld_done(sd.ctl)) return;
+  if (!load_tile(ctile, &maps.c, 16 * a, 0, &bar, sd.ctl)) return;
+  const int M = sd.p.M;
+  int it = 0;
+  for (int s = r0; s < M; s += R, ++it) {
+    float2* ob = obuf + (it & 1) * (kScratchBytes / 8);
+    // the store issued from this buffer two radii ago has read it
+    if (threadIdx.x == 0) bulk_wait_read1();
+    __syncthreads();
+    const float lo = __ldg(&sd.p.rlo32[s * 256 + l1]);
+    float2 v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const float rp = lo * __ldg(&sd.p.rhi32[s * 256 + t + 16 * q]);
+      const float2 x = ctile[swz16(t + 16 * q, g)];  // l2 = t + 16 q
+      v[q] = make_float2(x.x * rp, x.y * rp);
+    }
+    fft_run<float, L8, 1>(v, t, ob + g * S8::SMEM, sd.p.st32);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) ob[swz16(fft_out_index<float, L8>(t, e), g)] = cmul<float>(v[e], tw[e]);
     fence_proxy_async();
     __syncthreads();
-    if (threadIdx.x == 0) tma_store_2d(&maps.c, 16 * b, 0, tile);
-  } else {
-    // best two of the CTA's 4096 grid points (j = j2 + 256 j1)
-    float v1 = -1.f, v2 = -1.f;
-    int i1 = INT_MAX, i2 = INT_MAX;
+    if (threadIdx.x == 0) tma_store_2d_async(&maps.xs, 16 * a, s * 256, ob);
+  }
+  if (threadIdx.x == 0) bulk_wait_all();
+}
+
+// Grid pass 2 (see the file comment): items (s, b) = (i / 16, i mod 16), i =
+// blockIdx.x, + gridDim.x, ...
+__global__ void __launch_bounds__(kThreads)
+k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Maps maps) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ alignas(8) uint64_t bars[2];
+  __shared__ float rv1[16], rv2[16];
+  __shared__ int rj1[16], rj2[16];
+  __shared__ int s_last, s_ok;
+  pdl_launch_dependents();
+  const SlotDev& sd = slots[0];
+  float2* in = align1024(smem_raw);
+  float2* fbuf = in + 2 * kTileElems;
+  const int g = threadIdx.x >> 4, t = threadIdx.x & 15;
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0]);
+    mbar_init(&bars[1]);
+  }
+  __syncthreads();
+  pdl_wait();
+  if (ld_done(sd.ctl)) return;
+  const int items = 16 * sd.p.M;
+  // thread 0: the TMA load of this CTA's item number i into ring slot i mod 2
+  auto issue = [&](int i) {
+    const int item = (int)blockIdx.x + i * (int)gridDim.x;
+    if (item >= items) return;
+    mbar_expect_tx(&bars[i & 1], kTileBytes);
+    tma_load_2d(in + (i & 1) * kTileElems, &maps.xl, 0, (item >> 4) * 256 + 16 * (item & 15), &bars[i & 1]);
+  };
+  if (threadIdx.x == 0) {
+    issue(0);
+    issue(1);
+  }
+  int i = 0;
+  for (;; ++i) {
+    const int item = (int)blockIdx.x + i * (int)gridDim.x;
+    if (item >= items) break;
+    const int s = item >> 4, b = item & 15;
+    const int j2 = 16 * b + g;
+    const float2* tile = in + (i & 1) * kTileElems;
+    if (!cta_wait(&bars[i & 1], (i >> 1) & 1, &s_ok)) break;
+    float2 v[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const float o = v[e].x * v[e].x + v[e].y * v[e].y;
-      const int j = j2 + 256 * fft_out_index<float, L8>(t, e);
-      if (better2(o, j, v1, i1)) { v2 = v1; i2 = i1; v1 = o; i1 = j; }
-      else if (better2(o, j, v2, i2)) { v2 = o; i2 = j; }
-    }
+    for (int q = 0; q < 16; ++q) v[q] = tile[g * 256 + t + 16 * q];  // row j2, l1 = t + 16 q
+    __syncthreads();  // the slot is read: refill it
+    if (threadIdx.x == 0) issue(i + 2);
+    fft_run<float, L8, 1>(v, t, fbuf + g * S8::SMEM, sd.p.st32);
+    // best two of the item's 4096 grid points (j = j2 + 256 j1); a thread's
+    // outputs come in increasing j1 = t + 16 e
+    Best2F bb;
+    bb.init();
 #pragma unroll
-    for (int off = 8; off > 0; off >>= 1) {
-      const float ov1 = __shfl_xor_sync(0xffffffffu, v1, off), ov2 = __shfl_xor_sync(0xffffffffu, v2, off);
-      const int oi1 = __shfl_xor_sync(0xffffffffu, i1, off), oi2 = __shfl_xor_sync(0xffffffffu, i2, off);
-      if (better2(ov1, oi1, v1, i1)) {
-        if (better2(v1, i1, ov2, oi2)) { v2 = v1; i2 = i1; } else { v2 = ov2; i2 = oi2; }
-        v1 = ov1; i1 = oi1;
-      } else if (better2(ov1, oi1, v2, i2)) {
-        v2 = ov1; i2 = oi1;
-      }
+    for (int e = 0; e < 16; ++e) bb.push_ascending(v[e].x * v[e].x + v[e].y * v[e].y, j2 + 256 * (t + 16 * e));
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) bb.merge(bb.shfl(off));
+    if (t == 0) {
+      rv1[g] = bb.v1;
+      rv2[g] = bb.v2;
+      rj1[g] = bb.j1;
+      rj2[g] = bb.j2;
     }
-    if (t == 0) { rv1[g] = v1; rv2[g] = v2; rj1[g] = i1; rj2[g] = i2; }
     __syncthreads();
     if (threadIdx.x == 0) {
-      float b1 = -1.f, b2 = -1.f;
-      int k1 = INT_MAX, k2 = INT_MAX;
+      Best2F o;
+      o.init();
       for (int q = 0; q < 16; ++q) {
-        const float cand[2] = {rv1[q], rv2[q]};
-        const int cj[2] = {rj1[q], rj2[q]};
-        for (int u = 0; u < 2; ++u) {
-          if (better2(cand[u], cj[u], b1, k1)) { b2 = b1; k2 = k1; b1 = cand[u]; k1 = cj[u]; }
-          else if (better2(cand[u], cj[u], b2, k2)) { b2 = cand[u]; k2 = cj[u]; }
-        }
+        o.insert(rv1[q], rj1[q]);
+        o.insert(rv2[q], rj2[q]);
       }
       const float w2 = sd.p.wsq32[s];
-      Top2F o;
-      o.v1 = b1 * w2;
-      o.v2 = b2 * w2;
-      o.j1 = k1;
-      o.j2 = k2;
-      reinterpret_cast<Top2F*>(sd.top2)[s * 16 + b] = o;
-      if (o.v1 >= 0.0f && o.v1 <= 3.402823466e38f) atomicMax(&sd.ctl->vmax_bits, __float_as_uint(o.v1));
+      Top2F r;
+      r.v1 = o.v1 * w2;
+      r.v2 = o.v2 * w2;
+      r.j1 = o.j1;
+      r.j2 = o.j2;
+      reinterpret_cast<Top2F*>(sd.top2)[s * 16 + b] = r;
+      if (r.v1 >= 0.0f && r.v1 <= 3.402823466e38f) atomicMax(&sd.ctl->vmax_bits, __float_as_uint(r.v1));
     }
-    if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x * gridDim.y, &s_last)) return;
-    select_candidates_f32<kThreads>(sd, sd.ctl->k, 16);
   }
+  if ((int)blockIdx.x + i * (int)gridDim.x < items) {
+    // a load did not arrive: flag the signal and leave once the copies this
+    // CTA started have landed (bounded)
+    if (threadIdx.x == 0) {
+      atomicOr(&sd.ctl->err, 4);
+      sd.ctl->done = 1;
+      mbar_wait_bounded(&bars[i & 1], (i >> 1) & 1);
+      if ((int)blockIdx.x + (i + 1) * (int)gridDim.x < items) mbar_wait_bounded(&bars[(i + 1) & 1], ((i + 1) >> 1) & 1);
+    }
+    return;
+  }
+  if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
+  select_candidates_f32<kThreads>(sd, sd.ctl->k, 16);
 }
 
 cudaError_t fft2_configure() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_fft2_pass1<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_fft2_pass1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_fft2_pass2<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes)))
-    return e;
-  return cudaFuncSetAttribute(k_fft2_pass2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  const auto smem = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  const auto carve = cudaFuncAttributePreferredSharedMemoryCarveout;
+  if ((e = cudaFuncSetAttribute(k_fwd2_pass1, smem, (int)kSmemBytes))) return e;
+  if ((e = cudaFuncSetAttribute(k_fwd2_pass2, smem, (int)kSmemBytes))) return e;
+  if ((e = cudaFuncSetAttribute(k_grid2_pass1, smem, (int)kP1Smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_grid2_pass2, smem, (int)kP2Smem))) return e;
+  // two CTAs of either grid pass per SM
+  if ((e = cudaFuncSetAttribute(k_grid2_pass1, carve, (int)cudaSharedmemCarveoutMaxShared))) return e;
+  return cudaFuncSetAttribute(k_grid2_pass2, carve, (int)cudaSharedmemCarveoutMaxShared);
 }
 
 namespace {
 template <typename K>
-cudaError_t launch2(K kernel, dim3 grid, const SlotDev* slots, const Fft2Maps& maps, cudaStream_t st) {
+cudaError_t launch2(K kernel, dim3 grid, size_t smem, const SlotDev* slots, const Fft2Maps& maps,
+                    cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -280,18 +400,34 @@ cudaError_t launch2(K kernel, dim3 grid, const SlotDev* slots, const Fft2Maps& m
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, slots, maps);
 }
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || n < 1)
+      n = 1;
+  }
+  return n;
+}
 }  // namespace
 
 cudaError_t launch_grid2(const SlotDev* slots, const Fft2Maps& maps, int M, cudaStream_t st) {
-  cudaError_t e = launch2(k_fft2_pass1<0>, dim3(16, M), slots, maps, st);
+  // two CTAs per SM: pass 1 as 16 column blocks x R radius sets
+  const int ctas = 2 * sm_count();
+  int R = ctas / 16;
+  R = R < 1 ? 1 : (R > M ? M : R);
+  cudaError_t e = launch2(k_grid2_pass1, dim3(16 * R), kP1Smem, slots, maps, st);
   if (e != cudaSuccess) return e;
-  return launch2(k_fft2_pass2<0>, dim3(16, M), slots, maps, st);
+  const int items = 16 * M;
+  return launch2(k_grid2_pass2, dim3(items < ctas ? items : ctas), kP2Smem, slots, maps, st);
 }
 
 cudaError_t launch_forward2(const SlotDev* slots, const Fft2Maps& maps, cudaStream_t st) {
-  cudaError_t e = launch2(k_fft2_pass1<1>, dim3(16, 1), slots, maps, st);
+  cudaError_t e = launch2(k_fwd2_pass1, dim3(16), kSmemBytes, slots, maps, st);
   if (e != cudaSuccess) return e;
-  return launch2(k_fft2_pass2<1>, dim3(16, 1), slots, maps, st);
+  return launch2(k_fwd2_pass2, dim3(16), kSmemBytes, slots, maps, st);
 }
 
 namespace {

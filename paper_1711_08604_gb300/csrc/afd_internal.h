@@ -63,7 +63,8 @@ struct PlanDev {
   const double* w64;        // [M] w_s
   const double* sq64;       // [M] sqrt(1 - r_s^2)
   const double2* K64;       // [M * N] 1 / (1 - r_s exp(2 pi i d / N)), FP64
-  const float2* tw32n;      // [N] exp(+2 pi i k / N) in FP32 (two-pass and mixed-radix paths)
+  const float2* tw32n;      // [N] exp(+2 pi i k / N) in FP32 (two-pass and mixed-radix paths); two-pass:
+                            // followed by [4096] exp(+2 pi i m / 4096)
   double inv_n;             // 1 / N (exact for powers of two)
   int mix_npass;            // mixed-radix path (N not a power of two): passes and radices
   unsigned char mix_radix[MIXED_MAX_PASSES];

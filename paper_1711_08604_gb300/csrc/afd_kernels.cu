@@ -111,7 +111,10 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
     Best2F b;
     b.init();
 #pragma unroll
-    for (int e = 0; e < P; ++e) b.insert(v[e].x * v[e].x + v[e].y * v[e].y, fft_out_index<T, LOGN>(t, e));
+    for (int u = 0; u < P; ++u) {
+      const V2<T> x = v[fft_out_slot<T, LOGN>(u)];
+      b.push_ascending(x.x * x.x + x.y * x.y, t + TPF * u);
+    }
     group_reduce<TPF>(b, red);
     if (t == 0 && active) {
       const float w2 = sd.p.wsq32[s];
@@ -123,6 +126,7 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
       reinterpret_cast<Top2F*>(sd.top2)[s] = o;
       // objectives are >= 0, so their bit patterns order like the values
       if (o.v1 >= 0.0f && o.v1 <= 3.402823466e38f) atomicMax(&sd.ctl->vmax_bits, __float_as_uint(o.v1));
+      __threadfence();  // read by the signal's last CTA
     }
     if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
     select_candidates_f32<THREADS>(sd, sd.ctl->k);
@@ -131,7 +135,10 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
     Best1D b;
     b.init();
 #pragma unroll
-    for (int e = 0; e < P; ++e) b.insert(v[e].x * v[e].x + v[e].y * v[e].y, fft_out_index<T, LOGN>(t, e), v[e]);
+    for (int u = 0; u < P; ++u) {
+      const V2<T> x = v[fft_out_slot<T, LOGN>(u)];
+      b.push_ascending(x.x * x.x + x.y * x.y, t + TPF * u, x);
+    }
     group_reduce<TPF>(b, red);
     if (t == 0 && active) {
       const double w = sd.p.w64[s];
@@ -143,6 +150,7 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
       o.j2 = INT_MAX;
       o.f2 = make_double2(0.0, 0.0);
       reinterpret_cast<Top2D*>(sd.top2)[s] = o;
+      __threadfence();  // read by the signal's last CTA
     }
     if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
     __syncthreads();
@@ -617,7 +625,10 @@ k_persistent(const SlotDev* __restrict__ slots) {
       Best2F b;
       b.init();
 #pragma unroll
-      for (int e = 0; e < P; ++e) b.insert(v[e].x * v[e].x + v[e].y * v[e].y, fft_out_index<float, LOGN>(t, e));
+      for (int u = 0; u < P; ++u) {
+        const float2 x = v[fft_out_slot<float, LOGN>(u)];
+        b.push_ascending(x.x * x.x + x.y * x.y, t + TPF * u);
+      }
       group_reduce<TPF>(b, red2);
       if (t == 0 && active) {
         const float w2 = sd.p.wsq32[s];

@@ -170,7 +170,7 @@ size_t Tables::bytes_for(int N, int M) {
   size_t off = 0;
   for (size_t b : {sizeof(double) * M, 16 * (size_t)N, 16 * tws, 8 * tws, 8 * (size_t)M * B, 8 * (size_t)M * H,
                    4 * (size_t)M * B, 4 * (size_t)M * H, 4 * (size_t)M, 8 * (size_t)M, 8 * (size_t)M,
-                   16 * (size_t)M * N, sh.tw32n() ? 8 * (size_t)N : 0})
+                   16 * (size_t)M * N, sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0})
     off = align_up(off + b);
   return off;
 }
@@ -239,7 +239,7 @@ afd_status Tables::build(int N_, const double* r, int M_) {
                  o_rlo64 = place(8 * rlo64.size()), o_rhi64 = place(8 * rhi64.size()),
                  o_rlo32 = place(4 * rlo32.size()), o_rhi32 = place(4 * rhi32.size()),
                  o_wsq = place(4 * (size_t)M), o_w64 = place(8 * (size_t)M), o_sq = place(8 * (size_t)M),
-                 o_K = place(16 * (size_t)M * N), o_tw32n = place(sh.tw32n() ? 8 * (size_t)N : 0);
+                 o_K = place(16 * (size_t)M * N), o_tw32n = place(sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0);
     CUDA_TRY(cudaMalloc(&mem, off));
     bytes = off;
     char* b = static_cast<char*>(mem);
@@ -275,9 +275,14 @@ afd_status Tables::build(int N_, const double* r, int M_) {
     dev.mix_npass = sh.mix_npass;
     for (int i = 0; i < MIXED_MAX_PASSES; ++i) dev.mix_radix[i] = i < sh.mix_npass ? sh.mix_radix[i] : 0;
     if (sh.tw32n()) {
-      std::vector<float> tw32n(2 * (size_t)N);
+      const size_t extra = two_pass ? 4096 : 0;  // exp(2 pi i m / 4096) = w^(16 m)
+      std::vector<float> tw32n(2 * ((size_t)N + extra));
       for (size_t i = 0; i < 2 * (size_t)N; ++i) tw32n[i] = (float)tw64[i];
-      CUDA_TRY(cudaMemcpy(b + o_tw32n, tw32n.data(), 8 * (size_t)N, cudaMemcpyHostToDevice));
+      for (size_t m = 0; m < extra; ++m) {
+        tw32n[2 * (N + m)] = (float)tw64[2 * 16 * m];
+        tw32n[2 * (N + m) + 1] = (float)tw64[2 * 16 * m + 1];
+      }
+      CUDA_TRY(cudaMemcpy(b + o_tw32n, tw32n.data(), 4 * tw32n.size(), cudaMemcpyHostToDevice));
       dev.tw32n = reinterpret_cast<const float2*>(b + o_tw32n);
     }
     CUDA_TRY(launch_kernel_table(dev.radii, M, N, reinterpret_cast<double2*>(b + o_K), nullptr));
