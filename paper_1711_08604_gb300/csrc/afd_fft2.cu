@@ -253,20 +253,29 @@ k_grid2_pass1(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
   if (ld_done(sd.ctl)) return;
   if (!load_tile(ctile, &maps.c, 16 * a, 0, &bar, sd.ctl)) return;
   const int M = sd.p.M;
+  // r_s^l = lo[l1] hi[l2] of the next radius, fetched one radius ahead
+  float lo_n = 0.f, h_n[16];
+  auto fetch = [&](int s) {
+    if (s >= M) return;
+    lo_n = __ldg(&sd.p.rlo32[s * 256 + l1]);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) h_n[q] = __ldg(&sd.p.rhi32[s * 256 + t + 16 * q]);
+  };
+  fetch(r0);
   int it = 0;
   for (int s = r0; s < M; s += R, ++it) {
     float2* ob = obuf + (it & 1) * (kScratchBytes / 8);
     // the store issued from this buffer two radii ago has read it
     if (threadIdx.x == 0) bulk_wait_read1();
     __syncthreads();
-    const float lo = __ldg(&sd.p.rlo32[s * 256 + l1]);
     float2 v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const float rp = lo * __ldg(&sd.p.rhi32[s * 256 + t + 16 * q]);
+      const float rp = lo_n * h_n[q];
       const float2 x = ctile[swz16(t + 16 * q, g)];  // l2 = t + 16 q
       v[q] = make_float2(x.x * rp, x.y * rp);
     }
+    fetch(s + R);
     fft_run<float, L8, 1>(v, t, ob + g * S8::SMEM, sd.p.st32);
 #pragma unroll
     for (int e = 0; e < 16; ++e) ob[swz16(fft_out_index<float, L8>(t, e), g)] = cmul<float>(v[e], tw[e]);
@@ -283,8 +292,8 @@ __global__ void __launch_bounds__(kThreads)
 k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Maps maps) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ alignas(8) uint64_t bars[2];
-  __shared__ float rv1[16], rv2[16];
-  __shared__ int rj1[16], rj2[16];
+  __shared__ float rv1[kThreads / 32], rv2[kThreads / 32];
+  __shared__ int rj1[kThreads / 32], rj2[kThreads / 32];
   __shared__ int s_last, s_ok;
   pdl_launch_dependents();
   const SlotDev& sd = slots[0];
@@ -330,30 +339,38 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
     bb.init();
 #pragma unroll
     for (int e = 0; e < 16; ++e) bb.push_ascending(v[e].x * v[e].x + v[e].y * v[e].y, j2 + 256 * (t + 16 * e));
+    // the warp's two transforms, then the CTA's eight warps
 #pragma unroll
-    for (int off = 8; off > 0; off >>= 1) bb.merge(bb.shfl(off));
-    if (t == 0) {
-      rv1[g] = bb.v1;
-      rv2[g] = bb.v2;
-      rj1[g] = bb.j1;
-      rj2[g] = bb.j2;
+    for (int off = 16; off > 0; off >>= 1) bb.merge(bb.shfl(off));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+      rv1[warp] = bb.v1;
+      rv2[warp] = bb.v2;
+      rj1[warp] = bb.j1;
+      rj2[warp] = bb.j2;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
       Best2F o;
       o.init();
-      for (int q = 0; q < 16; ++q) {
-        o.insert(rv1[q], rj1[q]);
-        o.insert(rv2[q], rj2[q]);
+      if (lane < kThreads / 32) {
+        o.v1 = rv1[lane];
+        o.v2 = rv2[lane];
+        o.j1 = rj1[lane];
+        o.j2 = rj2[lane];
       }
-      const float w2 = sd.p.wsq32[s];
-      Top2F r;
-      r.v1 = o.v1 * w2;
-      r.v2 = o.v2 * w2;
-      r.j1 = o.j1;
-      r.j2 = o.j2;
-      reinterpret_cast<Top2F*>(sd.top2)[s * 16 + b] = r;
-      if (r.v1 >= 0.0f && r.v1 <= 3.402823466e38f) atomicMax(&sd.ctl->vmax_bits, __float_as_uint(r.v1));
+#pragma unroll
+      for (int off = 4; off > 0; off >>= 1) o.merge(o.shfl(off));
+      if (lane == 0) {
+        const float w2 = sd.p.wsq32[s];
+        Top2F r;
+        r.v1 = o.v1 * w2;
+        r.v2 = o.v2 * w2;
+        r.j1 = o.j1;
+        r.j2 = o.j2;
+        reinterpret_cast<Top2F*>(sd.top2)[s * 16 + b] = r;
+        if (r.v1 >= 0.0f && r.v1 <= 3.402823466e38f) atomicMax(&sd.ctl->vmax_bits, __float_as_uint(r.v1));
+      }
     }
   }
   if ((int)blockIdx.x + i * (int)gridDim.x < items) {
