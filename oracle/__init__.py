@@ -62,8 +62,10 @@ def _load():
         lib.oracle_energy.argtypes = [ctypes.c_int, _dp]
         lib.oracle_energy.restype = ctypes.c_double
         lib.oracle_decompose.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int,
-                                         ctypes.c_double, ctypes.c_int, _ip, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int,
                                          _dp, _dp, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp]
+        lib.oracle_kernel_norm2.argtypes = [ctypes.c_int, ctypes.c_double]
+        lib.oracle_kernel_norm2.restype = ctypes.c_double
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -133,9 +135,20 @@ def energy(G) -> float:
     return float(_load().oracle_energy(g.size, _p(g)))
 
 
+def kernel_norm2(N: int, r: float) -> float:
+    """(1/N) sum_m |e_a(z_m)|^2 at a grid point of radius r (direct sum)."""
+    v = _load().oracle_kernel_norm2(int(N), float(r))
+    if v < 0:
+        raise ValueError("oracle_kernel_norm2: bad arguments")
+    return v
+
+
 def decompose(G, radii, K_max: int, energy_tol: float = 0.0, force_a1_zero: bool = False,
-              forced_idx=None, compute_grid: bool = True) -> dict:
+              forced_idx=None, compute_grid: bool = True, renormalise: bool = False) -> dict:
     """Core AFD: K_max greedy steps (or until delta <= energy_tol).
+
+    ``renormalise`` selects by |<G_k, e_a>~|^2 / ||e_a||_N^2 (the discrete norm,
+    ``kernel_norm2``) instead of |<G_k, e_a>~|^2.
 
     ``forced_idx`` is an optional (K_max, 2) int array of grid indices (s, j)
     to use instead of the argmax (rows with s < 0 are free).  With
@@ -161,7 +174,7 @@ def decompose(G, radii, K_max: int, energy_tol: float = 0.0, force_a1_zero: bool
     E = np.zeros(K + 1)
     Gf = np.zeros_like(g)
     steps = _load().oracle_decompose(
-        g.size, _p(g), r.size, _p(r), K, float(energy_tol), int(bool(force_a1_zero)),
+        g.size, _p(g), r.size, _p(r), K, float(energy_tol), int(bool(force_a1_zero)), int(bool(renormalise)),
         fi.ctypes.data_as(_ip) if fi is not None else None, int(bool(compute_grid)),
         _p(a), _p(c), idx.ctypes.data_as(_ip), own.ctypes.data_as(_ip), _p(objmax), _p(obj2),
         _p(objused), _p(delta), _p(E), _p(Gf))

@@ -143,14 +143,32 @@ int oracle_grid(int N, const double* G, int M, const double* radii, double* A) {
   return 0;
 }
 
-/* Maximal selection on the grid (Step 2): index of the largest |A|^2, the
- * lowest flat index winning ties.  Also reports the largest value and the
- * largest value at any other position (for near-tie analysis). */
-static long argmax_grid(const cplx* A, long total, double* best, double* second) {
+/* Discrete squared norm (1/N) sum_m |e_a(z_m)|^2 of the normalised Szego
+ * kernel at the grid point a = r (angle 0); by rotation it is the same at
+ * every angle of the circle.  The continuous norm is 1; the discrete one
+ * exceeds it when r^N is not negligible. */
+double oracle_kernel_norm2(int N, double r) {
+  if (N <= 0 || !(r >= 0.0 && r < 1.0)) return -1.0;
+  cplx a = r;
+  double na = sqrt(1.0 - r * r), acc = 0.0;
+  for (int m = 0; m < N; ++m) {
+    cplx e = na / (1.0 - conj(a) * sample_point(m, N));
+    acc += creal(e * conj(e));
+  }
+  return acc / (double)N;
+}
+
+/* Maximal selection on the grid (Step 2): index of the largest objective,
+ * |A|^2, or |A|^2 / ||e_a||_N^2 when norm2 (one value per radius) is given
+ * (the renormalised selection), the lowest flat index winning ties.  Also
+ * reports the largest value and the largest value at any other position (for
+ * near-tie analysis). */
+static long argmax_grid(const cplx* A, long total, int N, const double* norm2, double* best, double* second) {
   long arg = 0;
   double b = -1.0, s2 = -1.0;
   for (long f = 0; f < total; ++f) {
     double v = creal(A[f] * conj(A[f]));
+    if (norm2) v /= norm2[f / N];
     if (v > b) {
       s2 = b;
       b = v;
@@ -201,6 +219,8 @@ double oracle_energy(int N, const double* G) {
  * Inputs: N samples of G (interleaved complex), M ascending radii in [0, 1),
  * K_max >= 1, energy_tol (stop once delta_k <= energy_tol; 0 disables).
  * force_a1_zero != 0 sets a_1 = 0 (requires radii[0] == 0; index (0, 0)).
+ * renormalise != 0 selects by |A|^2 / ||e_a||_N^2 (oracle_kernel_norm2) instead
+ * of |A|^2; the coefficient is <G_k, e_a>~ either way.
  * forced_idx (2*K_max ints, (s, j) per step, s < 0 meaning "free") makes a
  * step use the given grid point instead of the argmax; compute_grid == 0
  * skips the O(M N^2) grid (allowed only when every step is forced) and takes
@@ -210,15 +230,15 @@ double oracle_energy(int N, const double* G) {
  *   a_out[2k], coeff_out[2k]    a_k and <G_k, e_{a_k}>~ of the step used;
  *   idx_out[2k]                 (s, j) actually used;
  *   own_idx_out[2k]             the oracle's own argmax (-1 if no grid);
- *   objmax_out[k], obj2_out[k]  largest |A|^2 and largest at another point;
- *   objused_out[k]              |A|^2 at the point used;
+ *   objmax_out[k], obj2_out[k]  largest objective and largest at another point;
+ *   objused_out[k]              objective at the point used;
  *   delta_out[0..K]             delta_0 = 1, delta_k = E_{k+1} / E_1;
  *   energy_out[0..K]            E_1 .. E_{K+1};
  *   G_final                     G_{k+1} after the last step (2N doubles).
  * Returns the number of steps done (>= 1), or -1 on bad arguments.
  */
 int oracle_decompose(int N, const double* G, int M, const double* radii, int K_max,
-                     double energy_tol, int force_a1_zero, const int* forced_idx,
+                     double energy_tol, int force_a1_zero, int renormalise, const int* forced_idx,
                      int compute_grid, double* a_out, double* coeff_out, int* idx_out,
                      int* own_idx_out, double* objmax_out, double* obj2_out,
                      double* objused_out, double* delta_out, double* energy_out,
@@ -239,12 +259,15 @@ int oracle_decompose(int N, const double* G, int M, const double* radii, int K_m
   cplx* g = (cplx*)malloc(sizeof(cplx) * (size_t)N);
   cplx* A = compute_grid ? (cplx*)malloc(sizeof(cplx) * (size_t)total) : NULL;
   cplx* z = make_points(N);
-  if (!g || !z || (compute_grid && !A)) {
+  double* norm2 = renormalise ? (double*)malloc(sizeof(double) * (size_t)M) : NULL;
+  if (!g || !z || (compute_grid && !A) || (renormalise && !norm2)) {
     free(g);
     free(A);
     free(z);
+    free(norm2);
     return -1;
   }
+  for (int s = 0; renormalise && s < M; ++s) norm2[s] = oracle_kernel_norm2(N, radii[s]);
   memcpy(g, G, sizeof(cplx) * (size_t)N);
   double E1 = oracle_energy(N, (const double*)g);
   if (delta_out) delta_out[0] = 1.0;
@@ -257,7 +280,7 @@ int oracle_decompose(int N, const double* G, int M, const double* radii, int K_m
     long own = -1;
     if (compute_grid) {
       oracle_grid(N, (const double*)g, M, radii, (double*)A);
-      own = argmax_grid(A, total, &best, &second);
+      own = argmax_grid(A, total, N, norm2, &best, &second);
     }
     if (k == 0 && force_a1_zero) {
       s_used = 0;
@@ -269,6 +292,7 @@ int oracle_decompose(int N, const double* G, int M, const double* radii, int K_m
         free(g);
         free(A);
         free(z);
+        free(norm2);
         return -1;
       }
     } else {
@@ -278,6 +302,7 @@ int oracle_decompose(int N, const double* G, int M, const double* radii, int K_m
     cplx a = grid_point(radii[s_used], j_used, N);
     cplx c = compute_grid ? A[(long)s_used * N + j_used] : inner_with_table(N, g, z, a);
     double used = creal(c * conj(c));
+    if (norm2) used /= norm2[s_used];
 
     if (a_out) { a_out[2 * k] = creal(a); a_out[2 * k + 1] = cimag(a); }
     if (coeff_out) { coeff_out[2 * k] = creal(c); coeff_out[2 * k + 1] = cimag(c); }
@@ -302,5 +327,6 @@ int oracle_decompose(int N, const double* G, int M, const double* radii, int K_m
   free(g);
   free(A);
   free(z);
+  free(norm2);
   return steps;
 }

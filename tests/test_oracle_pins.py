@@ -217,3 +217,53 @@ def test_paper_tables_soft_pin(fname, signal, tol):
     d = oracle.decompose(signal(1024), W.radii_paper(), 10, force_a1_zero=True)
     got = d["delta"][1:11]
     assert np.max(np.abs(got - want)) <= tol
+
+
+# ----------------------------------------------- renormalised selection --
+# The discrete objective |<G, e_a>~|^2 is inflated at small N with r -> 1
+# because the discrete norm of e_a exceeds 1; the renormalised selection
+# divides it by ||e_a||_N^2 (the paper follows the continuous norm; this is the
+# optional reading of the discrete one).
+
+@pytest.mark.parametrize("N,r", [(8, 0.0), (16, 0.5), (32, 0.97), (64, 0.99), (256, 0.98), (1024, 0.8)])
+def test_kernel_norm_matches_geometric_series(N, r):
+    # (1/N) sum_m |e_a(z_m)|^2 for a on the grid sums the aliased geometric
+    # series of |e_a|^2 = (1 - r^2) sum_{l, l'} ...: (1 + r^N) / (1 - r^N)
+    assert abs(oracle.kernel_norm2(N, r) - (1 + r ** N) / (1 - r ** N)) <= 1e-13 * (1 + r ** N) / (1 - r ** N)
+
+
+def test_renormalised_selection_brute_force():
+    # On a small grid with radii near 1 the renormalised pick is the argmax of
+    # |A|^2 / ||e_a||^2 with the norm summed at every grid point, and differs
+    # from the plain pick.
+    N = 16
+    radii = np.array([0.0, 0.3, 0.6, 0.85, 0.93])
+    # e_b at r = 0.6 plus a weaker e_b at r = 0.93, whose plain objective is
+    # inflated by ||e_b||^2 = 1.91 at N = 16
+    b = np.array([0.6 * np.exp(2j * np.pi * 2 / N), 0.93 * np.exp(2j * np.pi * 10 / N)])
+    G = W.szego_sum(N, b, np.array([1.0, 0.5]))
+    A = oracle.grid(G, radii).reshape(radii.size, N)
+    z = np.exp(2j * np.pi * np.arange(N) / N)
+    norm2 = np.empty((radii.size, N))
+    for s, r in enumerate(radii):
+        for j in range(N):
+            a = r * np.exp(2j * np.pi * j / N)
+            e = np.sqrt(1 - r * r) / (1 - np.conj(a) * z)
+            norm2[s, j] = np.mean(e.real ** 2 + e.imag ** 2)
+    obj = (A.real ** 2 + A.imag ** 2) / norm2
+    want = np.unravel_index(int(np.argmax(obj)), obj.shape)
+    ren = oracle.decompose(G, radii, 1, renormalise=True)
+    plain = oracle.decompose(G, radii, 1)
+    assert tuple(ren["idx"][0]) == tuple(int(v) for v in want)
+    assert abs(ren["objused"][0] - obj[want]) <= 1e-12 * obj[want]
+    assert tuple(ren["idx"][0]) != tuple(plain["idx"][0])
+    assert ren["coeff"][0] == A[want]  # the coefficient is <G, e_a>~ itself
+
+
+def test_renormalised_equals_plain_when_rN_negligible():
+    s = W.paper_f1(1024)
+    radii = W.radii_paper()  # r <= 0.8: r^N ~ 1e-100
+    ren = oracle.decompose(s, radii, 6, renormalise=True)
+    plain = oracle.decompose(s, radii, 6)
+    assert np.array_equal(ren["idx"], plain["idx"])
+    assert np.allclose(ren["coeff"], plain["coeff"], rtol=1e-14, atol=0)
