@@ -71,6 +71,11 @@ typedef struct afd_plan_opts {
                           runs as one persistent cooperative kernel (bounded grid barriers
                           between the phases of a step); 0: one launch per kernel per step.
                           Results are identical either way.  Batches and serving ignore it. */
+  int renormalise;     /* 1: select by |<G_k, e_a>~|^2 / ||e_a||_N^2, the objective divided by
+                          the discrete norm (1 + r^N)/(1 - r^N) of the kernel at a grid point
+                          (the continuous norm of Sec. 2 is 1; the discrete one inflates the
+                          outer circles when r^N is not negligible).  The coefficient is
+                          <G_k, e_a>~ either way.  0 (default): the paper's objective. */
 } afd_plan_opts;
 
 typedef struct afd_plan afd_plan;

@@ -87,7 +87,7 @@ def _opts(opts=None, **kw) -> PlanOpts:
     for k, v in kw.items():
         if k == "stream" and v is not None and not isinstance(v, int):
             v = int(getattr(v, "cuda_stream", v))
-        if k in ("force_a1_zero", "use_graph", "persistent"):
+        if k in ("force_a1_zero", "use_graph", "persistent", "renormalise"):
             v = int(bool(v))
         setattr(o, k, v)
     return o

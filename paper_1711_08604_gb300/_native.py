@@ -19,7 +19,7 @@ P = ctypes.POINTER
 class PlanOpts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("guard_tau", c_double), ("guard_cap", c_int),
                 ("force_a1_zero", c_int), ("device", c_int), ("stream", c_void_p),
-                ("use_graph", c_int), ("persistent", c_int)]
+                ("use_graph", c_int), ("persistent", c_int), ("renormalise", c_int)]
 
 
 class Result(ctypes.Structure):

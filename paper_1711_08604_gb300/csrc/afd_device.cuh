@@ -374,7 +374,7 @@ __device__ void select_best_f64(const SlotDev& sd, int k, Best1D* red) {
     r.a_im = rr * z.y;
     r.c_re = w * b.f.x;
     r.c_im = w * b.f.y;
-    r.obj = r.c_re * r.c_re + r.c_im * r.c_im;
+    r.obj = (r.c_re * r.c_re + r.c_im * r.c_im) * obj_rho64(sd, s);
     r.obj32 = b.v;
   }
 }

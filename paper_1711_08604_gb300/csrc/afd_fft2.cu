@@ -362,7 +362,7 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
 #pragma unroll
       for (int off = 4; off > 0; off >>= 1) o.merge(o.shfl(off));
       if (lane == 0) {
-        const float w2 = sd.p.wsq32[s];
+        const float w2 = obj_w32(sd, s);
         Top2F r;
         r.v1 = o.v1 * w2;
         r.v2 = o.v2 * w2;

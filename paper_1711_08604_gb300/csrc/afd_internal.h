@@ -62,6 +62,8 @@ struct PlanDev {
   const float* wsq32;       // [M] w_s^2 with w_s = sqrt(1 - r_s^2) / (1 - r_s^N)
   const double* w64;        // [M] w_s
   const double* sq64;       // [M] sqrt(1 - r_s^2)
+  const double* rho64;      // [M] 1 / ||e_a||_N^2 = (1 - r_s^N) / (1 + r_s^N) (renormalised selection)
+  const float* rho32;       // [M] the same in FP32
   const double2* K64;       // [M * N] 1 / (1 - r_s exp(2 pi i d / N)), FP64
   const float2* tw32n;      // [N] exp(+2 pi i k / N) in FP32 (two-pass and mixed-radix paths); two-pass:
                             // followed by [4096] exp(+2 pi i m / 4096)
@@ -108,6 +110,7 @@ struct SlotDev {
   int prec;                 // 0: FP64 plain, 1: FP32 grid + FP64 guard
   int cap;                  // guard candidate cap
   int force_a1_zero;
+  int renorm;               // select by the objective times rho (renormalised)
   double tol;               // stop once delta <= tol (0: never)
   double tau;               // guard window: obj32 >= (1 - tau) * max32
   double E1_given;          // > 0: reference energy E_1 of a resumed decomposition
@@ -125,10 +128,18 @@ struct SlotDev {
   long long* phase_clk;     // persistent kernel, optional: 8 SM-clock stamps per step (CTA 0)
   unsigned* bar;            // persistent kernel: grid-barrier arrival counter (own 128-byte line)
 };
+// Selection weight of radius s: the FP32 objective weight w_s^2 and the FP64
+// factor applied to |c|^2, both times rho_s when the selection is renormalised.
+__device__ __forceinline__ float obj_w32(const SlotDev& sd, int s) {
+  const float w = sd.p.wsq32[s];
+  return sd.renorm ? w * sd.p.rho32[s] : w;
+}
+__device__ __forceinline__ double obj_rho64(const SlotDev& sd, int s) { return sd.renorm ? sd.p.rho64[s] : 1.0; }
+
 // Host-visible layout sizes (the bench reports per-step transfer bytes from them).
 static_assert(sizeof(StepRec) == 80, "StepRec layout");
 static_assert(sizeof(SlotCtl) == 64, "SlotCtl layout");
-static_assert(sizeof(SlotDev) == 304, "SlotDev layout");
+static_assert(sizeof(SlotDev) == 328, "SlotDev layout");
 
 // Kernel launchers (afd_kernels.cu).  `ids` lists the slots of one launch, all
 // with the same logN; `n` is their number.  Each returns the launch status.

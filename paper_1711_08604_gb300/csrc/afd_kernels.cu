@@ -117,7 +117,7 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
     }
     group_reduce<TPF>(b, red);
     if (t == 0 && active) {
-      const float w2 = sd.p.wsq32[s];
+      const float w2 = obj_w32(sd, s);
       Top2F o;
       o.v1 = b.v1 * w2;
       o.v2 = b.v2 * w2;
@@ -143,7 +143,7 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
     if (t == 0 && active) {
       const double w = sd.p.w64[s];
       Top2D o;
-      o.v1 = b.v * (w * w);
+      o.v1 = b.v * (w * w) * obj_rho64(sd, s);
       o.j1 = b.j;
       o.f1 = b.f;
       o.v2 = -1.0;
@@ -227,7 +227,7 @@ k_guard(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
   double bv = -1.0, bre = 0.0, bim = 0.0;
   for (int c = 0; c < n_cand; ++c) {
     const int2 cj = sd.cand[c];
-    const double v = s_re[c] * s_re[c] + s_im[c] * s_im[c];
+    const double v = (s_re[c] * s_re[c] + s_im[c] * s_im[c]) * obj_rho64(sd, cj.x);
     const int f = cj.x * N + cj.y, bf = bs * N + bj;
     if (bs < 0 || v > bv || (v == bv && f < bf)) {
       bs = cj.x; bj = cj.y; bv = v; bre = s_re[c]; bim = s_im[c];
@@ -631,7 +631,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
       }
       group_reduce<TPF>(b, red2);
       if (t == 0 && active) {
-        const float w2 = sd.p.wsq32[s];
+        const float w2 = obj_w32(sd, s);
         Top2F o;
         o.v1 = b.v1 * w2;
         o.v2 = b.v2 * w2;
@@ -719,7 +719,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
         const double re = sc * tot.x, im = sc * tot.y;
         s_re[c] = re;
         s_im[c] = im;
-        s_v[c] = re * re + im * im;
+        s_v[c] = (re * re + im * im) * obj_rho64(sd, s_cand[c].x);
       }
     }
     __syncthreads();

@@ -182,7 +182,7 @@ k_grid_mixed(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
     }
     group_reduce<MX_THREADS>(best, red);
     if (threadIdx.x == 0 && active) {
-      const float w2 = sd.p.wsq32[s];
+      const float w2 = obj_w32(sd, s);
       Top2F o;
       o.v1 = best.v1 * w2;
       o.v2 = best.v2 * w2;
@@ -214,7 +214,7 @@ k_grid_mixed(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
     if (threadIdx.x == 0 && active) {
       const double w = sd.p.w64[s];
       Top2D o;
-      o.v1 = best.v * (w * w);
+      o.v1 = best.v * (w * w) * obj_rho64(sd, s);
       o.j1 = best.j;
       o.f1 = best.f;
       o.v2 = -1.0;

@@ -170,7 +170,7 @@ size_t Tables::bytes_for(int N, int M) {
   size_t off = 0;
   for (size_t b : {sizeof(double) * M, 16 * (size_t)N, 16 * tws, 8 * tws, 8 * (size_t)M * B, 8 * (size_t)M * H,
                    4 * (size_t)M * B, 4 * (size_t)M * H, 4 * (size_t)M, 8 * (size_t)M, 8 * (size_t)M,
-                   16 * (size_t)M * N, sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0})
+                   8 * (size_t)M, 4 * (size_t)M, 16 * (size_t)M * N, sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0})
     off = align_up(off + b);
   return off;
 }
@@ -190,7 +190,8 @@ afd_status Tables::build(int N_, const double* r, int M_) {
         rlo64((size_t)M * B), rhi64((size_t)M * H);
     std::vector<float> st32(2 * (size_t)std::max(TWS, 1)), rlo32((size_t)M * B), rhi32((size_t)M * H),
         wsq32(M);
-    std::vector<double> w64(M), sq64(M);
+    std::vector<double> w64(M), sq64(M), rho64(M);
+    std::vector<float> rho32(M);
     const double two_pi = 6.283185307179586476925286766559;
     for (int k = 0; k < N; ++k) {
       // exact values at the quarter turns, libm elsewhere
@@ -229,6 +230,10 @@ afd_status Tables::build(int N_, const double* r, int M_) {
       const double one_m_rN = 1.0 - std::pow(rr, (double)N);
       sq64[s] = std::sqrt(one_m_r2);
       w64[s] = sq64[s] / one_m_rN;
+      // 1 / ||e_a||_N^2 at a grid point: the aliased geometric series gives
+      // ||e_a||_N^2 = (1 + r^N) / (1 - r^N)
+      rho64[s] = one_m_rN / (2.0 - one_m_rN);
+      rho32[s] = (float)rho64[s];
       wsq32[s] = (float)(one_m_r2 / (one_m_rN * one_m_rN));
     }
     // one allocation, 256-byte aligned sub-arrays (sizes as in Tables::bytes_for)
@@ -239,7 +244,7 @@ afd_status Tables::build(int N_, const double* r, int M_) {
                  o_rlo64 = place(8 * rlo64.size()), o_rhi64 = place(8 * rhi64.size()),
                  o_rlo32 = place(4 * rlo32.size()), o_rhi32 = place(4 * rhi32.size()),
                  o_wsq = place(4 * (size_t)M), o_w64 = place(8 * (size_t)M), o_sq = place(8 * (size_t)M),
-                 o_K = place(16 * (size_t)M * N), o_tw32n = place(sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0);
+                 o_rho64 = place(8 * (size_t)M), o_rho32 = place(4 * (size_t)M), o_K = place(16 * (size_t)M * N), o_tw32n = place(sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0);
     CUDA_TRY(cudaMalloc(&mem, off));
     bytes = off;
     char* b = static_cast<char*>(mem);
@@ -254,6 +259,8 @@ afd_status Tables::build(int N_, const double* r, int M_) {
     CUDA_TRY(cudaMemcpy(b + o_wsq, wsq32.data(), 4 * (size_t)M, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b + o_w64, w64.data(), 8 * (size_t)M, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b + o_sq, sq64.data(), 8 * (size_t)M, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_rho64, rho64.data(), 8 * (size_t)M, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b + o_rho32, rho32.data(), 4 * (size_t)M, cudaMemcpyHostToDevice));
     dev.N = N;
     dev.logN = logN;
     dev.M = M;
@@ -269,6 +276,8 @@ afd_status Tables::build(int N_, const double* r, int M_) {
     dev.wsq32 = reinterpret_cast<const float*>(b + o_wsq);
     dev.w64 = reinterpret_cast<const double*>(b + o_w64);
     dev.sq64 = reinterpret_cast<const double*>(b + o_sq);
+    dev.rho64 = reinterpret_cast<const double*>(b + o_rho64);
+    dev.rho32 = reinterpret_cast<const float*>(b + o_rho32);
     dev.K64 = reinterpret_cast<const double2*>(b + o_K);
     dev.tw32n = nullptr;
     dev.inv_n = 1.0 / (double)N;
@@ -399,6 +408,7 @@ struct SlotPool {
       d.prec = prec;
       d.cap = cap;
       d.force_a1_zero = o.force_a1_zero;
+      d.renorm = o.renormalise != 0;
       d.tol = 0.0;
       d.tau = o.guard_tau;
       d.G = reinterpret_cast<double2*>(b + o_G) + g_off[i] / 2;
@@ -761,6 +771,7 @@ void afd_plan_opts_default(afd_plan_opts* o) {
   if (!o) return;
   o->precision = AFD_FP32_GUARDED;
   o->guard_tau = 1e-4;
+  o->renormalise = 0;
   o->guard_cap = 16;
   o->force_a1_zero = 0;
   o->device = -1;

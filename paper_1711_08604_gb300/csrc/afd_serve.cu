@@ -270,6 +270,7 @@ struct afd_server {
       d.prec = prec;
       d.cap = cap;
       d.force_a1_zero = opts.force_a1_zero;
+      d.renorm = opts.renormalise != 0;
       d.tol = r.tol;
       d.tau = opts.guard_tau;
       d.G = reinterpret_cast<double2*>(b + L.G);

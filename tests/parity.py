@@ -25,7 +25,7 @@ ABS_FLOOR = 1e3 * np.finfo(np.float64).eps
 
 
 def check(G, radii, res, prec: int, *, full_grid=True, grid_steps=(), force_a1_zero=False,
-          energy_tol=0.0, coeff_tol=None):
+          energy_tol=0.0, coeff_tol=None, renormalise=False):
     """Compare a GPU result dict (afd_decompose output) with the oracle.
 
     full_grid=True recomputes the oracle grid at every step; otherwise only
@@ -40,7 +40,7 @@ def check(G, radii, res, prec: int, *, full_grid=True, grid_steps=(), force_a1_z
     idx = np.asarray(res["idx"]).reshape(steps, 2)
     tol = COEFF_TOL[prec] if coeff_tol is None else coeff_tol
     ora = oracle.decompose(G, radii, steps, energy_tol=0.0, force_a1_zero=force_a1_zero,
-                           forced_idx=idx, compute_grid=full_grid)
+                           forced_idx=idx, compute_grid=full_grid, renormalise=renormalise)
     E1 = ora["energy"][0]
     out = {"coeff_rel": 0.0, "delta_abs": 0.0, "a_abs": 0.0, "ties": 0}
     for k in range(steps):
@@ -69,8 +69,11 @@ def check(G, radii, res, prec: int, *, full_grid=True, grid_steps=(), force_a1_z
                 continue
             Gk = G if k == 0 else oracle.decompose(G, radii, k, force_a1_zero=force_a1_zero,
                                                     forced_idx=idx[:k], compute_grid=False)["G_final"]
-            A = oracle.grid(Gk, radii)
-            obj = (A.real ** 2 + A.imag ** 2).reshape(-1)
+            A = oracle.grid(Gk, radii).reshape(radii.size, G.size)
+            obj = A.real ** 2 + A.imag ** 2
+            if renormalise:
+                obj = obj / np.array([oracle.kernel_norm2(G.size, r) for r in radii])[:, None]
+            obj = obj.reshape(-1)
             f_own = int(np.argmax(obj))
             f_gpu = int(idx[k][0]) * G.size + int(idx[k][1])
             if f_gpu != f_own:
