@@ -286,6 +286,7 @@ typedef struct afd_serve_stats {
   long long kernel_launches;
   int queued, active;
   size_t bytes_reserved, bytes_in_use;
+  unsigned long long suspended;  /* slots moved to host memory by afd_serve_suspend */
 } afd_serve_stats;
 
 afd_status afd_serve_create(afd_server** out, size_t mem_budget_bytes, const afd_plan_opts* opts);
@@ -293,6 +294,20 @@ afd_status afd_serve_submit(afd_server* server, int N, const double* radii, int 
                             int K_max, double energy_tol, uint64_t* req_id);
 afd_status afd_serve_poll(afd_server* server, uint64_t req_id, afd_result* out);
 afd_status afd_serve_wait(afd_server* server, uint64_t req_id, double timeout_s, afd_result* out);
+/*
+ * Slot eviction (no counterpart in the paper, which runs one decomposition at
+ * a time).  afd_serve_suspend moves a request out of the device: a queued one
+ * leaves the queue; an active one leaves its slot at the next step boundary
+ * (its remainder G_k, step records and E_1 are copied to host memory and the
+ * slot's memory is freed for other requests); the call blocks until then, at
+ * most timeout_s seconds (AFD_ERR_TIMEOUT).  AFD_ERR_INVALID if the request
+ * has finished (its result stays available), AFD_ERR_NOT_FOUND if unknown.
+ * afd_serve_resume queues a suspended request again; its result is bitwise
+ * the one it would have had without the suspension.  Polling a suspended
+ * request returns AFD_PENDING.
+ */
+afd_status afd_serve_suspend(afd_server* server, uint64_t req_id, double timeout_s);
+afd_status afd_serve_resume(afd_server* server, uint64_t req_id);
 afd_status afd_serve_get_stats(afd_server* server, afd_serve_stats* out);
 afd_status afd_serve_destroy(afd_server* server);
 

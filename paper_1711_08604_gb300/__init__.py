@@ -28,7 +28,8 @@ __all__ = [
     "afd_decompose", "afd_decompose_from", "afd_plan_last_info", "afd_plan_set_profiling", "afd_plan_counters",
     "afd_plan_reset_counters", "afd_plan_get_stream", "afd_plan_kernel_times", "afd_plan_phase_cycles", "afd_batch_create", "afd_batch_run", "afd_batch_counters",
     "afd_batch_destroy", "afd_decompose_batch", "afd_synthesize", "afd_serve_create", "afd_serve_submit",
-    "afd_serve_poll", "afd_serve_wait", "afd_serve_get_stats", "afd_serve_destroy",
+    "afd_serve_poll", "afd_serve_wait", "afd_serve_suspend", "afd_serve_resume", "afd_serve_get_stats",
+    "afd_serve_destroy",
     "afd_inner_products_noalloc", "library_path",
 ]
 
@@ -383,6 +384,16 @@ def afd_serve_wait(server: Server, req_id: int, timeout_s: float = 60.0, K_cap: 
     out = _result_dict(res, bufs)
     _check(st, out)
     return out
+
+
+def afd_serve_suspend(server: Server, req_id: int, timeout_s: float = 60.0) -> None:
+    """Move a request out of the device (its state to host memory)."""
+    _check(_lib().afd_serve_suspend(server.handle, int(req_id), float(timeout_s)))
+
+
+def afd_serve_resume(server: Server, req_id: int) -> None:
+    """Queue a suspended request again; it continues where it stopped."""
+    _check(_lib().afd_serve_resume(server.handle, int(req_id)))
 
 
 def afd_serve_get_stats(server: Server) -> dict:

@@ -31,7 +31,8 @@ class ServeStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_ulonglong), ("completed", ctypes.c_ulonglong),
                 ("failed", ctypes.c_ulonglong), ("ticks", ctypes.c_ulonglong),
                 ("kernel_launches", c_ll), ("queued", c_int), ("active", c_int),
-                ("bytes_reserved", c_size_t), ("bytes_in_use", c_size_t)]
+                ("bytes_reserved", c_size_t), ("bytes_in_use", c_size_t),
+                ("suspended", ctypes.c_ulonglong)]
 
 
 # name -> (restype, argtypes)
@@ -65,6 +66,8 @@ SIGNATURES = {
     "afd_serve_submit": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_double, P(c_u64)]),
     "afd_serve_poll": (c_int, [c_void_p, c_u64, P(Result)]),
     "afd_serve_wait": (c_int, [c_void_p, c_u64, c_double, P(Result)]),
+    "afd_serve_suspend": (c_int, [c_void_p, ctypes.c_uint64, c_double]),
+    "afd_serve_resume": (c_int, [c_void_p, ctypes.c_uint64]),
     "afd_serve_get_stats": (c_int, [c_void_p, P(ServeStats)]),
     "afd_serve_destroy": (c_int, [c_void_p]),
     "afd_inner_products_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),

@@ -12,6 +12,12 @@
 //   retire  slots whose stop rule fired (delta <= tol or K steps): their step
 //           records are copied to the host, the request completes and the
 //           slot and its memory are reused by the next admission.
+//   evict   slots whose request was suspended (afd_serve_suspend): the
+//           remainder G_k, the step records and E_1 go to host memory and the
+//           slot is freed; afd_serve_resume queues the request again, and its
+//           admission restores that state (the initialisation recomputes the
+//           FP32 copy and the spectrum from G_k, with E_1 given), so the
+//           decomposition continues bit-identically.
 // Requests that arrive while others run join at the next tick, so their work
 // overlaps on the device.  A request computes exactly what afd_decompose
 // computes for it alone: the kernels, their work split (which depends on N
@@ -160,10 +166,12 @@ struct Request {
   uint64_t id = 0;
   int N = 0, K = 0;
   double tol = 0.0;
-  std::vector<double> radii, G;
-  int state = 0;  // 0 queued, 1 active, 2 done
+  std::vector<double> radii, G;  // G: the samples to start from (G_k after a suspension)
+  int state = 0;  // 0 queued, 1 active, 2 done, 3 suspended
+  bool suspend = false;  // asked to leave its slot at the next tick boundary
   afd_status status = AFD_OK;
-  int steps = 0;
+  int steps = 0;              // steps done (records in recs)
+  double E1 = 0.0;            // E_1 of a suspended decomposition (0: not started)
   std::vector<StepRec> recs;
   Clock::time_point t_submit, t_done;
 };
@@ -273,6 +281,7 @@ struct afd_server {
       d.renorm = opts.renormalise != 0;
       d.tol = r.tol;
       d.tau = opts.guard_tau;
+      d.E1_given = r.E1;  // > 0 when resuming
       d.G = reinterpret_cast<double2*>(b + L.G);
       d.g32 = prec ? reinterpret_cast<float2*>(b + L.g32) : nullptr;
       d.c32 = prec ? reinterpret_cast<float2*>(b + L.c) : nullptr;
@@ -287,7 +296,14 @@ struct afd_server {
       CUDA_TRY(cudaMemcpyAsync(slots_dev + si, slotdev_host + si, sizeof(SlotDev), cudaMemcpyHostToDevice,
                                stream));
       CUDA_TRY(cudaMemcpyAsync(d.G, r.G.data(), 16 * (size_t)r.N, cudaMemcpyHostToDevice, stream));
-      CUDA_TRY(cudaMemsetAsync(ctl_dev + si, 0, sizeof(SlotCtl), stream));
+      // control block: zero, or the step count of a resumed decomposition
+      // (its records go back to the slot)
+      ctl_host[si] = SlotCtl{};
+      ctl_host[si].k = r.steps;
+      CUDA_TRY(cudaMemcpyAsync(ctl_dev + si, ctl_host + si, sizeof(SlotCtl), cudaMemcpyHostToDevice, stream));
+      if (r.steps > 0)
+        CUDA_TRY(cudaMemcpyAsync(d.rec, r.recs.data(), sizeof(StepRec) * (size_t)r.steps, cudaMemcpyHostToDevice,
+                                 stream));
       Slot& sl = slots[si];
       sl.used = true;
       sl.fresh = true;
@@ -355,6 +371,57 @@ struct afd_server {
     std::lock_guard<std::mutex> lk(mu);
     st.ticks += 1;
     st.kernel_launches += launches;
+    return AFD_OK;
+  }
+
+  // Moves the slots of suspended requests to host memory (after retire: a
+  // request that finished in the last tick completes instead).
+  afd_status evict() {
+    std::vector<int> out;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (int i = 0; i < kMaxSlots; ++i) {
+        if (!slots[i].used) continue;
+        auto it = reqs.find(slots[i].req);
+        if (it != reqs.end() && it->second->suspend) out.push_back(i);
+      }
+    }
+    if (out.empty()) return AFD_OK;
+    std::vector<std::vector<double>> G(out.size());
+    std::vector<std::vector<StepRec>> R(out.size());
+    for (size_t q = 0; q < out.size(); ++q) {
+      const int i = out[q];
+      const Slot& sl = slots[i];
+      const int k = ctl_host[i].k;
+      const int N = slotdev_host[i].p.N;
+      G[q].resize(2 * (size_t)N);
+      R[q].resize((size_t)k);
+      CUDA_TRY(cudaMemcpyAsync(G[q].data(), slotdev_host[i].G, 16 * (size_t)N, cudaMemcpyDeviceToHost, stream));
+      if (k > 0)
+        CUDA_TRY(cudaMemcpyAsync(R[q].data(), static_cast<char*>(sl.block) + sl.L.rec, sizeof(StepRec) * k,
+                                 cudaMemcpyDeviceToHost, stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    std::lock_guard<std::mutex> lk(mu);
+    for (size_t q = 0; q < out.size(); ++q) {
+      const int i = out[q];
+      Slot& sl = slots[i];
+      auto it = reqs.find(sl.req);
+      if (it != reqs.end()) {
+        Request& r = *it->second;
+        r.G = std::move(G[q]);
+        r.recs = std::move(R[q]);
+        r.steps = ctl_host[i].k;
+        r.E1 = ctl_host[i].E1;
+        r.state = 3;
+        r.suspend = false;
+        st.suspended += 1;
+      }
+      arena.release(sl.block, sl.bytes);
+      sl = Slot{};
+      --n_active;
+    }
+    cv_done.notify_all();
     return AFD_OK;
   }
 
@@ -471,6 +538,7 @@ struct afd_server {
       }
       afd_status s = tick();
       if (s == AFD_OK) s = retire();
+      if (s == AFD_OK) s = evict();
       if (s != AFD_OK) fail_all(s);
     }
   }
@@ -608,6 +676,45 @@ afd_status afd_serve_wait(afd_server* s, uint64_t req_id, double timeout_s, afd_
     s->reqs.erase(it);
   }
   return fill_result(*r, out);
+}
+
+afd_status afd_serve_suspend(afd_server* s, uint64_t req_id, double timeout_s) {
+  if (!s) return set_error(AFD_ERR_INVALID, "server is NULL");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(req_id);
+  if (it == s->reqs.end()) return set_error(AFD_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)req_id);
+  Request& r = *it->second;
+  if (r.state == 3) return AFD_OK;
+  if (r.state == 2) return set_error(AFD_ERR_INVALID, "request %llu has finished", (unsigned long long)req_id);
+  if (r.state == 0) {  // still queued: nothing on the device yet
+    s->queue.erase(std::find(s->queue.begin(), s->queue.end(), req_id));
+    r.state = 3;
+    return AFD_OK;
+  }
+  r.suspend = true;
+  s->cv_work.notify_one();
+  auto pred = [&] {
+    auto i2 = s->reqs.find(req_id);
+    return i2 == s->reqs.end() || i2->second->state != 1;
+  };
+  const auto limit = std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0.0);
+  if (!s->cv_done.wait_for(lk, limit, pred)) return set_error(AFD_ERR_TIMEOUT, "request still in its slot");
+  auto i3 = s->reqs.find(req_id);
+  if (i3 == s->reqs.end() || i3->second->state == 2)
+    return set_error(AFD_ERR_INVALID, "request %llu finished before it could be suspended", (unsigned long long)req_id);
+  return AFD_OK;
+}
+
+afd_status afd_serve_resume(afd_server* s, uint64_t req_id) {
+  if (!s) return set_error(AFD_ERR_INVALID, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(req_id);
+  if (it == s->reqs.end()) return set_error(AFD_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)req_id);
+  if (it->second->state != 3) return set_error(AFD_ERR_INVALID, "request %llu is not suspended", (unsigned long long)req_id);
+  it->second->state = 0;
+  s->queue.push_back(req_id);
+  s->cv_work.notify_one();
+  return AFD_OK;
 }
 
 afd_status afd_serve_get_stats(afd_server* s, afd_serve_stats* out) {

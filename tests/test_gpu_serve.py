@@ -123,3 +123,62 @@ def test_budget_admits_in_waves():
     for s, o in zip(reqs, outs):
         one = alone(s.G, s.radii, s.K, 0.0)
         assert np.array_equal(o["coeff"], one["coeff"])
+
+
+def test_suspend_resume_is_bitwise():
+    # a long request is moved to host memory mid-run and resumed while others
+    # keep running; its result is the uninterrupted one
+    radii = W.radii_linear(128)
+    sigs = [W.random_signal(N, 900 + i) for i, N in enumerate([4096, 1024, 2048, 512])]
+    K = [200, 30, 30, 30]
+    alone = []
+    for G, k in zip(sigs, K):
+        plan = afd.afd_plan_create(G.size, radii)
+        alone.append(afd.afd_decompose(plan, G, k))
+        plan.close()
+    srv = afd.afd_serve_create(512 << 20)
+    ids = [afd.afd_serve_submit(srv, G, radii, k) for G, k in zip(sigs, K)]
+    import time
+    t0 = time.time()
+    while afd.afd_serve_get_stats(srv)["ticks"] < 10 and time.time() - t0 < 60:
+        time.sleep(0.001)  # running: 10 of its 200 steps at least
+    afd.afd_serve_suspend(srv, ids[0])
+    assert afd.afd_serve_poll(srv, ids[0]) is None  # pending while suspended
+    others = [afd.afd_serve_wait(srv, i, 60.0) for i in ids[1:]]
+    afd.afd_serve_resume(srv, ids[0])
+    first = afd.afd_serve_wait(srv, ids[0], 60.0)
+    stats = afd.afd_serve_get_stats(srv)
+    srv.close()
+    assert stats["suspended"] == 1
+    for got, want in zip([first] + others, alone):
+        assert got["steps"] == want["steps"]
+        for key in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(got[key], want[key]), key
+
+
+def test_suspend_queued_and_finished_requests():
+    radii = W.radii_linear(32)
+    srv = afd.afd_serve_create(64 << 20)
+    G = W.random_signal(256, 5)
+    i = afd.afd_serve_submit(srv, G, radii, 4)
+    o = afd.afd_serve_wait(srv, i, 60.0)
+    with pytest.raises(afd.AfdError) as e:
+        afd.afd_serve_suspend(srv, i)            # handed out already: unknown
+    assert e.value.status == -6
+    with pytest.raises(afd.AfdError) as e:
+        afd.afd_serve_resume(srv, 12345)
+    assert e.value.status == -6
+    j = afd.afd_serve_submit(srv, G, radii, 4)
+    try:
+        afd.afd_serve_suspend(srv, j)            # queued or running: leaves the device
+    except afd.AfdError as err:                  # or it finished first
+        assert err.status == -1
+        assert afd.afd_serve_wait(srv, j, 60.0)["steps"] == 4
+    else:
+        with pytest.raises(afd.AfdError):
+            afd.afd_serve_resume(srv, 999999)
+        afd.afd_serve_resume(srv, j)
+        r = afd.afd_serve_wait(srv, j, 60.0)
+        for key in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(r[key], o[key]), key
+    srv.close()
