@@ -16,6 +16,10 @@ What each function computes, with the paper passage it follows:
 * ``energy``  -- (1/N) sum |G(z_m)|^2, the discrete norm in the measure dt/2pi of Eq. (formula2).
 * ``decompose`` -- the greedy loop of Sec. 2 with the grid selection of Sec. 3.2
   (Step 2) and the relative error delta of Eq. (er).
+* ``kernel_norm2`` -- the discrete squared norm of e_a at a grid point (renormalised selection).
+* ``nu_inner``, ``nu_update``, ``nu_energy``, ``nu_decompose`` (``afd_oracle_nu.c``) --
+  the same on non-uniform samples z_m = exp(i theta_m) with quadrature weights
+  w_m (the remark after Step 2 of Sec. 3.2) and a grid of L equispaced angles.
 """
 from __future__ import annotations
 
@@ -27,7 +31,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "afd_oracle.c")
+_SRCS = [os.path.join(_HERE, "afd_oracle.c"), os.path.join(_HERE, "afd_oracle_nu.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -37,12 +41,12 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile ``afd_oracle.c`` into ``liboracle.so`` (gcc -O2, OpenMP, no fast-math, no FMA contraction)."""
+    """Compile the oracle sources into ``liboracle.so`` (gcc -O2, OpenMP, no fast-math, no FMA contraction)."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(f) for f in _SRCS)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -66,6 +70,14 @@ def _load():
                                          _dp, _dp, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp]
         lib.oracle_kernel_norm2.argtypes = [ctypes.c_int, ctypes.c_double]
         lib.oracle_kernel_norm2.restype = ctypes.c_double
+        lib.oracle_nu_inner.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
+        lib.oracle_nu_energy.argtypes = [ctypes.c_int, _dp, _dp]
+        lib.oracle_nu_energy.restype = ctypes.c_double
+        lib.oracle_nu_update.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, _dp]
+        lib.oracle_nu_decompose.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, _dp, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_double, _ip, ctypes.c_int,
+                                            _dp, _dp, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp]
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -180,6 +192,65 @@ def decompose(G, radii, K_max: int, energy_tol: float = 0.0, force_a1_zero: bool
         _p(objused), _p(delta), _p(E), _p(Gf))
     if steps < 0:
         raise ValueError("oracle_decompose: bad arguments")
+    return {"steps": steps, "a": a[:steps], "coeff": c[:steps], "idx": idx[:steps],
+            "own_idx": own[:steps], "objmax": objmax[:steps], "obj2": obj2[:steps],
+            "objused": objused[:steps], "delta": delta[: steps + 1], "energy": E[: steps + 1],
+            "G_final": Gf}
+
+
+# ------------------------------------------------------- non-uniform samples --
+
+def nu_inner(G, theta, w, a: complex) -> complex:
+    """sqrt(1-|a|^2) sum_m w_m G(z_m) / (1 - a conj(z_m)), z_m = exp(i theta_m)."""
+    g, t, ww = _cvec(G), _rvec(theta), _rvec(w)
+    out = np.zeros(2)
+    if _load().oracle_nu_inner(g.size, _p(g), _p(t), _p(ww), float(np.real(a)), float(np.imag(a)), _p(out)) != 0:
+        raise ValueError("oracle_nu_inner: bad arguments")
+    return complex(out[0], out[1])
+
+
+def nu_energy(G, w) -> float:
+    """sum_m w_m |G(z_m)|^2."""
+    g, ww = _cvec(G), _rvec(w)
+    return _load().oracle_nu_energy(g.size, _p(g), _p(ww))
+
+
+def nu_update(G, theta, a: complex, c: complex) -> np.ndarray:
+    """The Blaschke update of Sec. 2 at the points exp(i theta_m)."""
+    g, t = _cvec(G), _rvec(theta)
+    out = np.zeros_like(g)
+    if _load().oracle_nu_update(g.size, _p(g), _p(t), float(np.real(a)), float(np.imag(a)),
+                                float(np.real(c)), float(np.imag(c)), _p(out)) != 0:
+        raise ValueError("oracle_nu_update: bad arguments")
+    return out
+
+
+def nu_decompose(G, theta, w, radii, L: int, K_max: int, energy_tol: float = 0.0, forced_idx=None,
+                 compute_grid: bool = True) -> dict:
+    """Core AFD on non-uniform samples with a grid of L equispaced angles (flat
+    index s L + j); the same outputs as ``decompose``."""
+    g, t, ww, r = _cvec(G), _rvec(theta), _rvec(w), _rvec(radii)
+    K = int(K_max)
+    fi = None
+    if forced_idx is not None:
+        fi = np.full((K, 2), -1, dtype=np.int32)
+        f = np.asarray(forced_idx, dtype=np.int32).reshape(-1, 2)
+        fi[: min(K, f.shape[0])] = f[:K]
+        fi = np.ascontiguousarray(fi)
+    a = np.zeros(K, dtype=np.complex128)
+    c = np.zeros(K, dtype=np.complex128)
+    idx = np.zeros((K, 2), dtype=np.int32)
+    own = np.zeros((K, 2), dtype=np.int32)
+    objmax, obj2, objused = np.zeros(K), np.zeros(K), np.zeros(K)
+    delta, E = np.zeros(K + 1), np.zeros(K + 1)
+    Gf = np.zeros_like(g)
+    steps = _load().oracle_nu_decompose(
+        g.size, _p(g), _p(t), _p(ww), r.size, _p(r), int(L), K, float(energy_tol),
+        fi.ctypes.data_as(_ip) if fi is not None else None, int(bool(compute_grid)),
+        _p(a), _p(c), idx.ctypes.data_as(_ip), own.ctypes.data_as(_ip), _p(objmax), _p(obj2),
+        _p(objused), _p(delta), _p(E), _p(Gf))
+    if steps < 0:
+        raise ValueError("oracle_nu_decompose: bad arguments")
     return {"steps": steps, "a": a[:steps], "coeff": c[:steps], "idx": idx[:steps],
             "own_idx": own[:steps], "objmax": objmax[:steps], "obj2": obj2[:steps],
             "objused": objused[:steps], "delta": delta[: steps + 1], "energy": E[: steps + 1],

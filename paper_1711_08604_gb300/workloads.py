@@ -202,3 +202,58 @@ def paper_f2(N: int = 1024) -> np.ndarray:
 def random_signal(N: int, seed: int) -> np.ndarray:
     """Complex standard Gaussian samples (tests of small cases)."""
     return _cgauss(np.random.default_rng(seed), N)
+
+
+# ----------------------------------------------------- non-uniform samples --
+
+def nonuniform_angles(N: int, seed: int, jitter: float = 0.45) -> np.ndarray:
+    """N ascending angles in [0, 2 pi): 2 pi (m + jitter U_m) / N, U_m uniform
+    in (-1, 1) (seeded), kept ascending by jitter < 0.5."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(-1.0, 1.0, N)
+    t = 2.0 * np.pi * (np.arange(N) + 0.5 + jitter * u) / N
+    return np.sort(np.mod(t, 2.0 * np.pi))
+
+
+def trapezoid_weights(theta: np.ndarray) -> np.ndarray:
+    """Quadrature weights of the normalised measure dt / 2 pi on the circle:
+    half the arc to each neighbour, (theta_{m+1} - theta_{m-1}) / (4 pi),
+    cyclically; they sum to 1."""
+    t = np.asarray(theta, dtype=np.float64)
+    nxt = np.roll(t, -1)
+    nxt[-1] += 2.0 * np.pi
+    prv = np.roll(t, 1)
+    prv[0] -= 2.0 * np.pi
+    return (nxt - prv) / (4.0 * np.pi)
+
+
+def szego_sum_at(theta: np.ndarray, b: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """sum_j w_j sqrt(1-|b_j|^2) / (1 - conj(b_j) z) at z = exp(i theta)."""
+    z = np.exp(1j * np.asarray(theta, dtype=np.float64))
+    G = np.zeros(z.size, dtype=np.complex128)
+    for bj, wj in zip(np.atleast_1d(b), np.atleast_1d(w)):
+        G += wj * np.sqrt(1.0 - abs(bj) ** 2) / (1.0 - np.conj(bj) * z)
+    return G
+
+
+@dataclass
+class NonuniformSignal:
+    theta: np.ndarray
+    weights: np.ndarray
+    G: np.ndarray
+    radii: np.ndarray
+    L: int
+    K: int
+
+
+def nonuniform(item: int = 0, N: int = 3000, L: int = 1024, M: int = 64, K: int = 12) -> NonuniformSignal:
+    """Non-uniform sampling case: N jittered angles with trapezoid weights, a
+    grid of L equispaced angles and M radii i/M; G = 3..12 Szego kernels with
+    |b| <= 0.9 (area-uniform) and complex Gaussian weights, plus complex noise
+    1e-3."""
+    rng = np.random.default_rng(6000 + item)
+    theta = nonuniform_angles(N, 6500 + item)
+    q = int(rng.integers(3, 13))
+    b = 0.9 * np.sqrt(rng.uniform(0, 1, q)) * np.exp(2j * np.pi * rng.uniform(0, 1, q))
+    G = szego_sum_at(theta, b, _cgauss(rng, q)) + 1e-3 * _cgauss(rng, N)
+    return NonuniformSignal(theta, trapezoid_weights(theta), G, radii_linear(M), L, K)

@@ -267,3 +267,68 @@ def test_renormalised_equals_plain_when_rN_negligible():
     plain = oracle.decompose(s, radii, 6)
     assert np.array_equal(ren["idx"], plain["idx"])
     assert np.allclose(ren["coeff"], plain["coeff"], rtol=1e-14, atol=0)
+
+
+# ------------------------------------------------------ non-uniform samples --
+# The weighted rectangle rule on z_m = exp(i theta_m) (the remark after Step 2
+# of Sec. 3.2), a grid of L equispaced angles.
+
+def test_nonuniform_oracle_reduces_to_uniform():
+    s = W.kernel_sum(item=1)
+    N = s.N
+    theta = 2 * np.pi * np.arange(N) / N
+    w = np.full(N, 1.0 / N)
+    nu = oracle.nu_decompose(s.G, theta, w, s.radii, N, 6)
+    un = oracle.decompose(s.G, s.radii, 6)
+    assert np.array_equal(nu["idx"], un["idx"])
+    assert np.max(np.abs(nu["coeff"] - un["coeff"])) <= 1e-13 * np.max(np.abs(un["coeff"]))
+    assert np.max(np.abs(nu["delta"] - un["delta"])) <= 1e-13
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_nonuniform_inner_equals_series_route(seed):
+    # 1/(1 - a conj(z)) = sum_l a^l conj(z)^l for |a| < 1: the inner product is
+    # sqrt(1 - |a|^2) sum_l a^l c_l with c_l = sum_m w_m G(z_m) exp(-i l theta_m)
+    # (the non-uniform DFT the GPU route folds onto L angles)
+    N = 37
+    theta = W.nonuniform_angles(N, 10 + seed)
+    w = W.trapezoid_weights(theta)
+    G = W.random_signal(N, 40 + seed)
+    l = np.arange(4000)
+    c = (np.exp(-1j * np.outer(l, theta)) * (w * G)[None, :]).sum(axis=1)
+    for a in (0.0, 0.5 * np.exp(1j), 0.97 * np.exp(-2.5j)):
+        series = np.sqrt(1 - abs(a) ** 2) * np.sum(a ** l * c)
+        assert abs(oracle.nu_inner(G, theta, w, a) - series) <= 1e-12 * max(1.0, abs(series))
+
+
+def test_nonuniform_weights_sum_to_one_and_update_keeps_modulus():
+    N = 50
+    theta = W.nonuniform_angles(N, 3)
+    w = W.trapezoid_weights(theta)
+    assert abs(w.sum() - 1.0) <= 1e-14
+    G = W.random_signal(N, 4)
+    a = 0.8 * np.exp(0.7j)
+    c = oracle.nu_inner(G, theta, w, a)
+    G1 = oracle.nu_update(G, theta, a, c)
+    # |(1 - conj(a) z) / (z - a)| = 1 on the circle: the energy after the
+    # update is that of G - c e_a
+    z = np.exp(1j * theta)
+    r = G - c * np.sqrt(1 - abs(a) ** 2) / (1 - np.conj(a) * z)
+    assert abs(oracle.nu_energy(G1, w) - np.sum(w * np.abs(r) ** 2)) <= 1e-13 * np.sum(w * np.abs(r) ** 2)
+
+
+def test_nonuniform_brute_force_argmax():
+    N, L = 29, 16
+    theta = W.nonuniform_angles(N, 8)
+    w = W.trapezoid_weights(theta)
+    G = W.random_signal(N, 9)
+    radii = np.array([0.0, 0.4, 0.7, 0.9])
+    best, arg = -1.0, None
+    for s, r in enumerate(radii):
+        for j in range(L):
+            c = oracle.nu_inner(G, theta, w, r * np.exp(2j * np.pi * j / L))
+            v = c.real * c.real + c.imag * c.imag
+            if v > best:
+                best, arg = v, (s, j)
+    d = oracle.nu_decompose(G, theta, w, radii, L, 1)
+    assert tuple(d["idx"][0]) == arg and d["objmax"][0] == best
