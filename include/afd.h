@@ -114,6 +114,33 @@ const char* afd_version(void);
 afd_status afd_plan_create(afd_plan** out, int N, const double* radii, int M,
                            const afd_plan_opts* opts);
 
+/*
+ * Plan for non-uniform samples (the remark after Step 2 of the algorithm of
+ * Sec. 3.2: the method holds for non-uniform sampling through non-uniform
+ * DFTs).  The signal is known at z_m = exp(i theta_m), m < N, with quadrature
+ * weights w_m of the normalised measure dt / 2 pi, and the rectangle rule of
+ * Eq. (formula1) becomes
+ *     <G, e_a>~ = sqrt(1 - |a|^2) sum_m w_m G(z_m) / (1 - a conj(z_m));
+ * the grid keeps L equispaced angles, a_{s,j} = r_s exp(2 pi i j / L); the
+ * energy is sum_m w_m |G(z_m)|^2.
+ *   N        1 <= N <= 2^20 samples.
+ *   theta    host array of N angles, strictly ascending in [0, 2 pi); copied.
+ *   weights  host array of N positive weights (normally summing to 1), or
+ *            NULL for the trapezoid rule (theta_{m+1} - theta_{m-1}) / (4 pi),
+ *            cyclic; copied.
+ *   L        grid angles, a power of two, 8 <= L <= 8192.
+ *   radii, M as for afd_plan_create; every radius needs r^(64 L) <= 2^-64
+ *            (at most 64 folds of the non-uniform DFT onto L angles), else
+ *            AFD_ERR_INVALID: use more angles.
+ *   opts     the FP32-guarded precision only; force_a1_zero and renormalise
+ *            are not supported; persistent is ignored.
+ * afd_decompose / afd_decompose_from then take G as N samples at theta and
+ * return a_k on the L-angle grid (idx: (s, j), j < L).  Errors as
+ * afd_plan_create.
+ */
+afd_status afd_plan_create_nonuniform(afd_plan** out, int N, const double* theta, const double* weights, int L,
+                                      const double* radii, int M, const afd_plan_opts* opts);
+
 /* Frees the plan and its device memory.  NULL is accepted. */
 afd_status afd_plan_destroy(afd_plan* plan);
 

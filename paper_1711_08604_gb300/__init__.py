@@ -23,6 +23,7 @@ from . import _native
 from ._native import PlanOpts
 
 __all__ = [
+    "afd_plan_create_nonuniform",
     "AFD_FP64_PLAIN", "AFD_FP32_GUARDED", "AfdError", "PlanOpts", "afd_plan_opts_default",
     "afd_status_str", "afd_last_error", "afd_version", "afd_plan_create", "afd_plan_destroy",
     "afd_decompose", "afd_decompose_from", "afd_plan_last_info", "afd_plan_set_profiling", "afd_plan_counters",
@@ -145,6 +146,20 @@ def afd_plan_create(N: int, radii, opts: PlanOpts | None = None, **kw) -> Plan:
     h = ctypes.c_void_p()
     _check(_lib().afd_plan_create(ctypes.byref(h), int(N), r.ctypes.data, int(r.size), ctypes.byref(o)))
     return Plan(h, int(N), int(r.size), o)
+
+
+def afd_plan_create_nonuniform(theta, radii, L: int, weights=None, opts: PlanOpts | None = None, **kw) -> Plan:
+    """Plan for samples at exp(i theta_m) (ascending angles in [0, 2 pi)) with
+    quadrature weights (None: the trapezoid rule) and a grid of L angles."""
+    t = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    r = np.ascontiguousarray(np.asarray(radii, dtype=np.float64))
+    w = None if weights is None else np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    o = _opts(opts, **kw)
+    h = ctypes.c_void_p()
+    _check(_lib().afd_plan_create_nonuniform(ctypes.byref(h), int(t.size), t.ctypes.data,
+                                             None if w is None else w.ctypes.data, int(L), r.ctypes.data,
+                                             int(r.size), ctypes.byref(o)))
+    return Plan(h, int(t.size), int(r.size), o)
 
 
 def afd_plan_destroy(plan: Plan) -> None:

@@ -42,6 +42,8 @@ SIGNATURES = {
     "afd_last_error": (c_char_p, []),
     "afd_version": (c_char_p, []),
     "afd_plan_create": (c_int, [P(c_void_p), c_int, c_void_p, c_int, P(PlanOpts)]),
+    "afd_plan_create_nonuniform": (c_int, [P(c_void_p), c_int, c_void_p, c_void_p, c_int, c_void_p, c_int,
+                                           P(PlanOpts)]),
     "afd_plan_destroy": (c_int, [c_void_p]),
     "afd_decompose": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_void_p]),

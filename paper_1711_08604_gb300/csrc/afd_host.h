@@ -55,16 +55,25 @@ struct DeviceScope {
 
 // Device tables of one (N, radii) pair (see afd_runtime.cu).
 struct Tables {
-  int N = 0, M = 0;
+  int N = 0, M = 0;  // N: grid angles (and samples, unless non-uniform)
   std::vector<double> radii;
   void* mem = nullptr;
   size_t bytes = 0;
   PlanDev dev{};
+  // non-uniform samples: nN samples at exp(i theta_m), spectrum length nLc
+  bool nu = false;
+  int nN = 0, nLc = 0;
+  void* nu_mem = nullptr;
   Tables() = default;
   Tables(const Tables&) = delete;
   Tables& operator=(const Tables&) = delete;
   ~Tables();
   afd_status build(int N, const double* radii, int M);
+  // grid of L angles; samples theta[nN] (ascending in [0, 2 pi)) with
+  // weights w[nN] (NULL: the trapezoid rule)
+  afd_status build_nu(int nN, const double* theta, const double* w, int L, const double* radii, int M);
+  int samples() const { return nu ? nN : N; }
+  int spectrum() const { return nu ? nLc : N; }
   static size_t bytes_for(int N, int M);  // device bytes build() allocates
 };
 

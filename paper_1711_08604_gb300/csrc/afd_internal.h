@@ -68,6 +68,15 @@ struct PlanDev {
   const float2* tw32n;      // [N] exp(+2 pi i k / N) in FP32 (two-pass and mixed-radix paths); two-pass:
                             // followed by [4096] exp(+2 pi i m / 4096)
   double inv_n;             // 1 / N (exact for powers of two)
+  // Non-uniform samples (nN > 0): the grid has N angles; the signal is known
+  // at exp(i theta_m), m < nN, with quadrature weights w_m (sum 1)
+  int nN;                   // number of samples (0: the N equispaced samples)
+  int nLc;                  // length of the non-uniform DFT: the most folds of any radius x N
+  const double2* nz64;      // [nN] exp(i theta_m)
+  const double* nw64;       // [nN] w_m
+  const unsigned long long* nU;  // [nN] theta_m / 2 pi as a 64-bit fixed-point fraction
+  const int* nP;            // [M] folds of radius s: r_s^(nP N) <= 2^-64
+  const float* nrN32;       // [M] r_s^N in FP32
   int mix_npass;            // mixed-radix path (N not a power of two): passes and radices
   unsigned char mix_radix[MIXED_MAX_PASSES];
 };
@@ -139,7 +148,7 @@ __device__ __forceinline__ double obj_rho64(const SlotDev& sd, int s) { return s
 // Host-visible layout sizes (the bench reports per-step transfer bytes from them).
 static_assert(sizeof(StepRec) == 80, "StepRec layout");
 static_assert(sizeof(SlotCtl) == 64, "SlotCtl layout");
-static_assert(sizeof(SlotDev) == 328, "SlotDev layout");
+static_assert(sizeof(SlotDev) == 376, "SlotDev layout");
 
 // Kernel launchers (afd_kernels.cu).  `ids` lists the slots of one launch, all
 // with the same logN; `n` is their number.  Each returns the launch status.
@@ -156,6 +165,13 @@ cudaError_t launch_grid_mixed(const SlotDev* slots, const int* ids, int n, int N
                               cudaStream_t st);
 cudaError_t launch_forward_mixed(const SlotDev* slots, const int* ids, int n, int N, int prec, cudaStream_t st);
 cudaError_t mixed_configure();
+// Non-uniform samples (afd_nu.cu), single-signal FP32-path plans.
+constexpr int NU_MIN_LOGN = 3, NU_MAX_LOGN = 13, NU_MAX_FOLDS = 64;
+cudaError_t launch_nudft(const SlotDev* slots, const int* ids, int Lc, cudaStream_t st);
+cudaError_t launch_grid_nu(const SlotDev* slots, const int* ids, int logN, int M, cudaStream_t st);
+cudaError_t launch_guard_nu(const SlotDev* slots, const int* ids, int nN, int cap, cudaStream_t st);
+cudaError_t launch_update_nu(const SlotDev* slots, const int* ids, int nN, bool init, cudaStream_t st);
+cudaError_t nu_configure();
 size_t mixed_smem_bytes(int N, int prec);
 cudaError_t launch_forward(const SlotDev* slots, const int* ids, int n, int logN, int prec,
                            cudaStream_t st);

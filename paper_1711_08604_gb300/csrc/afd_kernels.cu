@@ -871,6 +871,7 @@ cudaError_t configure_kernels() {
 #undef X
   if ((e = set_attrs<float, 14>()) != cudaSuccess) return e;
   if ((e = mixed_configure()) != cudaSuccess) return e;
+  if ((e = nu_configure()) != cudaSuccess) return e;
   return fft2_configure();
 }
 

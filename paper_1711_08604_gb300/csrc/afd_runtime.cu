@@ -139,6 +139,69 @@ afd_status normalise_opts(const afd_plan_opts* in, afd_plan_opts& o, int& dev) {
 
 Tables::~Tables() {
   if (mem) cudaFree(mem);
+  if (nu_mem) cudaFree(nu_mem);
+}
+
+afd_status Tables::build_nu(int nN_, const double* theta, const double* w, int L, const double* r, int M_) {
+  AFD_TRY(build(L, r, M_));
+  nu = true;
+  nN = nN_;
+  const double two_pi = 6.283185307179586476925286766559;
+  // folds per radius: r^(P L) <= 2^-64
+  std::vector<int> P(M);
+  std::vector<float> rN32(M), wsq(M);
+  int Pmax = 1;
+  for (int s = 0; s < M; ++s) {
+    const double rr = radii[s];
+    int f = 1;
+    if (rr > 0.0) f = (int)std::ceil(64.0 * std::log(2.0) / ((double)L * -std::log(rr)));
+    f = std::max(f, 1);
+    if (f > NU_MAX_FOLDS)
+      return set_error(AFD_ERR_INVALID, "radius %g needs %d folds of %d angles (at most %d): use more angles", rr, f,
+                       L, NU_MAX_FOLDS);
+    P[s] = f;
+    Pmax = std::max(Pmax, f);
+    rN32[s] = (float)std::pow(rr, (double)L);
+    wsq[s] = (float)((1.0 - rr) * (1.0 + rr));  // objective weight: (1 - r^2) |F|^2
+  }
+  nLc = Pmax * L;
+  std::vector<double> z(2 * (size_t)nN), ww(nN);
+  std::vector<unsigned long long> U(nN);
+  for (int m = 0; m < nN; ++m) {
+    z[2 * m] = std::cos(theta[m]);
+    z[2 * m + 1] = std::sin(theta[m]);
+    if (w) {
+      ww[m] = w[m];
+    } else {  // half the arc to each neighbour, cyclically
+      const double nxt = m + 1 < nN ? theta[m + 1] : theta[0] + two_pi;
+      const double prv = m > 0 ? theta[m - 1] : theta[nN - 1] - two_pi;
+      ww[m] = (nxt - prv) / (2.0 * two_pi);
+    }
+    const double frac = theta[m] / two_pi;  // in [0, 1)
+    U[m] = (unsigned long long)std::ldexp(frac, 64);
+  }
+  size_t off = 0;
+  auto place = [&](size_t b) { size_t o = off; off = align_up(off + b); return o; };
+  const size_t o_z = place(16 * (size_t)nN), o_w = place(8 * (size_t)nN), o_U = place(8 * (size_t)nN),
+               o_P = place(4 * (size_t)M), o_rN = place(4 * (size_t)M), o_wsq = place(4 * (size_t)M);
+  CUDA_TRY(cudaMalloc(&nu_mem, off));
+  bytes += off;
+  char* b = static_cast<char*>(nu_mem);
+  CUDA_TRY(cudaMemcpy(b + o_z, z.data(), 16 * (size_t)nN, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b + o_w, ww.data(), 8 * (size_t)nN, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b + o_U, U.data(), 8 * (size_t)nN, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b + o_P, P.data(), 4 * (size_t)M, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b + o_rN, rN32.data(), 4 * (size_t)M, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b + o_wsq, wsq.data(), 4 * (size_t)M, cudaMemcpyHostToDevice));
+  dev.nN = nN;
+  dev.nLc = nLc;
+  dev.nz64 = reinterpret_cast<const double2*>(b + o_z);
+  dev.nw64 = reinterpret_cast<const double*>(b + o_w);
+  dev.nU = reinterpret_cast<const unsigned long long*>(b + o_U);
+  dev.nP = reinterpret_cast<const int*>(b + o_P);
+  dev.nrN32 = reinterpret_cast<const float*>(b + o_rN);
+  dev.wsq32 = reinterpret_cast<const float*>(b + o_wsq);
+  return AFD_OK;
 }
 
 // Shape of a plan's tables: the power-table split r^l = lo[l mod B] hi[l div B]
@@ -321,7 +384,11 @@ struct SlotPool {
   double2* G_dev = nullptr;         // packed remainders
   StepRec* rec_host = nullptr;      // pinned mirrors
   SlotCtl* ctl_host = nullptr;
-  struct Group { int N, logN, first, count, Mmax; };  // logN = -1: mixed-radix N
+  struct Group {
+    int N, logN, first, count, Mmax;  // logN = -1: mixed-radix N
+    bool nu;                          // non-uniform samples (single-signal plans)
+    int nN, nLc;
+  };
   std::vector<Group> groups;
   std::vector<Fft2Maps> maps;       // TMA descriptors of two-pass slots (N = 65536)
   bool persistent = false;          // single FP32 slot: one persistent launch per decomposition
@@ -352,8 +419,10 @@ struct SlotPool {
     groups.clear();
     for (int idx = 0; idx < n; ++idx) {
       const int i = order[idx];
-      const int Ni = tables[i]->N;
-      if (groups.empty() || groups.back().N != Ni) groups.push_back({Ni, is_pow2(Ni) ? ilog2(Ni) : -1, idx, 0, 0});
+      const Tables& T = *tables[i];
+      const int Ni = T.N;
+      if (groups.empty() || groups.back().N != Ni || groups.back().nu != T.nu)
+        groups.push_back({Ni, is_pow2(Ni) ? ilog2(Ni) : -1, idx, 0, 0, T.nu, T.nN, T.nLc});
       groups.back().count++;
       groups.back().Mmax = std::max(groups.back().Mmax, tables[i]->M);
     }
@@ -362,16 +431,16 @@ struct SlotPool {
     g_total = 0;
     for (int i = 0; i < n; ++i) {
       g_off[i] = g_total;
-      g_total += 2 * (size_t)tables[i]->N;
+      g_total += 2 * (size_t)tables[i]->samples();
     }
     size_t off = 0;
     auto place = [&](size_t bytes) { size_t o2 = off; off = align_up(off + bytes); return o2; };
     const size_t o_G = place(8 * g_total);
     std::vector<size_t> o_c(n), o_g32(n), o_top(n), o_cand(n), o_gp(n), o_ep(n), o_X(n);
     for (int i = 0; i < n; ++i) {
-      const int N = tables[i]->N, M = tables[i]->M;
-      const bool two_pass = N == (1 << TWO_PASS_LOGN);
-      o_c[i] = place((prec ? 8 : 16) * (size_t)N);
+      const int N = tables[i]->samples(), M = tables[i]->M;
+      const bool two_pass = !tables[i]->nu && N == (1 << TWO_PASS_LOGN);
+      o_c[i] = place((prec ? 8 : 16) * (size_t)tables[i]->spectrum());
       o_g32[i] = place(prec ? 8 * (size_t)N : 0);
       o_X[i] = place(two_pass ? 8 * (size_t)M * N : 0);
       // two-pass: one best pair per (radius, 16-row block of pass 2)
@@ -414,7 +483,7 @@ struct SlotPool {
       d.G = reinterpret_cast<double2*>(b + o_G) + g_off[i] / 2;
       d.c32 = prec ? reinterpret_cast<float2*>(b + o_c[i]) : nullptr;
       d.g32 = prec ? reinterpret_cast<float2*>(b + o_g32[i]) : nullptr;
-      d.X = tables[i]->N == (1 << TWO_PASS_LOGN) ? reinterpret_cast<float2*>(b + o_X[i]) : nullptr;
+      d.X = !tables[i]->nu && tables[i]->N == (1 << TWO_PASS_LOGN) ? reinterpret_cast<float2*>(b + o_X[i]) : nullptr;
       d.c64 = prec ? nullptr : reinterpret_cast<double2*>(b + o_c[i]);
       d.top2 = b + o_top[i];
       d.cand = reinterpret_cast<int2*>(b + o_cand[i]);
@@ -506,6 +575,33 @@ afd_status enqueue_group(const SlotPool& pool, const SlotPool::Group& g, int K, 
   const int prec = pool.prec;
   const bool t = timer && timer->on;
   // the two-pass path (N = 65536) serves single-signal plans: slot 0
+  if (g.nu) {
+    // non-uniform samples: init, non-uniform DFT, then per step grid, guard,
+    // update and the next non-uniform DFT
+    CUDA_TRY(launch_update_nu(slots, ids, g.nN, true, st));
+    CUDA_TRY(launch_nudft(slots, ids, g.nLc, st));
+    cnt.launches += 2;
+    if (t) AFD_TRY(timer->mark(st, -1));
+    for (int k = 0; k < K; ++k) {
+      CUDA_TRY(launch_grid_nu(slots, ids, g.logN, g.Mmax, st));
+      if (t) AFD_TRY(timer->mark(st, 0));
+      CUDA_TRY(launch_guard_nu(slots, ids, g.nN, pool.cap, st));
+      if (t) AFD_TRY(timer->mark(st, 1));
+      CUDA_TRY(launch_update_nu(slots, ids, g.nN, false, st));
+      if (t) AFD_TRY(timer->mark(st, 2));
+      cnt.n[0] += 1;
+      cnt.n[1] += 1;
+      cnt.n[2] += 1;
+      cnt.launches += 3;
+      if (k + 1 < K) {
+        CUDA_TRY(launch_nudft(slots, ids, g.nLc, st));
+        if (t) AFD_TRY(timer->mark(st, 3));
+        cnt.n[3] += 1;
+        cnt.launches += 1;
+      }
+    }
+    return AFD_OK;
+  }
   const bool two_pass = g.logN == TWO_PASS_LOGN;
   const bool mixed = g.logN < 0;
   if (two_pass && (g.count != 1 || pool.n != 1)) return set_error(AFD_ERR_INVALID, "N = 65536 needs its own plan");
@@ -828,6 +924,48 @@ afd_status afd_plan_create(afd_plan** out, int N, const double* radii, int M, co
   return AFD_OK;
 }
 
+afd_status afd_plan_create_nonuniform(afd_plan** out, int N, const double* theta, const double* weights, int L,
+                                      const double* radii, int M, const afd_plan_opts* opts) {
+  clear_last_error();
+  if (!out) return set_error(AFD_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  afd_plan_opts o;
+  int dev = 0;
+  AFD_TRY(normalise_opts(opts, o, dev));
+  if (o.precision != AFD_FP32_GUARDED)
+    return set_error(AFD_ERR_INVALID, "non-uniform samples: the FP32-guarded path only");
+  if (o.force_a1_zero || o.renormalise)
+    return set_error(AFD_ERR_INVALID, "non-uniform samples: force_a1_zero and renormalise are not supported");
+  if (N < 1 || N > (1 << 20) || !theta) return set_error(AFD_ERR_INVALID, "need 1 <= N <= 2^20 samples and theta");
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < N; ++m) {
+    if (!(theta[m] >= 0.0 && theta[m] < two_pi) || (m > 0 && !(theta[m] > theta[m - 1])))
+      return set_error(AFD_ERR_INVALID, "theta must ascend strictly within [0, 2 pi) (index %d)", m);
+    if (weights && !(weights[m] > 0.0 && weights[m] < 1e300))
+      return set_error(AFD_ERR_INVALID, "weights must be positive and finite (index %d)", m);
+  }
+  if (!is_pow2(L) || L < (1 << NU_MIN_LOGN) || L > (1 << NU_MAX_LOGN))
+    return set_error(AFD_ERR_INVALID, "L = %d: a power of two in [%d, %d]", L, 1 << NU_MIN_LOGN, 1 << NU_MAX_LOGN);
+  AFD_TRY(check_radii(radii, M));
+  DeviceScope scope(dev);
+  if (!scope.ok) return set_error(AFD_ERR_CUDA, "cannot make device %d current", dev);
+  AFD_TRY(ensure_configured(dev));
+  std::unique_ptr<afd_plan> p(new (std::nothrow) afd_plan());
+  if (!p) return set_error(AFD_ERR_NOMEM, "host allocation failed");
+  p->device = dev;
+  p->opts = o;
+  p->opts.persistent = 0;
+  if (o.stream) {
+    p->runner.main = static_cast<cudaStream_t>(o.stream);
+  } else {
+    CUDA_TRY(cudaStreamCreateWithFlags(&p->runner.main, cudaStreamNonBlocking));
+    p->own_stream = true;
+  }
+  AFD_TRY(p->tables.build_nu(N, theta, weights, L, radii, M));
+  *out = p.release();
+  return AFD_OK;
+}
+
 afd_status afd_plan_destroy(afd_plan* plan) {
   if (!plan) return AFD_OK;
   DeviceScope scope(plan->device);
@@ -856,7 +994,7 @@ afd_status afd_decompose_from(afd_plan* plan, const double* G, double E1_in, int
   }
   if (plan->own_stream) AFD_TRY(plan->runner.order_after_default());
   const bool stamps = plan->timer.on && pool.persistent && plan->opts.precision == AFD_FP32_GUARDED &&
-                      plan->tables.N <= (1 << PERSISTENT_MAX_LOGN);
+                      !plan->tables.nu && plan->tables.N <= (1 << PERSISTENT_MAX_LOGN);
   if (stamps && plan->phase_cap < K_max) {
     if (plan->phase_dev) cudaFree(plan->phase_dev);
     plan->phase_dev = nullptr;
@@ -868,7 +1006,7 @@ afd_status afd_decompose_from(afd_plan* plan, const double* G, double E1_in, int
   pool.host[0].E1_given = E1_in;
   pool.host[0].force_a1_zero = (plan->opts.force_a1_zero && E1_in == 0.0) ? 1 : 0;
   AFD_TRY(pool.upload(energy_tol, st));
-  CUDA_TRY(cudaMemcpyAsync(pool.G_dev, G, 16 * (size_t)plan->tables.N, cudaMemcpyDefault, st));
+  CUDA_TRY(cudaMemcpyAsync(pool.G_dev, G, 16 * (size_t)plan->tables.samples(), cudaMemcpyDefault, st));
   AFD_TRY(plan->runner.run(pool, K_max, plan->opts.use_graph != 0, plan->cnt, &plan->timer));
   AFD_TRY(fetch_results(pool, st));
   const int steps = pool.ctl_host[0].k;
@@ -883,7 +1021,7 @@ afd_status afd_decompose_from(afd_plan* plan, const double* G, double E1_in, int
   AFD_TRY(write_outputs(pool, 0, K_max, steps, a_out, coeff_out, delta_out, idx_out));
   if (steps_done) AFD_TRY(copy_out(steps_done, &steps, sizeof(int)));
   if (E1_out) AFD_TRY(copy_out(E1_out, &pool.ctl_host[0].E1, sizeof(double)));
-  if (G_final) CUDA_TRY(cudaMemcpy(G_final, pool.G_dev, 16 * (size_t)plan->tables.N, cudaMemcpyDefault));
+  if (G_final) CUDA_TRY(cudaMemcpy(G_final, pool.G_dev, 16 * (size_t)plan->tables.samples(), cudaMemcpyDefault));
   if (pool.ctl_host[0].err & 2) return set_error(AFD_ERR_NUMERIC, "non-finite objective at step %d", steps);
   return AFD_OK;
 }
