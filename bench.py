@@ -173,6 +173,7 @@ def bench_batch(afd, torch, dev, reps: int = 3) -> dict:
         t0 = time.perf_counter()
         r = afd.afd_batch_run(b, packed)
         times.append(time.perf_counter() - t0)
+    tuning = afd.afd_batch_tuning(b)
     b.close()
     evals = sum(int(x.M) * x.N * int(st) for x, st in zip(sigs, r["steps"]))
     flops = sum(int(x.M) * x.N * int(st) * (5 * int(np.log2(x.N)) + 6) for x, st in zip(sigs, r["steps"]))
@@ -184,6 +185,8 @@ def bench_batch(afd, torch, dev, reps: int = 3) -> dict:
             "timing": "host wall clock around afd_batch_run (device-resident input), best of %d" % reps,
             "grid_fp32_tflops": flops / t / 1e12,
             "grid_fp32_frac_of_peak": flops / t / 1e12 / peak,
+            "autotuner": {str(t["N"]): {"variant": ["default", "32 points/thread", "512-thread CTAs"][t["variant"]],
+                                        "grid_us": t["us"]} for t in tuning},
             "fp32_note": "grid flops (5 log2 N + 6 per grid evaluation) over the whole batch time, "
                          "FP64 guard/update and forward FFTs included in the time; peak derived: "
                          f"{sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x 2070 MHz"}

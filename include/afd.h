@@ -76,6 +76,12 @@ typedef struct afd_plan_opts {
                           (the continuous norm of Sec. 2 is 1; the discrete one inflates the
                           outer circles when r^N is not negligible).  The coefficient is
                           <G_k, e_a>~ either way.  0 (default): the paper's objective. */
+  int autotune;        /* batches: 1 (default) chooses, per N-class, the fastest of the grid
+                          kernel's bitwise-equivalent variants (points per thread, CTA width)
+                          by timing each on the batch's first step; choices are cached per
+                          process.  0: the default variant. */
+  int grid_variant;    /* -1 (default): as autotune decides; 0..2: use this grid-kernel variant
+                          wherever it exists (plans and batches; for tests and profiling) */
 } afd_plan_opts;
 
 typedef struct afd_plan afd_plan;
@@ -246,6 +252,15 @@ afd_status afd_batch_create(afd_batch** out, int n_signals, const int* N, const 
 afd_status afd_batch_run(afd_batch* batch, const double* G_packed, double energy_tol,
                          double* a_out, double* coeff_out, double* delta_out, int* idx_out,
                          int* steps_out);
+/*
+ * The autotuner's choices: *n_groups N-classes; for the first max_groups of
+ * them N, the grid-kernel variant (0 default, 1: 32 points per thread,
+ * 2: 512-thread CTAs) and its measured time per launch in microseconds (0 if
+ * not tuned).  Output pointers may be NULL.
+ */
+afd_status afd_batch_tuning(const afd_batch* batch, int max_groups, int* n_groups, int* N_out, int* variant_out,
+                            float* us_out);
+
 afd_status afd_batch_counters(const afd_batch* batch, long long* kernel_launches);
 afd_status afd_batch_destroy(afd_batch* batch);
 

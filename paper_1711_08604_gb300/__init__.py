@@ -23,7 +23,7 @@ from . import _native
 from ._native import PlanOpts
 
 __all__ = [
-    "afd_plan_create_nonuniform",
+    "afd_plan_create_nonuniform", "afd_batch_tuning",
     "AFD_FP64_PLAIN", "AFD_FP32_GUARDED", "AfdError", "PlanOpts", "afd_plan_opts_default",
     "afd_status_str", "afd_last_error", "afd_version", "afd_plan_create", "afd_plan_destroy",
     "afd_decompose", "afd_decompose_from", "afd_plan_last_info", "afd_plan_set_profiling", "afd_plan_counters",
@@ -89,7 +89,7 @@ def _opts(opts=None, **kw) -> PlanOpts:
     for k, v in kw.items():
         if k == "stream" and v is not None and not isinstance(v, int):
             v = int(getattr(v, "cuda_stream", v))
-        if k in ("force_a1_zero", "use_graph", "persistent", "renormalise"):
+        if k in ("force_a1_zero", "use_graph", "persistent", "renormalise", "autotune"):
             v = int(bool(v))
         setattr(o, k, v)
     return o
@@ -300,6 +300,18 @@ def afd_batch_run(batch: Batch, G_packed, energy_tol: float = 0.0) -> dict:
         res["idx"].append(ix[2 * i * K: 2 * (i * K + s)].reshape(s, 2))
     _check(st, res)
     return res
+
+
+def afd_batch_tuning(batch: Batch) -> list:
+    """The autotuner's choice per N-class: dicts N, variant, us (time per grid launch)."""
+    n = ctypes.c_int(0)
+    _check(_lib().afd_batch_tuning(batch.handle, 0, ctypes.byref(n), None, None, None))
+    k = n.value
+    Ns, vs = np.zeros(k, dtype=np.int32), np.zeros(k, dtype=np.int32)
+    us = np.zeros(k, dtype=np.float32)
+    _check(_lib().afd_batch_tuning(batch.handle, k, ctypes.byref(n), Ns.ctypes.data, vs.ctypes.data,
+                                   us.ctypes.data))
+    return [{"N": int(a), "variant": int(b), "us": float(c)} for a, b, c in zip(Ns, vs, us)]
 
 
 def afd_batch_counters(batch: Batch) -> dict:

@@ -19,7 +19,8 @@ P = ctypes.POINTER
 class PlanOpts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("guard_tau", c_double), ("guard_cap", c_int),
                 ("force_a1_zero", c_int), ("device", c_int), ("stream", c_void_p),
-                ("use_graph", c_int), ("persistent", c_int), ("renormalise", c_int)]
+                ("use_graph", c_int), ("persistent", c_int), ("renormalise", c_int),
+                ("autotune", c_int), ("grid_variant", c_int)]
 
 
 class Result(ctypes.Structure):
@@ -59,6 +60,7 @@ SIGNATURES = {
     "afd_batch_create": (c_int, [P(c_void_p), c_int, c_void_p, c_void_p, c_int, c_int, P(PlanOpts)]),
     "afd_batch_run": (c_int, [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p]),
+    "afd_batch_tuning": (c_int, [c_void_p, c_int, P(c_int), c_void_p, c_void_p, c_void_p]),
     "afd_batch_counters": (c_int, [c_void_p, P(c_ll)]),
     "afd_batch_destroy": (c_int, [c_void_p]),
     "afd_decompose_batch": (c_int, [c_int, c_void_p, c_void_p, c_int, c_void_p, c_int, c_double,

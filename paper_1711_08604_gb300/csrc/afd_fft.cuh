@@ -117,12 +117,14 @@ struct FftSchedule {
   static __host__ __device__ constexpr int pow_b(int logn) { return (1 << logn) / radix(logn, 0); }
 };
 
-// Compile-time shape of one transform.
-template <typename T, int LOGN>
+// Compile-time shape of one transform.  PP: points per thread, 0 for the
+// default (16; 32 for FP32 at N = 16384 to keep 512 threads); a multiple of
+// the radix 16 otherwise.
+template <typename T, int LOGN, int PP = 0>
 struct FftShape {
   static constexpr int N = 1 << LOGN;
-  // Points per thread: 16 (32 for FP32 at N = 16384 to keep 512 threads).
-  static constexpr int P = LOGN < 4 ? N : ((sizeof(T) == 4 && LOGN >= 14) ? 32 : 16);
+  static constexpr int P = LOGN < 4 ? N : (PP ? PP : ((sizeof(T) == 4 && LOGN >= 14) ? 32 : 16));
+  static_assert(LOGN < 4 || (P % 16 == 0 && P <= N), "points per thread: a multiple of 16");
   static constexpr int TPF = N / P;                    // threads per transform
   static constexpr int NPASS = FftSchedule::npass(LOGN);
   static constexpr int SMEM = N + N / 16 + 1;          // padded elements per transform
@@ -133,9 +135,9 @@ struct FftShape {
 // Twiddles of pass PASS applied to the thread's butterflies, then the DFTs.
 // tw is the stage twiddle table of FftSchedule, in global memory (read through
 // the read-only cache) or, with TW_SMEM, in shared memory.
-template <typename T, int LOGN, int DIR, int PASS, bool TW_SMEM = false>
+template <typename T, int LOGN, int DIR, int PASS, bool TW_SMEM = false, int PP = 0>
 __device__ __forceinline__ void fft_pass(V2<T>* v, int t, const V2<T>* __restrict__ tw) {
-  using S = FftShape<T, LOGN>;
+  using S = FftShape<T, LOGN, PP>;
   constexpr int R = S::radix(PASS), NS = S::ns(PASS), NB = S::P / R;
   constexpr int OFF = FftSchedule::tw_off(LOGN, PASS);
 #pragma unroll
@@ -154,9 +156,9 @@ __device__ __forceinline__ void fft_pass(V2<T>* v, int t, const V2<T>* __restric
 }
 
 // Store the outputs of pass PASS to shared memory.
-template <typename T, int LOGN, int PASS>
+template <typename T, int LOGN, int PASS, int PP = 0>
 __device__ __forceinline__ void fft_store(const V2<T>* v, int t, V2<T>* buf) {
-  using S = FftShape<T, LOGN>;
+  using S = FftShape<T, LOGN, PP>;
   constexpr int R = S::radix(PASS), NS = S::ns(PASS), NB = S::P / R;
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
@@ -169,9 +171,9 @@ __device__ __forceinline__ void fft_store(const V2<T>* v, int t, V2<T>* buf) {
 }
 
 // Load the inputs of pass PASS from shared memory.
-template <typename T, int LOGN, int PASS>
+template <typename T, int LOGN, int PASS, int PP = 0>
 __device__ __forceinline__ void fft_load(V2<T>* v, int t, const V2<T>* buf) {
-  using S = FftShape<T, LOGN>;
+  using S = FftShape<T, LOGN, PP>;
   constexpr int R = S::radix(PASS), NB = S::P / R;
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
@@ -182,17 +184,17 @@ __device__ __forceinline__ void fft_load(V2<T>* v, int t, const V2<T>* buf) {
 }
 
 // Global index of the input held in register slot e before pass 0.
-template <typename T, int LOGN>
+template <typename T, int LOGN, int PP = 0>
 __device__ __forceinline__ int fft_in_index(int t, int e) {
-  using S = FftShape<T, LOGN>;
+  using S = FftShape<T, LOGN, PP>;
   constexpr int R = S::radix(0);
   return t + (e / R) * S::TPF + (e % R) * (S::N / R);
 }
 
 // Output index held in register slot e after the last pass.
-template <typename T, int LOGN>
+template <typename T, int LOGN, int PP = 0>
 __device__ __forceinline__ int fft_out_index(int t, int e) {
-  using S = FftShape<T, LOGN>;
+  using S = FftShape<T, LOGN, PP>;
   constexpr int LP = S::NPASS - 1;
   constexpr int R = S::radix(LP), NS = S::ns(LP);
   const int b = t + (e / R) * S::TPF;
@@ -202,9 +204,9 @@ __device__ __forceinline__ int fft_out_index(int t, int e) {
 
 // Register slot of the u-th smallest output index of a thread after the last
 // pass; that index is t + TPF u.
-template <typename T, int LOGN>
+template <typename T, int LOGN, int PP = 0>
 __host__ __device__ constexpr int fft_out_slot(int u) {
-  using S = FftShape<T, LOGN>;
+  using S = FftShape<T, LOGN, PP>;
   constexpr int R = S::radix(S::NPASS - 1), NB = S::P / R;
   return (u % NB) * R + u / NB;
 }
@@ -212,16 +214,16 @@ __host__ __device__ constexpr int fft_out_slot(int u) {
 // Runs passes PASS..NPASS-1; v holds the inputs of pass PASS.  Every thread of
 // the CTA must call this (it contains __syncthreads), including threads whose
 // transform is idle.
-template <typename T, int LOGN, int DIR, int PASS = 0, bool TW_SMEM = false>
+template <typename T, int LOGN, int DIR, int PASS = 0, bool TW_SMEM = false, int PP = 0>
 __device__ __forceinline__ void fft_run(V2<T>* v, int t, V2<T>* buf, const V2<T>* __restrict__ tw) {
-  using S = FftShape<T, LOGN>;
-  fft_pass<T, LOGN, DIR, PASS, TW_SMEM>(v, t, tw);
+  using S = FftShape<T, LOGN, PP>;
+  fft_pass<T, LOGN, DIR, PASS, TW_SMEM, PP>(v, t, tw);
   if constexpr (PASS + 1 < S::NPASS) {
-    fft_store<T, LOGN, PASS>(v, t, buf);
+    fft_store<T, LOGN, PASS, PP>(v, t, buf);
     __syncthreads();
-    fft_load<T, LOGN, PASS + 1>(v, t, buf);
+    fft_load<T, LOGN, PASS + 1, PP>(v, t, buf);
     __syncthreads();
-    fft_run<T, LOGN, DIR, PASS + 1, TW_SMEM>(v, t, buf, tw);
+    fft_run<T, LOGN, DIR, PASS + 1, TW_SMEM, PP>(v, t, buf, tw);
   }
 }
 

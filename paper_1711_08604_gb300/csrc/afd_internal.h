@@ -154,7 +154,11 @@ static_assert(sizeof(SlotDev) == 376, "SlotDev layout");
 // with the same logN; `n` is their number.  Each returns the launch status.
 cudaError_t launch_init(const SlotDev* slots, const int* ids, int n, int N, cudaStream_t st);
 cudaError_t launch_grid(const SlotDev* slots, const int* ids, int n, int logN, int prec, int Mmax,
-                        cudaStream_t st);
+                        cudaStream_t st, int variant = 0);
+// Grid-kernel variants (0: default; 1: 32 points per thread; 2: 512-thread
+// CTAs), all bitwise equivalent; which exist for (logN, precision).
+constexpr int GRID_VARIANTS = 3;
+bool grid_variant_ok(int logN, int prec, int variant);
 // Whole FP32-path decomposition of slot 0 in one cooperative launch (after
 // launch_init); logN <= MAX_LOGN_RESIDENT.
 cudaError_t launch_persistent(const SlotDev* slots, int logN, int M, cudaStream_t st);

@@ -33,18 +33,22 @@ namespace afd {
 
 // ------------------------------------------------------------ grid kernel --
 
-template <typename T, int LOGN>
+// PP: points per thread (0: the default of FftShape); CT: the CTA width the
+// transforms are packed up to (several radii per CTA when one transform has
+// fewer threads).  The variants compute bitwise the same values: only which
+// thread computes which butterfly changes.
+template <typename T, int LOGN, int PP = 0, int CT = 256>
 struct GridCfg {
-  using S = FftShape<T, LOGN>;
-  static constexpr int FPC = S::TPF >= 256 ? 1 : 256 / S::TPF;  // transforms per CTA
+  using S = FftShape<T, LOGN, PP>;
+  static constexpr int FPC = S::TPF >= CT ? 1 : CT / S::TPF;  // transforms per CTA
   static constexpr int THREADS = S::TPF * FPC;
 };
 
-template <typename T, int LOGN>
-__global__ void __launch_bounds__(GridCfg<T, LOGN>::THREADS)
+template <typename T, int LOGN, int PP = 0, int CT = 256>
+__global__ void __launch_bounds__(GridCfg<T, LOGN, PP, CT>::THREADS)
 k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
-  using S = FftShape<T, LOGN>;
-  using C = GridCfg<T, LOGN>;
+  using S = FftShape<T, LOGN, PP>;
+  using C = GridCfg<T, LOGN, PP, CT>;
   constexpr int N = S::N, P = S::P, TPF = S::TPF, FPC = C::FPC, THREADS = C::THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_last;
@@ -103,7 +107,7 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
     for (int e = 0; e < P; ++e) v[e] = mk2<T>((T)0, (T)0);
   }
 
-  fft_run<T, LOGN, +1>(v, t, buf, tw);
+  fft_run<T, LOGN, +1, 0, false, PP>(v, t, buf, tw);
 
   // Objective and per-radius best, straight from registers.
   if constexpr (sizeof(T) == 4) {
@@ -112,7 +116,7 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
     b.init();
 #pragma unroll
     for (int u = 0; u < P; ++u) {
-      const V2<T> x = v[fft_out_slot<T, LOGN>(u)];
+      const V2<T> x = v[fft_out_slot<T, LOGN, PP>(u)];
       b.push_ascending(x.x * x.x + x.y * x.y, t + TPF * u);
     }
     group_reduce<TPF>(b, red);
@@ -136,7 +140,7 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
     b.init();
 #pragma unroll
     for (int u = 0; u < P; ++u) {
-      const V2<T> x = v[fft_out_slot<T, LOGN>(u)];
+      const V2<T> x = v[fft_out_slot<T, LOGN, PP>(u)];
       b.push_ascending(x.x * x.x + x.y * x.y, t + TPF * u, x);
     }
     group_reduce<TPF>(b, red);
@@ -820,10 +824,10 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <typename T, int LOGN>
+template <typename T, int LOGN, int PP = 0, int CT = 256>
 size_t grid_smem() {
-  using S = FftShape<T, LOGN>;
-  return sizeof(V2<T>) * (size_t)S::SMEM * GridCfg<T, LOGN>::FPC;
+  using S = FftShape<T, LOGN, PP>;
+  return sizeof(V2<T>) * (size_t)S::SMEM * GridCfg<T, LOGN, PP, CT>::FPC;
 }
 template <typename T, int LOGN>
 size_t fwd_smem() {
@@ -831,11 +835,39 @@ size_t fwd_smem() {
   return sizeof(V2<T>) * (size_t)S::SMEM;
 }
 
-template <typename T, int LOGN>
+template <typename T, int LOGN, int PP = 0, int CT = 256>
 cudaError_t grid_launch(const SlotDev* slots, const int* ids, int n, int Mmax, cudaStream_t st) {
-  using C = GridCfg<T, LOGN>;
+  using C = GridCfg<T, LOGN, PP, CT>;
   dim3 grid((Mmax + C::FPC - 1) / C::FPC, n);
-  return launch_pdl(k_grid<T, LOGN>, grid, dim3(C::THREADS), grid_smem<T, LOGN>(), st, slots, ids);
+  return launch_pdl(k_grid<T, LOGN, PP, CT>, grid, dim3(C::THREADS), grid_smem<T, LOGN, PP, CT>(), st, slots,
+                    ids);
+}
+
+// Grid-kernel variants the autotuner chooses from (FP32, 2^8 <= N <= 2^13):
+// 1: 32 points per thread; 2: CTAs of 512 threads (2^8 <= N <= 2^12).
+template <int LOGN>
+cudaError_t grid_variant_launch(int variant, const SlotDev* slots, const int* ids, int n, int Mmax,
+                                cudaStream_t st) {
+  if constexpr (LOGN >= 8 && LOGN <= 13) {
+    if (variant == 1) return grid_launch<float, LOGN, 32, 256>(slots, ids, n, Mmax, st);
+    if constexpr (LOGN <= 12)
+      if (variant == 2) return grid_launch<float, LOGN, 0, 512>(slots, ids, n, Mmax, st);
+  }
+  return grid_launch<float, LOGN>(slots, ids, n, Mmax, st);
+}
+
+template <int LOGN>
+cudaError_t set_variant_attrs() {
+  cudaError_t e = cudaSuccess;
+  if constexpr (LOGN >= 8 && LOGN <= 13) {
+    e = cudaFuncSetAttribute(k_grid<float, LOGN, 32, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)grid_smem<float, LOGN, 32, 256>());
+    if (e != cudaSuccess) return e;
+    if constexpr (LOGN <= 12)
+      e = cudaFuncSetAttribute(k_grid<float, LOGN, 0, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)grid_smem<float, LOGN, 0, 512>());
+  }
+  return e;
 }
 
 template <typename T, int LOGN>
@@ -864,9 +896,10 @@ cudaError_t set_attrs() {
 
 cudaError_t configure_kernels() {
   cudaError_t e = cudaSuccess;
-#define X(L)                                             \
-  if ((e = set_attrs<float, L>()) != cudaSuccess) return e; \
-  if ((e = set_attrs<double, L>()) != cudaSuccess) return e;
+#define X(L)                                                       \
+  if ((e = set_attrs<float, L>()) != cudaSuccess) return e;         \
+  if ((e = set_attrs<double, L>()) != cudaSuccess) return e;        \
+  if ((e = set_variant_attrs<L>()) != cudaSuccess) return e;
   AFD_FOR_EACH_LOGN(X)
 #undef X
   if ((e = set_attrs<float, 14>()) != cudaSuccess) return e;
@@ -905,13 +938,19 @@ int grid_ffts_per_cta(int logN, int prec) {
   }
 }
 
+bool grid_variant_ok(int logN, int prec, int variant) {
+  if (variant == 0) return true;
+  if (!prec || logN < 8 || logN > 13) return false;
+  return variant == 1 || (variant == 2 && logN <= 12);
+}
+
 cudaError_t launch_grid(const SlotDev* slots, const int* ids, int n, int logN, int prec, int Mmax,
-                        cudaStream_t st) {
+                        cudaStream_t st, int variant) {
   if (n <= 0) return cudaSuccess;
   switch (logN) {
 #define X(L)                                                                          \
   case L:                                                                             \
-    return prec ? grid_launch<float, L>(slots, ids, n, Mmax, st)                      \
+    return prec ? grid_variant_launch<L>(variant, slots, ids, n, Mmax, st)            \
                 : grid_launch<double, L>(slots, ids, n, Mmax, st);
     AFD_FOR_EACH_LOGN(X)
 #undef X

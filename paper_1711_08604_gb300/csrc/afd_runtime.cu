@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -85,6 +86,8 @@ afd_status check_opts(const afd_plan_opts& o) {
     return set_error(AFD_ERR_INVALID, "guard_tau must lie in [0, 1)");
   if (o.guard_cap < 1 || o.guard_cap > MAX_CAP)
     return set_error(AFD_ERR_INVALID, "guard_cap must lie in 1..%d", MAX_CAP);
+  if (o.grid_variant < -1 || o.grid_variant >= GRID_VARIANTS)
+    return set_error(AFD_ERR_INVALID, "grid_variant must lie in -1..%d", GRID_VARIANTS - 1);
   return AFD_OK;
 }
 
@@ -388,6 +391,8 @@ struct SlotPool {
     int N, logN, first, count, Mmax;  // logN = -1: mixed-radix N
     bool nu;                          // non-uniform samples (single-signal plans)
     int nN, nLc;
+    int variant = 0;                  // grid-kernel variant (autotuned for batches)
+    float variant_us = 0.f;           // its measured time per launch (0: not tuned)
   };
   std::vector<Group> groups;
   std::vector<Fft2Maps> maps;       // TMA descriptors of two-pass slots (N = 65536)
@@ -422,10 +427,12 @@ struct SlotPool {
       const Tables& T = *tables[i];
       const int Ni = T.N;
       if (groups.empty() || groups.back().N != Ni || groups.back().nu != T.nu)
-        groups.push_back({Ni, is_pow2(Ni) ? ilog2(Ni) : -1, idx, 0, 0, T.nu, T.nN, T.nLc});
+        groups.push_back({Ni, is_pow2(Ni) ? ilog2(Ni) : -1, idx, 0, 0, T.nu, T.nN, T.nLc, 0, 0.f});
       groups.back().count++;
       groups.back().Mmax = std::max(groups.back().Mmax, tables[i]->M);
     }
+    for (auto& g : groups)
+      if (o.grid_variant >= 0 && grid_variant_ok(g.logN, prec, o.grid_variant)) g.variant = o.grid_variant;
     // sizes
     g_off.assign(n, 0);
     g_total = 0;
@@ -627,7 +634,7 @@ afd_status enqueue_group(const SlotPool& pool, const SlotPool::Group& g, int K, 
   for (int k = 0; k < K; ++k) {
     if (two_pass) CUDA_TRY(launch_grid2(slots, pool.maps[0], g.Mmax, st));
     else if (mixed) CUDA_TRY(launch_grid_mixed(slots, ids, g.count, g.N, prec, g.Mmax, st));
-    else CUDA_TRY(launch_grid(slots, ids, g.count, g.logN, prec, g.Mmax, st));
+    else CUDA_TRY(launch_grid(slots, ids, g.count, g.logN, prec, g.Mmax, st, g.variant));
     if (t) AFD_TRY(timer->mark(st, 0));
     cnt.n[0] += per;
     cnt.launches += per;
@@ -651,6 +658,72 @@ afd_status enqueue_group(const SlotPool& pool, const SlotPool::Group& g, int K, 
   return AFD_OK;
 }
 
+// --------------------------------------------------------------- autotuner --
+//
+// A batch chooses, per N-class, among the bitwise-equivalent grid-kernel
+// variants (points per thread, CTA width) by timing each on the batch's own
+// first step: the group's slots are initialised and transformed, then every
+// variant runs one warm-up and kTuneReps timed launches (CUDA events on the
+// batch's stream); the fastest is kept.  Choices are cached per process by
+// (device, N, radii count, signal count), so later batches of the same shape
+// skip the measurement.
+constexpr int kTuneReps = 3;
+std::mutex g_tune_mu;
+std::map<std::array<int, 4>, std::pair<int, float>> g_tune_cache;
+
+afd_status autotune(SlotPool& pool, int device, cudaStream_t st) {
+  for (auto& g : pool.groups) {
+    if (g.nu || g.logN < 0 || g.logN == TWO_PASS_LOGN || pool.prec != AFD_FP32_GUARDED) continue;
+    int n_ok = 0;
+    for (int v = 0; v < GRID_VARIANTS; ++v) n_ok += grid_variant_ok(g.logN, pool.prec, v) ? 1 : 0;
+    if (n_ok < 2) continue;
+    const std::array<int, 4> key{device, g.N, g.Mmax, g.count};
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        g.variant = it->second.first;
+        g.variant_us = it->second.second;
+        continue;
+      }
+    }
+    const int* ids = pool.ids_dev + g.first;
+    CUDA_TRY(cudaMemsetAsync(pool.ctl_dev, 0, sizeof(SlotCtl) * pool.n, st));
+    CUDA_TRY(launch_init(pool.slots_dev, ids, g.count, g.N, st));
+    CUDA_TRY(launch_forward(pool.slots_dev, ids, g.count, g.logN, pool.prec, st));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    int best = 0;
+    float best_us = 0.f;
+    cudaError_t err = cudaSuccess;
+    for (int v = 0; v < GRID_VARIANTS && err == cudaSuccess; ++v) {
+      if (!grid_variant_ok(g.logN, pool.prec, v)) continue;
+      err = launch_grid(pool.slots_dev, ids, g.count, g.logN, pool.prec, g.Mmax, st, v);
+      if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+      for (int r = 0; r < kTuneReps && err == cudaSuccess; ++r)
+        err = launch_grid(pool.slots_dev, ids, g.count, g.logN, pool.prec, g.Mmax, st, v);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      const float us = 1e3f * ms / kTuneReps;
+      if (err == cudaSuccess && (v == 0 || us < best_us)) {
+        best = v;
+        best_us = us;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(err, "autotune", __LINE__);
+    g.variant = best;
+    g.variant_us = best_us;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = {best, best_us};
+  }
+  return AFD_OK;
+}
+
 // Runs the whole K-step sequence for every group of the pool: groups on
 // their own streams (forked from and joined back to `main`).
 struct Runner {
@@ -667,6 +740,14 @@ struct Runner {
   Counters graph_cnt;  // launches of one replay
 
   ~Runner() { destroy(); }
+  // Drops the captured graph (the launch sequence changed).
+  void destroy_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    graph_K = -1;
+  }
   void destroy() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -797,6 +878,7 @@ struct afd_batch {
   int device = 0;
   afd_plan_opts opts{};
   bool own_stream = false;
+  bool tuned = false;
   std::vector<std::unique_ptr<Tables>> tables;
   SlotPool pool;
   Runner runner;
@@ -868,6 +950,8 @@ void afd_plan_opts_default(afd_plan_opts* o) {
   o->precision = AFD_FP32_GUARDED;
   o->guard_tau = 1e-4;
   o->renormalise = 0;
+  o->autotune = 1;
+  o->grid_variant = -1;
   o->guard_cap = 16;
   o->force_a1_zero = 0;
   o->device = -1;
@@ -1148,6 +1232,12 @@ afd_status afd_batch_run(afd_batch* b, const double* G_packed, double energy_tol
   if (b->own_stream) AFD_TRY(b->runner.order_after_default());
   AFD_TRY(pool.upload(energy_tol, st));
   CUDA_TRY(cudaMemcpyAsync(pool.G_dev, G_packed, 8 * pool.g_total, cudaMemcpyDefault, st));
+  if (!b->tuned && b->opts.autotune && b->opts.grid_variant < 0) {
+    // before the first capture of the step sequence
+    AFD_TRY(autotune(pool, b->device, st));
+    b->runner.destroy_graph();
+  }
+  b->tuned = true;
   AFD_TRY(b->runner.run(pool, pool.K_max, b->opts.use_graph != 0, b->cnt, nullptr));
   AFD_TRY(fetch_results(pool, st));
   bool numeric = false;
@@ -1159,6 +1249,19 @@ afd_status afd_batch_run(afd_batch* b, const double* G_packed, double energy_tol
   }
   if (steps_out) AFD_TRY(copy_out(steps_out, steps.data(), sizeof(int) * steps.size()));
   if (numeric) return set_error(AFD_ERR_NUMERIC, "non-finite objective in at least one signal");
+  return AFD_OK;
+}
+
+afd_status afd_batch_tuning(const afd_batch* b, int max_groups, int* n_groups, int* N_out, int* variant_out,
+                            float* us_out) {
+  if (!b) return set_error(AFD_ERR_INVALID, "batch is NULL");
+  const auto& gs = b->pool.groups;
+  if (n_groups) *n_groups = (int)gs.size();
+  for (int i = 0; i < (int)gs.size() && i < max_groups; ++i) {
+    if (N_out) N_out[i] = gs[i].N;
+    if (variant_out) variant_out[i] = gs[i].variant;
+    if (us_out) us_out[i] = gs[i].variant_us;
+  }
   return AFD_OK;
 }
 

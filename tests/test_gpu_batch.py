@@ -98,3 +98,31 @@ def test_workload3_full_batch_sampled_parity():
         # every step through the forced oracle; full-grid selection at step 1
         # for the two smallest sizes (the oracle grid is O(M N^2))
         parity.check(sigs[i].G, radii, r, 1, full_grid=False, grid_steps=(1,) if N <= 2048 else ())
+
+
+def test_grid_variants_are_bitwise_equivalent():
+    # the autotuner's candidates (points per thread, CTA width) compute the
+    # same values
+    sigs = small_batch(n=8, Ns=(256, 1024, 4096, 8192), seed=4)
+    radii = W.radii_linear(24)
+    ref = afd.afd_decompose_batch(sigs, radii, 5, autotune=False)
+    for v in (0, 1, 2):
+        r = afd.afd_decompose_batch(sigs, radii, 5, grid_variant=v)
+        for i in range(len(sigs)):
+            for key in ("a", "coeff", "delta", "idx"):
+                assert np.array_equal(r[key][i], ref[key][i]), (v, i, key)
+
+
+def test_autotuner_reports_choices_and_keeps_results():
+    sigs = small_batch(n=16, Ns=(1024, 2048, 4096, 8192), seed=6)
+    radii = W.radii_linear(50)
+    b = afd.afd_batch_create([g.size for g in sigs], radii, 6)
+    r = afd.afd_batch_run(b, np.concatenate(sigs))
+    tun = afd.afd_batch_tuning(b)
+    b.close()
+    assert [t["N"] for t in tun] == [1024, 2048, 4096, 8192]
+    assert all(t["variant"] in (0, 1, 2) and t["us"] > 0 for t in tun)
+    ref = afd.afd_decompose_batch(sigs, radii, 6, autotune=False)
+    for i in range(len(sigs)):
+        for key in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(r[key][i], ref[key][i]), (i, key)
