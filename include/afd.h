@@ -106,8 +106,8 @@ const char* afd_version(void);
  *   N      a power of two, 8 <= N <= 16384 (FP32 path) or 8192 (FP64 path),
  *          or N = 65536 (FP32 path, single-signal plans only);
  *          or N = 2^a 3^b 5^c >= 9 that is not a power of two, N <= 12800
- *          (FP32 path) or 6400 (FP64 path): the remark of Sec. 3.1 that the
- *          radix-2 split of Theorem 2.1 extends to N = p^K, taken here as
+ *          (FP32 path) or 6400 (FP64 path): the remark after Table 9
+ *          (Sec. 4.2) that the algorithm holds for N = p^K, taken here as
  *          mixed radices 2, 3, 4, 5, 8 and 16.  Not persistent; not served
  *          by afd_serve_* (power-of-two sizes only there).
  *   radii  host array of M ascending values in [0, 1); copied.

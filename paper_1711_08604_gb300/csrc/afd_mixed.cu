@@ -1,8 +1,8 @@
 // Grid and forward kernels for N = 2^a 3^b 5^c that is not a power of two.
 //
 // The paper's fast route (Eq. (rcl), Theorem 2.1, Sec. 3.1) splits the sum
-// over l by the factors of N; its closing remark on N = p^K notes that the
-// same split works for any radix p.  Here the transform is a mixed-radix
+// over l by the factors of N; the remark after Table 9 (Sec. 4.2) notes that
+// the algorithm stays valid for N = p^K, p prime.  Here the transform is a mixed-radix
 // Stockham FFT with radices 16, 8, 4, 2, 3 and 5 (mixed_schedule): pass p of
 // radix R over sub-transforms of length Ns reads x[b + q N/R] (q < R) for
 // butterfly b, multiplies input q by w^(dir q (b mod Ns) N/(Ns R)) with

@@ -1,5 +1,5 @@
 """N = 2^a 3^b 5^c that is not a power of two: the mixed-radix path against the
-oracle (the remark of Sec. 3.1 that the split of Theorem 2.1 extends to N = p^K)."""
+oracle (the remark after Table 9, Sec. 4.2: the algorithm stays valid for N = p^K)."""
 import numpy as np
 import pytest
 
