@@ -254,6 +254,35 @@ def bench_chirp(afd, torch, dev, reps: int = 3) -> dict:
                                        "ms_per_step": grid_ms / max(1, steps)}}
 
 
+def bench_single(afd, torch, dev, sig, precision, reps: int = 20) -> dict:
+    """One signal's whole decomposition through afd_decompose (device-resident
+    input; CUDA events on the plan's stream), best of `reps`."""
+    stream = torch.cuda.Stream(device=dev)
+    plan = afd.afd_plan_create(sig.N, sig.radii, precision=precision, device=dev.index,
+                               stream=stream.cuda_stream, use_graph=True)
+    Gd = torch.from_numpy(sig.G).to(dev)
+    K = sig.K
+    out = {"a": torch.zeros(2 * K, dtype=torch.float64, device=dev),
+           "coeff": torch.zeros(2 * K, dtype=torch.float64, device=dev),
+           "delta": torch.zeros(K + 1, dtype=torch.float64, device=dev),
+           "idx": torch.zeros(2 * K, dtype=torch.int32, device=dev)}
+    times = []
+    for i in range(reps + 3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        afd.afd_decompose(plan, Gd, K, 0.0, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= 3:
+            times.append(e0.elapsed_time(e1))
+    plan.close()
+    ms = min(times)
+    return {"ms_per_decomposition": ms, "p50_ms": float(np.percentile(times, 50)),
+            "p99_ms": float(np.percentile(times, 99)), "grid_evals_per_s": sig.M * sig.N * K / (ms * 1e-3),
+            "signals_per_s": 1e3 / ms,
+            "timing": "CUDA events around afd_decompose (device-resident input), min / p50 / p99 of %d" % reps}
+
+
 def bench_serve(afd, duration: float = 3.0, fp64_sample: int = 40) -> dict:
     """Workload 4: Poisson arrivals at 2000 req/s; N in {512..16384}, M = 128,
     stop at delta <= 1e-4 or K = 64; 40 GB admission budget.  Latency is
@@ -508,7 +537,13 @@ def run_afd(args):
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(s)
         if not args.no_extra:
-            line["other_workloads"] = {"batch": bench_batch(afd, torch, dev),
+            from paper_1711_08604_gb300 import workloads as W
+            line["other_workloads"] = {
+                "c1_kernel_sum": dict(bench_single(afd, torch, dev, W.kernel_sum(), afd.AFD_FP64_PLAIN),
+                                      workload="kernel sum: N=256, M=50 radii i/50, K=10, FP64 plain"),
+                "c2_tones_fp64_plain": dict(bench_single(afd, torch, dev, s, afd.AFD_FP64_PLAIN, reps=10),
+                                            workload="tones: N=4096, M=200, K=50, FP64 plain (the comparator)"),
+                "batch": bench_batch(afd, torch, dev),
                                        "large_two_pass": bench_chirp(afd, torch, dev),
                                        "serving": bench_serve(afd, args.serve_seconds),
                                        "paper_table9": bench_paper_sweep(afd)}

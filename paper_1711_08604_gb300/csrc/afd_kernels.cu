@@ -40,7 +40,11 @@ namespace afd {
 template <typename T, int LOGN, int PP = 0, int CT = 256>
 struct GridCfg {
   using S = FftShape<T, LOGN, PP>;
-  static constexpr int FPC = S::TPF >= CT ? 1 : CT / S::TPF;  // transforms per CTA
+  // FP32 packs small transforms into CTAs of CT threads; FP64 keeps one warp
+  // per CTA at most, so that its FP64 work (1/64 of the FP32 rate) spreads
+  // over as many SMs as there are radii
+  static constexpr int CTA = sizeof(T) == 4 ? CT : 32;
+  static constexpr int FPC = S::TPF >= CTA ? 1 : CTA / S::TPF;  // transforms per CTA
   static constexpr int THREADS = S::TPF * FPC;
 };
 
