@@ -311,20 +311,36 @@ __device__ __forceinline__ double2 sum_fp64_group(double x, double y, double* re
 // Reduced-remainder update of Sec. 2 at z_m for a = r_s w^j and
 // c' = c sqrt(1 - r_s^2):  G_{k+1}(z_m) = (G_k(z_m) u - c') / (z_m - a) with
 // u = 1 - conj(a) z_m = 1 - r_s w^d, d = (m - j) mod N.  Because
-// z_m - a = z_m conj(u), the division is (...) conj(z_m) conj(K_s[d]).
-__device__ __forceinline__ double2 update_point(const SlotDev& sd, int m, int s, int j, double r, double cr,
-                                                double ci, double2 g) {
+// z_m - a = z_m conj(u), dividing by it is multiplying by
+// B = conj(z_m) conj(K_s[d]), so G_{k+1}(z_m) = A - c' B with A = G_k(z_m) u B.
+// A and B depend on the selected point but not on its coefficient, so the
+// persistent kernel forms them while the coefficient is still being summed.
+struct UpdCoef {
+  double2 A, B;
+};
+__device__ __forceinline__ UpdCoef update_coef(const SlotDev& sd, int m, int s, int j, double r, double2 g) {
   const int N = sd.p.N;
   const int d = wrap_mod(m - j, N);
   const double2 w = __ldg(&sd.p.tw64[d]);
   const double2 z = __ldg(&sd.p.tw64[m]);
   const double2 kd = __ldg(&sd.p.K64[(size_t)s * N + d]);
   const double ur = fma(-r, w.x, 1.0), ui = -r * w.y;
-  const double xr = fma(g.x, ur, fma(-g.y, ui, -cr));
-  const double xi = fma(g.x, ui, fma(g.y, ur, -ci));
-  const double yr = fma(xr, kd.x, xi * kd.y);  // (x) conj(K)
-  const double yi = fma(xi, kd.x, -xr * kd.y);
-  return make_double2(fma(yr, z.x, yi * z.y), fma(yi, z.x, -yr * z.y));  // (y) conj(z)
+  // B = conj(K z)
+  const double br = fma(kd.x, z.x, -kd.y * z.y);
+  const double bi = -fma(kd.x, z.y, kd.y * z.x);
+  // A = (g u) B
+  const double gr = fma(g.x, ur, -g.y * ui), gi = fma(g.x, ui, g.y * ur);
+  UpdCoef o;
+  o.A = make_double2(fma(gr, br, -gi * bi), fma(gr, bi, gi * br));
+  o.B = make_double2(br, bi);
+  return o;
+}
+__device__ __forceinline__ double2 update_apply(const UpdCoef& q, double cr, double ci) {
+  return make_double2(q.A.x - fma(cr, q.B.x, -ci * q.B.y), q.A.y - fma(cr, q.B.y, ci * q.B.x));
+}
+__device__ __forceinline__ double2 update_point(const SlotDev& sd, int m, int s, int j, double r, double cr,
+                                                double ci, double2 g) {
+  return update_apply(update_coef(sd, m, s, j, r, g), cr, ci);
 }
 
 // FP64 selection: global best of the per-radius maxima; writes the step record.

@@ -487,17 +487,32 @@ k_persistent(const SlotDev* __restrict__ slots) {
 #pragma unroll
     for (int i = 0; i < NB0; ++i) lb0[i] = __ldg(&sd.p.rlo32[(size_t)s_first * B + t + i * TPF]);
   }
-  // warp-sized FP64 items: W per candidate (guard) and W for the update, four
-  // per 128-sample chunk; global warp gw takes items gw, gw + nw, ...
+  // Warp-sized FP64 items: W per candidate (guard) and W for the update, four
+  // per 128-sample chunk.  Guard items run on the warps with (warp & 2) == 0,
+  // update items on the others, so that the two sit on different SM
+  // sub-partitions (warp w runs on sub-partition w mod 4) and their FP64 work
+  // overlaps; within a role, warp gw = slot * nb + blockIdx takes items gw,
+  // gw + nw, ...
   constexpr int WPC = FP64_CHUNK / 32;
+  constexpr int NWARP = THREADS / 32;
+  static_assert(NWARP == 8, "two FP64 roles of four warps");
   const int W = WPC * Pc;
-  const int nw = (int)nb * (THREADS / 32);
-  const int gw = warp * (int)nb + (int)blockIdx.x;
-  // the warp's first update item keeps its samples G(z_m) in registers: the
+  const bool upd_role = (warp & 2) != 0;
+  const int role_slot = ((warp >> 2) << 1) | (warp & 1);
+  const int nw = 4 * (int)nb;
+  const int gw = role_slot * (int)nb + (int)blockIdx.x;
+  const int gwa = warp * (int)nb + (int)blockIdx.x;  // over all warps
+  const int nwa = NWARP * (int)nb;
+  // an update warp's first item keeps its samples G(z_m) in registers: the
   // same lane updates the same sample at every step
-  const int m_own = gw < W ? gw * 32 + lane : -1;
+  const int m_own = upd_role && gw < W ? gw * 32 + lane : -1;
   double2 g_own = make_double2(0.0, 0.0);
   if (m_own >= 0 && m_own < N) g_own = sd.G[m_own];
+  // update terms A, B (update_coef) of the first role slot's item for the
+  // first NPRE candidates, formed while the guard sums run
+  constexpr int NPRE = 4;
+  __shared__ UpdCoef s_upd[NPRE][32];
+  const bool pre_warp = upd_role && role_slot == 0 && m_own >= 0;
   __syncthreads();
 
   // Energy of the remainder after step kk, E = (1/N) sum |G|^2, from that
@@ -540,7 +555,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
   // one warp per step (over all CTAs) writes energy and delta.
   auto finish_all = [&](int steps) {
     const double E1 = __ldcg(&ctl->E1);
-    for (int kk = gw; kk < steps; kk += nw) {
+    for (int kk = gwa; kk < steps; kk += nwa) {
       const double E = energy_of(kk);
       if (lane == 0) {
         StepRec& rec = sd.rec[kk];
@@ -556,6 +571,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
   // Energy partial of each of the warp's update items of step kk: a shuffle
   // tree over its 32 samples of the new remainder.
   auto energy_items = [&](int kk) {
+    if (!upd_role) return;
     for (int i = gw; i < W; i += nw) {
       const int m = i * 32 + lane;
       double e = 0.0;
@@ -665,7 +681,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
     // G at the warp's first guard item (the item index modulo W does not
     // depend on the candidates), fetched while the candidates are selected
     const int m_g0 = (gw % W) * 32 + lane;
-    const double2 g_g0 = m_g0 < N ? sd.G[m_g0] : make_double2(0.0, 0.0);
+    const double2 g_g0 = !upd_role && m_g0 < N ? sd.G[m_g0] : make_double2(0.0, 0.0);
     const float vmax = __uint_as_float(__ldcg(&ctl->vmax2[k & 1]));
     int n = 1, count = 1;
     if (sd.force_a1_zero && k == 0) {
@@ -682,7 +698,13 @@ k_persistent(const SlotDev* __restrict__ slots) {
       ctl->n_cand = n;
       for (int c = 0; c < n; ++c) sd.cand[c] = s_cand[c];
     }
-    for (int it = gw; it < n * W; it += nw) {
+    if (pre_warp) {
+      for (int c = 0; c < n && c < NPRE; ++c) {
+        const int2 cj = s_cand[c];
+        if (m_own < N) s_upd[c][lane] = update_coef(sd, m_own, cj.x, cj.y, sd.p.radii[cj.x], g_own);
+      }
+    }
+    for (int it = upd_role ? n * W : gw; it < n * W; it += nw) {
       const int c = it / W, i = it % W;
       const int m = i * 32 + lane;
       double ar = 0.0, ai = 0.0;
@@ -785,10 +807,12 @@ k_persistent(const SlotDev* __restrict__ slots) {
       const double na = s_sq[s_pc];
       const double r = s_rad[s_pc], cr = s_pre * na, ci = s_pim * na;
       const double inv_n = sd.p.inv_n;
-      for (int i = gw; i < W; i += nw) {
+      for (int i = upd_role ? gw : W; i < W; i += nw) {
         const int m = i * 32 + lane;
         if (m < N) {
-          const double2 gn = update_point(sd, m, ps, pj, r, cr, ci, m == m_own ? g_own : sd.G[m]);
+          double2 gn;
+          if (pre_warp && m == m_own && s_pc < NPRE) gn = update_apply(s_upd[s_pc][lane], cr, ci);
+          else gn = update_point(sd, m, ps, pj, r, cr, ci, m == m_own ? g_own : sd.G[m]);
           if (m == m_own) g_own = gn;
           sd.G[m] = gn;
           sd.g32[m] = make_float2((float)(gn.x * inv_n), (float)(gn.y * inv_n));
