@@ -65,7 +65,8 @@ struct PlanDev {
   const double* rho64;      // [M] 1 / ||e_a||_N^2 = (1 - r_s^N) / (1 + r_s^N) (renormalised selection)
   const float* rho32;       // [M] the same in FP32
   const double2* K64;       // [M * N] 1 / (1 - r_s exp(2 pi i d / N)), FP64
-  const float2* tw32n;      // [N] exp(+2 pi i k / N) in FP32 (two-pass and mixed-radix paths); two-pass:
+  const float* sh32;        // [N] sin(pi d / N) in FP32 (persistent-kernel sizes, N <= 4096)
+  const float2* tw32n;      // [N] exp(+2 pi i k / N) in FP32 (two-pass, mixed-radix, N <= 4096); two-pass:
                             // followed by [4096] exp(+2 pi i m / 4096)
   double inv_n;             // 1 / N (exact for powers of two)
   // Non-uniform samples (nN > 0): the grid has N angles; the signal is known
@@ -124,6 +125,8 @@ struct SlotDev {
   double tau;               // guard window: obj32 >= (1 - tau) * max32
   double E1_given;          // > 0: reference energy E_1 of a resumed decomposition
   double2* G;               // [N] remainder G_k(z_m), FP64
+  double2* G2;              // persistent kernel: second remainder buffer (odd steps)
+  float2* g32b;             // persistent kernel: second FP32 copy (odd steps)
   float2* g32;              // [N] G_k(z_m) / N rounded to FP32 (input of the FP32 forward FFT)
   float2* c32;              // [N] spectrum c_l / N, FP32
   float2* X;                // two-pass path: [M * N] pass-1 output, X_s[j2][l1]
@@ -148,7 +151,7 @@ __device__ __forceinline__ double obj_rho64(const SlotDev& sd, int s) { return s
 // Host-visible layout sizes (the bench reports per-step transfer bytes from them).
 static_assert(sizeof(StepRec) == 80, "StepRec layout");
 static_assert(sizeof(SlotCtl) == 64, "SlotCtl layout");
-static_assert(sizeof(SlotDev) == 376, "SlotDev layout");
+static_assert(sizeof(SlotDev) == 400, "SlotDev layout");
 
 // Kernel launchers (afd_kernels.cu).  `ids` lists the slots of one launch, all
 // with the same logN; `n` is their number.  Each returns the launch status.

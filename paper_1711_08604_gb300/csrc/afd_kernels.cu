@@ -457,6 +457,8 @@ k_persistent(const SlotDev* __restrict__ slots) {
   __shared__ double s_rad[MAX_CAP], s_sq[MAX_CAP];  // radius and sqrt(1 - r^2) of each candidate
   __shared__ int s_ok, s_pc, s_ps, s_pj;
   __shared__ double s_pre, s_pim, s_pv, s_E;
+  __shared__ float s_f32[5];  // the winner's c'/N (re, im), r, 1 - r, 2 r in FP32
+  __shared__ float s_cf32[MAX_CAP][5];  // the same for every candidate
 
   // the descriptor lives in shared memory for the kernel's lifetime: its
   // fields are read after every grid barrier
@@ -513,6 +515,21 @@ k_persistent(const SlotDev* __restrict__ slots) {
   constexpr int NPRE = 4;
   __shared__ UpdCoef s_upd[NPRE][32];
   const bool pre_warp = upd_role && role_slot == 0 && m_own >= 0;
+  // FP64 -> FP32 conversions run on the slow FP64 pipe: none per step and thread
+  const float tau32 = (float)sd.tau;
+  // G_k and its FP32 copy G_k / N alternate between two buffers (even k: the
+  // slot's own), so that step k's update can write G_{k+1} while other CTAs
+  // still read G_k
+  auto Gbuf = [&](int kk) -> double2* { return (kk & 1) ? sd.G2 : sd.G; };
+  auto g32buf = [&](int kk) -> float2* { return (kk & 1) ? sd.g32b : sd.g32; };
+  // the final remainder goes to the slot's own buffer (update warps)
+  auto publish_remainder = [&](int kk) {
+    if (!upd_role) return;
+    for (int i = gw; i < W; i += nw) {
+      const int m = i * 32 + lane;
+      if (m < N) sd.G[m] = m == m_own ? g_own : Gbuf(kk)[m];
+    }
+  };
   __syncthreads();
 
   // Energy of the remainder after step kk, E = (1/N) sum |G|^2, from that
@@ -593,22 +610,52 @@ k_persistent(const SlotDev* __restrict__ slots) {
       return;
     }
     if (clk) clk[8 * k + 0] = clock64();
-    // inputs of this step that no later phase of it changes
-    float2 vin[P];
+    // The forward transform's input G_k / N.  Step 0: the FP32 copy the
+    // initialisation wrote.  Later steps: formed here in FP32 from step k-1's
+    // FP32 copy and its winner, G_k = (G_{k-1} u - c') B (update_coef), while
+    // the update warps write the FP64 G_k; so no grid barrier separates an
+    // update from the next step's transforms.  The FP32 grid only proposes
+    // candidates; the FP64 guard on the FP64 G_k decides.
+    auto load_input = [&](float2* v) {
+      if (k == 0) {
 #pragma unroll
-    for (int e = 0; e < P; ++e) vin[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
+        for (int e = 0; e < P; ++e) v[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
+        return;
+      }
+      const float2* gp = g32buf(k - 1);
+      // the winner's scalars, converted once per CTA (in phase C)
+      const float crn = s_f32[0], cin = s_f32[1], r = s_f32[2], omr = s_f32[3], r2 = s_f32[4];
+      const int pj = s_pj;
+      float2 gin[P], win[P], zin[P];
+      float shin[P];
+#pragma unroll
+      for (int e = 0; e < P; ++e) {
+        const int m = fft_in_index<float, LOGN>(t, e);
+        const int d = (m - pj) & (N - 1);
+        gin[e] = __ldcg(&gp[m]);
+        win[e] = __ldg(&sd.p.tw32n[d]);
+        shin[e] = __ldg(&sd.p.sh32[d]);
+        zin[e] = __ldg(&sd.p.tw32n[m]);
+      }
+#pragma unroll
+      for (int e = 0; e < P; ++e) {
+        // u = 1 - r w^d with 1 - r cos = (1 - r) + 2 r sin^2(pi d / N) (no
+        // cancellation); G_k / N = (g u - c'/N) u conj(z) / |u|^2
+        const float2 g2 = gin[e], w = win[e], z = zin[e];
+        const float sh = shin[e];
+        const float ur = fmaf(r2 * sh, sh, omr), ui = -r * w.y;
+        const float ik = __fdividef(1.0f, fmaf(ur, ur, ui * ui));
+        const float xr = fmaf(g2.x, ur, fmaf(-g2.y, ui, -crn)), xi = fmaf(g2.x, ui, fmaf(g2.y, ur, -cin));
+        const float yr = fmaf(xr, ur, -xi * ui), yi = fmaf(xr, ui, xi * ur);
+        v[e] = make_float2(fmaf(yr, z.x, yi * z.y) * ik, fmaf(yi, z.x, -yr * z.y) * ik);
+      }
+    };
     // ---------------------------------------------------------------- A --
     for (int tile = blockIdx.x; tile < n_tiles; tile += nb) {
       const int s = tile * FPC + g;
       const bool active = s < M;
       float2 v[P];
-      if (tile == (int)blockIdx.x) {
-#pragma unroll
-        for (int e = 0; e < P; ++e) v[e] = vin[e];
-      } else {
-#pragma unroll
-        for (int e = 0; e < P; ++e) v[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
-      }
+      load_input(v);
       fft_run<float, LOGN, -1, 0, true>(v, t, buf, s_tw);
       // The forward transform leaves c_l, l = t + TPF e, in register e (its
       // last pass is one full-width butterfly per thread); the inverse
@@ -675,20 +722,24 @@ k_persistent(const SlotDev* __restrict__ slots) {
     // step k-1 is complete: with a tolerance, its energy, delta and the stop
     // rule (the FFTs of step k ran speculatively; nothing of step k is
     // recorded before this)
-    if (k > 0 && sd.tol > 0.0 && finish_step(k - 1)) return;
+    if (k > 0 && sd.tol > 0.0 && finish_step(k - 1)) {
+      publish_remainder(k);
+      return;
+    }
 
     // ---------------------------------------------------------------- B --
     // G at the warp's first guard item (the item index modulo W does not
     // depend on the candidates), fetched while the candidates are selected
     const int m_g0 = (gw % W) * 32 + lane;
-    const double2 g_g0 = !upd_role && m_g0 < N ? sd.G[m_g0] : make_double2(0.0, 0.0);
+    const double2* Gk = Gbuf(k);
+    const double2 g_g0 = !upd_role && m_g0 < N ? Gk[m_g0] : make_double2(0.0, 0.0);
     const float vmax = __uint_as_float(__ldcg(&ctl->vmax2[k & 1]));
     int n = 1, count = 1;
     if (sd.force_a1_zero && k == 0) {
       if (threadIdx.x == 0) s_cand[0] = make_int2(0, 0);
       __syncthreads();
     } else {
-      select_core<THREADS>(top, M, N, 1, vmax - vmax * (float)sd.tau, sd.cap, s_cand, &n, &count);
+      select_core<THREADS>(top, M, N, 1, vmax - vmax * tau32, sd.cap, s_cand, &n, &count);
     }
     if (cta0 && threadIdx.x == 0) {
       ctl->vmax2[(k + 1) & 1] = 0u;  // the next step's accumulator
@@ -708,7 +759,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
       const int c = it / W, i = it % W;
       const int m = i * 32 + lane;
       double ar = 0.0, ai = 0.0;
-      if (m < N) guard_term(sd, s_cand[c].x, s_cand[c].y, m, m == m_g0 ? g_g0 : sd.G[m], ar, ai);
+      if (m < N) guard_term(sd, s_cand[c].x, s_cand[c].y, m, m == m_g0 ? g_g0 : Gk[m], ar, ai);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         ar += __shfl_xor_sync(0xffffffffu, ar, off);
@@ -722,8 +773,13 @@ k_persistent(const SlotDev* __restrict__ slots) {
 
     // ---------------------------------------------------------------- C --
     if (threadIdx.x < n) {
-      s_rad[threadIdx.x] = sd.p.radii[s_cand[threadIdx.x].x];
+      const double rd = sd.p.radii[s_cand[threadIdx.x].x];
+      s_rad[threadIdx.x] = rd;
       s_sq[threadIdx.x] = sd.p.sq64[s_cand[threadIdx.x].x];
+      // FP32 scalars of the next step's local update, one candidate per thread
+      s_cf32[threadIdx.x][2] = (float)rd;
+      s_cf32[threadIdx.x][3] = (float)(1.0 - rd);
+      s_cf32[threadIdx.x][4] = (float)(2.0 * rd);
     }
     for (int c = warp; c < n; c += THREADS / 32) {
       double x = 0.0, y = 0.0;
@@ -750,6 +806,9 @@ k_persistent(const SlotDev* __restrict__ slots) {
         s_re[c] = re;
         s_im[c] = im;
         s_v[c] = (re * re + im * im) * obj_rho64(sd, s_cand[c].x);
+        const double cn = sd.p.sq64[s_cand[c].x] * sd.p.inv_n;  // c' / N = c sqrt(1 - r^2) / N
+        s_cf32[c][0] = (float)(re * cn);
+        s_cf32[c][1] = (float)(im * cn);
       }
     }
     __syncthreads();
@@ -771,6 +830,8 @@ k_persistent(const SlotDev* __restrict__ slots) {
       s_pre = bre;
       s_pim = bim;
       s_pv = bv;
+      if (bc >= 0)
+        for (int q = 0; q < 5; ++q) s_f32[q] = s_cf32[bc][q];
     }
     __syncthreads();
     const int ps = s_ps, pj = s_pj;
@@ -787,6 +848,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
       } else {
         finish_all(k);  // the energies of the steps done
       }
+      publish_remainder(k);
       return;
     }
     // the step record, by the last CTA (the update items start at CTA 0)
@@ -807,23 +869,29 @@ k_persistent(const SlotDev* __restrict__ slots) {
       const double na = s_sq[s_pc];
       const double r = s_rad[s_pc], cr = s_pre * na, ci = s_pim * na;
       const double inv_n = sd.p.inv_n;
+      const bool last = k + 1 >= sd.K_max;
+      const double2* Gk = Gbuf(k);
+      // G_{k+1}: the next buffer, or the slot's own after the last step
+      double2* Gn = last ? sd.G : Gbuf(k + 1);
+      float2* gn32 = g32buf(k + 1);
       for (int i = upd_role ? gw : W; i < W; i += nw) {
         const int m = i * 32 + lane;
         if (m < N) {
           double2 gn;
           if (pre_warp && m == m_own && s_pc < NPRE) gn = update_apply(s_upd[s_pc][lane], cr, ci);
-          else gn = update_point(sd, m, ps, pj, r, cr, ci, m == m_own ? g_own : sd.G[m]);
+          else gn = update_point(sd, m, ps, pj, r, cr, ci, m == m_own ? g_own : Gk[m]);
           if (m == m_own) g_own = gn;
-          sd.G[m] = gn;
-          sd.g32[m] = make_float2((float)(gn.x * inv_n), (float)(gn.y * inv_n));
+          Gn[m] = gn;
+          if (!last) gn32[m] = make_float2((float)(gn.x * inv_n), (float)(gn.y * inv_n));
         }
       }
       // the energy partials: now after the last step, else during the next
       // step's FFTs
-      if (k + 1 >= sd.K_max) energy_items(k);
+      if (last) energy_items(k);
     }
     if (clk) clk[8 * k + 5] = clock64();
-    if (!grid_barrier(sd, nb * ++epoch, &s_ok)) return;
+    // after the last step every CTA must see all energy partials
+    if (k + 1 >= sd.K_max && !grid_barrier(sd, nb * ++epoch, &s_ok)) return;
     if (clk) {
       clk[8 * k + 6] = clock64();
       clk[8 * k + 7] = clk[8 * k + 6];  // the energy phase is timed inside the next step's stamps

@@ -226,7 +226,9 @@ struct TableShape {
     H = N / B;
     tws = mixed ? 1 : std::max(FftSchedule::tw_size(two_pass ? 8 : logN), 1);
   }
-  bool tw32n() const { return two_pass || mixed; }
+  bool tw32n() const { return two_pass || mixed || sh32(); }
+  // FP32 half-angle sines: the persistent kernel's sizes
+  bool sh32() const { return !mixed && logN <= PERSISTENT_MAX_LOGN; }
 };
 
 size_t Tables::bytes_for(int N, int M) {
@@ -236,7 +238,7 @@ size_t Tables::bytes_for(int N, int M) {
   size_t off = 0;
   for (size_t b : {sizeof(double) * M, 16 * (size_t)N, 16 * tws, 8 * tws, 8 * (size_t)M * B, 8 * (size_t)M * H,
                    4 * (size_t)M * B, 4 * (size_t)M * H, 4 * (size_t)M, 8 * (size_t)M, 8 * (size_t)M,
-                   8 * (size_t)M, 4 * (size_t)M, 16 * (size_t)M * N, sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0})
+                   8 * (size_t)M, 4 * (size_t)M, 16 * (size_t)M * N, sh.sh32() ? 4 * (size_t)N : 0, sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0})
     off = align_up(off + b);
   return off;
 }
@@ -310,7 +312,8 @@ afd_status Tables::build(int N_, const double* r, int M_) {
                  o_rlo64 = place(8 * rlo64.size()), o_rhi64 = place(8 * rhi64.size()),
                  o_rlo32 = place(4 * rlo32.size()), o_rhi32 = place(4 * rhi32.size()),
                  o_wsq = place(4 * (size_t)M), o_w64 = place(8 * (size_t)M), o_sq = place(8 * (size_t)M),
-                 o_rho64 = place(8 * (size_t)M), o_rho32 = place(4 * (size_t)M), o_K = place(16 * (size_t)M * N), o_tw32n = place(sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0);
+                 o_rho64 = place(8 * (size_t)M), o_rho32 = place(4 * (size_t)M), o_K = place(16 * (size_t)M * N),
+                 o_sh32 = place(sh.sh32() ? 4 * (size_t)N : 0), o_tw32n = place(sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0);
     CUDA_TRY(cudaMalloc(&mem, off));
     bytes = off;
     char* b = static_cast<char*>(mem);
@@ -359,6 +362,13 @@ afd_status Tables::build(int N_, const double* r, int M_) {
       }
       CUDA_TRY(cudaMemcpy(b + o_tw32n, tw32n.data(), 4 * tw32n.size(), cudaMemcpyHostToDevice));
       dev.tw32n = reinterpret_cast<const float2*>(b + o_tw32n);
+    }
+    dev.sh32 = nullptr;
+    if (sh.sh32()) {  // sin(pi d / N) for the persistent kernel's FP32 update
+      std::vector<float> sh32(N);
+      for (int d = 0; d < N; ++d) sh32[d] = (float)std::sin(3.14159265358979323846 * (double)d / (double)N);
+      CUDA_TRY(cudaMemcpy(b + o_sh32, sh32.data(), 4 * (size_t)N, cudaMemcpyHostToDevice));
+      dev.sh32 = reinterpret_cast<const float*>(b + o_sh32);
     }
     CUDA_TRY(launch_kernel_table(dev.radii, M, N, reinterpret_cast<double2*>(b + o_K), nullptr));
     CUDA_TRY(cudaDeviceSynchronize());
@@ -443,12 +453,15 @@ struct SlotPool {
     size_t off = 0;
     auto place = [&](size_t bytes) { size_t o2 = off; off = align_up(off + bytes); return o2; };
     const size_t o_G = place(8 * g_total);
-    std::vector<size_t> o_c(n), o_g32(n), o_top(n), o_cand(n), o_gp(n), o_ep(n), o_X(n);
+    std::vector<size_t> o_c(n), o_g32(n), o_top(n), o_cand(n), o_gp(n), o_ep(n), o_X(n), o_G2(n), o_g32b(n);
     for (int i = 0; i < n; ++i) {
       const int N = tables[i]->samples(), M = tables[i]->M;
       const bool two_pass = !tables[i]->nu && N == (1 << TWO_PASS_LOGN);
       o_c[i] = place((prec ? 8 : 16) * (size_t)tables[i]->spectrum());
       o_g32[i] = place(prec ? 8 * (size_t)N : 0);
+      // the persistent kernel alternates two remainder buffers and two FP32 copies
+      o_G2[i] = place(persistent ? 16 * (size_t)N : 0);
+      o_g32b[i] = place(persistent && prec ? 8 * (size_t)N : 0);
       o_X[i] = place(two_pass ? 8 * (size_t)M * N : 0);
       // two-pass: one best pair per (radius, 16-row block of pass 2)
       o_top[i] = place((prec ? sizeof(Top2F) : sizeof(Top2D)) * (size_t)M * (two_pass ? 16 : 1));
@@ -490,6 +503,8 @@ struct SlotPool {
       d.G = reinterpret_cast<double2*>(b + o_G) + g_off[i] / 2;
       d.c32 = prec ? reinterpret_cast<float2*>(b + o_c[i]) : nullptr;
       d.g32 = prec ? reinterpret_cast<float2*>(b + o_g32[i]) : nullptr;
+      d.G2 = persistent ? reinterpret_cast<double2*>(b + o_G2[i]) : nullptr;
+      d.g32b = persistent && prec ? reinterpret_cast<float2*>(b + o_g32b[i]) : nullptr;
       d.X = !tables[i]->nu && tables[i]->N == (1 << TWO_PASS_LOGN) ? reinterpret_cast<float2*>(b + o_X[i]) : nullptr;
       d.c64 = prec ? nullptr : reinterpret_cast<double2*>(b + o_c[i]);
       d.top2 = b + o_top[i];
