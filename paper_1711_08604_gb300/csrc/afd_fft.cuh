@@ -211,18 +211,29 @@ __host__ __device__ constexpr int fft_out_slot(int u) {
   return (u % NB) * R + u / NB;
 }
 
+// The exchange between passes synchronises the threads of one transform: a
+// warp barrier when the TPF threads of a transform lie in one warp, else the
+// CTA barrier.
+template <typename T, int LOGN, int PP = 0>
+__device__ __forceinline__ void fft_sync() {
+  if constexpr (FftShape<T, LOGN, PP>::TPF <= 32) __syncwarp();
+  else __syncthreads();
+}
+
 // Runs passes PASS..NPASS-1; v holds the inputs of pass PASS.  Every thread of
-// the CTA must call this (it contains __syncthreads), including threads whose
-// transform is idle.
+// the CTA must call this (it synchronises with fft_sync), including threads
+// whose transform is idle.  When a transform fits in a warp nothing orders
+// other warps' use of shared memory: a caller that reuses buf across
+// transforms synchronises itself.
 template <typename T, int LOGN, int DIR, int PASS = 0, bool TW_SMEM = false, int PP = 0>
 __device__ __forceinline__ void fft_run(V2<T>* v, int t, V2<T>* buf, const V2<T>* __restrict__ tw) {
   using S = FftShape<T, LOGN, PP>;
   fft_pass<T, LOGN, DIR, PASS, TW_SMEM, PP>(v, t, tw);
   if constexpr (PASS + 1 < S::NPASS) {
     fft_store<T, LOGN, PASS, PP>(v, t, buf);
-    __syncthreads();
+    fft_sync<T, LOGN, PP>();
     fft_load<T, LOGN, PASS + 1, PP>(v, t, buf);
-    __syncthreads();
+    fft_sync<T, LOGN, PP>();
     fft_run<T, LOGN, DIR, PASS + 1, TW_SMEM, PP>(v, t, buf, tw);
   }
 }

@@ -183,6 +183,7 @@ k_fwd2_pass1(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Maps
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = tile[swz16(t + 16 * q, g)];  // l2 = t + 16 q
   fft_run<float, L8, -1>(v, t, fbuf + g * S8::SMEM, sd.p.st32);
+  __syncthreads();  // every warp has read its inputs from the tile
   // twiddle w^{-j2 l1} and the transposed tile X[j2][l1]
 #pragma unroll
   for (int e = 0; e < 16; ++e) {
@@ -217,6 +218,7 @@ k_fwd2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Maps
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = tile[g * 256 + t + 16 * q];  // row j2, l1 = t + 16 q
   fft_run<float, L8, -1>(v, t, fbuf + g * S8::SMEM, sd.p.st32);
+  __syncthreads();  // every warp has read its inputs from the tile
 #pragma unroll
   for (int e = 0; e < 16; ++e) tile[swz16(fft_out_index<float, L8>(t, e), g)] = v[e];
   fence_proxy_async();
@@ -277,6 +279,7 @@ k_grid2_pass1(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
     }
     fetch(s + R);
     fft_run<float, L8, 1>(v, t, ob + g * S8::SMEM, sd.p.st32);
+    __syncthreads();  // the tile below overlaps other transforms' exchange space
 #pragma unroll
     for (int e = 0; e < 16; ++e) ob[swz16(fft_out_index<float, L8>(t, e), g)] = cmul<float>(v[e], tw[e]);
     fence_proxy_async();
