@@ -18,6 +18,25 @@ __device__ __forceinline__ bool better_d(double va, int ja, double vb, int jb) {
   return va > vb || (va == vb && ja < jb);
 }
 
+// FP64 -> FP32 rounded to nearest even, on the integer pipe.  A cast is an
+// FP64-pipe instruction, as slow as a multiply on this chip.  Results below
+// 2^-126 in magnitude flush to zero; overflow gives infinity, NaN stays NaN.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int ex = (int)((hi >> 20) & 0x7ffu);
+  if (ex == 0x7ff) return __int_as_float(sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u));
+  const int e = ex - 1023 + 127;
+  if (e <= 0) return __int_as_float(sign);
+  if (e >= 255) return __int_as_float(sign | 0x7f800000u);
+  // keep 23 of the 52 fraction bits; the 29 dropped ones decide the rounding
+  unsigned r = ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ++r;  // a carry into the exponent is right
+  return __int_as_float(sign | r);
+}
+
 struct Best2F {
   float v1, v2;
   int j1, j2;
@@ -86,14 +105,21 @@ __device__ __forceinline__ void group_reduce(B& b, B* red) {
 #pragma unroll
   for (int off = W / 2; off > 0; off >>= 1) b.merge(b.shfl(off));
   if constexpr (TPF > 32) {
+    // the group's warp results, merged by a shuffle tree in its first warp
+    // (the best pair of a set of distinct indices does not depend on the
+    // order of the merges)
     constexpr int WPG = TPF / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) red[warp] = b;
     __syncthreads();
-    if (lane == 0 && (warp % WPG) == 0) {
-#pragma unroll 1
-      for (int w = 1; w < WPG; ++w) b.merge(red[warp + w]);
+    if ((warp % WPG) == 0) {
+      B o;
+      if (lane < WPG) o = red[warp + lane];
+      else o.init();
+#pragma unroll
+      for (int off = WPG / 2; off > 0; off >>= 1) o.merge(o.shfl(off));
+      if (lane == 0) b = o;
     }
   }
 }
@@ -152,6 +178,28 @@ __device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned target, 
   const bool last = *s_flag != 0;
   if (last) __threadfence();
   return last;
+}
+
+// Ampere-style asynchronous 16-byte copy global -> shared through L2 (.cg),
+// in the generic proxy.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Four doubles read with one 256-bit load through L2 (32-byte aligned).
+struct double4v {
+  double x, y, z, w;
+};
+__device__ __forceinline__ double4v ld_cg_v4(const double* p) {
+  double4v r;
+  asm volatile("ld.global.cg.v4.f64 {%0, %1, %2, %3}, [%4];"
+               : "=d"(r.x), "=d"(r.y), "=d"(r.z), "=d"(r.w)
+               : "l"(p)
+               : "memory");
+  return r;
 }
 
 __device__ __forceinline__ int ld_done(const SlotCtl* c) { return *((volatile const int*)&c->done); }

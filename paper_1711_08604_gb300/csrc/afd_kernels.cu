@@ -385,18 +385,19 @@ k_kernel_table(const double* __restrict__ radii, int N, double2* __restrict__ K)
 
 constexpr long kBarrierLimit = 1L << 24;  // polls before a barrier gives up (seconds)
 
-__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
 // Grid-wide barrier of a cooperative launch (all CTAs are co-resident).  The
 // arrival counter only grows during a launch (the host zeroes it before), so
 // barrier number e of the launch is passed once it reaches nblocks * (e + 1):
-// one reduction per CTA and a poll, no reset.  Thread 0 publishes its CTA's
-// writes with a release fence before arriving and acquires the others' once
-// the count is reached.  Bounded: a CTA that polls kBarrierLimit times flags a
+// one reduction per CTA and a poll, no reset.  Thread 0 arrives with a
+// release reduction (after the CTA barrier, so it publishes the CTA's writes)
+// and polls with acquire loads, so the others' writes are visible once the
+// count is reached.  Bounded: a CTA that polls kBarrierLimit times flags a
 // timeout (error bit 2), and every CTA that sees the flag leaves.  False in
 // every thread when the kernel must stop.
 __device__ __forceinline__ bool grid_barrier(const SlotDev& sd, unsigned target, int* s_ok) {
@@ -405,9 +406,8 @@ __device__ __forceinline__ bool grid_barrier(const SlotDev& sd, unsigned target,
     SlotCtl* ctl = sd.ctl;
     unsigned* bar = sd.bar;
     int ok = 1;
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
-    for (long it = 1; ld_relaxed_gpu(bar) < target; ++it) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    for (long it = 1; ld_acquire_gpu(bar) < target; ++it) {
       if (it > kBarrierLimit) {
         atomicOr(&ctl->err, 4);
         ok = 0;
@@ -419,7 +419,6 @@ __device__ __forceinline__ bool grid_barrier(const SlotDev& sd, unsigned target,
       }
       __nanosleep(20);
     }
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     if (*((volatile int*)&ctl->err) & 4) ok = 0;
     *s_ok = ok;
   }
@@ -455,6 +454,9 @@ k_persistent(const SlotDev* __restrict__ slots) {
   __shared__ int2 s_cand[MAX_CAP];
   __shared__ double s_re[MAX_CAP], s_im[MAX_CAP], s_v[MAX_CAP];
   __shared__ double s_rad[MAX_CAP], s_sq[MAX_CAP];  // radius and sqrt(1 - r^2) of each candidate
+  __shared__ double s_scn[MAX_CAP], s_rho[MAX_CAP];  // sqrt(1 - r^2) / N and the objective's factor
+  __shared__ double s_cr[MAX_CAP], s_ci[MAX_CAP];    // c' = c sqrt(1 - r^2) of each candidate
+  __shared__ float2 s_rot1[P], s_rot2[P];  // e^(i pi o_e / N), e^(2 pi i o_e / N); o_e: offset of point e
   __shared__ int s_ok, s_pc, s_ps, s_pj;
   __shared__ double s_pre, s_pim, s_pv, s_E;
   __shared__ float s_f32[5];  // the winner's c'/N (re, im), r, 1 - r, 2 r in FP32
@@ -480,21 +482,44 @@ k_persistent(const SlotDev* __restrict__ slots) {
   Top2F* top = reinterpret_cast<Top2F*>(sd.top2);
   long long* clk = (cta0 && threadIdx.x == 0) ? sd.phase_clk : nullptr;
   for (int i = threadIdx.x; i < FftSchedule::tw_size(LOGN); i += THREADS) s_tw[i] = sd.p.st32[i];
-  // the radial powers of this CTA's first tile stay in registers across steps
+  // Point e of a thread's transform input is sample m = t + o_e.  The FP32
+  // local update needs w^d and sin(pi d / N) for d = m - j (j: the step's
+  // winning angle) and z_m; they are formed from e^(i pi (t - j) / N), the
+  // per-point rotations below and z_t, with no table reads.
+  constexpr float INV_N = 1.0f / (float)N;  // exact: N is a power of two
+  if (threadIdx.x < P) {
+    const float o = (float)fft_in_index<float, LOGN>(0, threadIdx.x) * INV_N;
+    float sn, cs;
+    sincospif(o, &sn, &cs);
+    s_rot1[threadIdx.x] = make_float2(cs, sn);
+    sincospif(2.0f * o, &sn, &cs);
+    s_rot2[threadIdx.x] = make_float2(cs, sn);
+  }
+  float2 z_t;
+  sincospif(2.0f * (float)t * INV_N, &z_t.y, &z_t.x);
+  // the radial powers and objective weight of this CTA's first tile stay in
+  // registers across steps
   const int s_first = blockIdx.x * FPC + g;
   float h0[R0], lb0[NB0];
+  float w2_0 = 0.0f;
   if (s_first < M) {
 #pragma unroll
     for (int q = 0; q < R0; ++q) h0[q] = __ldg(&sd.p.rhi32[(size_t)s_first * R0 + q]);
 #pragma unroll
     for (int i = 0; i < NB0; ++i) lb0[i] = __ldg(&sd.p.rlo32[(size_t)s_first * B + t + i * TPF]);
+    w2_0 = obj_w32(sd, s_first);
   }
   // Warp-sized FP64 items: W per candidate (guard) and W for the update, four
-  // per 128-sample chunk.  Guard items run on the warps with (warp & 2) == 0,
-  // update items on the others, so that the two sit on different SM
-  // sub-partitions (warp w runs on sub-partition w mod 4) and their FP64 work
-  // overlaps; within a role, warp gw = slot * nb + blockIdx takes items gw,
-  // gw + nw, ...
+  // per 128-sample chunk.  An FP64 warp instruction occupies its SM
+  // sub-partition's FP64 pipe for tens of cycles whatever the active lanes,
+  // so the work is spread over sub-partitions (warp w runs on w mod 4):
+  //  - guard items on the warps with (warp & 2) == 0, the real part of an
+  //    item's sum on one warp and the imaginary part on its neighbour;
+  //  - update items on the others, warp gw = slot * nb + blockIdx taking
+  //    items gw, gw + nw, ...; while the guard runs, update slot c forms the
+  //    update terms of the CTA's first item for candidate c, and the last
+  //    warp the energy partials of the previous step and the candidates'
+  //    scalars.
   constexpr int WPC = FP64_CHUNK / 32;
   constexpr int NWARP = THREADS / 32;
   static_assert(NWARP == 8, "two FP64 roles of four warps");
@@ -511,10 +536,13 @@ k_persistent(const SlotDev* __restrict__ slots) {
   double2 g_own = make_double2(0.0, 0.0);
   if (m_own >= 0 && m_own < N) g_own = sd.G[m_own];
   // update terms A, B (update_coef) of the first role slot's item for the
-  // first NPRE candidates, formed while the guard sums run
+  // first NPRE candidates, formed while the guard sums run, candidate c by
+  // update slot c from the item's samples in s_gown
   constexpr int NPRE = 4;
   __shared__ UpdCoef s_upd[NPRE][32];
+  __shared__ double2 s_gown[32];
   const bool pre_warp = upd_role && role_slot == 0 && m_own >= 0;
+  if (pre_warp) s_gown[lane] = g_own;
   // FP64 -> FP32 conversions run on the slow FP64 pipe: none per step and thread
   const float tau32 = (float)sd.tau;
   // G_k and its FP32 copy G_k / N alternate between two buffers (even k: the
@@ -616,46 +644,56 @@ k_persistent(const SlotDev* __restrict__ slots) {
     // the update warps write the FP64 G_k; so no grid barrier separates an
     // update from the next step's transforms.  The FP32 grid only proposes
     // candidates; the FP64 guard on the FP64 G_k decides.
-    auto load_input = [&](float2* v) {
+    // from_smem: step k-1's FP32 copy was prefetched into shared memory
+    // during step k-1 (the CTA's first tile)
+    auto load_input = [&](float2* v, bool from_smem) {
       if (k == 0) {
 #pragma unroll
         for (int e = 0; e < P; ++e) v[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
         return;
       }
-      const float2* gp = g32buf(k - 1);
+      const float2* gp = from_smem ? reinterpret_cast<const float2*>(smem_raw) : g32buf(k - 1);
+      if (from_smem) {
+        cp_async_wait_all();
+        __syncthreads();
+      }
       // the winner's scalars, converted once per CTA (in phase C)
       const float crn = s_f32[0], cin = s_f32[1], r = s_f32[2], omr = s_f32[3], r2 = s_f32[4];
-      const int pj = s_pj;
-      float2 gin[P], win[P], zin[P];
-      float shin[P];
+      // e^(i pi (t - j) / N); the argument is exact
+      float hs, hc;
+      sincospif((float)(t - s_pj) * INV_N, &hs, &hc);
+      float2 gin[P];
 #pragma unroll
       for (int e = 0; e < P; ++e) {
         const int m = fft_in_index<float, LOGN>(t, e);
-        const int d = (m - pj) & (N - 1);
-        gin[e] = __ldcg(&gp[m]);
-        win[e] = __ldg(&sd.p.tw32n[d]);
-        shin[e] = __ldg(&sd.p.sh32[d]);
-        zin[e] = __ldg(&sd.p.tw32n[m]);
+        gin[e] = from_smem ? gp[m] : __ldcg(&gp[m]);
       }
 #pragma unroll
       for (int e = 0; e < P; ++e) {
+        // h = e^(i pi (m - j) / N): sin(pi d / N) = +-Im h and w^d = h^2
+        const float2 q1 = s_rot1[e], q2 = s_rot2[e];
+        const float hx = fmaf(hc, q1.x, -hs * q1.y), sh = fmaf(hc, q1.y, hs * q1.x);
+        const float wy = 2.0f * hx * sh;
+        const float2 z = make_float2(fmaf(z_t.x, q2.x, -z_t.y * q2.y), fmaf(z_t.x, q2.y, z_t.y * q2.x));
         // u = 1 - r w^d with 1 - r cos = (1 - r) + 2 r sin^2(pi d / N) (no
         // cancellation); G_k / N = (g u - c'/N) u conj(z) / |u|^2
-        const float2 g2 = gin[e], w = win[e], z = zin[e];
-        const float sh = shin[e];
-        const float ur = fmaf(r2 * sh, sh, omr), ui = -r * w.y;
+        const float2 g2 = gin[e];
+        const float ur = fmaf(r2 * sh, sh, omr), ui = -r * wy;
         const float ik = __fdividef(1.0f, fmaf(ur, ur, ui * ui));
         const float xr = fmaf(g2.x, ur, fmaf(-g2.y, ui, -crn)), xi = fmaf(g2.x, ui, fmaf(g2.y, ur, -cin));
         const float yr = fmaf(xr, ur, -xi * ui), yi = fmaf(xr, ui, xi * ur);
         v[e] = make_float2(fmaf(yr, z.x, yi * z.y) * ik, fmaf(yi, z.x, -yr * z.y) * ik);
       }
+      // the transform below reuses the prefetch buffer
+      if (from_smem) __syncthreads();
     };
     // ---------------------------------------------------------------- A --
     for (int tile = blockIdx.x; tile < n_tiles; tile += nb) {
       const int s = tile * FPC + g;
       const bool active = s < M;
+      const float w2 = active ? (tile == (int)blockIdx.x ? w2_0 : obj_w32(sd, s)) : 0.0f;
       float2 v[P];
-      load_input(v);
+      load_input(v, tile == (int)blockIdx.x);
       fft_run<float, LOGN, -1, 0, true>(v, t, buf, s_tw);
       // The forward transform leaves c_l, l = t + TPF e, in register e (its
       // last pass is one full-width butterfly per thread); the inverse
@@ -702,7 +740,6 @@ k_persistent(const SlotDev* __restrict__ slots) {
       }
       group_reduce<TPF>(b, red2);
       if (t == 0 && active) {
-        const float w2 = obj_w32(sd, s);
         Top2F o;
         o.v1 = b.v1 * w2;
         o.v2 = b.v2 * w2;
@@ -713,26 +750,23 @@ k_persistent(const SlotDev* __restrict__ slots) {
       }
       __syncthreads();
     }
-    // energy partials of step k-1, left out of its update phase so that the
-    // FFTs above did not wait for them
-    if (k > 0) energy_items(k - 1);
     if (clk) clk[8 * k + 1] = clock64();
     if (!grid_barrier(sd, nb * ++epoch, &s_ok)) return;
     if (clk) clk[8 * k + 2] = clock64();
-    // step k-1 is complete: with a tolerance, its energy, delta and the stop
-    // rule (the FFTs of step k ran speculatively; nothing of step k is
-    // recorded before this)
-    if (k > 0 && sd.tol > 0.0 && finish_step(k - 1)) {
-      publish_remainder(k);
-      return;
-    }
-
     // ---------------------------------------------------------------- B --
-    // G at the warp's first guard item (the item index modulo W does not
-    // depend on the candidates), fetched while the candidates are selected
-    const int m_g0 = (gw % W) * 32 + lane;
     const double2* Gk = Gbuf(k);
-    const double2 g_g0 = !upd_role && m_g0 < N ? Gk[m_g0] : make_double2(0.0, 0.0);
+    // guard warp pairs: pair gp = (warp >> 2) nb + blockIdx takes items gp,
+    // gp + 2 nb, ...; comp 0 sums the real parts, comp 1 the imaginary ones.
+    // G at the pair's first item (its sample range does not depend on the
+    // candidates) and, on the last warp, at its first energy item are
+    // fetched while the candidates are selected.
+    const int comp = warp & 1;
+    const int gpair = (warp >> 2) * (int)nb + (int)blockIdx.x;
+    const int m_g0 = (gpair % W) * 32 + lane;
+    const double2 g_g0 = !upd_role && m_g0 < N ? __ldcg(&Gk[m_g0]) : make_double2(0.0, 0.0);
+    const bool e_warp = warp == NWARP - 1;
+    const int m_e0 = (int)blockIdx.x * 32 + lane;
+    const double2 g_e0 = k > 0 && e_warp && m_e0 < N ? __ldcg(&Gk[m_e0]) : make_double2(0.0, 0.0);
     const float vmax = __uint_as_float(__ldcg(&ctl->vmax2[k & 1]));
     int n = 1, count = 1;
     if (sd.force_a1_zero && k == 0) {
@@ -749,89 +783,144 @@ k_persistent(const SlotDev* __restrict__ slots) {
       ctl->n_cand = n;
       for (int c = 0; c < n; ++c) sd.cand[c] = s_cand[c];
     }
-    if (pre_warp) {
-      for (int c = 0; c < n && c < NPRE; ++c) {
-        const int2 cj = s_cand[c];
-        if (m_own < N) s_upd[c][lane] = update_coef(sd, m_own, cj.x, cj.y, sd.p.radii[cj.x], g_own);
+    if (upd_role) {
+      if (e_warp) {
+        // energy partials of step k-1 (the remainder G_k), in the lane order
+        // of energy_items
+        if (k > 0) {
+          for (int i = blockIdx.x; i < W; i += (int)nb) {
+            const int m = i * 32 + lane;
+            double e = 0.0;
+            if (m < N) {
+              const double2 g2 = i == (int)blockIdx.x ? g_e0 : __ldcg(&Gk[m]);
+              e = fma(g2.x, g2.x, g2.y * g2.y);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+            if (lane == 0) sd.epart[(size_t)(k - 1) * W + i] = e;
+          }
+        }
+        // the candidates' scalars for phase C and the next step's FP32 update
+        for (int c = lane; c < n; c += 32) {
+          const int s = s_cand[c].x;
+          const double rd = sd.p.radii[s], sq = sd.p.sq64[s];
+          s_rad[c] = rd;
+          s_sq[c] = sq;
+          s_scn[c] = sq * sd.p.inv_n;  // exact scaling: N is a power of two
+          s_rho[c] = obj_rho64(sd, s);
+          const float r32 = d2f_rn(rd);
+          s_cf32[c][2] = r32;
+          s_cf32[c][3] = d2f_rn(1.0 - rd);
+          s_cf32[c][4] = 2.0f * r32;
+        }
+      }
+      // update terms of the CTA's first update item for candidate role_slot
+      if (role_slot < n && role_slot < NPRE && (int)blockIdx.x < W) {
+        const int m0 = (int)blockIdx.x * 32 + lane;
+        const int2 cj = s_cand[role_slot];
+        if (m0 < N) s_upd[role_slot][lane] = update_coef(sd, m0, cj.x, cj.y, sd.p.radii[cj.x], s_gown[lane]);
+      }
+    } else {
+      // real parts at gpart64[it], imaginary parts cap W further on
+      double* gpart64 = reinterpret_cast<double*>(sd.gpart) + (size_t)comp * sd.cap * W;
+      for (int it = gpair; it < n * W; it += 2 * (int)nb) {
+        const int c = it / W, i = it % W;
+        const int m = i * 32 + lane;
+        double a = 0.0;
+        if (m < N) {
+          // one component of guard_term
+          const double2 gm = it == gpair ? g_g0 : __ldcg(&Gk[m]);
+          const double2 kd = __ldg(&sd.p.K64[(size_t)s_cand[c].x * N + wrap_mod(s_cand[c].y - m, N)]);
+          a = comp ? fma(gm.x, kd.y, gm.y * kd.x) : fma(gm.x, kd.x, -gm.y * kd.y);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        if (lane == 0) gpart64[it] = a;
       }
     }
-    for (int it = upd_role ? n * W : gw; it < n * W; it += nw) {
-      const int c = it / W, i = it % W;
-      const int m = i * 32 + lane;
-      double ar = 0.0, ai = 0.0;
-      if (m < N) guard_term(sd, s_cand[c].x, s_cand[c].y, m, m == m_g0 ? g_g0 : Gk[m], ar, ai);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        ar += __shfl_xor_sync(0xffffffffu, ar, off);
-        ai += __shfl_xor_sync(0xffffffffu, ai, off);
-      }
-      if (lane == 0) sd.gpart[it] = make_double2(ar, ai);
+    // Prefetch of G_k / N (FP32, written in step k-1's update) for step
+    // k+1's input, after this step's critical reads: it lands during the
+    // barrier and phase C.  cp.async reads through L2 in the generic proxy,
+    // ordered after the barrier's acquire.
+    if (k + 1 < sd.K_max && (int)blockIdx.x < n_tiles) {
+      const float4* src = reinterpret_cast<const float4*>(g32buf(k));
+      float4* dst = reinterpret_cast<float4*>(smem_raw);
+      for (int i = threadIdx.x; i < N / 2; i += THREADS) cp_async16(dst + i, src + i);
+      cp_async_commit();
     }
     if (clk) clk[8 * k + 3] = clock64();
-    if (!grid_barrier(sd, nb * ++epoch, &s_ok)) return;
+    if (!grid_barrier(sd, nb * ++epoch, &s_ok)) {
+      cp_async_wait_all();
+      return;
+    }
     if (clk) clk[8 * k + 4] = clock64();
 
     // ---------------------------------------------------------------- C --
-    if (threadIdx.x < n) {
-      const double rd = sd.p.radii[s_cand[threadIdx.x].x];
-      s_rad[threadIdx.x] = rd;
-      s_sq[threadIdx.x] = sd.p.sq64[s_cand[threadIdx.x].x];
-      // FP32 scalars of the next step's local update, one candidate per thread
-      s_cf32[threadIdx.x][2] = (float)rd;
-      s_cf32[threadIdx.x][3] = (float)(1.0 - rd);
-      s_cf32[threadIdx.x][4] = (float)(2.0 * rd);
+    // step k-1 is complete: with a tolerance, its energy, delta and the stop
+    // rule (step k ran speculatively so far; nothing of it is recorded before
+    // this)
+    if (k > 0 && sd.tol > 0.0 && finish_step(k - 1)) {
+      publish_remainder(k);
+      cp_async_wait_all();
+      return;
     }
-    for (int c = warp; c < n; c += THREADS / 32) {
-      double x = 0.0, y = 0.0;
-      for (int q = lane; q < Pc; q += 32) {
-        double cx = 0.0, cy = 0.0;  // chunk q: its four warp sums in warp order
-#pragma unroll
-        for (int w = 0; w < WPC; ++w) {
-          const double2 v = __ldcg(&sd.gpart[c * W + q * WPC + w]);
-          cx += v.x;
-          cy += v.y;
+    // The candidates' sums, one component per warp: chunk q adds its four
+    // warp sums in warp order, then the chunks go through a shuffle tree, as
+    // in the separate kernels.  A lane reads its chunk's four partials with
+    // one 32-byte load, so that a warp's reads are contiguous (every CTA
+    // reads them: fewer L2 requests per line).
+    static_assert(WPC == 4, "one 32-byte load per chunk");
+    {
+      for (int u = warp; u < 2 * n; u += NWARP) {
+        const int c = u >> 1, cp = u & 1;
+        const double* part = reinterpret_cast<const double*>(sd.gpart) + (size_t)cp * sd.cap * W + (size_t)c * W;
+        double x = 0.0;
+        for (int q = lane; q < Pc; q += 32) {
+          const double4v p4 = ld_cg_v4(part + q * WPC);
+          x += ((p4.x + p4.y) + p4.z) + p4.w;
         }
-        x += cx;
-        y += cy;
-      }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        x += __shfl_xor_sync(0xffffffffu, x, off);
-        y += __shfl_xor_sync(0xffffffffu, y, off);
-      }
-      const double2 tot = make_double2(x, y);
-      if (lane == 0) {
-        const double sc = sd.p.sq64[s_cand[c].x] * sd.p.inv_n;  // exact scaling: N is a power of two
-        const double re = sc * tot.x, im = sc * tot.y;
-        s_re[c] = re;
-        s_im[c] = im;
-        s_v[c] = (re * re + im * im) * obj_rho64(sd, s_cand[c].x);
-        const double cn = sd.p.sq64[s_cand[c].x] * sd.p.inv_n;  // c' / N = c sqrt(1 - r^2) / N
-        s_cf32[c][0] = (float)(re * cn);
-        s_cf32[c][1] = (float)(im * cn);
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (lane == 0) {
+          const double re = s_scn[c] * x;  // the coefficient's component
+          (cp ? s_im : s_re)[c] = re;
+          (cp ? s_ci : s_cr)[c] = re * s_sq[c];   // c' = c sqrt(1 - r^2)
+          s_cf32[c][cp] = d2f_rn(re * s_scn[c]);  // c' / N
+        }
       }
     }
     __syncthreads();
+    if (threadIdx.x < n) {
+      const int c = threadIdx.x;
+      const double re = s_re[c], im = s_im[c];
+      s_v[c] = (re * re + im * im) * s_rho[c];
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      int bc = -1, bs = -1, bj = -1;
-      double bv = -1.0, bre = 0.0, bim = 0.0;
+      // best objective, ties to the lower flat index; the values are >= 0 or
+      // NaN, so their bit patterns order as the values do (NaN never wins
+      // against an earlier candidate)
+      int bc = -1, bs = -1, bj = -1, bf = 0;
+      long long bb = 0;
       for (int c = 0; c < n; ++c) {
         const int2 cj = s_cand[c];
-        const double v = s_v[c];
-        const int f = cj.x * N + cj.y, bf = bs * N + bj;
-        if (bs < 0 || v > bv || (v == bv && f < bf)) {
-          bc = c; bs = cj.x; bj = cj.y; bv = v; bre = s_re[c]; bim = s_im[c];
+        const long long vb = __double_as_longlong(s_v[c]);
+        const bool nan = (vb & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+        const int f = cj.x * N + cj.y;
+        if (bs < 0 || (!nan && (vb > bb || (vb == bb && f < bf)))) {
+          bc = c; bs = cj.x; bj = cj.y; bb = vb; bf = f;
         }
       }
-      if (bs >= 0 && !(bv <= 1.79e308)) bs = -1;
+      if (bs >= 0 && !((bb & 0x7fffffffffffffffLL) <= __double_as_longlong(1.79e308))) bs = -1;
       s_pc = bc;
       s_ps = bs;
       s_pj = bj;
-      s_pre = bre;
-      s_pim = bim;
-      s_pv = bv;
-      if (bc >= 0)
+      if (bc >= 0) {
+        s_pre = s_re[bc];
+        s_pim = s_im[bc];
+        s_pv = s_v[bc];
         for (int q = 0; q < 5; ++q) s_f32[q] = s_cf32[bc][q];
+      }
     }
     __syncthreads();
     const int ps = s_ps, pj = s_pj;
@@ -849,6 +938,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
         finish_all(k);  // the energies of the steps done
       }
       publish_remainder(k);
+      cp_async_wait_all();
       return;
     }
     // the step record, by the last CTA (the update items start at CTA 0)
@@ -866,11 +956,8 @@ k_persistent(const SlotDev* __restrict__ slots) {
       rec.obj = s_pv;
     }
     {
-      const double na = s_sq[s_pc];
-      const double r = s_rad[s_pc], cr = s_pre * na, ci = s_pim * na;
-      const double inv_n = sd.p.inv_n;
+      const double r = s_rad[s_pc], cr = s_cr[s_pc], ci = s_ci[s_pc];
       const bool last = k + 1 >= sd.K_max;
-      const double2* Gk = Gbuf(k);
       // G_{k+1}: the next buffer, or the slot's own after the last step
       double2* Gn = last ? sd.G : Gbuf(k + 1);
       float2* gn32 = g32buf(k + 1);
@@ -880,13 +967,17 @@ k_persistent(const SlotDev* __restrict__ slots) {
           double2 gn;
           if (pre_warp && m == m_own && s_pc < NPRE) gn = update_apply(s_upd[s_pc][lane], cr, ci);
           else gn = update_point(sd, m, ps, pj, r, cr, ci, m == m_own ? g_own : Gk[m]);
-          if (m == m_own) g_own = gn;
+          if (m == m_own) {
+            g_own = gn;
+            if (pre_warp) s_gown[lane] = gn;
+          }
           Gn[m] = gn;
-          if (!last) gn32[m] = make_float2((float)(gn.x * inv_n), (float)(gn.y * inv_n));
+          // G_{k+1} / N in FP32: scaling by a power of two commutes with the rounding
+          if (!last) gn32[m] = make_float2(d2f_rn(gn.x) * INV_N, d2f_rn(gn.y) * INV_N);
         }
       }
       // the energy partials: now after the last step, else during the next
-      // step's FFTs
+      // step's guard
       if (last) energy_items(k);
     }
     if (clk) clk[8 * k + 5] = clock64();
