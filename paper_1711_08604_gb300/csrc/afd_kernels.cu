@@ -455,10 +455,11 @@ k_persistent(const SlotDev* __restrict__ slots) {
   __shared__ double s_re[MAX_CAP], s_im[MAX_CAP], s_v[MAX_CAP];
   __shared__ double s_rad[MAX_CAP], s_sq[MAX_CAP];  // radius and sqrt(1 - r^2) of each candidate
   __shared__ double s_scn[MAX_CAP], s_rho[MAX_CAP];  // sqrt(1 - r^2) / N and the objective's factor
+  __shared__ float s_scn32[MAX_CAP];                  // sqrt(1 - r^2) / N in FP32
   __shared__ double s_cr[MAX_CAP], s_ci[MAX_CAP];    // c' = c sqrt(1 - r^2) of each candidate
   __shared__ float2 s_rot1[P], s_rot2[P];  // e^(i pi o_e / N), e^(2 pi i o_e / N); o_e: offset of point e
   __shared__ int s_ok, s_pc, s_ps, s_pj;
-  __shared__ double s_pre, s_pim, s_pv, s_E;
+  __shared__ double s_E;
   __shared__ float s_f32[5];  // the winner's c'/N (re, im), r, 1 - r, 2 r in FP32
   __shared__ float s_cf32[MAX_CAP][5];  // the same for every candidate
 
@@ -784,10 +785,10 @@ k_persistent(const SlotDev* __restrict__ slots) {
       for (int c = 0; c < n; ++c) sd.cand[c] = s_cand[c];
     }
     if (upd_role) {
-      if (e_warp) {
+      if (e_warp && k > 0) {
         // energy partials of step k-1 (the remainder G_k), in the lane order
         // of energy_items
-        if (k > 0) {
+        {
           for (int i = blockIdx.x; i < W; i += (int)nb) {
             const int m = i * 32 + lane;
             double e = 0.0;
@@ -800,6 +801,8 @@ k_persistent(const SlotDev* __restrict__ slots) {
             if (lane == 0) sd.epart[(size_t)(k - 1) * W + i] = e;
           }
         }
+      }
+      if (warp == NWARP - 2) {
         // the candidates' scalars for phase C and the next step's FP32 update
         for (int c = lane; c < n; c += 32) {
           const int s = s_cand[c].x;
@@ -807,6 +810,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
           s_rad[c] = rd;
           s_sq[c] = sq;
           s_scn[c] = sq * sd.p.inv_n;  // exact scaling: N is a power of two
+          s_scn32[c] = d2f_rn(sq) * INV_N;
           s_rho[c] = obj_rho64(sd, s);
           const float r32 = d2f_rn(rd);
           s_cf32[c][2] = r32;
@@ -884,12 +888,27 @@ k_persistent(const SlotDev* __restrict__ slots) {
         if (lane == 0) {
           const double re = s_scn[c] * x;  // the coefficient's component
           (cp ? s_im : s_re)[c] = re;
-          (cp ? s_ci : s_cr)[c] = re * s_sq[c];   // c' = c sqrt(1 - r^2)
-          s_cf32[c][cp] = d2f_rn(re * s_scn[c]);  // c' / N
+          (cp ? s_ci : s_cr)[c] = re * s_sq[c];     // c' = c sqrt(1 - r^2)
+          s_cf32[c][cp] = d2f_rn(re) * s_scn32[c];  // c' / N, for the FP32 update
         }
       }
     }
     __syncthreads();
+    // One candidate (most steps): it wins unless its objective may not be
+    // finite, and every thread knows that at once.  |re|, |im| < 2^498 keep
+    // (re^2 + im^2) rho finite (rho <= 1); the general path decides otherwise.
+    int pc = 0, ps = -1, pj = -1;
+    const long long kBig = 0x5f10000000000000LL;  // 2^498
+    if (n == 1 && (__double_as_longlong(s_re[0]) & 0x7fffffffffffffffLL) < kBig &&
+        (__double_as_longlong(s_im[0]) & 0x7fffffffffffffffLL) < kBig) {
+      ps = s_cand[0].x;
+      pj = s_cand[0].y;
+      // for the next step's FP32 update (read after its next barrier)
+      if (threadIdx.x == 0) {
+        s_pj = pj;
+        for (int q = 0; q < 5; ++q) s_f32[q] = s_cf32[0][q];
+      }
+    } else {
     if (threadIdx.x < n) {
       const int c = threadIdx.x;
       const double re = s_re[c], im = s_im[c];
@@ -915,15 +934,14 @@ k_persistent(const SlotDev* __restrict__ slots) {
       s_pc = bc;
       s_ps = bs;
       s_pj = bj;
-      if (bc >= 0) {
-        s_pre = s_re[bc];
-        s_pim = s_im[bc];
-        s_pv = s_v[bc];
+      if (bc >= 0)
         for (int q = 0; q < 5; ++q) s_f32[q] = s_cf32[bc][q];
-      }
     }
     __syncthreads();
-    const int ps = s_ps, pj = s_pj;
+    pc = s_pc;
+    ps = s_ps;
+    pj = s_pj;
+    }
     if (ps < 0) {
       if (cta0 && threadIdx.x == 0) {
         StepRec& rec = sd.rec[k];
@@ -944,19 +962,19 @@ k_persistent(const SlotDev* __restrict__ slots) {
     // the step record, by the last CTA (the update items start at CTA 0)
     if (blockIdx.x == nb - 1 && threadIdx.x == 0) {
       StepRec& rec = sd.rec[k];
-      const double rr = s_rad[s_pc];
+      const double rr = s_rad[pc], re = s_re[pc], im = s_im[pc];
       const double2 z = sd.p.tw64[pj];
       rec.s = ps;
       rec.j = pj;
       rec.n_cand = n;
       rec.a_re = rr * z.x;
       rec.a_im = rr * z.y;
-      rec.c_re = s_pre;
-      rec.c_im = s_pim;
-      rec.obj = s_pv;
+      rec.c_re = re;
+      rec.c_im = im;
+      rec.obj = (re * re + im * im) * s_rho[pc];  // as s_v
     }
     {
-      const double r = s_rad[s_pc], cr = s_cr[s_pc], ci = s_ci[s_pc];
+      const double r = s_rad[pc], cr = s_cr[pc], ci = s_ci[pc];
       const bool last = k + 1 >= sd.K_max;
       // G_{k+1}: the next buffer, or the slot's own after the last step
       double2* Gn = last ? sd.G : Gbuf(k + 1);
@@ -965,7 +983,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
         const int m = i * 32 + lane;
         if (m < N) {
           double2 gn;
-          if (pre_warp && m == m_own && s_pc < NPRE) gn = update_apply(s_upd[s_pc][lane], cr, ci);
+          if (pre_warp && m == m_own && pc < NPRE) gn = update_apply(s_upd[pc][lane], cr, ci);
           else gn = update_point(sd, m, ps, pj, r, cr, ci, m == m_own ? g_own : Gk[m]);
           if (m == m_own) {
             g_own = gn;
