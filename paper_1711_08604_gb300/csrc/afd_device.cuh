@@ -180,15 +180,6 @@ __device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned target, 
   return last;
 }
 
-// Ampere-style asynchronous 16-byte copy global -> shared through L2 (.cg),
-// in the generic proxy.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Four doubles read with one 256-bit load through L2 (32-byte aligned).
 struct double4v {
   double x, y, z, w;

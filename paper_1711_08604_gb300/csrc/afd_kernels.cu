@@ -645,19 +645,13 @@ k_persistent(const SlotDev* __restrict__ slots) {
     // the update warps write the FP64 G_k; so no grid barrier separates an
     // update from the next step's transforms.  The FP32 grid only proposes
     // candidates; the FP64 guard on the FP64 G_k decides.
-    // from_smem: step k-1's FP32 copy was prefetched into shared memory
-    // during step k-1 (the CTA's first tile)
-    auto load_input = [&](float2* v, bool from_smem) {
+    auto load_input = [&](float2* v) {
       if (k == 0) {
 #pragma unroll
         for (int e = 0; e < P; ++e) v[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
         return;
       }
-      const float2* gp = from_smem ? reinterpret_cast<const float2*>(smem_raw) : g32buf(k - 1);
-      if (from_smem) {
-        cp_async_wait_all();
-        __syncthreads();
-      }
+      const float2* gp = g32buf(k - 1);
       // the winner's scalars, converted once per CTA (in phase C)
       const float crn = s_f32[0], cin = s_f32[1], r = s_f32[2], omr = s_f32[3], r2 = s_f32[4];
       // e^(i pi (t - j) / N); the argument is exact
@@ -667,7 +661,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
 #pragma unroll
       for (int e = 0; e < P; ++e) {
         const int m = fft_in_index<float, LOGN>(t, e);
-        gin[e] = from_smem ? gp[m] : __ldcg(&gp[m]);
+        gin[e] = __ldcg(&gp[m]);
       }
 #pragma unroll
       for (int e = 0; e < P; ++e) {
@@ -685,16 +679,15 @@ k_persistent(const SlotDev* __restrict__ slots) {
         const float yr = fmaf(xr, ur, -xi * ui), yi = fmaf(xr, ui, xi * ur);
         v[e] = make_float2(fmaf(yr, z.x, yi * z.y) * ik, fmaf(yi, z.x, -yr * z.y) * ik);
       }
-      // the transform below reuses the prefetch buffer
-      if (from_smem) __syncthreads();
     };
+    const long long tA0 = clock64();
     // ---------------------------------------------------------------- A --
     for (int tile = blockIdx.x; tile < n_tiles; tile += nb) {
       const int s = tile * FPC + g;
       const bool active = s < M;
       const float w2 = active ? (tile == (int)blockIdx.x ? w2_0 : obj_w32(sd, s)) : 0.0f;
       float2 v[P];
-      load_input(v, tile == (int)blockIdx.x);
+      load_input(v);
       fft_run<float, LOGN, -1, 0, true>(v, t, buf, s_tw);
       // The forward transform leaves c_l, l = t + TPF e, in register e (its
       // last pass is one full-width butterfly per thread); the inverse
@@ -751,9 +744,11 @@ k_persistent(const SlotDev* __restrict__ slots) {
       }
       __syncthreads();
     }
+    const long long tA1 = clock64();
     if (clk) clk[8 * k + 1] = clock64();
     if (!grid_barrier(sd, nb * ++epoch, &s_ok)) return;
     if (clk) clk[8 * k + 2] = clock64();
+    const long long tB0 = clock64();
     // ---------------------------------------------------------------- B --
     const double2* Gk = Gbuf(k);
     // guard warp pairs: pair gp = (warp >> 2) nb + blockIdx takes items gp,
@@ -842,22 +837,11 @@ k_persistent(const SlotDev* __restrict__ slots) {
         if (lane == 0) gpart64[it] = a;
       }
     }
-    // Prefetch of G_k / N (FP32, written in step k-1's update) for step
-    // k+1's input, after this step's critical reads: it lands during the
-    // barrier and phase C.  cp.async reads through L2 in the generic proxy,
-    // ordered after the barrier's acquire.
-    if (k + 1 < sd.K_max && (int)blockIdx.x < n_tiles) {
-      const float4* src = reinterpret_cast<const float4*>(g32buf(k));
-      float4* dst = reinterpret_cast<float4*>(smem_raw);
-      for (int i = threadIdx.x; i < N / 2; i += THREADS) cp_async16(dst + i, src + i);
-      cp_async_commit();
-    }
+    const long long tB1 = clock64();
     if (clk) clk[8 * k + 3] = clock64();
-    if (!grid_barrier(sd, nb * ++epoch, &s_ok)) {
-      cp_async_wait_all();
-      return;
-    }
+    if (!grid_barrier(sd, nb * ++epoch, &s_ok)) return;
     if (clk) clk[8 * k + 4] = clock64();
+    const long long tC0 = clock64();
 
     // ---------------------------------------------------------------- C --
     // step k-1 is complete: with a tolerance, its energy, delta and the stop
@@ -865,7 +849,6 @@ k_persistent(const SlotDev* __restrict__ slots) {
     // this)
     if (k > 0 && sd.tol > 0.0 && finish_step(k - 1)) {
       publish_remainder(k);
-      cp_async_wait_all();
       return;
     }
     // The candidates' sums, one component per warp: chunk q adds its four
@@ -956,7 +939,6 @@ k_persistent(const SlotDev* __restrict__ slots) {
         finish_all(k);  // the energies of the steps done
       }
       publish_remainder(k);
-      cp_async_wait_all();
       return;
     }
     // the step record, by the last CTA (the update items start at CTA 0)
@@ -999,6 +981,8 @@ k_persistent(const SlotDev* __restrict__ slots) {
       if (last) energy_items(k);
     }
     if (clk) clk[8 * k + 5] = clock64();
+    if (sd.phase_clk && threadIdx.x == 0 && k >= 10 && k < 14) { unsigned smid; asm volatile("mov.u32 %0, %%smid;" : "=r"(smid)); long long* pp = sd.phase_clk + 8 * sd.K_max + 8 * (blockIdx.x + nb * (k - 10));
+      pp[0] = smid; pp[1] = tA1 - tA0; pp[2] = tB0 - tA1; pp[3] = tB1 - tB0; pp[4] = tC0 - tB1; pp[5] = clock64() - tC0; pp[6] = n; }
     // after the last step every CTA must see all energy partials
     if (k + 1 >= sd.K_max && !grid_barrier(sd, nb * ++epoch, &s_ok)) return;
     if (clk) {
