@@ -680,7 +680,6 @@ k_persistent(const SlotDev* __restrict__ slots) {
         v[e] = make_float2(fmaf(yr, z.x, yi * z.y) * ik, fmaf(yi, z.x, -yr * z.y) * ik);
       }
     };
-    const long long tA0 = clock64();
     // ---------------------------------------------------------------- A --
     for (int tile = blockIdx.x; tile < n_tiles; tile += nb) {
       const int s = tile * FPC + g;
@@ -744,11 +743,9 @@ k_persistent(const SlotDev* __restrict__ slots) {
       }
       __syncthreads();
     }
-    const long long tA1 = clock64();
     if (clk) clk[8 * k + 1] = clock64();
     if (!grid_barrier(sd, nb * ++epoch, &s_ok)) return;
     if (clk) clk[8 * k + 2] = clock64();
-    const long long tB0 = clock64();
     // ---------------------------------------------------------------- B --
     const double2* Gk = Gbuf(k);
     // guard warp pairs: pair gp = (warp >> 2) nb + blockIdx takes items gp,
@@ -837,11 +834,9 @@ k_persistent(const SlotDev* __restrict__ slots) {
         if (lane == 0) gpart64[it] = a;
       }
     }
-    const long long tB1 = clock64();
     if (clk) clk[8 * k + 3] = clock64();
     if (!grid_barrier(sd, nb * ++epoch, &s_ok)) return;
     if (clk) clk[8 * k + 4] = clock64();
-    const long long tC0 = clock64();
 
     // ---------------------------------------------------------------- C --
     // step k-1 is complete: with a tolerance, its energy, delta and the stop
@@ -981,8 +976,6 @@ k_persistent(const SlotDev* __restrict__ slots) {
       if (last) energy_items(k);
     }
     if (clk) clk[8 * k + 5] = clock64();
-    if (sd.phase_clk && threadIdx.x == 0 && k >= 10 && k < 14) { unsigned smid; asm volatile("mov.u32 %0, %%smid;" : "=r"(smid)); long long* pp = sd.phase_clk + 8 * sd.K_max + 8 * (blockIdx.x + nb * (k - 10));
-      pp[0] = smid; pp[1] = tA1 - tA0; pp[2] = tB0 - tA1; pp[3] = tB1 - tB0; pp[4] = tC0 - tB1; pp[5] = clock64() - tC0; pp[6] = n; }
     // after the last step every CTA must see all energy partials
     if (k + 1 >= sd.K_max && !grid_barrier(sd, nb * ++epoch, &s_ok)) return;
     if (clk) {
