@@ -213,28 +213,37 @@ __host__ __device__ constexpr int fft_out_slot(int u) {
 
 // The exchange between passes synchronises the threads of one transform: a
 // warp barrier when the TPF threads of a transform lie in one warp, else the
-// CTA barrier.
-template <typename T, int LOGN, int PP = 0>
+// CTA barrier, or with GS the named barrier 1 + g of transform group g (TPF
+// threads), so that the groups of a CTA run their transforms independently.
+template <typename T, int LOGN, int PP = 0, bool GS = false>
 __device__ __forceinline__ void fft_sync() {
-  if constexpr (FftShape<T, LOGN, PP>::TPF <= 32) __syncwarp();
-  else __syncthreads();
+  constexpr int TPF = FftShape<T, LOGN, PP>::TPF;
+  if constexpr (TPF <= 32) {
+    __syncwarp();
+  } else if constexpr (GS) {
+    static_assert(TPF % 32 == 0, "whole warps per group");
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / TPF)), "n"(TPF) : "memory");
+  } else {
+    __syncthreads();
+  }
 }
 
 // Runs passes PASS..NPASS-1; v holds the inputs of pass PASS.  Every thread of
-// the CTA must call this (it synchronises with fft_sync), including threads
-// whose transform is idle.  When a transform fits in a warp nothing orders
-// other warps' use of shared memory: a caller that reuses buf across
-// transforms synchronises itself.
-template <typename T, int LOGN, int DIR, int PASS = 0, bool TW_SMEM = false, int PP = 0>
+// the CTA (with GS: of the transform group) must call this, as it
+// synchronises with fft_sync, including threads whose transform is idle.
+// When a transform fits in a warp (or with GS) nothing orders other warps'
+// use of shared memory: a caller that reuses buf across transforms
+// synchronises itself.
+template <typename T, int LOGN, int DIR, int PASS = 0, bool TW_SMEM = false, int PP = 0, bool GS = false>
 __device__ __forceinline__ void fft_run(V2<T>* v, int t, V2<T>* buf, const V2<T>* __restrict__ tw) {
   using S = FftShape<T, LOGN, PP>;
   fft_pass<T, LOGN, DIR, PASS, TW_SMEM, PP>(v, t, tw);
   if constexpr (PASS + 1 < S::NPASS) {
     fft_store<T, LOGN, PASS, PP>(v, t, buf);
-    fft_sync<T, LOGN, PP>();
+    fft_sync<T, LOGN, PP, GS>();
     fft_load<T, LOGN, PASS + 1, PP>(v, t, buf);
-    fft_sync<T, LOGN, PP>();
-    fft_run<T, LOGN, DIR, PASS + 1, TW_SMEM, PP>(v, t, buf, tw);
+    fft_sync<T, LOGN, PP, GS>();
+    fft_run<T, LOGN, DIR, PASS + 1, TW_SMEM, PP, GS>(v, t, buf, tw);
   }
 }
 

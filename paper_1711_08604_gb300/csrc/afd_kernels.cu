@@ -440,11 +440,14 @@ __device__ __forceinline__ bool grid_barrier(const SlotDev& sd, unsigned target,
 // item keeps its warp's shuffle-tree sum, and the consumers add the four warp
 // sums of a 128-sample chunk in warp order, then the chunks as the separate
 // kernels do: results are bitwise those of the multi-kernel sequence.
+constexpr int PERSIST_CTA = 512;  // threads per CTA of the persistent kernel (one CTA per SM)
+
 template <int LOGN>
-__global__ void __launch_bounds__(GridCfg<float, LOGN>::THREADS, 2)
+__global__ void __launch_bounds__(GridCfg<float, LOGN, 0, PERSIST_CTA>::THREADS, 1)
 k_persistent(const SlotDev* __restrict__ slots) {
   using S = FftShape<float, LOGN>;
-  using C = GridCfg<float, LOGN>;
+  using C = GridCfg<float, LOGN, 0, PERSIST_CTA>;
+  static_assert(C::FPC >= 2, "transform groups share one forward transform");
   constexpr int N = S::N, P = S::P, TPF = S::TPF, FPC = C::FPC, THREADS = C::THREADS;
   constexpr int R0 = S::radix(0), B = FftSchedule::pow_b(LOGN), NB0 = P / R0;
   constexpr int TWS = FftSchedule::tw_size(LOGN) > 0 ? FftSchedule::tw_size(LOGN) : 1;
@@ -480,6 +483,8 @@ k_persistent(const SlotDev* __restrict__ slots) {
   const int g = threadIdx.x / TPF, t = threadIdx.x % TPF;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float2* buf = reinterpret_cast<float2*>(smem_raw) + g * S::SMEM;
+  // the forward spectrum, handed from group 0 to the others (natural order)
+  float2* spec = reinterpret_cast<float2*>(smem_raw) + FPC * S::SMEM;
   Top2F* top = reinterpret_cast<Top2F*>(sd.top2);
   long long* clk = (cta0 && threadIdx.x == 0) ? sd.phase_clk : nullptr;
   for (int i = threadIdx.x; i < FftSchedule::tw_size(LOGN); i += THREADS) s_tw[i] = sd.p.st32[i];
@@ -523,11 +528,12 @@ k_persistent(const SlotDev* __restrict__ slots) {
   //    scalars.
   constexpr int WPC = FP64_CHUNK / 32;
   constexpr int NWARP = THREADS / 32;
-  static_assert(NWARP == 8, "two FP64 roles of four warps");
+  static_assert(NWARP % 4 == 0 && NWARP >= 8, "two FP64 roles over whole quads of warps");
+  constexpr int NPAIR = NWARP / 4;  // guard warp pairs per CTA
   const int W = WPC * Pc;
   const bool upd_role = (warp & 2) != 0;
   const int role_slot = ((warp >> 2) << 1) | (warp & 1);
-  const int nw = 4 * (int)nb;
+  const int nw = (NWARP / 2) * (int)nb;
   const int gw = role_slot * (int)nb + (int)blockIdx.x;
   const int gwa = warp * (int)nb + (int)blockIdx.x;  // over all warps
   const int nwa = NWARP * (int)nb;
@@ -686,17 +692,32 @@ k_persistent(const SlotDev* __restrict__ slots) {
       const bool active = s < M;
       const float w2 = active ? (tile == (int)blockIdx.x ? w2_0 : obj_w32(sd, s)) : 0.0f;
       float2 v[P];
-      load_input(v);
-      fft_run<float, LOGN, -1, 0, true>(v, t, buf, s_tw);
-      // The forward transform leaves c_l, l = t + TPF e, in register e (its
-      // last pass is one full-width butterfly per thread); the inverse
-      // transform's pass 0 wants l = t + i TPF + q B = t + TPF (i + q NB0) in
-      // register i R0 + q.  The spectrum therefore stays in registers.
+      // The forward transform, once per CTA by group 0 (group barriers only),
+      // leaves c_l, l = t + TPF e, in register e (its last pass is one
+      // full-width butterfly per thread); it goes to spec for the other
+      // groups.  The inverse transform's pass 0 wants l = t + i TPF + q B =
+      // t + TPF (i + q NB0) in register i R0 + q.  A group narrower than a
+      // warp synchronises with __syncwarp, which needs the whole warp: there
+      // all groups of warp 0 run the (identical) forward transform.
       static_assert(LOGN < 4 || (P == 16 && S::radix(S::NPASS - 1) == 16 && S::ns(S::NPASS - 1) == TPF),
                     "forward outputs t + TPF e");
-      float2 vf[P];
+      if (TPF >= 32 ? g == 0 : warp == 0) {
+        load_input(v);
+        fft_run<float, LOGN, -1, 0, true, 0, true>(v, t, buf, s_tw);
+        if (g == 0) {
 #pragma unroll
-      for (int e = 0; e < P; ++e) vf[e] = v[e];
+          for (int e = 0; e < P; ++e) spec[t + TPF * e] = v[e];
+        }
+      }
+      __syncthreads();
+      float2 vf[P];
+      if (g == 0) {
+#pragma unroll
+        for (int e = 0; e < P; ++e) vf[e] = v[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < P; ++e) vf[e] = spec[t + TPF * e];
+      }
       if (active) {
         float h[R0], lb[NB0];
         if (tile == (int)blockIdx.x) {
@@ -723,7 +744,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
 #pragma unroll
         for (int e = 0; e < P; ++e) v[e] = make_float2(0.f, 0.f);
       }
-      fft_run<float, LOGN, +1, 0, true>(v, t, buf, s_tw);
+      fft_run<float, LOGN, +1, 0, true, 0, true>(v, t, buf, s_tw);
       Best2F b;
       b.init();
 #pragma unroll
@@ -749,7 +770,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
     // ---------------------------------------------------------------- B --
     const double2* Gk = Gbuf(k);
     // guard warp pairs: pair gp = (warp >> 2) nb + blockIdx takes items gp,
-    // gp + 2 nb, ...; comp 0 sums the real parts, comp 1 the imaginary ones.
+    // gp + NPAIR nb, ...; comp 0 sums the real parts, comp 1 the imaginary ones.
     // G at the pair's first item (its sample range does not depend on the
     // candidates) and, on the last warp, at its first energy item are
     // fetched while the candidates are selected.
@@ -819,7 +840,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
     } else {
       // real parts at gpart64[it], imaginary parts cap W further on
       double* gpart64 = reinterpret_cast<double*>(sd.gpart) + (size_t)comp * sd.cap * W;
-      for (int it = gpair; it < n * W; it += 2 * (int)nb) {
+      for (int it = gpair; it < n * W; it += NPAIR * (int)nb) {
         const int c = it / W, i = it % W;
         const int m = i * 32 + lane;
         double a = 0.0;
@@ -1011,6 +1032,13 @@ size_t grid_smem() {
   using S = FftShape<T, LOGN, PP>;
   return sizeof(V2<T>) * (size_t)S::SMEM * GridCfg<T, LOGN, PP, CT>::FPC;
 }
+// the persistent kernel: one exchange buffer per transform group and the
+// shared forward spectrum
+template <int LOGN>
+size_t persist_smem() {
+  using S = FftShape<float, LOGN>;
+  return sizeof(float2) * ((size_t)S::SMEM * GridCfg<float, LOGN, 0, PERSIST_CTA>::FPC + S::N);
+}
 template <typename T, int LOGN>
 size_t fwd_smem() {
   using S = FftShape<T, LOGN>;
@@ -1065,7 +1093,7 @@ cudaError_t set_attrs() {
   if (e != cudaSuccess) return e;
   if constexpr (sizeof(T) == 4 && LOGN <= PERSISTENT_MAX_LOGN) {
     e = cudaFuncSetAttribute(k_persistent<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)grid_smem<T, LOGN>());
+                             (int)persist_smem<LOGN>());
     if (e != cudaSuccess) return e;
   }
   return cudaFuncSetAttribute(k_forward<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1163,8 +1191,8 @@ int g_persist_blocks[PERSISTENT_MAX_LOGN + 1] = {};  // co-resident CTAs per log
 
 template <int LOGN>
 cudaError_t persistent_launch(const SlotDev* slots, int M, cudaStream_t st) {
-  using C = GridCfg<float, LOGN>;
-  const size_t smem = grid_smem<float, LOGN>();
+  using C = GridCfg<float, LOGN, 0, PERSIST_CTA>;
+  const size_t smem = persist_smem<LOGN>();
   if (!g_persist_blocks[LOGN]) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1175,8 +1203,10 @@ cudaError_t persistent_launch(const SlotDev* slots, int M, cudaStream_t st) {
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     g_persist_blocks[LOGN] = per_sm * sms;
   }
+  // enough CTAs for the tiles and for one 32-sample FP64 item each
   const int n_tiles = (M + C::FPC - 1) / C::FPC;
-  int blocks = n_tiles > chunks_of(1 << LOGN) ? n_tiles : chunks_of(1 << LOGN);
+  const int items = chunks_of(1 << LOGN) * (FP64_CHUNK / 32);
+  int blocks = n_tiles > items ? n_tiles : items;
   if (blocks > g_persist_blocks[LOGN]) blocks = g_persist_blocks[LOGN];
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
