@@ -54,13 +54,17 @@ struct Best2F {
     v1 = p1 ? v : v1;
     j1 = p1 ? j : j1;
   }
+  // both pairs ordered (first better than second); selects, no branches
   __device__ __forceinline__ void merge(const Best2F& o) {
-    if (better_f(o.v1, o.j1, v1, j1)) {
-      if (better_f(v1, j1, o.v2, o.j2)) { v2 = v1; j2 = j1; } else { v2 = o.v2; j2 = o.j2; }
-      v1 = o.v1; j1 = o.j1;
-    } else if (better_f(o.v1, o.j1, v2, j2)) {
-      v2 = o.v1; j2 = o.j1;
-    }
+    const bool a = better_f(o.v1, o.j1, v1, j1);
+    const bool b1 = better_f(v1, j1, o.v2, o.j2);
+    const bool b2 = better_f(o.v1, o.j1, v2, j2);
+    const float nv2 = a ? (b1 ? v1 : o.v2) : (b2 ? o.v1 : v2);
+    const int nj2 = a ? (b1 ? j1 : o.j2) : (b2 ? o.j1 : j2);
+    v1 = a ? o.v1 : v1;
+    j1 = a ? o.j1 : j1;
+    v2 = nv2;
+    j2 = nj2;
   }
   __device__ __forceinline__ Best2F shfl(int off) const {
     Best2F r;

@@ -23,6 +23,7 @@
 // fixed launch sequence (or a captured CUDA graph) can run any number of steps.
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "afd_device.cuh"
 #include "afd_fft.cuh"
@@ -651,39 +652,65 @@ k_persistent(const SlotDev* __restrict__ slots) {
     // the update warps write the FP64 G_k; so no grid barrier separates an
     // update from the next step's transforms.  The FP32 grid only proposes
     // candidates; the FP64 guard on the FP64 G_k decides.
-    auto load_input = [&](float2* v) {
-      if (k == 0) {
-#pragma unroll
-        for (int e = 0; e < P; ++e) v[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
-        return;
-      }
+    // Points e0 <= e < e0 + CNT of the thread's transform input (k >= 1),
+    // into out[e - e0].
+    auto input_points = [&](auto cnt_tag, int e0, float2* out) {
+      constexpr int CNT = decltype(cnt_tag)::value;
       const float2* gp = g32buf(k - 1);
       // the winner's scalars, converted once per CTA (in phase C)
       const float crn = s_f32[0], cin = s_f32[1], r = s_f32[2], omr = s_f32[3], r2 = s_f32[4];
       // e^(i pi (t - j) / N); the argument is exact
       float hs, hc;
       sincospif((float)(t - s_pj) * INV_N, &hs, &hc);
-      float2 gin[P];
+      float2 gin[CNT];
 #pragma unroll
-      for (int e = 0; e < P; ++e) {
-        const int m = fft_in_index<float, LOGN>(t, e);
-        gin[e] = __ldcg(&gp[m]);
-      }
+      for (int i = 0; i < CNT; ++i) gin[i] = __ldcg(&gp[fft_in_index<float, LOGN>(t, e0 + i)]);
 #pragma unroll
-      for (int e = 0; e < P; ++e) {
+      for (int i = 0; i < CNT; ++i) {
         // h = e^(i pi (m - j) / N): sin(pi d / N) = +-Im h and w^d = h^2
-        const float2 q1 = s_rot1[e], q2 = s_rot2[e];
+        const float2 q1 = s_rot1[e0 + i], q2 = s_rot2[e0 + i];
         const float hx = fmaf(hc, q1.x, -hs * q1.y), sh = fmaf(hc, q1.y, hs * q1.x);
         const float wy = 2.0f * hx * sh;
         const float2 z = make_float2(fmaf(z_t.x, q2.x, -z_t.y * q2.y), fmaf(z_t.x, q2.y, z_t.y * q2.x));
         // u = 1 - r w^d with 1 - r cos = (1 - r) + 2 r sin^2(pi d / N) (no
         // cancellation); G_k / N = (g u - c'/N) u conj(z) / |u|^2
-        const float2 g2 = gin[e];
+        const float2 g2 = gin[i];
         const float ur = fmaf(r2 * sh, sh, omr), ui = -r * wy;
         const float ik = __fdividef(1.0f, fmaf(ur, ur, ui * ui));
         const float xr = fmaf(g2.x, ur, fmaf(-g2.y, ui, -crn)), xi = fmaf(g2.x, ui, fmaf(g2.y, ur, -cin));
         const float yr = fmaf(xr, ur, -xi * ui), yi = fmaf(xr, ui, xi * ur);
-        v[e] = make_float2(fmaf(yr, z.x, yi * z.y) * ik, fmaf(yi, z.x, -yr * z.y) * ik);
+        out[i] = make_float2(fmaf(yr, z.x, yi * z.y) * ik, fmaf(yi, z.x, -yr * z.y) * ik);
+      }
+    };
+    // The forward transform's input in group 0 (all of warp 0 when a group
+    // is narrower than a warp).  From step 1 on, with groups of whole warps,
+    // group 1 forms the upper half of the points and hands them over in spec.
+    constexpr bool SPLIT = TPF >= 32 && P >= 2;
+    const bool lead = TPF >= 32 ? g == 0 : warp == 0;
+    auto load_input = [&](float2* v) {
+      if (k == 0) {
+        if (lead) {
+#pragma unroll
+          for (int e = 0; e < P; ++e) v[e] = sd.g32[fft_in_index<float, LOGN>(t, e)];
+        }
+        return;
+      }
+      if constexpr (SPLIT) {
+        if (g == 1) {
+          float2 hi[P / 2];
+          input_points(std::integral_constant<int, P / 2>{}, P / 2, hi);
+#pragma unroll
+          for (int i = 0; i < P / 2; ++i) spec[t + TPF * i] = hi[i];
+        } else if (g == 0) {
+          input_points(std::integral_constant<int, P / 2>{}, 0, v);
+        }
+        __syncthreads();
+        if (g == 0) {
+#pragma unroll
+          for (int i = 0; i < P / 2; ++i) v[P / 2 + i] = spec[t + TPF * i];
+        }
+      } else {
+        if (lead) input_points(std::integral_constant<int, P>{}, 0, v);
       }
     };
     // ---------------------------------------------------------------- A --
@@ -701,8 +728,10 @@ k_persistent(const SlotDev* __restrict__ slots) {
       // all groups of warp 0 run the (identical) forward transform.
       static_assert(LOGN < 4 || (P == 16 && S::radix(S::NPASS - 1) == 16 && S::ns(S::NPASS - 1) == TPF),
                     "forward outputs t + TPF e");
-      if (TPF >= 32 ? g == 0 : warp == 0) {
-        load_input(v);
+      load_input(v);  // every thread (it may synchronise the CTA)
+      if (lead) {
+        // group 0 reads its points from spec before any of its threads can
+        // finish the transform (group barriers) and write the spectrum there
         fft_run<float, LOGN, -1, 0, true, 0, true>(v, t, buf, s_tw);
         if (g == 0) {
 #pragma unroll
