@@ -58,7 +58,9 @@ constexpr int kScratchBytes = 35 * 1024;
 static_assert(sizeof(float2) * 16 * S8::SMEM <= (size_t)kScratchBytes && kTileBytes <= kScratchBytes,
               "scratch holds the transforms and the tile");
 constexpr size_t kP1Smem = 1024 + kTileBytes + 2 * (size_t)kScratchBytes;
-constexpr size_t kP2Smem = 1024 + 2 * (size_t)kTileBytes + kScratchBytes;
+// pass 2: the two ring slots only (each transform exchanges in its own row of
+// the slot it read), so that three CTAs fit on an SM
+constexpr size_t kP2Smem = 1024 + 2 * (size_t)kTileBytes;
 constexpr long kWaitLimit = 1L << 22;  // mbarrier polls before giving up
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -158,6 +160,31 @@ __device__ bool load_tile(float2* tile, const CUtensorMap* map, int x, int y, ui
 }
 
 
+
+// A 256-point transform of one 16-thread group (half a warp) in registers,
+// exchanging through x (256 float2) with an XOR swizzle instead of padding:
+// element e = 16 a + b sits at 16 a + (b ^ a), so both exchange patterns are
+// free of bank conflicts and the exchange needs no more room than the data.
+// The arithmetic is that of fft_run<float, 8> (two radix-16 Stockham passes,
+// stage twiddles tw from global memory), so the values are bitwise the same.
+// In: v[q] = x_{t + 16 q}; out: v[k] = X_{t + 16 k}.  The whole warp calls it
+// (it synchronises with __syncwarp); x may hold the inputs being read, once
+// the warp is past its reads of them.
+template <int DIR>
+__device__ __forceinline__ void fft256_swz(float2* v, int t, float2* x, const float2* __restrict__ tw) {
+  dft<16, DIR, float>(v);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[16 * t + (k ^ t)] = v[k];
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = x[16 * q + (t ^ q)];
+#pragma unroll
+  for (int q = 1; q < 16; ++q) {
+    const float2 w = __ldg(&tw[(q - 1) * 16 + t]);
+    v[q] = DIR > 0 ? cmul<float>(v[q], w) : cmulc<float>(v[q], w);
+  }
+  dft<16, DIR, float>(v);
+}
 
 }  // namespace
 
@@ -301,8 +328,8 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
   pdl_launch_dependents();
   const SlotDev& sd = slots[0];
   float2* in = align1024(smem_raw);
-  float2* fbuf = in + 2 * kTileElems;
   const int g = threadIdx.x >> 4, t = threadIdx.x & 15;
+  static_assert(FftSchedule::npass(L8) == 2 && FftSchedule::tw_off(L8, 1) == 0, "fft256_swz: 16 x 16");
   if (threadIdx.x == 0) {
     mbar_init(&bars[0]);
     mbar_init(&bars[1]);
@@ -328,14 +355,15 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
     if (item >= items) break;
     const int s = item >> 4, b = item & 15;
     const int j2 = 16 * b + g;
-    const float2* tile = in + (i & 1) * kTileElems;
+    float2* tile = in + (i & 1) * kTileElems;
     if (!cta_wait(&bars[i & 1], (i >> 1) & 1, &s_ok)) break;
     float2 v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = tile[g * 256 + t + 16 * q];  // row j2, l1 = t + 16 q
-    __syncthreads();  // the slot is read: refill it
-    if (threadIdx.x == 0) issue(i + 2);
-    fft_run<float, L8, 1>(v, t, fbuf + g * S8::SMEM, sd.p.st32);
+    __syncwarp();  // the warp's two rows are read: they become its exchange space
+    fft256_swz<1>(v, t, tile + g * 256, sd.p.st32);
+    // the slot's generic writes before the TMA load that refills it
+    fence_proxy_async();
     // best two of the item's 4096 grid points (j = j2 + 256 j1); a thread's
     // outputs come in increasing j1 = t + 16 e
     Best2F bb;
@@ -353,6 +381,8 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
       rj2[warp] = bb.j2;
     }
     __syncthreads();
+    // every warp is done with the slot: refill it
+    if (threadIdx.x == 0) issue(i + 2);
     if (warp == 0) {
       Best2F o;
       o.init();
@@ -399,7 +429,7 @@ cudaError_t fft2_configure() {
   if ((e = cudaFuncSetAttribute(k_fwd2_pass2, smem, (int)kSmemBytes))) return e;
   if ((e = cudaFuncSetAttribute(k_grid2_pass1, smem, (int)kP1Smem))) return e;
   if ((e = cudaFuncSetAttribute(k_grid2_pass2, smem, (int)kP2Smem))) return e;
-  // two CTAs of either grid pass per SM
+  // two CTAs of grid pass 1, three of pass 2 per SM
   if ((e = cudaFuncSetAttribute(k_grid2_pass1, carve, (int)cudaSharedmemCarveoutMaxShared))) return e;
   return cudaFuncSetAttribute(k_grid2_pass2, carve, (int)cudaSharedmemCarveoutMaxShared);
 }
@@ -434,14 +464,15 @@ int sm_count() {
 }  // namespace
 
 cudaError_t launch_grid2(const SlotDev* slots, const Fft2Maps& maps, int M, cudaStream_t st) {
-  // two CTAs per SM: pass 1 as 16 column blocks x R radius sets
+  // pass 1: two CTAs per SM, as 16 column blocks x R radius sets; pass 2:
+  // three CTAs per SM
   const int ctas = 2 * sm_count();
   int R = ctas / 16;
   R = R < 1 ? 1 : (R > M ? M : R);
   cudaError_t e = launch2(k_grid2_pass1, dim3(16 * R), kP1Smem, slots, maps, st);
   if (e != cudaSuccess) return e;
-  const int items = 16 * M;
-  return launch2(k_grid2_pass2, dim3(items < ctas ? items : ctas), kP2Smem, slots, maps, st);
+  const int items = 16 * M, ctas2 = 3 * sm_count();
+  return launch2(k_grid2_pass2, dim3(items < ctas2 ? items : ctas2), kP2Smem, slots, maps, st);
 }
 
 cudaError_t launch_forward2(const SlotDev* slots, const Fft2Maps& maps, cudaStream_t st) {
