@@ -65,8 +65,7 @@ struct PlanDev {
   const double* rho64;      // [M] 1 / ||e_a||_N^2 = (1 - r_s^N) / (1 + r_s^N) (renormalised selection)
   const float* rho32;       // [M] the same in FP32
   const double2* K64;       // [M * N] 1 / (1 - r_s exp(2 pi i d / N)), FP64
-  const float* sh32;        // [N] sin(pi d / N) in FP32 (persistent-kernel sizes, N <= 4096)
-  const float2* tw32n;      // [N] exp(+2 pi i k / N) in FP32 (two-pass, mixed-radix, N <= 4096); two-pass:
+  const float2* tw32n;      // [N] exp(+2 pi i k / N) in FP32 (two-pass, mixed-radix); two-pass:
                             // followed by [4096] exp(+2 pi i m / 4096)
   double inv_n;             // 1 / N (exact for powers of two)
   // Non-uniform samples (nN > 0): the grid has N angles; the signal is known
@@ -151,7 +150,7 @@ __device__ __forceinline__ double obj_rho64(const SlotDev& sd, int s) { return s
 // Host-visible layout sizes (the bench reports per-step transfer bytes from them).
 static_assert(sizeof(StepRec) == 80, "StepRec layout");
 static_assert(sizeof(SlotCtl) == 64, "SlotCtl layout");
-static_assert(sizeof(SlotDev) == 400, "SlotDev layout");
+static_assert(sizeof(SlotDev) == 392, "SlotDev layout");
 
 // Kernel launchers (afd_kernels.cu).  `ids` lists the slots of one launch, all
 // with the same logN; `n` is their number.  Each returns the launch status.

@@ -112,7 +112,8 @@ k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
     for (int e = 0; e < P; ++e) v[e] = mk2<T>((T)0, (T)0);
   }
 
-  fft_run<T, LOGN, +1, 0, false, PP>(v, t, buf, tw);
+  // the CTA's transforms synchronise on their own group barriers
+  fft_run<T, LOGN, +1, 0, false, PP, (FPC > 1)>(v, t, buf, tw);
 
   // Objective and per-radius best, straight from registers.
   if constexpr (sizeof(T) == 4) {

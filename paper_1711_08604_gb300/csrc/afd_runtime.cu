@@ -226,9 +226,7 @@ struct TableShape {
     H = N / B;
     tws = mixed ? 1 : std::max(FftSchedule::tw_size(two_pass ? 8 : logN), 1);
   }
-  bool tw32n() const { return two_pass || mixed || sh32(); }
-  // FP32 half-angle sines: the persistent kernel's sizes
-  bool sh32() const { return !mixed && logN <= PERSISTENT_MAX_LOGN; }
+  bool tw32n() const { return two_pass || mixed; }
 };
 
 size_t Tables::bytes_for(int N, int M) {
@@ -238,7 +236,7 @@ size_t Tables::bytes_for(int N, int M) {
   size_t off = 0;
   for (size_t b : {sizeof(double) * M, 16 * (size_t)N, 16 * tws, 8 * tws, 8 * (size_t)M * B, 8 * (size_t)M * H,
                    4 * (size_t)M * B, 4 * (size_t)M * H, 4 * (size_t)M, 8 * (size_t)M, 8 * (size_t)M,
-                   8 * (size_t)M, 4 * (size_t)M, 16 * (size_t)M * N, sh.sh32() ? 4 * (size_t)N : 0, sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0})
+                   8 * (size_t)M, 4 * (size_t)M, 16 * (size_t)M * N, sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0})
     off = align_up(off + b);
   return off;
 }
@@ -313,7 +311,7 @@ afd_status Tables::build(int N_, const double* r, int M_) {
                  o_rlo32 = place(4 * rlo32.size()), o_rhi32 = place(4 * rhi32.size()),
                  o_wsq = place(4 * (size_t)M), o_w64 = place(8 * (size_t)M), o_sq = place(8 * (size_t)M),
                  o_rho64 = place(8 * (size_t)M), o_rho32 = place(4 * (size_t)M), o_K = place(16 * (size_t)M * N),
-                 o_sh32 = place(sh.sh32() ? 4 * (size_t)N : 0), o_tw32n = place(sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0);
+                 o_tw32n = place(sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0);
     CUDA_TRY(cudaMalloc(&mem, off));
     bytes = off;
     char* b = static_cast<char*>(mem);
@@ -362,13 +360,6 @@ afd_status Tables::build(int N_, const double* r, int M_) {
       }
       CUDA_TRY(cudaMemcpy(b + o_tw32n, tw32n.data(), 4 * tw32n.size(), cudaMemcpyHostToDevice));
       dev.tw32n = reinterpret_cast<const float2*>(b + o_tw32n);
-    }
-    dev.sh32 = nullptr;
-    if (sh.sh32()) {  // sin(pi d / N) for the persistent kernel's FP32 update
-      std::vector<float> sh32(N);
-      for (int d = 0; d < N; ++d) sh32[d] = (float)std::sin(3.14159265358979323846 * (double)d / (double)N);
-      CUDA_TRY(cudaMemcpy(b + o_sh32, sh32.data(), 4 * (size_t)N, cudaMemcpyHostToDevice));
-      dev.sh32 = reinterpret_cast<const float*>(b + o_sh32);
     }
     CUDA_TRY(launch_kernel_table(dev.radii, M, N, reinterpret_cast<double2*>(b + o_K), nullptr));
     CUDA_TRY(cudaDeviceSynchronize());
