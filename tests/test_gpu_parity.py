@@ -192,18 +192,22 @@ def test_nan_input_reports_numeric_error(prec):
     assert e.value.status == -7
 
 
-@pytest.mark.parametrize("N", [256, 1024, 4096])
+@pytest.mark.parametrize("N", [8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096])
 def test_persistent_kernel_equals_kernel_sequence(N):
     # one cooperative launch per decomposition vs one launch per kernel per
-    # step: the same arithmetic in the same order, so bitwise equal results
+    # step: the same FP64 arithmetic in the same order, so bitwise equal
+    # results.  Every transform shape of the persistent kernel: groups
+    # narrower than a warp (forward transform by all of warp 0), one warp,
+    # and whole-warp groups on named barriers with the split input.
     s = W.tones(item=3, N=N, M=40, K=12) if N >= 1024 else W.kernel_sum(item=3, N=N, M=40, K=12)
     a, _ = run(s.G, s.radii, s.K, 1, persistent=True)
     b, _ = run(s.G, s.radii, s.K, 1, persistent=False)
     for k in ("a", "coeff", "delta", "idx"):
         assert np.array_equal(a[k], b[k]), k
     tol = float(a["delta"][6]) * 1.0000001
-    c, _ = run(s.G, s.radii, s.K, 1, tol=tol, persistent=True)
-    assert c["steps"] == 6 and np.array_equal(c["coeff"], a["coeff"][:6])
+    if tol > 0.0 and float(a["delta"][5]) > tol:  # the stop rule fires at step 6
+        c, _ = run(s.G, s.radii, s.K, 1, tol=tol, persistent=True)
+        assert c["steps"] == 6 and np.array_equal(c["coeff"], a["coeff"][:6])
 
 
 def test_persistent_kernel_profiled():
