@@ -351,15 +351,33 @@ __device__ __forceinline__ double2 sum_fp64_group(double x, double y, double* re
   return make_double2(tx, ty);
 }
 
+// The same for one component (the energy): the x half of sum_fp64_group,
+// bitwise the same total.
+__device__ __forceinline__ double sum_fp64_group1(double x, double* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0 && warp < FP64_THREADS / 32) red[warp] = x;
+  __syncthreads();
+  double tx = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < FP64_THREADS / 32; ++w) tx += red[w];
+  }
+  return tx;
+}
+
 // Reduced-remainder update of Sec. 2 at z_m for a = r_s w^j and
 // c' = c sqrt(1 - r_s^2):  G_{k+1}(z_m) = (G_k(z_m) u - c') / (z_m - a) with
 // u = 1 - conj(a) z_m = 1 - r_s w^d, d = (m - j) mod N.  Because
 // z_m - a = z_m conj(u), dividing by it is multiplying by
-// B = conj(z_m) conj(K_s[d]), so G_{k+1}(z_m) = A - c' B with A = G_k(z_m) u B.
-// A and B depend on the selected point but not on its coefficient, so the
+// B = conj(z_m) conj(K_s[d]), so G_{k+1}(z_m) = (U - c') B with U = G_k(z_m) u.
+// U and B depend on the selected point but not on its coefficient, so the
 // persistent kernel forms them while the coefficient is still being summed.
+// (Ten FP64 operations for U and B, six to apply: FP64 is the scarce pipe.)
 struct UpdCoef {
-  double2 A, B;
+  double2 U, B;
 };
 __device__ __forceinline__ UpdCoef update_coef(const SlotDev& sd, int m, int s, int j, double r, double2 g) {
   const int N = sd.p.N;
@@ -371,15 +389,14 @@ __device__ __forceinline__ UpdCoef update_coef(const SlotDev& sd, int m, int s, 
   // B = conj(K z)
   const double br = fma(kd.x, z.x, -kd.y * z.y);
   const double bi = -fma(kd.x, z.y, kd.y * z.x);
-  // A = (g u) B
-  const double gr = fma(g.x, ur, -g.y * ui), gi = fma(g.x, ui, g.y * ur);
   UpdCoef o;
-  o.A = make_double2(fma(gr, br, -gi * bi), fma(gr, bi, gi * br));
+  o.U = make_double2(fma(g.x, ur, -g.y * ui), fma(g.x, ui, g.y * ur));
   o.B = make_double2(br, bi);
   return o;
 }
 __device__ __forceinline__ double2 update_apply(const UpdCoef& q, double cr, double ci) {
-  return make_double2(q.A.x - fma(cr, q.B.x, -ci * q.B.y), q.A.y - fma(cr, q.B.y, ci * q.B.x));
+  const double xr = q.U.x - cr, xi = q.U.y - ci;
+  return make_double2(fma(xr, q.B.x, -xi * q.B.y), fma(xr, q.B.y, xi * q.B.x));
 }
 __device__ __forceinline__ double2 update_point(const SlotDev& sd, int m, int s, int j, double r, double cr,
                                                 double ci, double2 g) {

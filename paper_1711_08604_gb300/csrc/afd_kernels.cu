@@ -276,6 +276,7 @@ template <bool INIT>
 __global__ void __launch_bounds__(FP64_THREADS)
 k_update(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
   __shared__ double red[2 * (FP64_THREADS / 32)];
+  __shared__ double s_cp[2];  // c' = c sqrt(1 - r^2), formed once per CTA
   __shared__ int s_last;
   pdl_launch_dependents();
   const SlotDev& sd = slots[ids[blockIdx.y]];
@@ -287,20 +288,34 @@ k_update(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
   const int p = blockIdx.x;
   const int m = p * FP64_CHUNK + threadIdx.x;
   const int k = ctl->k;
+  if constexpr (!INIT) {
+    // (FP64 instructions cost the same per warp whatever the active lanes)
+    if (threadIdx.x == 0) {
+      const StepRec& rec = sd.rec[k];
+      const double na = sd.p.sq64[rec.s];
+      s_cp[0] = rec.c_re * na;
+      s_cp[1] = rec.c_im * na;
+    }
+    __syncthreads();
+  }
   double e = 0.0;
   if (m < N) {
     double2 g = sd.G[m];
     if constexpr (!INIT) {
       const StepRec& rec = sd.rec[k];
       const int s = rec.s;
-      const double na = sd.p.sq64[s];
-      g = update_point(sd, m, s, rec.j, sd.p.radii[s], rec.c_re * na, rec.c_im * na, g);
+      g = update_point(sd, m, s, rec.j, sd.p.radii[s], s_cp[0], s_cp[1], g);
       sd.G[m] = g;
     }
     e = fma(g.x, g.x, g.y * g.y);
-    if (sd.prec) sd.g32[m] = make_float2((float)(g.x * sd.p.inv_n), (float)(g.y * sd.p.inv_n));
+    // G / N in FP32, converted on the integer pipe: scaling by a power of two
+    // commutes with the rounding
+    if (sd.prec) {
+      const float inv_n = d2f_rn(sd.p.inv_n);
+      sd.g32[m] = make_float2(d2f_rn(g.x) * inv_n, d2f_rn(g.y) * inv_n);
+    }
   }
-  const double es = sum_fp64_group(e, 0.0, red).x;
+  const double es = sum_fp64_group1(e, red);
   if (threadIdx.x == 0) sd.epart[p] = es;
   if (!arrive_last(&ctl->cnt_update, gridDim.x, &s_last)) return;
   if (threadIdx.x >= 32) return;

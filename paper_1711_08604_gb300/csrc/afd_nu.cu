@@ -301,9 +301,9 @@ k_update_nu(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
       sd.G[m] = g;
     }
     e = w * fma(g.x, g.x, g.y * g.y);
-    sd.g32[m] = make_float2((float)(w * g.x), (float)(w * g.y));
+    sd.g32[m] = make_float2(d2f_rn(w * g.x), d2f_rn(w * g.y));  // integer-pipe conversion
   }
-  const double es = sum_fp64_group(e, 0.0, red).x;
+  const double es = sum_fp64_group1(e, red);
   if (threadIdx.x == 0) sd.epart[p] = es;
   if (!arrive_last(&ctl->cnt_update, gridDim.x, &s_last)) return;
   if (threadIdx.x >= 32) return;
