@@ -668,12 +668,14 @@ afd_status enqueue_group(const SlotPool& pool, const SlotPool::Group& g, int K, 
 //
 // A batch chooses, per N-class, among the bitwise-equivalent grid-kernel
 // variants (points per thread, CTA width) by timing each on the batch's own
-// first step: the group's slots are initialised and transformed, then every
-// variant runs one warm-up and kTuneReps timed launches (CUDA events on the
-// batch's stream); the fastest is kept.  Choices are cached per process by
+// first step: the group's slots are initialised and transformed, then in
+// each of kTuneRounds rounds every variant runs one warm-up and kTuneReps
+// timed launches (CUDA events on the batch's stream); the variant with the
+// fastest round is kept.  Choices are cached per process by
 // (device, N, radii count, signal count), so later batches of the same shape
 // skip the measurement.
 constexpr int kTuneReps = 3;
+constexpr int kTuneRounds = 3;  // interleaved rounds over the variants
 std::mutex g_tune_mu;
 std::map<std::array<int, 4>, std::pair<int, float>> g_tune_cache;
 
@@ -700,25 +702,33 @@ afd_status autotune(SlotPool& pool, int device, cudaStream_t st) {
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    int best = 0;
-    float best_us = 0.f;
+    // Rounds over all variants, each variant's best round counts: a
+    // variant timed while the clocks ramp up or another process runs is not
+    // chosen or dropped for that alone.
+    float var_us[GRID_VARIANTS];
+    for (int v = 0; v < GRID_VARIANTS; ++v) var_us[v] = 3.0e38f;
     cudaError_t err = cudaSuccess;
-    for (int v = 0; v < GRID_VARIANTS && err == cudaSuccess; ++v) {
-      if (!grid_variant_ok(g.logN, pool.prec, v)) continue;
-      err = launch_grid(pool.slots_dev, ids, g.count, g.logN, pool.prec, g.Mmax, st, v);
-      if (err == cudaSuccess) err = cudaEventRecord(e0, st);
-      for (int r = 0; r < kTuneReps && err == cudaSuccess; ++r)
+    for (int round = 0; round < kTuneRounds && err == cudaSuccess; ++round) {
+      for (int v = 0; v < GRID_VARIANTS && err == cudaSuccess; ++v) {
+        if (!grid_variant_ok(g.logN, pool.prec, v)) continue;
         err = launch_grid(pool.slots_dev, ids, g.count, g.logN, pool.prec, g.Mmax, st, v);
-      if (err == cudaSuccess) err = cudaEventRecord(e1, st);
-      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-      const float us = 1e3f * ms / kTuneReps;
-      if (err == cudaSuccess && (v == 0 || us < best_us)) {
-        best = v;
-        best_us = us;
+        if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+        for (int r = 0; r < kTuneReps && err == cudaSuccess; ++r)
+          err = launch_grid(pool.slots_dev, ids, g.count, g.logN, pool.prec, g.Mmax, st, v);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess) var_us[v] = std::min(var_us[v], 1e3f * ms / kTuneReps);
       }
     }
+    int best = 0;
+    float best_us = var_us[0];
+    for (int v = 1; v < GRID_VARIANTS; ++v)
+      if (grid_variant_ok(g.logN, pool.prec, v) && var_us[v] < best_us) {
+        best = v;
+        best_us = var_us[v];
+      }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess) return cuda_fail(err, "autotune", __LINE__);
