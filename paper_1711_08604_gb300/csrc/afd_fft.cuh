@@ -155,7 +155,10 @@ __device__ __forceinline__ void fft_pass(V2<T>* v, int t, const V2<T>* __restric
   }
 }
 
-// Store the outputs of pass PASS to shared memory.
+// Store the outputs of pass PASS to shared memory.  When the stride is a
+// multiple of 16, smem_pad(base + q s) = smem_pad(base) + q (s + s / 16): one
+// padded base per butterfly and constant offsets (no index arithmetic per
+// element).
 template <typename T, int LOGN, int PASS, int PP = 0>
 __device__ __forceinline__ void fft_store(const V2<T>* v, int t, V2<T>* buf) {
   using S = FftShape<T, LOGN, PP>;
@@ -165,21 +168,34 @@ __device__ __forceinline__ void fft_store(const V2<T>* v, int t, V2<T>* buf) {
     const int b = t + i * S::TPF;
     const int k = b & (NS - 1);
     const int base = (b - k) * R + k;
+    if constexpr (NS % 16 == 0) {
+      V2<T>* p = buf + smem_pad(base);
 #pragma unroll
-    for (int q = 0; q < R; ++q) buf[smem_pad(base + q * NS)] = v[i * R + q];
+      for (int q = 0; q < R; ++q) p[q * (NS + NS / 16)] = v[i * R + q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) buf[smem_pad(base + q * NS)] = v[i * R + q];
+    }
   }
 }
 
-// Load the inputs of pass PASS from shared memory.
+// Load the inputs of pass PASS from shared memory (constant offsets from one
+// padded base when the stride N / R is a multiple of 16, as in fft_store).
 template <typename T, int LOGN, int PASS, int PP = 0>
 __device__ __forceinline__ void fft_load(V2<T>* v, int t, const V2<T>* buf) {
   using S = FftShape<T, LOGN, PP>;
-  constexpr int R = S::radix(PASS), NB = S::P / R;
+  constexpr int R = S::radix(PASS), NB = S::P / R, ST = S::N / R;
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int b = t + i * S::TPF;
+    if constexpr (ST % 16 == 0) {
+      const V2<T>* p = buf + smem_pad(b);
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[i * R + q] = buf[smem_pad(b + q * (S::N / R))];
+      for (int q = 0; q < R; ++q) v[i * R + q] = p[q * (ST + ST / 16)];
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) v[i * R + q] = buf[smem_pad(b + q * ST)];
+    }
   }
 }
 
