@@ -254,12 +254,17 @@ def bench_chirp(afd, torch, dev, reps: int = 3) -> dict:
                                        "ms_per_step": grid_ms / max(1, steps)}}
 
 
-def bench_single(afd, torch, dev, sig, precision, reps: int = 20) -> dict:
+def bench_single(afd, torch, dev, sig, precision, reps: int = 20, plan=None, grid_angles=None, **plan_kw) -> dict:
     """One signal's whole decomposition through afd_decompose (device-resident
-    input; CUDA events on the plan's stream), best of `reps`."""
-    stream = torch.cuda.Stream(device=dev)
-    plan = afd.afd_plan_create(sig.N, sig.radii, precision=precision, device=dev.index,
-                               stream=stream.cuda_stream, use_graph=True)
+    input; CUDA events on the plan's stream), best of `reps`.  plan: an
+    existing plan (its stream is used); grid_angles: angles of the grid when
+    they are not the samples (non-uniform plans)."""
+    if plan is None:
+        stream = torch.cuda.Stream(device=dev)
+        plan = afd.afd_plan_create(sig.N, sig.radii, precision=precision, device=dev.index,
+                                   stream=stream.cuda_stream, use_graph=True, **plan_kw)
+    else:
+        stream = torch.cuda.ExternalStream(afd.afd_plan_get_stream(plan), device=dev)
     Gd = torch.from_numpy(sig.G).to(dev)
     K = sig.K
     out = {"a": torch.zeros(2 * K, dtype=torch.float64, device=dev),
@@ -277,10 +282,34 @@ def bench_single(afd, torch, dev, sig, precision, reps: int = 20) -> dict:
             times.append(e0.elapsed_time(e1))
     plan.close()
     ms = min(times)
+    L = grid_angles or sig.N
     return {"ms_per_decomposition": ms, "p50_ms": float(np.percentile(times, 50)),
-            "p99_ms": float(np.percentile(times, 99)), "grid_evals_per_s": sig.M * sig.N * K / (ms * 1e-3),
+            "p99_ms": float(np.percentile(times, 99)), "grid_evals_per_s": sig.M * L * K / (ms * 1e-3),
             "signals_per_s": 1e3 / ms,
             "timing": "CUDA events around afd_decompose (device-resident input), min / p50 / p99 of %d" % reps}
+
+
+def bench_next(afd, torch, dev, reps: int = 10) -> dict:
+    """The NEXT rows, one signal each, FP32 grid + FP64 guard: a mixed-radix
+    size (N = 3000 = 2^3 3 5^3), non-uniform samples (3000 jittered angles,
+    L = 1024 grid angles) and the renormalised objective on workload 2."""
+    from paper_1711_08604_gb300 import workloads as W
+    fp32 = afd.AFD_FP32_GUARDED
+    out = {}
+    mixed = W.tones(item=5, N=3000, M=100, K=20)
+    out["mixed_radix"] = dict(bench_single(afd, torch, dev, mixed, fp32, reps=reps),
+                              workload="tones: N=3000 (2^3 3 5^3, mixed radix), M=100, K=20")
+    x = W.nonuniform()
+    stream = torch.cuda.Stream(device=dev)
+    plan = afd.afd_plan_create_nonuniform(x.theta, x.radii, x.L, weights=x.weights, device=dev.index,
+                                          stream=stream.cuda_stream, use_graph=True)
+    out["nonuniform"] = dict(bench_single(afd, torch, dev, x, fp32, reps=reps, plan=plan, grid_angles=x.L),
+                             workload="non-uniform: %d jittered samples, L=%d grid angles, M=%d, K=%d"
+                                      % (x.N, x.L, x.M, x.K))
+    t = W.tones()
+    out["renormalised"] = dict(bench_single(afd, torch, dev, t, fp32, reps=reps, renormalise=True),
+                               workload="tones: N=4096, M=200, K=50, renormalised objective")
+    return out
 
 
 def bench_serve(afd, duration: float = 3.0, fp64_sample: int = 40) -> dict:
@@ -546,7 +575,8 @@ def run_afd(args):
                 "batch": bench_batch(afd, torch, dev),
                                        "large_two_pass": bench_chirp(afd, torch, dev),
                                        "serving": bench_serve(afd, args.serve_seconds),
-                                       "paper_table9": bench_paper_sweep(afd)}
+                                       "paper_table9": bench_paper_sweep(afd),
+                                       "next_rows": bench_next(afd, torch, dev)}
         print(json.dumps(line))
     plan.close()
     if ws > 1:
@@ -564,7 +594,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and serving workloads")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
-    ap.add_argument("--workload", choices=["main", "batch", "serve", "sweep", "large"], default="main",
+    ap.add_argument("--workload", choices=["main", "batch", "serve", "sweep", "large", "next"], default="main",
                     help="main: the contract line; batch / serve / sweep: only that workload's figures "
                          "(for profiling), printed as one JSON object")
     args = ap.parse_args()
@@ -578,7 +608,8 @@ def main():
         afd._native.load()
         dev = torch.device("cuda", 0)
         fn = {"batch": lambda: bench_batch(afd, torch, dev), "serve": lambda: bench_serve(afd, args.serve_seconds),
-              "sweep": lambda: bench_paper_sweep(afd), "large": lambda: bench_chirp(afd, torch, dev)}[args.workload]
+              "sweep": lambda: bench_paper_sweep(afd), "large": lambda: bench_chirp(afd, torch, dev),
+              "next": lambda: bench_next(afd, torch, dev)}[args.workload]
         print(json.dumps(fn()))
         return 0
     return run_afd(args)

@@ -245,6 +245,14 @@ class NonuniformSignal:
     L: int
     K: int
 
+    @property
+    def N(self) -> int:  # samples
+        return int(self.theta.size)
+
+    @property
+    def M(self) -> int:  # radii
+        return int(self.radii.size)
+
 
 def nonuniform(item: int = 0, N: int = 3000, L: int = 1024, M: int = 64, K: int = 12) -> NonuniformSignal:
     """Non-uniform sampling case: N jittered angles with trapezoid weights, a
