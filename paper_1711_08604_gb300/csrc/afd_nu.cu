@@ -35,7 +35,9 @@ namespace afd {
 
 namespace {
 
-constexpr int NUDFT_L = 64, NUDFT_GROUPS = 4;  // l values per CTA; sample groups per l
+// l values per CTA; sample groups per l.  Many groups: a step's DFT has only
+// Lc (a few thousand) outputs, so the samples are split 32 ways to fill the GPU.
+constexpr int NUDFT_L = 16, NUDFT_GROUPS = 32;
 
 template <int LOGN>
 struct NuCfg {
