@@ -570,6 +570,8 @@ def run_afd(args):
             line["other_workloads"] = {
                 "c1_kernel_sum": dict(bench_single(afd, torch, dev, W.kernel_sum(), afd.AFD_FP64_PLAIN),
                                       workload="kernel sum: N=256, M=50 radii i/50, K=10, FP64 plain"),
+                "c1_kernel_sum_fp32": dict(bench_single(afd, torch, dev, W.kernel_sum(), afd.AFD_FP32_GUARDED),
+                                           workload="kernel sum: N=256, M=50 radii i/50, K=10, FP32 grid + FP64 guard"),
                 "c2_tones_fp64_plain": dict(bench_single(afd, torch, dev, s, afd.AFD_FP64_PLAIN, reps=10),
                                             workload="tones: N=4096, M=200, K=50, FP64 plain (the comparator)"),
                 "batch": bench_batch(afd, torch, dev),
