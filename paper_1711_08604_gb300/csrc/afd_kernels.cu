@@ -443,20 +443,24 @@ __device__ __forceinline__ bool grid_barrier(const SlotDev& sd, unsigned target,
   return *s_ok != 0;
 }
 
-// All greedy steps of one FP32-path signal in one launch.  Per step:
-//   A  each CTA: forward FFT of G_k from its FP32 copy (the arithmetic of
-//      k_forward), its radii's inverse FFTs with the objective and best pairs
-//      (as k_grid) -- barrier --
+// All greedy steps of one FP32-path signal in one launch, one CTA of two or
+// more transform groups per SM.  Per step:
+//   A  each CTA: the FP32 input G_k / N formed from step k-1's FP32 copy and
+//      winner, the forward FFT once (group 0), then each group's radius:
+//      inverse FFT, objective and best pairs (as k_grid)     -- barrier --
 //   B  each CTA: the candidate list (the same in every CTA), then warp-sized
-//      items (one candidate, 32 samples) of the guard's sums -- barrier --
+//      FP64 items (one candidate, 32 samples, one component) of the guard's
+//      sums, the update terms, the previous step's energy partials -- barrier --
 //   C  each CTA: the winner from the partial sums (the same in every CTA),
-//      warp-sized items of the remainder update and energy -- barrier --
-// and, at the top of the next step, the energy, delta and stop rule (the same
-// in every CTA).  FP64 throughput per SM is low, so the guard and update work
-// goes out in 32-sample items over all CTAs, warp 0 of every CTA first.  Each
-// item keeps its warp's shuffle-tree sum, and the consumers add the four warp
-// sums of a 128-sample chunk in warp order, then the chunks as the separate
-// kernels do: results are bitwise those of the multi-kernel sequence.
+//      warp-sized items of the remainder update; no barrier before the next
+//      step's phase A, which needs only step k's FP32 copy and winner.
+// With an energy tolerance, step k-1's energy, delta and stop rule come after
+// step k's first barrier (the same in every CTA).  FP64 throughput per SM
+// sub-partition is low, so the FP64 work goes out in 32-sample items over
+// all CTAs and sub-partitions.  Each item keeps its warp's shuffle-tree sum,
+// and the consumers add the four warp sums of a 128-sample chunk in warp
+// order, then the chunks, as the separate kernels do: results are bitwise
+// those of the multi-kernel sequence.
 constexpr int PERSIST_CTA = 512;  // threads per CTA of the persistent kernel (one CTA per SM)
 
 template <int LOGN>
