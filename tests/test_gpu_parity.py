@@ -210,6 +210,17 @@ def test_persistent_kernel_equals_kernel_sequence(N):
         assert c["steps"] == 6 and np.array_equal(c["coeff"], a["coeff"][:6])
 
 
+def test_persistent_kernel_several_tiles_per_cta():
+    # more radius tiles than CTAs (one CTA per SM): CTAs loop over tiles, and
+    # tiles after the first read their radial powers and weights from memory
+    s = W.tones(item=6, N=4096, M=400, K=8)
+    a, _ = run(s.G, s.radii, s.K, 1, persistent=True)
+    b, _ = run(s.G, s.radii, s.K, 1, persistent=False)
+    for k in ("a", "coeff", "delta", "idx"):
+        assert np.array_equal(a[k], b[k]), k
+    parity.check(s.G, s.radii, a, 1, full_grid=False, grid_steps=(1, 8))
+
+
 def test_persistent_kernel_profiled():
     s = W.tones(item=4, K=8)
     plan = afd.afd_plan_create(s.N, s.radii)
