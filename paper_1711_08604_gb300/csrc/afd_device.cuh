@@ -394,6 +394,19 @@ __device__ __forceinline__ UpdCoef update_coef(const SlotDev& sd, int m, int s, 
   o.B = make_double2(br, bi);
   return o;
 }
+// The two halves of update_coef on their own (bitwise the same values), for
+// forming them on two warps: U = G u and B = conj(K z).
+__device__ __forceinline__ double2 update_u(const SlotDev& sd, int m, int j, double r, double2 g) {
+  const double2 w = __ldg(&sd.p.tw64[wrap_mod(m - j, sd.p.N)]);
+  const double ur = fma(-r, w.x, 1.0), ui = -r * w.y;
+  return make_double2(fma(g.x, ur, -g.y * ui), fma(g.x, ui, g.y * ur));
+}
+__device__ __forceinline__ double2 update_b(const SlotDev& sd, int m, int s, int j) {
+  const int N = sd.p.N;
+  const double2 z = __ldg(&sd.p.tw64[m]);
+  const double2 kd = __ldg(&sd.p.K64[(size_t)s * N + wrap_mod(m - j, N)]);
+  return make_double2(fma(kd.x, z.x, -kd.y * z.y), -fma(kd.x, z.y, kd.y * z.x));
+}
 __device__ __forceinline__ double2 update_apply(const UpdCoef& q, double cr, double ci) {
   const double xr = q.U.x - cr, xi = q.U.y - ci;
   return make_double2(fma(xr, q.B.x, -xi * q.B.y), fma(xr, q.B.y, xi * q.B.x));

@@ -543,10 +543,10 @@ k_persistent(const SlotDev* __restrict__ slots) {
   //  - guard items on the warps with (warp & 2) == 0, the real part of an
   //    item's sum on one warp and the imaginary part on its neighbour;
   //  - update items on the others, warp gw = slot * nb + blockIdx taking
-  //    items gw, gw + nw, ...; while the guard runs, update slot c forms the
-  //    update terms of the CTA's first item for candidate c, and the last
-  //    warp the energy partials of the previous step and the candidates'
-  //    scalars.
+  //    items gw, gw + nw, ...; while the guard runs, update slots 2c and
+  //    2c + 1 form the update terms of the CTA's first item for candidate c,
+  //    and the last two warps the energy partials of the previous step and
+  //    the candidates' scalars.
   constexpr int WPC = FP64_CHUNK / 32;
   constexpr int NWARP = THREADS / 32;
   static_assert(NWARP % 4 == 0 && NWARP >= 8, "two FP64 roles over whole quads of warps");
@@ -563,9 +563,9 @@ k_persistent(const SlotDev* __restrict__ slots) {
   const int m_own = upd_role && gw < W ? gw * 32 + lane : -1;
   double2 g_own = make_double2(0.0, 0.0);
   if (m_own >= 0 && m_own < N) g_own = sd.G[m_own];
-  // update terms A, B (update_coef) of the first role slot's item for the
-  // first NPRE candidates, formed while the guard sums run, candidate c by
-  // update slot c from the item's samples in s_gown
+  // update terms U, B (update_coef) of the first role slot's item for the
+  // first NPRE candidates, formed while the guard sums run: U of candidate c
+  // by update slot 2c, B by slot 2c + 1, from the item's samples in s_gown
   constexpr int NPRE = 4;
   __shared__ UpdCoef s_upd[NPRE][32];
   __shared__ double2 s_gown[32];
@@ -880,11 +880,16 @@ k_persistent(const SlotDev* __restrict__ slots) {
           s_cf32[c][4] = 2.0f * r32;
         }
       }
-      // update terms of the CTA's first update item for candidate role_slot
-      if (role_slot < n && role_slot < NPRE && (int)blockIdx.x < W) {
+      // update terms of the CTA's first update item: candidate c = slot / 2,
+      // U on one update warp and B on the next (another sub-partition)
+      const int pc_ = role_slot >> 1;
+      if (pc_ < n && pc_ < NPRE && (int)blockIdx.x < W) {
         const int m0 = (int)blockIdx.x * 32 + lane;
-        const int2 cj = s_cand[role_slot];
-        if (m0 < N) s_upd[role_slot][lane] = update_coef(sd, m0, cj.x, cj.y, sd.p.radii[cj.x], s_gown[lane]);
+        const int2 cj = s_cand[pc_];
+        if (m0 < N) {
+          if (role_slot & 1) s_upd[pc_][lane].B = update_b(sd, m0, cj.x, cj.y);
+          else s_upd[pc_][lane].U = update_u(sd, m0, cj.y, sd.p.radii[cj.x], s_gown[lane]);
+        }
       }
     } else {
       // real parts at gpart64[it], imaginary parts cap W further on
