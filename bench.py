@@ -47,7 +47,7 @@ STEPREC_BYTES, SLOTCTL_BYTES, SLOTDEV_BYTES = 80, 64, 392  # StepRec, SlotCtl, S
 def kernel_sources_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("afd_kernels.cu", "afd_fft.cuh", "afd_internal.h"):
+    for f in ("afd_kernels.cu", "afd_device.cuh", "afd_fft.cuh", "afd_internal.h"):
         with open(os.path.join(ROOT, "paper_1711_08604_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -103,7 +103,9 @@ struct Best1D {
 
 // Reduce B over each group of TPF consecutive threads; the group's thread
 // t == 0 ends with the result.  All threads of the CTA must call it.
-template <int TPF, class B>
+// FRESH: red was last read before a CTA barrier the caller has passed since,
+// so the barrier that protects its reuse can be skipped.
+template <int TPF, class B, bool FRESH = false>
 __device__ __forceinline__ void group_reduce(B& b, B* red) {
   constexpr int W = TPF < 32 ? TPF : 32;
 #pragma unroll
@@ -114,7 +116,7 @@ __device__ __forceinline__ void group_reduce(B& b, B* red) {
     // order of the merges)
     constexpr int WPG = TPF / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
+    if constexpr (!FRESH) __syncthreads();
     if (lane == 0) red[warp] = b;
     __syncthreads();
     if ((warp % WPG) == 0) {
@@ -223,7 +225,8 @@ __device__ void select_core(const Top2F* top, int M, int N, int sub, float thr, 
   __shared__ int s_count;
   __shared__ float sv[32];
   __shared__ int sf[32];
-  __syncthreads();
+  // (the buffers above are this function's own: every read of them comes
+  // before the CTA barrier that ends the previous call)
   if (threadIdx.x == 0) s_count = 0;
   __syncthreads();
   for (int r = threadIdx.x; r < M * sub; r += THREADS) {

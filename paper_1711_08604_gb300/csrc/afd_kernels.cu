@@ -801,7 +801,8 @@ k_persistent(const SlotDev* __restrict__ slots) {
         const float2 x = v[fft_out_slot<float, LOGN>(u)];
         b.push_ascending(x.x * x.x + x.y * x.y, t + TPF * u);
       }
-      group_reduce<TPF>(b, red2);
+      // (red2 was last read before this tile's spectrum barrier)
+      group_reduce<TPF, Best2F, true>(b, red2);
       if (t == 0 && active) {
         Top2F o;
         o.v1 = b.v1 * w2;
@@ -811,7 +812,9 @@ k_persistent(const SlotDev* __restrict__ slots) {
         top[s] = o;
         if (o.v1 >= 0.0f && o.v1 <= 3.402823466e38f) atomicMax(&ctl->vmax2[k & 1], __float_as_uint(o.v1));
       }
-      __syncthreads();
+      // the CTA's next tile reuses the exchange buffers and red2 (after the
+      // last tile the grid barrier synchronises the CTA)
+      if (tile + (int)nb < n_tiles) __syncthreads();
     }
     if (clk) clk[8 * k + 1] = clock64();
     if (!grid_barrier(sd, nb * ++epoch, &s_ok)) return;
