@@ -130,24 +130,6 @@ __device__ __forceinline__ void group_reduce(B& b, B* red) {
   }
 }
 
-// Deterministic FP64 block sum (fixed shuffle tree, warps added in order).
-// Result valid in thread 0.
-template <int THREADS>
-__device__ __forceinline__ double block_sum(double x, double* red) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = x;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0) {
-#pragma unroll 1
-    for (int w = 0; w < THREADS / 32; ++w) s += red[w];
-  }
-  return s;
-}
-
 // Block-wide best (v, flat) over all threads; every thread gets the result.
 template <int THREADS>
 __device__ __forceinline__ void block_best_f(float& v, int& f, float* sv, int* sf) {

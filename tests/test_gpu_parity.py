@@ -64,6 +64,18 @@ def test_small_and_ragged_sizes(prec, N):
     parity.check(G, radii, res, prec)
 
 
+@pytest.mark.parametrize("prec,N", [(afd.AFD_FP64_PLAIN, 8192), (afd.AFD_FP32_GUARDED, 8192),
+                                    (afd.AFD_FP32_GUARDED, 16384)])
+def test_largest_resident_sizes(prec, N):
+    # the largest transforms held on chip: N = 8192 (the FP64 limit) and
+    # N = 16384 (FP32, 32 points per thread); every grid point at every step
+    G = W.random_signal(N, 11 * N)
+    radii = np.array([0.0, 0.4, 0.9, 0.995])
+    res, _ = run(G, radii, 3, prec)
+    assert res["steps"] == 3
+    parity.check(G, radii, res, prec)
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_single_radius_and_zero_radius_ties(prec):
     # only r = 0: every angle ties exactly, the lowest index must win
