@@ -153,9 +153,68 @@ def cpu_baseline(s, sample_steps: int = 2) -> dict:
     d = oracle.decompose(s.G, s.radii, sample_steps)
     dt = time.perf_counter() - t0
     evals = s.M * s.N * d["steps"]
-    return {"value": evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"first {d['steps']} of {s.K} greedy steps of the same workload "
-                      f"(direct O(M N^2) grid, {evals} grid evals, {dt:.2f} s)"}
+    out = {"value": evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"first {d['steps']} of {s.K} greedy steps of the same workload "
+                     f"(direct O(M N^2) grid, {evals} grid evals, {dt:.2f} s)"}
+    out["single_thread"] = _oracle_single_thread(oracle, s)
+    out["other_configs"] = _oracle_other_configs(oracle)
+    return out
+
+
+def _oracle_single_thread(oracle, s) -> dict:
+    """The same oracle on one host thread: one greedy step over every 8th radius."""
+    sub = s.radii[::8]
+    n0 = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        d = oracle.decompose(s.G, sub, 1)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(n0)
+    evals = len(sub) * s.N * d["steps"]
+    return {"value": evals / dt, "unit": UNIT, "cores": 1,
+            "sample": f"1 greedy step over {len(sub)} of the {s.M} radii ({evals} grid evals, {dt:.2f} s)"}
+
+
+def _oracle_other_configs(oracle) -> dict:
+    """The oracle on all host threads for the other workloads: the kernel sum
+    (N = 256, M = 50, K = 10) in full; the batch and the chirp (N = 65536,
+    M = 1000, K = 100) on bounded samples, extrapolated by their M N^2 K."""
+    from paper_1711_08604_gb300 import workloads as W
+    k1 = W.kernel_sum()
+    t0 = time.perf_counter()
+    d = oracle.decompose(k1.G, k1.radii, k1.K)
+    dt1 = time.perf_counter() - t0
+    c5 = W.chirp()
+    sub = c5.radii[::500]
+    t0 = time.perf_counter()
+    d5 = oracle.decompose(c5.G, sub, 1)
+    dt5 = time.perf_counter() - t0
+    # the batch workload (1024 signals, N in {1024..8192}, M = 100, K = 30): one
+    # greedy step over 10 radii of its first 16 signals gives the oracle's rate
+    # in terms (grid evals x N) per second, extrapolated to the whole batch
+    sigs = W.batch()
+    t0 = time.perf_counter()
+    terms = 0
+    for sg in sigs[:16]:
+        db = oracle.decompose(sg.G, sg.radii[::10], 1)
+        terms += len(sg.radii[::10]) * sg.N * sg.N * db["steps"]
+    dtb = time.perf_counter() - t0
+    rate = terms / dtb
+    total = sum(sg.M * sg.N * sg.N * sg.K for sg in sigs)
+    return {
+        "batch_extrapolated": {"value": sum(sg.M * sg.N * sg.K for sg in sigs) / (total / rate), "unit": UNIT,
+                               "s_per_batch": total / rate,
+                               "sample": f"1 greedy step over 10 radii of 16 of the {len(sigs)} signals "
+                                         f"({dtb:.2f} s), extrapolated by M N^2 K per signal"},
+        "kernel_sum_full": {"value": k1.M * k1.N * d["steps"] / dt1, "unit": UNIT,
+                            "s_per_decomposition": dt1, "sample": "N=256, M=50, K=10 in full"},
+        "chirp_extrapolated": {"value": len(sub) * c5.N * d5["steps"] / dt5, "unit": UNIT,
+                               "s_per_decomposition": dt5 * (c5.M / len(sub)) * (c5.K / d5["steps"]),
+                               "sample": f"1 greedy step over {len(sub)} of the {c5.M} radii "
+                                         f"({dt5:.2f} s), extrapolated linearly in M K"},
+    }
 
 
 def bench_batch(afd, torch, dev, reps: int = 3) -> dict:
