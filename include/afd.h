@@ -384,6 +384,27 @@ afd_status afd_serve_destroy(afd_server* server);
 afd_status afd_inner_products_noalloc(const double* G, int N, const double* points, int n_points,
                                       double* out, void* stream);
 
+/*
+ * Self-test of the bounded waits (failure detection without a GPU fault).
+ * Every spin-wait in the library's kernels gives up after a fixed number of
+ * polls, flags the signal and returns, so that the host reads
+ * AFD_ERR_TIMEOUT and the CUDA context stays usable.  This call makes one
+ * such wait run out on purpose: it launches one CTA on `device` (-1: the
+ * current device) whose wait nothing can satisfy, then reads the kernel's
+ * error bits.
+ *   kind 0  the grid barrier of the persistent kernel: an arrival count of 2
+ *           with one CTA arriving once;
+ *   kind 1  the mbarrier wait of the TMA-staged N = 65536 passes: a phase
+ *           expecting 16 bytes from a copy that is never issued.
+ *   status   AFD_ERR_TIMEOUT when the wait ran out (the expected outcome),
+ *            AFD_OK otherwise.
+ *   seconds  how long the wait polled (the GPU's global timer).
+ * Returns AFD_OK, AFD_ERR_INVALID (NULL pointer, unknown kind or device) or
+ * AFD_ERR_CUDA / AFD_ERR_NOMEM.  Blocks the calling thread for the length of
+ * the wait (seconds); allocates and frees a few hundred bytes of device memory.
+ */
+afd_status afd_selftest_wait_timeout(int device, int kind, afd_status* status, double* seconds);
+
 #ifdef __cplusplus
 }
 #endif

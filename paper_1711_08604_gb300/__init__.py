@@ -446,3 +446,13 @@ def afd_inner_products_noalloc(G, points, out=None, stream=None):
     _check(_lib().afd_inner_products_noalloc(G.data_ptr(), int(G.numel()), points.data_ptr(),
                                              int(points.numel()), out.data_ptr(), s or None))
     return out
+
+
+def afd_selftest_wait_timeout(kind: int, device: int = -1) -> tuple[int, float]:
+    """Make one bounded wait run out on purpose (kind 0: the persistent
+    kernel's grid barrier; kind 1: the mbarrier wait of the TMA-staged
+    passes).  Returns (status the kernel reported, seconds the wait polled);
+    the expected status is AFD_ERR_TIMEOUT."""
+    st, sec = ctypes.c_int(), ctypes.c_double()
+    _check(_lib().afd_selftest_wait_timeout(int(device), int(kind), ctypes.byref(st), ctypes.byref(sec)))
+    return st.value, sec.value

@@ -75,6 +75,7 @@ SIGNATURES = {
     "afd_serve_get_stats": (c_int, [c_void_p, P(ServeStats)]),
     "afd_serve_destroy": (c_int, [c_void_p]),
     "afd_inner_products_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
+    "afd_selftest_wait_timeout": (c_int, [c_int, c_int, P(c_int), P(c_double)]),
 }
 
 _lib = None

@@ -37,6 +37,13 @@ __device__ __forceinline__ float d2f_rn(double x) {
   return __int_as_float(sign | r);
 }
 
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 struct Best2F {
   float v1, v2;
   int j1, j2;

@@ -421,6 +421,29 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
   select_candidates_f32<kThreads>(sd, sd.ctl->k, 16);
 }
 
+// Self-test of the mbarrier wait's bound (failure detection without a
+// fault): the phase expects 16 bytes that no copy delivers (none is issued),
+// so cta_wait polls kWaitLimit times and returns false; the kernel flags the
+// timeout (error bit 2 of ctl->err) as the TMA-staged passes do.
+__global__ void k_selftest_mbarrier(SlotCtl* ctl, unsigned long long* elapsed_ns) {
+  __shared__ alignas(8) uint64_t bar;
+  __shared__ int s_flag;
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
+  const unsigned long long t0 = globaltimer_ns();
+  if (threadIdx.x == 0) mbar_expect_tx(&bar, 16);
+  const bool ok = cta_wait(&bar, 0, &s_flag);
+  if (threadIdx.x == 0) {
+    if (!ok) atomicOr(&ctl->err, 4);
+    *elapsed_ns = globaltimer_ns() - t0;
+  }
+}
+
+cudaError_t launch_selftest_mbarrier(SlotCtl* ctl, unsigned long long* elapsed_ns, cudaStream_t st) {
+  k_selftest_mbarrier<<<1, 32, 0, st>>>(ctl, elapsed_ns);
+  return cudaGetLastError();
+}
+
 cudaError_t fft2_configure() {
   cudaError_t e;
   const auto smem = cudaFuncAttributeMaxDynamicSharedMemorySize;

@@ -164,6 +164,11 @@ bool grid_variant_ok(int logN, int prec, int variant);
 // Whole FP32-path decomposition of slot 0 in one cooperative launch (after
 // launch_init); logN <= MAX_LOGN_RESIDENT.
 cudaError_t launch_persistent(const SlotDev* slots, int logN, int M, cudaStream_t st);
+// Self-tests of the bounded waits: one CTA whose wait can never be satisfied
+// (the persistent kernel's grid barrier; an mbarrier of the TMA-staged
+// passes); elapsed_ns gets the wait's duration by the GPU's global timer.
+cudaError_t launch_selftest_barrier(const SlotDev* slot, unsigned long long* elapsed_ns, cudaStream_t st);
+cudaError_t launch_selftest_mbarrier(SlotCtl* ctl, unsigned long long* elapsed_ns, cudaStream_t st);
 cudaError_t launch_guard(const SlotDev* slots, const int* ids, int n, int N, int cap, cudaStream_t st);
 cudaError_t launch_update(const SlotDev* slots, const int* ids, int n, int N, cudaStream_t st);
 // Mixed-radix path (afd_mixed.cu): N = 2^a 3^b 5^c, not a power of two.

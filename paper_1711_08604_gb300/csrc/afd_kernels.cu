@@ -400,7 +400,7 @@ k_kernel_table(const double* __restrict__ radii, int N, double2* __restrict__ K)
 
 // ------------------------------------------------------ persistent kernel --
 
-constexpr long kBarrierLimit = 1L << 24;  // polls before a barrier gives up (seconds)
+constexpr long kBarrierLimit = 1L << 22;  // polls before a barrier gives up (about a second)
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
@@ -441,6 +441,22 @@ __device__ __forceinline__ bool grid_barrier(const SlotDev& sd, unsigned target,
   }
   __syncthreads();
   return *s_ok != 0;
+}
+
+// Self-test of the grid barrier's bound (failure detection without a fault):
+// one CTA waits for an arrival count that nothing supplies (2, with only its
+// own arrival), so grid_barrier polls kBarrierLimit times, flags the timeout
+// (error bit 2 of ctl->err) and returns false.
+__global__ void k_selftest_barrier(const SlotDev* __restrict__ slot, unsigned long long* elapsed_ns) {
+  __shared__ int s_ok;
+  const unsigned long long t0 = globaltimer_ns();
+  grid_barrier(slot[0], 2u, &s_ok);
+  if (threadIdx.x == 0) *elapsed_ns = globaltimer_ns() - t0;
+}
+
+cudaError_t launch_selftest_barrier(const SlotDev* slot, unsigned long long* elapsed_ns, cudaStream_t st) {
+  k_selftest_barrier<<<1, 32, 0, st>>>(slot, elapsed_ns);
+  return cudaGetLastError();
 }
 
 // All greedy steps of one FP32-path signal in one launch, one CTA of two or

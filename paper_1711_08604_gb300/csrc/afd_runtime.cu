@@ -995,6 +995,44 @@ const char* afd_last_error(void) { return last_error_text(); }
 
 const char* afd_version(void) { return "0.1.0"; }
 
+afd_status afd_selftest_wait_timeout(int device, int kind, afd_status* status, double* seconds) {
+  clear_last_error();
+  if (!status || !seconds) return set_error(AFD_ERR_INVALID, "status and seconds must not be NULL");
+  if (kind != 0 && kind != 1) return set_error(AFD_ERR_INVALID, "kind %d: 0 (grid barrier) or 1 (mbarrier)", kind);
+  int dev = device;
+  if (dev < 0) CUDA_TRY(cudaGetDevice(&dev));
+  DeviceScope scope(dev);
+  if (!scope.ok) return set_error(AFD_ERR_INVALID, "cannot select device %d", dev);
+  // one allocation: SlotCtl, the barrier counter and the timer (a 128-byte
+  // line each), then the SlotDev that points at the first two
+  constexpr size_t kBar = 128, kNs = 256, kSlot = 384;
+  unsigned char* mem = nullptr;
+  CUDA_TRY(cudaMalloc(&mem, kSlot + sizeof(SlotDev)));
+  cudaStream_t st = nullptr;
+  SlotDev h{};
+  h.ctl = reinterpret_cast<SlotCtl*>(mem);
+  h.bar = reinterpret_cast<unsigned*>(mem + kBar);
+  SlotCtl ctl{};
+  unsigned long long ns = 0;
+  auto* d_ns = reinterpret_cast<unsigned long long*>(mem + kNs);
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemsetAsync(mem, 0, kSlot, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mem + kSlot, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = kind == 0 ? launch_selftest_barrier(reinterpret_cast<const SlotDev*>(mem + kSlot), d_ns, st)
+                  : launch_selftest_mbarrier(h.ctl, d_ns, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, mem, sizeof(ctl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, d_ns, sizeof(ns), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  afd_status rc = e == cudaSuccess ? AFD_OK : cuda_fail(e, "wait self-test", __LINE__);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(mem);
+  if (rc != AFD_OK) return rc;
+  *status = (ctl.err & 4) ? AFD_ERR_TIMEOUT : AFD_OK;
+  *seconds = 1e-9 * (double)ns;
+  return AFD_OK;
+}
+
 afd_status afd_plan_create(afd_plan** out, int N, const double* radii, int M, const afd_plan_opts* opts) {
   clear_last_error();
   if (!out) return set_error(AFD_ERR_INVALID, "out is NULL");

@@ -64,3 +64,9 @@ def test_binding_names_match_header():
         assert n in _native.SIGNATURES, n
         if n not in ("afd_plan_opts_default",):
             assert hasattr(afd, n), n
+
+
+def test_wait_selftest_checks_arguments_before_any_cuda_call(lib):
+    st, sec = ctypes.c_int(), ctypes.c_double()
+    assert lib.afd_selftest_wait_timeout(-1, 2, ctypes.byref(st), ctypes.byref(sec)) == -1
+    assert lib.afd_selftest_wait_timeout(-1, 0, None, ctypes.byref(sec)) == -1
