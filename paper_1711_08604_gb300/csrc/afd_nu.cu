@@ -35,9 +35,10 @@ namespace afd {
 
 namespace {
 
-// l values per CTA; sample groups per l.  Many groups: a step's DFT has only
-// Lc (a few thousand) outputs, so the samples are split 32 ways to fill the GPU.
-constexpr int NUDFT_L = 16, NUDFT_GROUPS = 32;
+// l values per CTA and threads per CTA of the non-uniform DFT.  A step's DFT
+// has only Lc (a few thousand) outputs: short blocks of l give enough CTAs to
+// fill the GPU, and every thread walks its share of the samples.
+constexpr int NUDFT_L = 8, NUDFT_THREADS = 256;
 
 template <int LOGN>
 struct NuCfg {
@@ -48,43 +49,87 @@ struct NuCfg {
 };
 
 // c_l = sum_m w_m G(z_m) exp(-i l theta_m) for l < Lc.  CTA: NUDFT_L
-// consecutive l; thread group q (of NUDFT_GROUPS) takes the samples
-// m = q, q + NUDFT_GROUPS, ...; the group sums are added in group order.
-__global__ void __launch_bounds__(NUDFT_L * NUDFT_GROUPS)
+// consecutive l = l0 + i; thread t takes the samples m = t, t + NUDFT_THREADS,
+// ...  For each sample, exp(-i lc theta_m) at the block's middle lc = l0 +
+// NUDFT_L / 2 comes from the exact 64-bit fixed-point phase lc theta_m / 2 pi,
+// and the other powers from multiplying by exp(-+i theta_m) (at most
+// NUDFT_L / 2 products), whose phase keeps 48 bits (a first-order correction
+// of the 24-bit angle): one pair of sincospif per sample and block, not per
+// term.
+// Sums: each thread's partials, a shuffle tree in each warp, the warps in
+// order.
+__global__ void __launch_bounds__(NUDFT_THREADS)
 k_nudft(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
-  __shared__ float2 part[NUDFT_GROUPS][NUDFT_L];
+  __shared__ float2 part[NUDFT_THREADS / 32][NUDFT_L];
   pdl_launch_dependents();
   const SlotDev& sd = slots[ids[0]];
   pdl_wait();
   if (ld_done(sd.ctl)) return;
-  const int li = threadIdx.x % NUDFT_L, q = threadIdx.x / NUDFT_L;
-  const int l = blockIdx.x * NUDFT_L + li;
+  const int l0 = blockIdx.x * NUDFT_L;
   const int n = sd.p.nN;
-  float ax = 0.f, ay = 0.f;
-  if (l < sd.p.nLc) {
-    const unsigned long long ul = (unsigned long long)l;
-    for (int m = q; m < n; m += NUDFT_GROUPS) {
-      // l theta_m / 2 pi modulo 1, exact in 64-bit fixed point; its top 24
-      // bits as the float fraction (phase error below 2 pi 2^-25)
-      const unsigned long long ph = ul * __ldg(&sd.p.nU[m]);
-      const float frac = (float)(ph >> 40) * 5.9604644775390625e-8f;
-      float sn, cs;
-      sincospif(2.0f * frac, &sn, &cs);
-      const float2 g = __ldcg(&sd.g32[m]);  // w_m G(z_m)
-      ax = fmaf(g.x, cs, fmaf(g.y, sn, ax));  // g exp(-i phi)
-      ay = fmaf(g.y, cs, fmaf(-g.x, sn, ay));
+  constexpr int H = NUDFT_L / 2;
+  const unsigned long long ulc = (unsigned long long)(l0 + H);
+  constexpr float TWO_M24 = 5.9604644775390625e-8f;  // 2^-24
+  constexpr float TWO_PI_M48 = 2.2322566310269275e-14f;  // 2 pi 2^-48
+  float2 acc[NUDFT_L];
+#pragma unroll
+  for (int i = 0; i < NUDFT_L; ++i) acc[i] = make_float2(0.f, 0.f);
+  for (int m = threadIdx.x; m < n; m += NUDFT_THREADS) {
+    const unsigned long long u = __ldg(&sd.p.nU[m]);
+    // exp(-i lc theta_m): the top 24 bits of the phase fraction (error below
+    // 2 pi 2^-25)
+    float s0, c0;
+    sincospif(2.0f * ((float)((ulc * u) >> 40) * TWO_M24), &s0, &c0);
+    // exp(-i theta_m): the top 24 bits, then a rotation by the next 24 bits'
+    // angle d < 2 pi 2^-24 (cos d = 1 and sin d = d to FP32 precision)
+    float s1, c1;
+    sincospif(2.0f * ((float)(u >> 40) * TWO_M24), &s1, &c1);
+    const float d = (float)((u >> 16) & 0xffffffull) * TWO_PI_M48;
+    const float zr = fmaf(-s1, d, c1), zi = -fmaf(c1, d, s1);  // (c1 - i s1)(1 - i d)
+    const float2 g = __ldcg(&sd.g32[m]);  // w_m G(z_m)
+    // g exp(-i l theta_m) into acc[l - l0]: l = lc, then upwards (times
+    // exp(-i theta_m)) and downwards (times its conjugate)
+    float fr = c0, fi = -s0, br = c0, bi = -s0;
+    acc[H].x = fmaf(g.x, fr, fmaf(-g.y, fi, acc[H].x));
+    acc[H].y = fmaf(g.x, fi, fmaf(g.y, fr, acc[H].y));
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+      if (k < H) {
+        const float nr = fmaf(fr, zr, -fi * zi), ni = fmaf(fr, zi, fi * zr);
+        fr = nr;
+        fi = ni;
+        acc[H + k].x = fmaf(g.x, fr, fmaf(-g.y, fi, acc[H + k].x));
+        acc[H + k].y = fmaf(g.x, fi, fmaf(g.y, fr, acc[H + k].y));
+      }
+      const float nr = fmaf(br, zr, bi * zi), ni = fmaf(bi, zr, -br * zi);  // times conj(z)
+      br = nr;
+      bi = ni;
+      acc[H - k].x = fmaf(g.x, br, fmaf(-g.y, bi, acc[H - k].x));
+      acc[H - k].y = fmaf(g.x, bi, fmaf(g.y, br, acc[H - k].y));
     }
   }
-  part[q][li] = make_float2(ax, ay);
-  __syncthreads();
-  if (q == 0 && l < sd.p.nLc) {
-    float2 r = part[0][li];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 1; k < NUDFT_GROUPS; ++k) {
-      r.x += part[k][li].x;
-      r.y += part[k][li].y;
+  for (int i = 0; i < NUDFT_L; ++i) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc[i].x += __shfl_xor_sync(0xffffffffu, acc[i].x, off);
+      acc[i].y += __shfl_xor_sync(0xffffffffu, acc[i].y, off);
     }
-    sd.c32[l] = r;
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NUDFT_L; ++i) part[warp][i] = acc[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < NUDFT_L && l0 + (int)threadIdx.x < sd.p.nLc) {
+    float2 r = part[0][threadIdx.x];
+#pragma unroll
+    for (int w = 1; w < NUDFT_THREADS / 32; ++w) {
+      r.x += part[w][threadIdx.x].x;
+      r.y += part[w][threadIdx.x].y;
+    }
+    sd.c32[l0 + threadIdx.x] = r;
   }
 }
 
@@ -359,7 +404,7 @@ cudaError_t grid_nu_attr() {
 
 cudaError_t launch_nudft(const SlotDev* slots, const int* ids, int Lc, cudaStream_t st) {
   const dim3 grid((Lc + NUDFT_L - 1) / NUDFT_L);
-  return launch_pdl_nu(k_nudft, grid, dim3(NUDFT_L * NUDFT_GROUPS), 0, st, slots, ids);
+  return launch_pdl_nu(k_nudft, grid, dim3(NUDFT_THREADS), 0, st, slots, ids);
 }
 
 cudaError_t launch_grid_nu(const SlotDev* slots, const int* ids, int logN, int M, cudaStream_t st) {
