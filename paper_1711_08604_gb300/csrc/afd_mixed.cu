@@ -79,8 +79,9 @@ __device__ __forceinline__ void dft_any(V2<T>* v) {
 }
 
 // One Stockham pass of radix R; src(b, q, N/R) is input q of butterfly b,
-// dst(i, value) takes output i.
-template <typename T, int R, int DIR, class Src, class Dst>
+// dst(i, value) takes output i.  tw: the N twiddles w^k, in shared memory
+// (TWS) or in global memory (read through the read-only cache).
+template <typename T, int R, int DIR, bool TWS, class Src, class Dst>
 __device__ __forceinline__ void mx_pass(int N, int Ns, const V2<T>* __restrict__ tw, Src& src, Dst& dst) {
   const int NR = N / R, step = N / (Ns * R);
   for (int b = threadIdx.x; b < NR; b += MX_THREADS) {
@@ -91,7 +92,9 @@ __device__ __forceinline__ void mx_pass(int N, int Ns, const V2<T>* __restrict__
     if (k != 0) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
-        const V2<T> w = __ldg(&tw[q * k * step]);  // q k step < N
+        V2<T> w;  // q k step < N
+        if constexpr (TWS) w = tw[q * k * step];
+        else w = __ldg(&tw[q * k * step]);
         v[q] = DIR > 0 ? cmul<T>(v[q], w) : cmulc<T>(v[q], w);
       }
     }
@@ -102,29 +105,29 @@ __device__ __forceinline__ void mx_pass(int N, int Ns, const V2<T>* __restrict__
   }
 }
 
-template <typename T, int DIR, class Src, class Dst>
+template <typename T, int DIR, bool TWS, class Src, class Dst>
 __device__ __forceinline__ void mx_pass_any(int R, int N, int Ns, const V2<T>* __restrict__ tw, Src& src,
                                             Dst& dst) {
   switch (R) {
-    case 16: mx_pass<T, 16, DIR>(N, Ns, tw, src, dst); break;
-    case 8: mx_pass<T, 8, DIR>(N, Ns, tw, src, dst); break;
-    case 4: mx_pass<T, 4, DIR>(N, Ns, tw, src, dst); break;
-    case 2: mx_pass<T, 2, DIR>(N, Ns, tw, src, dst); break;
-    case 3: mx_pass<T, 3, DIR>(N, Ns, tw, src, dst); break;
-    default: mx_pass<T, 5, DIR>(N, Ns, tw, src, dst); break;
+    case 16: mx_pass<T, 16, DIR, TWS>(N, Ns, tw, src, dst); break;
+    case 8: mx_pass<T, 8, DIR, TWS>(N, Ns, tw, src, dst); break;
+    case 4: mx_pass<T, 4, DIR, TWS>(N, Ns, tw, src, dst); break;
+    case 2: mx_pass<T, 2, DIR, TWS>(N, Ns, tw, src, dst); break;
+    case 3: mx_pass<T, 3, DIR, TWS>(N, Ns, tw, src, dst); break;
+    default: mx_pass<T, 5, DIR, TWS>(N, Ns, tw, src, dst); break;
   }
 }
 
 // The whole transform (at least two passes): first(b, q, N/R0) supplies pass
 // 0's inputs, last(i, value) consumes the natural-order outputs.  buf holds
 // 2 N points.  Every thread of the CTA must call it.
-template <typename T, int DIR, class First, class Last>
+template <typename T, int DIR, bool TWS, class First, class Last>
 __device__ void mx_run(const PlanDev& p, V2<T>* buf, const V2<T>* __restrict__ tw, First& first, Last& last) {
   const int N = p.N, np = p.mix_npass;
   V2<T>* cur = buf;
   V2<T>* nxt = buf + N;
   auto to_cur = [&](int i, V2<T> x) { cur[i] = x; };
-  mx_pass_any<T, DIR>(p.mix_radix[0], N, 1, tw, first, to_cur);
+  mx_pass_any<T, DIR, TWS>(p.mix_radix[0], N, 1, tw, first, to_cur);
   int Ns = p.mix_radix[0];
   for (int ps = 1; ps < np; ++ps) {
     __syncthreads();
@@ -132,12 +135,12 @@ __device__ void mx_run(const PlanDev& p, V2<T>* buf, const V2<T>* __restrict__ t
     auto from_cur = [&](int b, int q, int NR) { return cur[b + q * NR]; };
     if (ps + 1 < np) {
       auto to_nxt = [&](int i, V2<T> x) { nxt[i] = x; };
-      mx_pass_any<T, DIR>(R, N, Ns, tw, from_cur, to_nxt);
+      mx_pass_any<T, DIR, TWS>(R, N, Ns, tw, from_cur, to_nxt);
       V2<T>* t = cur;
       cur = nxt;
       nxt = t;
     } else {
-      mx_pass_any<T, DIR>(R, N, Ns, tw, from_cur, last);
+      mx_pass_any<T, DIR, TWS>(R, N, Ns, tw, from_cur, last);
     }
     Ns *= R;
   }
@@ -146,6 +149,29 @@ __device__ void mx_run(const PlanDev& p, V2<T>* buf, const V2<T>* __restrict__ t
 template <typename T>
 __device__ __forceinline__ const V2<T>* mx_twiddles(const PlanDev& p) {
   if constexpr (sizeof(T) == 4) return p.tw32n; else return p.tw64;
+}
+
+// Whether the N twiddles fit in shared memory after the two N-point buffers.
+template <typename T>
+__host__ __device__ constexpr bool mx_tw_fits(int N) {
+  return 3 * (size_t)N * sizeof(V2<T>) <= (size_t)MIXED_MAX_SMEM;
+}
+
+// mx_run with the twiddles staged in shared memory (after buf's 2 N points)
+// when they fit: each pass then reads them without a global-memory round
+// trip.  Every thread of the CTA must call it.
+template <typename T, int DIR, class First, class Last>
+__device__ void mx_run_staged(const PlanDev& p, V2<T>* buf, First& first, Last& last) {
+  const V2<T>* twg = mx_twiddles<T>(p);
+  const int N = p.N;
+  if (mx_tw_fits<T>(N)) {
+    V2<T>* tws = buf + 2 * N;
+    for (int i = threadIdx.x; i < N; i += MX_THREADS) tws[i] = __ldg(&twg[i]);
+    __syncthreads();
+    mx_run<T, DIR, true>(p, buf, tws, first, last);
+  } else {
+    mx_run<T, DIR, false>(p, buf, twg, first, last);
+  }
 }
 
 template <typename T>
@@ -178,7 +204,7 @@ k_grid_mixed(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
         return make_float2(x.x * rp, x.y * rp);
       };
       auto last = [&](int i, float2 x) { best.insert(x.x * x.x + x.y * x.y, i); };
-      mx_run<float, +1>(sd.p, buf, mx_twiddles<float>(sd.p), first, last);
+      mx_run_staged<float, +1>(sd.p, buf, first, last);
     }
     group_reduce<MX_THREADS>(best, red);
     if (threadIdx.x == 0 && active) {
@@ -208,7 +234,7 @@ k_grid_mixed(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
         return make_double2(x.x * rp, x.y * rp);
       };
       auto last = [&](int i, double2 x) { best.insert(x.x * x.x + x.y * x.y, i, x); };
-      mx_run<double, +1>(sd.p, buf, mx_twiddles<double>(sd.p), first, last);
+      mx_run_staged<double, +1>(sd.p, buf, first, last);
     }
     group_reduce<MX_THREADS>(best, red);
     if (threadIdx.x == 0 && active) {
@@ -242,7 +268,7 @@ k_forward_mixed(const SlotDev* __restrict__ slots, const int* __restrict__ ids) 
     float2* c = sd.c32;
     auto first = [&](int b, int q, int NR) { return __ldcg(&g[b + q * NR]); };
     auto last = [&](int i, float2 x) { c[i] = x; };
-    mx_run<float, -1>(sd.p, buf, mx_twiddles<float>(sd.p), first, last);
+    mx_run_staged<float, -1>(sd.p, buf, first, last);
   } else {
     const double2* G = sd.G;
     double2* c = sd.c64;
@@ -252,7 +278,7 @@ k_forward_mixed(const SlotDev* __restrict__ slots, const int* __restrict__ ids) 
       return make_double2(x.x / n, x.y / n);
     };
     auto last = [&](int i, double2 x) { c[i] = x; };
-    mx_run<double, -1>(sd.p, buf, mx_twiddles<double>(sd.p), first, last);
+    mx_run_staged<double, -1>(sd.p, buf, first, last);
   }
 }
 
@@ -275,18 +301,28 @@ cudaError_t launch_pdl_mx(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaSt
 
 size_t mixed_smem_bytes(int N, int prec) { return 2 * (size_t)N * (prec == AFD_FP32_GUARDED ? 8 : 16); }
 
+namespace {
+// dynamic shared memory of a launch: the two buffers, and the twiddles when
+// they fit (mx_run_staged)
+size_t mixed_launch_smem(int N, int prec) {
+  const bool f32 = prec == AFD_FP32_GUARDED;
+  const bool tw = f32 ? mx_tw_fits<float>(N) : mx_tw_fits<double>(N);
+  return (tw ? 3 : 2) * (size_t)N * (f32 ? 8 : 16);
+}
+}  // namespace
+
 cudaError_t launch_grid_mixed(const SlotDev* slots, const int* ids, int n, int N, int prec, int Mmax,
                               cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const dim3 grid(Mmax, n);
-  const size_t smem = mixed_smem_bytes(N, prec);
+  const size_t smem = mixed_launch_smem(N, prec);
   if (prec == AFD_FP32_GUARDED) return launch_pdl_mx(k_grid_mixed<float>, grid, smem, st, slots, ids);
   return launch_pdl_mx(k_grid_mixed<double>, grid, smem, st, slots, ids);
 }
 
 cudaError_t launch_forward_mixed(const SlotDev* slots, const int* ids, int n, int N, int prec, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const size_t smem = mixed_smem_bytes(N, prec);
+  const size_t smem = mixed_launch_smem(N, prec);
   if (prec == AFD_FP32_GUARDED) return launch_pdl_mx(k_forward_mixed<float>, dim3(n), smem, st, slots, ids);
   return launch_pdl_mx(k_forward_mixed<double>, dim3(n), smem, st, slots, ids);
 }
