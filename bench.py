@@ -622,9 +622,11 @@ def run_afd(args):
             "e2e": e2e,
             "clocks": clocks,
         }
-        if not args.no_cpu_baseline:
+        # the CPU baseline and the other workloads at N = 1 only: with more
+        # ranks they would hold every GPU while rank 0 alone works
+        if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(s)
-        if not args.no_extra:
+        if ws == 1 and not args.no_extra:
             from paper_1711_08604_gb300 import workloads as W
             line["other_workloads"] = {
                 "c1_kernel_sum": dict(bench_single(afd, torch, dev, W.kernel_sum(), afd.AFD_FP64_PLAIN),
@@ -634,10 +636,10 @@ def run_afd(args):
                 "c2_tones_fp64_plain": dict(bench_single(afd, torch, dev, s, afd.AFD_FP64_PLAIN, reps=10),
                                             workload="tones: N=4096, M=200, K=50, FP64 plain (the comparator)"),
                 "batch": bench_batch(afd, torch, dev),
-                                       "large_two_pass": bench_chirp(afd, torch, dev),
-                                       "serving": bench_serve(afd, args.serve_seconds),
-                                       "paper_table9": bench_paper_sweep(afd),
-                                       "next_rows": bench_next(afd, torch, dev)}
+                "large_two_pass": bench_chirp(afd, torch, dev),
+                "serving": bench_serve(afd, args.serve_seconds),
+                "paper_table9": bench_paper_sweep(afd),
+                "next_rows": bench_next(afd, torch, dev)}
         print(json.dumps(line))
     plan.close()
     if ws > 1:
