@@ -36,7 +36,11 @@ inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 afd_status check_opts(const afd_plan_opts& o);
 afd_status check_size(int N, int prec, bool allow_two_pass = false, bool allow_mixed = false);
 afd_status check_radii(const double* radii, int M);
-// opts (NULL: defaults) validated into o; dev = the device to use.
+// opts (NULL: defaults) validated into o, with no CUDA call.
+afd_status resolve_opts(const afd_plan_opts* in, afd_plan_opts& o);
+// dev = the device o names (-1: the current one), checked to exist.
+afd_status resolve_device(const afd_plan_opts& o, int& dev);
+// resolve_opts, then resolve_device.
 afd_status normalise_opts(const afd_plan_opts* in, afd_plan_opts& o, int& dev);
 
 // Makes `dev` current for the scope and restores the caller's device.

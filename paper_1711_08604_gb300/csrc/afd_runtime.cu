@@ -126,16 +126,24 @@ afd_status check_radii(const double* radii, int M) {
   return AFD_OK;
 }
 
-afd_status normalise_opts(const afd_plan_opts* in, afd_plan_opts& o, int& dev) {
+afd_status resolve_opts(const afd_plan_opts* in, afd_plan_opts& o) {
   afd_plan_opts_default(&o);
   if (in) o = *in;
-  AFD_TRY(check_opts(o));
+  return check_opts(o);
+}
+
+afd_status resolve_device(const afd_plan_opts& o, int& dev) {
   dev = o.device;
   if (dev < 0) CUDA_TRY(cudaGetDevice(&dev));
   int count = 0;
   CUDA_TRY(cudaGetDeviceCount(&count));
   if (dev >= count) return set_error(AFD_ERR_INVALID, "device %d not present (%d devices)", dev, count);
   return AFD_OK;
+}
+
+afd_status normalise_opts(const afd_plan_opts* in, afd_plan_opts& o, int& dev) {
+  AFD_TRY(resolve_opts(in, o));
+  return resolve_device(o, dev);
 }
 
 // ------------------------------------------------------------------ tables --
@@ -1039,11 +1047,13 @@ afd_status afd_plan_create(afd_plan** out, int N, const double* radii, int M, co
   *out = nullptr;
   afd_plan_opts o;
   int dev = 0;
-  AFD_TRY(normalise_opts(opts, o, dev));
+  // every argument is checked before the first CUDA call
+  AFD_TRY(resolve_opts(opts, o));
   AFD_TRY(check_size(N, o.precision, true, true));
   AFD_TRY(check_radii(radii, M));
   if (o.force_a1_zero && radii[0] != 0.0)
     return set_error(AFD_ERR_INVALID, "force_a1_zero needs radii[0] == 0");
+  AFD_TRY(resolve_device(o, dev));
   DeviceScope scope(dev);
   if (!scope.ok) return set_error(AFD_ERR_CUDA, "cannot make device %d current", dev);
   AFD_TRY(ensure_configured(dev));
@@ -1069,7 +1079,8 @@ afd_status afd_plan_create_nonuniform(afd_plan** out, int N, const double* theta
   *out = nullptr;
   afd_plan_opts o;
   int dev = 0;
-  AFD_TRY(normalise_opts(opts, o, dev));
+  // every argument is checked before the first CUDA call
+  AFD_TRY(resolve_opts(opts, o));
   if (o.precision != AFD_FP32_GUARDED)
     return set_error(AFD_ERR_INVALID, "non-uniform samples: the FP32-guarded path only");
   if (o.force_a1_zero || o.renormalise)
@@ -1085,6 +1096,7 @@ afd_status afd_plan_create_nonuniform(afd_plan** out, int N, const double* theta
   if (!is_pow2(L) || L < (1 << NU_MIN_LOGN) || L > (1 << NU_MAX_LOGN))
     return set_error(AFD_ERR_INVALID, "L = %d: a power of two in [%d, %d]", L, 1 << NU_MIN_LOGN, 1 << NU_MAX_LOGN);
   AFD_TRY(check_radii(radii, M));
+  AFD_TRY(resolve_device(o, dev));
   DeviceScope scope(dev);
   if (!scope.ok) return set_error(AFD_ERR_CUDA, "cannot make device %d current", dev);
   AFD_TRY(ensure_configured(dev));
@@ -1238,11 +1250,13 @@ afd_status afd_batch_create(afd_batch** out, int n_signals, const int* N, const 
   if (K_max < 1 || K_max > (1 << 20)) return set_error(AFD_ERR_INVALID, "K_max = %d out of range", K_max);
   afd_plan_opts o;
   int dev = 0;
-  AFD_TRY(normalise_opts(opts, o, dev));
+  // every argument is checked before the first CUDA call
+  AFD_TRY(resolve_opts(opts, o));
   AFD_TRY(check_radii(radii, M));
   if (o.force_a1_zero && radii[0] != 0.0)
     return set_error(AFD_ERR_INVALID, "force_a1_zero needs radii[0] == 0");
   for (int i = 0; i < n_signals; ++i) AFD_TRY(check_size(N[i], o.precision, false, true));
+  AFD_TRY(resolve_device(o, dev));
   DeviceScope scope(dev);
   if (!scope.ok) return set_error(AFD_ERR_CUDA, "cannot make device %d current", dev);
   AFD_TRY(ensure_configured(dev));

@@ -70,3 +70,32 @@ def test_wait_selftest_checks_arguments_before_any_cuda_call(lib):
     st, sec = ctypes.c_int(), ctypes.c_double()
     assert lib.afd_selftest_wait_timeout(-1, 2, ctypes.byref(st), ctypes.byref(sec)) == -1
     assert lib.afd_selftest_wait_timeout(-1, 0, None, ctypes.byref(sec)) == -1
+
+
+@pytest.mark.parametrize("N,radii,kw", [
+    (112, [0.1, 0.2], {}),                # 7 x 16: neither 2^a nor 2^a 3^b 5^c
+    (64, [0.2, 0.1], {}),                 # radii not ascending
+    (64, [0.1, 1.0], {}),                 # a radius outside [0, 1)
+    (1 << 15, [0.1], {}),                 # above the largest resident size
+    (16384, [0.1], {"precision": 0}),     # above the FP64 path's largest size
+    (64, [0.1], {"guard_cap": 0}),
+    (64, [0.1, 0.2], {"force_a1_zero": True}),  # needs radii[0] == 0
+])
+def test_plan_arguments_checked_before_any_cuda_call(lib, N, radii, kw):
+    # AFD_ERR_INVALID on a machine without a GPU: no CUDA call comes first
+    import paper_1711_08604_gb300 as afd
+    with pytest.raises(afd.AfdError) as e:
+        afd.afd_plan_create(N, radii, **kw)
+    assert e.value.status == -1
+
+
+def test_nonuniform_plan_arguments_checked_before_any_cuda_call(lib):
+    import numpy as np
+    import paper_1711_08604_gb300 as afd
+    theta = 2 * np.pi * (np.arange(64) + 0.5) / 64
+    for args in [(theta[::-1], [0.0, 0.5], 64),      # angles not ascending
+                 (theta, [0.0, 0.5], 100),           # L not a power of two
+                 (theta, [0.5, 0.0], 64)]:           # radii not ascending
+        with pytest.raises(afd.AfdError) as e:
+            afd.afd_plan_create_nonuniform(*args)
+        assert e.value.status == -1
