@@ -99,3 +99,26 @@ def test_nonuniform_plan_arguments_checked_before_any_cuda_call(lib):
         with pytest.raises(afd.AfdError) as e:
             afd.afd_plan_create_nonuniform(*args)
         assert e.value.status == -1
+
+
+@pytest.mark.parametrize("N,prec,valid", [
+    (8, 1, True), (4, 1, False),              # smallest size
+    (16384, 1, True), (16384, 0, False),      # largest resident size per precision
+    (8192, 0, True), (32768, 1, False),
+    (65536, 1, True), (65536, 0, False),      # the two-pass size: FP32 path only
+    (9, 1, True), (3000, 1, True),            # 2^a 3^b 5^c
+    (21, 1, False), (112, 1, False),          # a factor 7
+    (12800, 1, True), (13500, 1, False),      # largest mixed-radix sizes: 16 N and
+    (6400, 0, True), (6480, 0, False),        # 32 N bytes of shared memory <= 204800
+])
+def test_size_rules(lib, N, prec, valid):
+    # a valid size passes every argument check: without a GPU the call then
+    # fails at the device lookup (AFD_ERR_CUDA), with one it makes a plan
+    import paper_1711_08604_gb300 as afd
+    try:
+        plan = afd.afd_plan_create(N, [0.5], precision=prec)
+    except afd.AfdError as e:
+        assert e.status == (-3 if valid else -1), (N, prec, e.status)
+    else:
+        assert valid, (N, prec)
+        plan.close()
