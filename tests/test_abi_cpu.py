@@ -122,3 +122,20 @@ def test_size_rules(lib, N, prec, valid):
     else:
         assert valid, (N, prec)
         plan.close()
+
+
+def test_batch_and_server_arguments_checked_before_any_cuda_call(lib):
+    import paper_1711_08604_gb300 as afd
+    bad_batches = [([256, 112], [0.1, 0.5], 5),    # a size with a factor 7
+                   ([256, 512], [0.5, 0.1], 5),    # radii not ascending
+                   ([256], [0.1], 0)]              # K_max below 1
+    for N, radii, K in bad_batches:
+        with pytest.raises(afd.AfdError) as e:
+            afd.afd_batch_create(N, radii, K)
+        assert e.value.status == -1
+    with pytest.raises(afd.AfdError) as e:
+        afd.afd_serve_create(1 << 19)              # budget below 1 MiB
+    assert e.value.status == -1
+    with pytest.raises(afd.AfdError) as e:
+        afd.afd_serve_create(1 << 30, guard_cap=0)  # an invalid option
+    assert e.value.status == -1
