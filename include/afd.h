@@ -369,11 +369,17 @@ afd_status afd_serve_destroy(afd_server* server);
  * exits.
  *   G       2N doubles (interleaved complex), device memory; 1 <= N <= AFD_NOALLOC_MAX_N.
  *   points  2*n_points doubles, device memory; 1 <= n_points <= AFD_NOALLOC_MAX_POINTS.
+ *           Each point must satisfy |a_p| < 1 and differ from every sample
+ *           point z_m; the points are not read by the host, so a point
+ *           outside the open disc or on a sample gives NaN or Inf in out[p]
+ *           (the call still returns AFD_OK).
  *   out     2*n_points doubles, device memory.
  *   stream  cudaStream_t to run on (NULL: the legacy default stream).
- * Asynchronous: the result is ready when the stream reaches that point.
- * Sizes beyond the limits, NULL or host (unmapped) pointers return
- * AFD_ERR_INVALID with a message in afd_last_error().  The first call on a
+ * All three buffers must belong to the current device (or be host memory
+ * mapped for it).  Asynchronous: the result is ready when the stream reaches
+ * that point.  Sizes beyond the limits, NULL pointers, host (unmapped)
+ * pointers and memory of another device return AFD_ERR_INVALID with a
+ * message in afd_last_error().  The first call on a
  * device looks up the scratch array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.
  * All calls share the one array: calls that overlap on the GPU (different

@@ -17,6 +17,9 @@ What each function computes, with the paper passage it follows:
 * ``decompose`` -- the greedy loop of Sec. 2 with the grid selection of Sec. 3.2
   (Step 2) and the relative error delta of Eq. (er).
 * ``kernel_norm2`` -- the discrete squared norm of e_a at a grid point (renormalised selection).
+* ``grid_fft``, ``select_fft`` -- the same grid and selection by the FFT route of
+  Theorem 2.1 / Eq. (rcl) with library FFTs in FP64 (fast enough to check the
+  selection at every step of the large workloads; pinned against ``grid``).
 * ``nu_inner``, ``nu_update``, ``nu_energy``, ``nu_decompose`` (``afd_oracle_nu.c``) --
   the same on non-uniform samples z_m = exp(i theta_m) with quadrature weights
   w_m (the remark after Step 2 of Sec. 3.2) and a grid of L equispaced angles.
@@ -67,7 +70,7 @@ def _load():
         lib.oracle_energy.restype = ctypes.c_double
         lib.oracle_decompose.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int,
-                                         _dp, _dp, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp]
+                                         _dp, _dp, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
         lib.oracle_kernel_norm2.argtypes = [ctypes.c_int, ctypes.c_double]
         lib.oracle_kernel_norm2.restype = ctypes.c_double
         lib.oracle_nu_inner.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
@@ -156,7 +159,8 @@ def kernel_norm2(N: int, r: float) -> float:
 
 
 def decompose(G, radii, K_max: int, energy_tol: float = 0.0, force_a1_zero: bool = False,
-              forced_idx=None, compute_grid: bool = True, renormalise: bool = False) -> dict:
+              forced_idx=None, compute_grid: bool = True, renormalise: bool = False,
+              keep_steps: bool = False) -> dict:
     """Core AFD: K_max greedy steps (or until delta <= energy_tol).
 
     ``renormalise`` selects by |<G_k, e_a>~|^2 / ||e_a||_N^2 (the discrete norm,
@@ -166,6 +170,8 @@ def decompose(G, radii, K_max: int, energy_tol: float = 0.0, force_a1_zero: bool
     to use instead of the argmax (rows with s < 0 are free).  With
     ``compute_grid=False`` every step must be forced and the O(M N^2) grid is
     skipped; the coefficient then comes from ``inner`` at the forced point.
+    ``keep_steps`` adds ``G_steps``: (steps, N) array of G_k at the start of
+    every step k (the remainder the step's selection runs on).
     """
     g, r = _cvec(G), _rvec(radii)
     K = int(K_max)
@@ -185,17 +191,105 @@ def decompose(G, radii, K_max: int, energy_tol: float = 0.0, force_a1_zero: bool
     delta = np.zeros(K + 1)
     E = np.zeros(K + 1)
     Gf = np.zeros_like(g)
+    Gs = np.zeros((K, g.size), dtype=np.complex128) if keep_steps else None
     steps = _load().oracle_decompose(
         g.size, _p(g), r.size, _p(r), K, float(energy_tol), int(bool(force_a1_zero)), int(bool(renormalise)),
         fi.ctypes.data_as(_ip) if fi is not None else None, int(bool(compute_grid)),
         _p(a), _p(c), idx.ctypes.data_as(_ip), own.ctypes.data_as(_ip), _p(objmax), _p(obj2),
-        _p(objused), _p(delta), _p(E), _p(Gf))
+        _p(objused), _p(delta), _p(E), _p(Gf), _p(Gs) if Gs is not None else None)
     if steps < 0:
         raise ValueError("oracle_decompose: bad arguments")
-    return {"steps": steps, "a": a[:steps], "coeff": c[:steps], "idx": idx[:steps],
-            "own_idx": own[:steps], "objmax": objmax[:steps], "obj2": obj2[:steps],
-            "objused": objused[:steps], "delta": delta[: steps + 1], "energy": E[: steps + 1],
-            "G_final": Gf}
+    out = {"steps": steps, "a": a[:steps], "coeff": c[:steps], "idx": idx[:steps],
+           "own_idx": own[:steps], "objmax": objmax[:steps], "obj2": obj2[:steps],
+           "objused": objused[:steps], "delta": delta[: steps + 1], "energy": E[: steps + 1],
+           "G_final": Gf}
+    if keep_steps:
+        out["G_steps"] = Gs[:steps]
+    return out
+
+
+# ------------------------------------------- the FFT route of Theorem 2.1 --
+
+def _fft_module():
+    try:
+        import scipy.fft as sf
+        return sf, {"workers": max(1, os.cpu_count() or 1)}
+    except ImportError:  # numpy's pocketfft, one thread
+        return np.fft, {}
+
+
+def grid_fft(G, radii, workers: int = 0) -> np.ndarray:
+    """(M, N) grid of <G, e_{a_{s,j}}>~ by the FFT route of Theorem 2.1 / Eq. (rcl).
+
+    Expanding 1/(1 - a conj(z_m)) = sum_l (a conj(z_m))^l and folding l mod N
+    (z_m^N = 1) gives, with c_l = sum_m G(z_m) w^{-ml} (Eq. (term4)),
+        <G, e_{a_{s,j}}>~ = sqrt(1 - r_s^2) / (N (1 - r_s^N)) sum_l r_s^l c_l w^{jl},
+    one forward DFT of the samples and, per radius, one inverse DFT of the
+    spectrum weighted by r_s^l.  The DFTs are library FFTs (scipy, else numpy)
+    in FP64.  The identity is exact; it is pinned against the direct sum
+    ``grid`` / ``inner_many`` by the test suite.
+    """
+    g, r = _cvec(G), _rvec(radii)
+    N = g.size
+    fft, kw = _fft_module()
+    if workers and kw:
+        kw = {"workers": workers}
+    c = fft.fft(g, **kw)
+    # r_s^l = r_s^(l mod B) * r_s^(B (l div B)): two short power tables and
+    # one product per entry instead of M N calls of pow (relative error a few
+    # ulp); the row scale sqrt(1 - r^2) / (1 - r^N) rides on the short table
+    B = min(N, 256)
+    scale = np.sqrt(1.0 - r * r) / (1.0 - r ** N)
+    lo = scale[:, None] * r[:, None] ** np.arange(B, dtype=np.float64)[None, :]
+    hi = r[:, None] ** (B * np.arange(-(-N // B), dtype=np.float64))[None, :]
+    w = (hi[:, :, None] * lo[:, None, :]).reshape(r.size, -1)[:, :N]
+    # the library's inverse DFT carries the 1/N of the formula
+    return fft.ifft(w * c[None, :], axis=1, **kw)
+
+
+def select_fft(G, radii, pick=None, renormalise: bool = False, rows_per_chunk: int = 0) -> dict:
+    """Maximal selection of Step 2 (Sec. 3.2) on the grid computed by ``grid_fft``.
+
+    Returns ``own`` = (s, j), the argmax of |<G, e_a>~|^2 (divided by the
+    discrete norm ``kernel_norm2`` per radius when ``renormalise``), ties to
+    the lowest flat index s N + j; ``objmax``, its value; and, when ``pick``
+    = (s, j) is given, ``objpick``, the objective there.  The grid is formed
+    in blocks of radii (host threads take blocks in parallel), so memory stays
+    near 50 N rows_per_chunk bytes per thread.
+    """
+    from concurrent.futures import ThreadPoolExecutor
+
+    g, r = _cvec(G), _rvec(radii)
+    N, M = g.size, r.size
+    if rows_per_chunk <= 0:
+        rows_per_chunk = max(1, min(M, (1 << 21) // max(N, 1)))
+    starts = list(range(0, M, rows_per_chunk))
+
+    def block(s0):
+        rr = r[s0:s0 + rows_per_chunk]
+        A = grid_fft(g, rr, workers=1)
+        obj = A.real ** 2 + A.imag ** 2
+        if renormalise:
+            obj /= np.array([kernel_norm2(N, x) for x in rr])[:, None]
+        f = int(np.argmax(obj))  # first occurrence: the lowest flat index
+        vp = None
+        if pick is not None and s0 <= int(pick[0]) < s0 + rr.size:
+            vp = float(obj[int(pick[0]) - s0, int(pick[1])])
+        return float(obj.reshape(-1)[f]), (s0 + f // N, f % N), vp
+
+    nthreads = max(1, min(len(starts), os.cpu_count() or 1, 16))
+    if nthreads == 1:
+        parts = [block(s0) for s0 in starts]
+    else:
+        with ThreadPoolExecutor(nthreads) as ex:
+            parts = list(ex.map(block, starts))
+    best, own, objpick = -1.0, None, None
+    for v, o, vp in parts:  # blocks in ascending radius order: strict > keeps the lowest index
+        if v > best:
+            best, own = v, o
+        if vp is not None:
+            objpick = vp
+    return {"own": own, "objmax": best, "objpick": objpick}
 
 
 # ------------------------------------------------------- non-uniform samples --

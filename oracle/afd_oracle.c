@@ -234,7 +234,9 @@ double oracle_energy(int N, const double* G) {
  *   objused_out[k]              objective at the point used;
  *   delta_out[0..K]             delta_0 = 1, delta_k = E_{k+1} / E_1;
  *   energy_out[0..K]            E_1 .. E_{K+1};
- *   G_final                     G_{k+1} after the last step (2N doubles).
+ *   G_final                     G_{k+1} after the last step (2N doubles);
+ *   G_steps                     G_k at the start of every step k = 1..steps
+ *                               (2N doubles per step, one after another).
  * Returns the number of steps done (>= 1), or -1 on bad arguments.
  */
 int oracle_decompose(int N, const double* G, int M, const double* radii, int K_max,
@@ -242,7 +244,7 @@ int oracle_decompose(int N, const double* G, int M, const double* radii, int K_m
                      int compute_grid, double* a_out, double* coeff_out, int* idx_out,
                      int* own_idx_out, double* objmax_out, double* obj2_out,
                      double* objused_out, double* delta_out, double* energy_out,
-                     double* G_final) {
+                     double* G_final, double* G_steps) {
   if (N <= 0 || M <= 0 || K_max <= 0 || !G || !radii) return -1;
   for (int s = 0; s < M; ++s) {
     if (!(radii[s] >= 0.0 && radii[s] < 1.0)) return -1;
@@ -277,6 +279,7 @@ int oracle_decompose(int N, const double* G, int M, const double* radii, int K_m
   for (int k = 0; k < K_max; ++k) {
     int s_used, j_used;
     double best = -1.0, second = -1.0;
+    if (G_steps) memcpy(G_steps + (size_t)2 * N * k, g, sizeof(cplx) * (size_t)N);
     long own = -1;
     if (compute_grid) {
       oracle_grid(N, (const double*)g, M, radii, (double*)A);

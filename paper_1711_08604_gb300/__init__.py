@@ -36,6 +36,8 @@ __all__ = [
 
 AFD_FP64_PLAIN = 0
 AFD_FP32_GUARDED = 1
+AFD_NOALLOC_MAX_N = 65536       # include/afd.h: limits of afd_inner_products_noalloc
+AFD_NOALLOC_MAX_POINTS = 64
 STATUS = {0: "AFD_OK", 1: "AFD_PENDING", -1: "AFD_ERR_INVALID", -2: "AFD_ERR_NOMEM",
           -3: "AFD_ERR_CUDA", -4: "AFD_ERR_TIMEOUT", -5: "AFD_ERR_BUDGET", -6: "AFD_ERR_NOT_FOUND",
           -7: "AFD_ERR_NUMERIC"}
@@ -440,8 +442,25 @@ def afd_inner_products_noalloc(G, points, out=None, stream=None):
     Asynchronous on ``stream`` (a torch stream or cudaStream_t int; default: the
     legacy default stream)."""
     import torch
-    if out is None:
+    if out is None and isinstance(points, torch.Tensor):
         out = torch.empty_like(points)
+    for name, t in (("G", G), ("points", points), ("out", out)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype != torch.complex128:
+            raise ValueError(f"{name} must be complex128, not {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.device.type != "cuda":
+            raise ValueError(f"{name} must be on a CUDA device, not {t.device}")
+    if not (G.device == points.device == out.device):
+        raise ValueError("G, points and out must be on the same CUDA device")
+    if not 1 <= G.numel() <= AFD_NOALLOC_MAX_N:
+        raise ValueError(f"len(G) must be in 1..{AFD_NOALLOC_MAX_N}")
+    if not 1 <= points.numel() <= AFD_NOALLOC_MAX_POINTS:
+        raise ValueError(f"len(points) must be in 1..{AFD_NOALLOC_MAX_POINTS}")
+    if out.numel() != points.numel():
+        raise ValueError("out must have one entry per point")
     s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
     _check(_lib().afd_inner_products_noalloc(G.data_ptr(), int(G.numel()), points.data_ptr(),
                                              int(points.numel()), out.data_ptr(), s or None))

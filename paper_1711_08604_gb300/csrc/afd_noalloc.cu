@@ -124,14 +124,17 @@ afd_status scratch_for_current_device(void** ptr, char* err, size_t errlen) {
   return AFD_OK;
 }
 
-bool device_accessible(const void* p) {
+// True if the current device (dev) can read and write p directly: device or
+// managed memory of that device, or host memory mapped for the device.
+// Device memory of another GPU is refused: the kernel runs on the current one.
+bool device_accessible(const void* p, int dev) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
-         (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr);
+  if (at.type == cudaMemoryTypeDevice) return at.device == dev;
+  return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr);
 }
 
 thread_local char g_noalloc_err[256];
@@ -161,9 +164,15 @@ extern "C" afd_status afd_inner_products_noalloc(const double* G, int N, const d
              n_points, AFD_NOALLOC_MAX_POINTS);
     return fail(AFD_ERR_INVALID);
   }
-  if (!device_accessible(G) || !device_accessible(points) || !device_accessible(out)) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(g_noalloc_err, sizeof(g_noalloc_err), "no current CUDA device");
+    return fail(AFD_ERR_CUDA);
+  }
+  if (!device_accessible(G, dev) || !device_accessible(points, dev) || !device_accessible(out, dev)) {
     snprintf(g_noalloc_err, sizeof(g_noalloc_err),
-             "G, points and out must be device memory (or host memory mapped for the device)");
+             "G, points and out must be memory of the current device %d (or host memory mapped for it)", dev);
     return fail(AFD_ERR_INVALID);
   }
   void* scratch = nullptr;

@@ -14,6 +14,8 @@ Energy curve: |delta_gpu - delta_ora| <= 1e-5 * delta_ora + 1e-14.
 """
 from __future__ import annotations
 
+import hashlib
+
 import numpy as np
 
 import oracle
@@ -24,14 +26,42 @@ COEFF_TOL = {0: 1e-11, 1: 1e-5}  # FP64 plain, FP32 guarded
 ABS_FLOOR = 1e3 * np.finfo(np.float64).eps
 
 
+_DIRECT_CACHE: dict = {}
+
+
+def _oracle_forced(G, radii, idx, steps, force_a1_zero, renormalise, mode):
+    """The oracle forced to the GPU's index sequence.  mode "direct" also
+    computes its own O(M N^2) grid at every step (cached by inputs, so a second
+    precision that picked the same points reuses it); "fft" keeps the
+    remainders G_k for the FFT-route selection check."""
+    if mode == "direct":
+        key = hashlib.sha1(G.tobytes() + radii.tobytes() + idx.astype(np.int32).tobytes()
+                           + bytes([force_a1_zero, renormalise])).hexdigest()
+        if key not in _DIRECT_CACHE:
+            _DIRECT_CACHE.clear()
+            _DIRECT_CACHE[key] = oracle.decompose(G, radii, steps, force_a1_zero=force_a1_zero,
+                                                  forced_idx=idx, compute_grid=True, renormalise=renormalise)
+        return _DIRECT_CACHE[key]
+    return oracle.decompose(G, radii, steps, force_a1_zero=force_a1_zero, forced_idx=idx,
+                            compute_grid=False, renormalise=renormalise, keep_steps=(mode == "fft"))
+
+
 def check(G, radii, res, prec: int, *, full_grid=True, grid_steps=(), force_a1_zero=False,
           energy_tol=0.0, coeff_tol=None, renormalise=False):
     """Compare a GPU result dict (afd_decompose output) with the oracle.
 
-    full_grid=True recomputes the oracle grid at every step; otherwise only
-    the steps listed in grid_steps (1-based) get a full-grid selection check
-    and the rest are checked through the forced oracle (coefficients, a_k and
-    delta).  Returns a dict of the largest observed errors.
+    Selection (the grid index of every step):
+      full_grid=True   the oracle's own direct grid (Eq. (formula1) at every
+                       grid point) at every step;
+      full_grid="fft"  the oracle's FFT-route grid (Theorem 2.1 / Eq. (rcl),
+                       ``oracle.select_fft``, pinned against the direct grid)
+                       at every step, for sizes where the direct grid is too
+                       slow;
+      full_grid=False  the direct grid only at the steps listed in grid_steps.
+    Coefficients, a_k and delta are checked at every step through the oracle
+    forced to the GPU's picks.  Returns a dict of the largest observed errors
+    and ``selection_checked``, the number of steps whose pick was checked
+    against a whole grid.
     """
     G = np.asarray(G, dtype=np.complex128)
     radii = np.asarray(radii, dtype=np.float64)
@@ -39,17 +69,23 @@ def check(G, radii, res, prec: int, *, full_grid=True, grid_steps=(), force_a1_z
     assert steps >= 1
     idx = np.asarray(res["idx"]).reshape(steps, 2)
     tol = COEFF_TOL[prec] if coeff_tol is None else coeff_tol
-    ora = oracle.decompose(G, radii, steps, energy_tol=0.0, force_a1_zero=force_a1_zero,
-                           forced_idx=idx, compute_grid=full_grid, renormalise=renormalise)
+    mode = "fft" if full_grid == "fft" else ("direct" if full_grid else "forced")
+    ora = _oracle_forced(G, radii, idx, steps, bool(force_a1_zero), bool(renormalise), mode)
     E1 = ora["energy"][0]
-    out = {"coeff_rel": 0.0, "delta_abs": 0.0, "a_abs": 0.0, "ties": 0}
+    out = {"coeff_rel": 0.0, "delta_abs": 0.0, "a_abs": 0.0, "ties": 0, "selection_checked": 0}
     for k in range(steps):
-        if full_grid and not (force_a1_zero and k == 0):
-            if tuple(idx[k]) != tuple(ora["own_idx"][k]):
-                assert ora["objused"][k] >= ora["objmax"][k] * (1.0 - NEAR_TIE), (
-                    f"step {k + 1}: GPU picked {tuple(idx[k])} (obj {ora['objused'][k]!r}), "
-                    f"oracle {tuple(ora['own_idx'][k])} (obj {ora['objmax'][k]!r})")
+        if mode != "forced" and not (force_a1_zero and k == 0):
+            if mode == "direct":
+                own, objmax, objpick = tuple(ora["own_idx"][k]), ora["objmax"][k], ora["objused"][k]
+            else:
+                sel = oracle.select_fft(ora["G_steps"][k], radii, pick=idx[k], renormalise=renormalise)
+                own, objmax, objpick = sel["own"], sel["objmax"], sel["objpick"]
+            if tuple(int(v) for v in idx[k]) != tuple(int(v) for v in own):
+                assert objpick >= objmax * (1.0 - NEAR_TIE), (
+                    f"step {k + 1}: GPU picked {tuple(idx[k])} (obj {objpick!r}), "
+                    f"oracle {tuple(own)} (obj {objmax!r}) [{mode} grid]")
                 out["ties"] += 1
+            out["selection_checked"] += 1
         c_g, c_o = res["coeff"][k], ora["coeff"][k]
         err = abs(c_g - c_o)
         rel = err / max(abs(c_o), 1e-300)
@@ -62,7 +98,7 @@ def check(G, radii, res, prec: int, *, full_grid=True, grid_steps=(), force_a1_z
         dg, do = res["delta"][k + 1], ora["delta"][k + 1]
         out["delta_abs"] = max(out["delta_abs"], abs(dg - do))
         assert abs(dg - do) <= DELTA_REL * do + 1e-14, f"step {k + 1}: delta {dg} vs {do}"
-    if not full_grid:
+    if mode == "forced":
         for k1 in grid_steps:
             k = k1 - 1
             if k >= steps or (force_a1_zero and k == 0):
@@ -80,6 +116,7 @@ def check(G, radii, res, prec: int, *, full_grid=True, grid_steps=(), force_a1_z
                 assert obj[f_gpu] >= obj[f_own] * (1.0 - NEAR_TIE), (
                     f"step {k1}: GPU picked {tuple(idx[k])}, oracle {divmod(f_own, G.size)}")
                 out["ties"] += 1
+            out["selection_checked"] += 1
     if energy_tol > 0.0:
         # stopped exactly when the oracle's curve first reaches the tolerance
         d = ora["delta"][1:]

@@ -139,3 +139,17 @@ def test_batch_and_server_arguments_checked_before_any_cuda_call(lib):
     with pytest.raises(afd.AfdError) as e:
         afd.afd_serve_create(1 << 30, guard_cap=0)  # an invalid option
     assert e.value.status == -1
+
+
+def test_noalloc_binding_rejects_bad_tensors_before_the_library():
+    # the binding refuses tensors the kernel would misread (wrong dtype,
+    # strided, host memory, too many points, short output) with ValueError,
+    # before any call into the library
+    torch = pytest.importorskip("torch")
+    import paper_1711_08604_gb300 as afd
+    G = torch.zeros(64, dtype=torch.complex128)
+    p = torch.zeros(4, dtype=torch.complex128)
+    for args in [(G.to(torch.complex64), p, p.clone()), (G, p, p.clone()), (G[::2], p, p.clone()),
+                 (G, torch.zeros(8, dtype=torch.complex128)[::2], p.clone()), ("G", p, p)]:
+        with pytest.raises(ValueError):
+            afd.afd_inner_products_noalloc(*args)

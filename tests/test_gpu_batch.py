@@ -82,8 +82,11 @@ def test_batch_reuse_and_counters():
         assert np.array_equal(r1["coeff"][i], r2["coeff"][i])
 
 
-def test_workload3_full_batch_sampled_parity():
-    # 1024 signals, N in {1024..8192}, M = 100, K = 30, FP32 grid + FP64 guard
+def test_workload3_full_batch_parity():
+    # 1024 signals, N in {1024..8192}, M = 100, K = 30, FP32 grid + FP64 guard.
+    # Four signals of every N-class (the first, the last and two between):
+    # the selection of all 30 steps against the oracle's FFT-route grid, and
+    # coefficients and delta through the forced oracle
     sigs = W.batch()
     G = [s.G for s in sigs]
     radii = sigs[0].radii
@@ -91,13 +94,15 @@ def test_workload3_full_batch_sampled_parity():
     assert np.all(res["steps"] == 30)
     by_n = {}
     for i, s in enumerate(sigs):
-        by_n.setdefault(s.N, i)
-    for N, i in sorted(by_n.items()):
-        r = {k: res[k][i] for k in ("a", "coeff", "delta", "idx")}
-        r["steps"] = 30
-        # every step through the forced oracle; full-grid selection at step 1
-        # for the two smallest sizes (the oracle grid is O(M N^2))
-        parity.check(sigs[i].G, radii, r, 1, full_grid=False, grid_steps=(1,) if N <= 2048 else ())
+        by_n.setdefault(s.N, []).append(i)
+    assert sorted(by_n) == [1024, 2048, 4096, 8192]
+    for N, members in sorted(by_n.items()):
+        pick = sorted({members[0], members[len(members) // 3], members[2 * len(members) // 3], members[-1]})
+        for i in pick:
+            r = {k: res[k][i] for k in ("a", "coeff", "delta", "idx")}
+            r["steps"] = 30
+            out = parity.check(sigs[i].G, radii, r, 1, full_grid="fft")
+            assert out["selection_checked"] == 30, (N, i)
 
 
 def test_grid_variants_are_bitwise_equivalent():

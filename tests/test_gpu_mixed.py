@@ -51,14 +51,14 @@ def test_mixed_larger_sizes(prec, N):
     G = G + 0.05 * W.random_signal(N, N)
     radii = W.radii_linear(40)
     res = run(G, radii, 5, prec)
-    parity.check(G, radii, res, prec, full_grid=False, grid_steps=(1, 2))
+    assert parity.check(G, radii, res, prec, full_grid="fft")["selection_checked"] == 5
 
 
 def test_mixed_largest_fp32_size():
     N = 12800
     G = W.random_signal(N, 3)
     res = run(G, RADII, 3, afd.AFD_FP32_GUARDED)
-    parity.check(G, RADII, res, afd.AFD_FP32_GUARDED, full_grid=False, grid_steps=(1,))
+    assert parity.check(G, RADII, res, afd.AFD_FP32_GUARDED, full_grid="fft")["selection_checked"] == 3
 
 
 @pytest.mark.parametrize("prec", PRECS)

@@ -82,11 +82,13 @@ def test_default_weights_are_the_trapezoid_rule():
         assert np.array_equal(a[key], b[key]), key
 
 
-def test_nonuniform_workload_sampled():
-    x = W.nonuniform()  # N = 3000 jittered samples, L = 1024, M = 64, K = 12
+def test_nonuniform_workload_full_grid():
+    # N = 3000 jittered samples, L = 1024, M = 64, K = 12: the oracle's own
+    # direct grid (65,536 points x 3000 samples) at every step
+    x = W.nonuniform()
     res = run(x.theta, x.weights, x.G, x.radii, x.L, x.K)
     assert res["steps"] == x.K
-    check_nu(x.theta, x.weights, x.G, x.radii, x.L, res, full_grid=False, grid_steps=(1, 2, 12))
+    check_nu(x.theta, x.weights, x.G, x.radii, x.L, res)
     assert np.all(np.diff(res["delta"]) <= 1e-12)
 
 
@@ -96,7 +98,7 @@ def test_radius_near_one_needs_folds():
     radii = np.array([0.0, 0.5, 0.9, 0.99, 0.999])
     G = W.szego_sum_at(x.theta, np.array([0.999 * np.exp(2j * np.pi * 300 / 1024)]), np.array([1.0])) + x.G
     res = run(x.theta, x.weights, G, radii, 1024, 4)
-    check_nu(x.theta, x.weights, G, radii, 1024, res, full_grid=False, grid_steps=(1, 2))
+    check_nu(x.theta, x.weights, G, radii, 1024, res)
     with pytest.raises(afd.AfdError) as e:
         afd.afd_plan_create_nonuniform(x.theta, radii, 256, weights=x.weights)
     assert e.value.status == -1

@@ -118,13 +118,18 @@ def test_paper_table4_forced_a1(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_workload2_tones_sampled(prec):
-    # N = 4096, M = 200, K = 50: coefficients and delta at every step through the
-    # forced oracle; full-grid selection checks at sampled steps.
+def test_workload2_tones_every_step(prec):
+    # N = 4096, M = 200, K = 50: the selection of every step against the
+    # oracle's own direct grid (all 819,200 points by Eq. (formula1), 3.4e9
+    # complex terms per step; the oracle run is shared by the two precisions
+    # when they pick the same points) and against the FFT-route grid;
+    # coefficients and delta at every step
     s = W.tones()
     res, _ = run(s.G, s.radii, s.K, prec)
     assert res["steps"] == s.K
-    parity.check(s.G, s.radii, res, prec, full_grid=False, grid_steps=(1, 2, 50))
+    out = parity.check(s.G, s.radii, res, prec, full_grid=True)
+    assert out["selection_checked"] == s.K
+    assert parity.check(s.G, s.radii, res, prec, full_grid="fft")["selection_checked"] == s.K
 
 
 def test_determinism_and_graph_equivalence():
@@ -230,7 +235,7 @@ def test_persistent_kernel_several_tiles_per_cta():
     b, _ = run(s.G, s.radii, s.K, 1, persistent=False)
     for k in ("a", "coeff", "delta", "idx"):
         assert np.array_equal(a[k], b[k]), k
-    parity.check(s.G, s.radii, a, 1, full_grid=False, grid_steps=(1, 8))
+    assert parity.check(s.G, s.radii, a, 1, full_grid="fft")["selection_checked"] == s.K
 
 
 def test_persistent_kernel_profiled():
@@ -241,7 +246,7 @@ def test_persistent_kernel_profiled():
     kt = afd.afd_plan_kernel_times(plan)
     assert r["steps"] == s.K
     assert kt["persistent"][1] == 1 and kt["persistent"][0] > 0
-    parity.check(s.G, s.radii, r, 1, full_grid=False, grid_steps=(1,))
+    assert parity.check(s.G, s.radii, r, 1, full_grid="fft")["selection_checked"] == s.K
 
 
 @pytest.mark.parametrize("prec", PRECS)

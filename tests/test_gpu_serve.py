@@ -69,11 +69,19 @@ def test_poisson_arrivals_parity_and_latency():
     srv.close()
     lat = np.array([o["latency_ms"] for o in outs])
     assert np.all(lat > 0)
-    for (_, s), o in list(zip(reqs, outs))[:: max(1, len(reqs) // 6)]:
-        if s.N <= 2048:
-            r = {k: o[k] for k in ("a", "coeff", "delta", "idx")}
-            r["steps"] = o["steps"]
-            parity.check(s.G, s.radii, r, 1, full_grid=False, grid_steps=(1,), energy_tol=s.tol)
+    # a sample of every N (up to 16384): the selection of every step against
+    # the oracle's FFT-route grid, coefficients, delta and the stop step
+    seen = {}
+    for n, (_, s) in enumerate(reqs):
+        seen.setdefault(s.N, []).append(n)
+    sample = sorted(n for ns in seen.values() for n in (ns[0], ns[-1]))
+    for n in sample:
+        s, o = reqs[n][1], outs[n]
+        r = {k: o[k] for k in ("a", "coeff", "delta", "idx")}
+        r["steps"] = o["steps"]
+        out = parity.check(s.G, s.radii, r, 1, full_grid="fft", energy_tol=s.tol)
+        assert out["selection_checked"] == o["steps"]
+    for (_, s), o in zip(reqs, outs):
         assert o["delta"][-1] <= s.tol or o["steps"] == s.K
 
 

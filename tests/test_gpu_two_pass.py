@@ -36,6 +36,18 @@ def test_two_pass_full_grid_parity_small_radius_set():
     parity.check(s.G, radii, res, 1, full_grid=True)
 
 
+@pytest.mark.parametrize("M,item", [(1000, 2), (1537, 3)])
+def test_two_pass_full_grid_many_radii(M, item):
+    # enough radii that every CTA of the persistent passes loops over several
+    # radii and the load ring wraps many times (M = 1537: a ragged last round);
+    # every grid point of every step against the FFT-route grid
+    G = W.random_signal(N, 40 + item) + W.chirp(item=item, M=2, K=1).G
+    radii = W.radii_linear(M)
+    res = run(G, radii, 4)
+    assert res["steps"] == 4
+    assert parity.check(G, radii, res, 1, full_grid="fft")["selection_checked"] == 4
+
+
 def test_two_pass_reproducing_kernel():
     # At N = 65536 and r = 0.7 the neighbouring angles' objectives differ from
     # the maximum by ~1.7e-8 relative, below FP32 resolution: a near-tie that the
@@ -71,12 +83,16 @@ def _sampled_selection_check(G, radii, idx, k, n_random=3000, seed=0):
 
 
 def test_workload5_chirp_full_size():
-    # N = 65536, M = 1000 radii i/1000, K = 100, FP32 grid + FP64 guard/update
+    # N = 65536, M = 1000 radii i/1000, K = 100, FP32 grid + FP64 guard/update:
+    # the selection of every step against the oracle's FFT-route grid (all
+    # 65.5 M points), plus the direct rectangle rule at the pick's neighbours
+    # and random points at the first and last steps
     s = W.chirp()
     res = run(s.G, s.radii, s.K)
     assert res["steps"] == s.K
-    parity.check(s.G, s.radii, res, 1, full_grid=False)
-    for k in (1, 2, 50, 100):
+    out = parity.check(s.G, s.radii, res, 1, full_grid="fft")
+    assert out["selection_checked"] == s.K
+    for k in (1, 100):
         _sampled_selection_check(s.G, s.radii, res["idx"], k)
     assert np.all(np.diff(res["delta"]) <= 1e-12)  # r^N is negligible here: energy only falls
 

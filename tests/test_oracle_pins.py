@@ -18,19 +18,6 @@ from paper_1711_08604_gb300 import workloads as W
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def _fft_route(G, radii):
-    """Eq. (rcl) / Theorem 2.1: <G,e_{a_j}>~ = sqrt(1-r^2)/(N(1-r^N)) sum_l r^l c_l w^{jl},
-    c = forward DFT of the samples (Eq. (term4)), evaluated with numpy's FFT."""
-    N = G.size
-    c = np.fft.fft(G)
-    l = np.arange(N)
-    rows = []
-    for r in radii:
-        # numpy's ifft is (1/N) sum_l f_l exp(+2 pi i j l / N)
-        rows.append(np.sqrt(1.0 - r * r) / (1.0 - r ** N) * np.fft.ifft((r ** l) * c))
-    return np.array(rows)
-
-
 def _discrete_szego_inner(a, b, N):
     """Closed form of the rectangle rule <e_b, e_a>~ on N points: summing the two
     geometric series and folding indices mod N gives
@@ -45,15 +32,65 @@ def test_direct_sum_equals_fft_route(N):
     G = W.random_signal(N, 17 + N)
     radii = np.array([0.0, 0.1, 0.5, 0.9, 0.99])
     A = oracle.grid(G, radii)
-    B = _fft_route(G, radii)
+    B = oracle.grid_fft(G, radii)
     assert np.max(np.abs(A - B)) <= 1e-13 * max(1.0, np.max(np.abs(B)))
 
 
 def test_direct_sum_equals_fft_route_workload1():
     s = W.kernel_sum()
     A = oracle.grid(s.G, s.radii)
-    B = _fft_route(s.G, s.radii)
+    B = oracle.grid_fft(s.G, s.radii)
     assert np.max(np.abs(A - B)) <= 1e-12 * np.max(np.abs(B))
+
+
+@pytest.mark.parametrize("N,rows", [(4096, (0.0, 0.5, 0.995)), (65536, (0.3, 0.999)), (3000, (0.2, 0.97)),
+                                    (2187, (0.9,))])
+def test_fft_route_sampled_rows_at_large_N(N, rows):
+    # the FFT route of Theorem 2.1 at the large transform sizes of the
+    # workloads (and two sizes that are not powers of two), against the direct
+    # rectangle rule at sampled grid points: whole rows at N = 4096, 512 angles
+    # per row (a contiguous run and random ones) at the others
+    G = W.random_signal(N, 5 + N) + W.szego_sum(N, np.array([0.97 * np.exp(0.3j)]), np.array([2.0]))
+    radii = np.array(rows)
+    B = oracle.grid_fft(G, radii)
+    rng = np.random.default_rng(N)
+    for s, r in enumerate(radii):
+        js = np.arange(N) if N <= 4096 else np.unique(np.concatenate([np.arange(256), rng.integers(0, N, 256)]))
+        A = oracle.inner_many(G, r * np.exp(2j * np.pi * js / N))
+        assert np.max(np.abs(A - B[s, js])) <= 1e-12 * np.max(np.abs(B[s])), (N, r)
+
+
+def test_fft_selection_equals_direct_selection():
+    # select_fft (blocks of radii) picks the direct oracle's argmax, ties
+    # included: G = 1 (every angle of r = 0 ties), random signals, one radius
+    # per block and all radii in one block
+    for G, radii in [(np.ones(32, complex), np.array([0.0, 0.5])),
+                     (W.random_signal(64, 8), np.array([0.0, 0.2, 0.7, 0.95])),
+                     (W.random_signal(48, 9), np.array([0.1, 0.6, 0.9]))]:
+        d = oracle.decompose(G, radii, 1)
+        for rows in (0, 1, 2):
+            sel = oracle.select_fft(G, radii, pick=tuple(d["own_idx"][0]), rows_per_chunk=rows)
+            assert sel["own"] == tuple(d["own_idx"][0])
+            assert abs(sel["objmax"] - d["objmax"][0]) <= 1e-13 * d["objmax"][0]
+            assert sel["objpick"] == sel["objmax"]
+    # renormalised selection
+    G, radii = W.random_signal(32, 2), np.array([0.0, 0.5, 0.9, 0.97])
+    d = oracle.decompose(G, radii, 1, renormalise=True)
+    assert oracle.select_fft(G, radii, renormalise=True)["own"] == tuple(d["own_idx"][0])
+
+
+def test_keep_steps_are_the_remainders():
+    # G_steps[k] is the remainder the (k+1)-th selection runs on: G_1 = G, and
+    # each next one is the Sec. 2 update of the previous with that step's a_k, c_k
+    s = W.kernel_sum(item=2)
+    d = oracle.decompose(s.G, s.radii, 6, keep_steps=True)
+    assert np.array_equal(d["G_steps"][0], s.G)
+    for k in range(5):
+        nxt = oracle.update(d["G_steps"][k], d["a"][k], d["coeff"][k])
+        assert np.array_equal(nxt, d["G_steps"][k + 1])
+        assert d["coeff"][k] == oracle.inner(d["G_steps"][k], d["a"][k])
+    f = oracle.decompose(s.G, s.radii, 6, forced_idx=d["idx"], compute_grid=False, keep_steps=True)
+    assert np.array_equal(f["G_steps"], d["G_steps"])
 
 
 @pytest.mark.parametrize("N", [8, 64, 256])

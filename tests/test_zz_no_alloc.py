@@ -1,19 +1,25 @@
 """The allocation-free entry point afd_inner_products_noalloc, called through the
-C ABI.  It is meant for callers that cannot allocate device memory (inside stream
-capture, in latency-critical loops, or under a host-imposed fixed memory pool);
-its scratch is a static device array shared by all calls.
+C ABI.  It is meant for callers that cannot allocate device memory: work issued
+while a stream is being captured, latency-critical loops where an allocation
+could synchronise the device, and hosts that give the library a fixed,
+pre-reserved memory pool.  Its scratch is a static device array shared by all
+calls, so each check below runs two calls in a row (the second one on the
+scratch the first left behind).
 
-The check: its FP64 inner products at the points a_k that afd_decompose selected
-must equal the coefficients afd_decompose returned for them, within the FP64
-coefficient tolerance of the parity tests, on two calls in a row (so the second
-call runs on scratch the first one left behind).  This file is named so pytest
-collects it last; it also passes on its own in a fresh process.
+The checks: its FP64 inner products at the points a_k that afd_decompose
+selected equal the coefficients afd_decompose returned for them; and at 64
+arbitrary points of the disc, for sizes from one partial 512-sample chunk to the
+128 chunks of N = 65536 (with ragged last chunks), every value equals the
+oracle's direct rectangle rule of Eq. (formula1), within the FP64 coefficient
+tolerance of the parity tests.  This file is named so pytest collects it last;
+it also passes on its own in a fresh process.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1711_08604_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -37,13 +43,12 @@ def env():
     return torch, afd, lib
 
 
-def _reference(afd, G, radii, K, prec):
-    """a_k and c_k of the existing entry point on the remainders G_k it starts from:
-    step 1 only, so c_1 = <G, e_{a_1}>~ for the original samples."""
-    plan = afd.afd_plan_create(G.size, radii, precision=prec)
-    r = afd.afd_decompose(plan, G, K)
-    plan.close()
-    return r["a"][:1], r["coeff"][:1]
+def _close(got, want, G):
+    E1 = np.mean(np.abs(G) ** 2)
+    err = np.abs(got - want)
+    bound = COEFF_TOL * np.abs(want) + ABS_FLOOR * np.sqrt(E1)
+    assert np.all(np.isfinite(got))
+    assert np.all(err <= bound), (int(np.argmax(err / bound)), float(np.max(err / bound)))
 
 
 def _noalloc(torch, lib, G, pts):
@@ -59,41 +64,72 @@ def _noalloc(torch, lib, G, pts):
 
 
 def test_noalloc_matches_decompose_on_two_calls(env):
+    # against the existing entry point: c_1 = <G, e_{a_1}>~ as afd_decompose
+    # returned it, at the a_1 it selected
     torch, afd, lib = env
     cases = [(W.kernel_sum(), afd.AFD_FP32_GUARDED), (W.tones(item=2, K=3), afd.AFD_FP64_PLAIN)]
     for s, prec in cases:                       # two calls in a row
-        a, c = _reference(afd, s.G, s.radii, 1, prec)
-        got = _noalloc(torch, lib, s.G, a)
-        E1 = np.mean(np.abs(s.G) ** 2)
-        err = np.abs(got - c)
-        assert np.all(err <= COEFF_TOL * np.abs(c) + ABS_FLOOR * np.sqrt(E1)), (got, c)
+        plan = afd.afd_plan_create(s.N, s.radii, precision=prec)
+        r = afd.afd_decompose(plan, s.G, 1)
+        plan.close()
+        got = _noalloc(torch, lib, s.G, r["a"][:1])
+        _close(got, r["coeff"][:1], s.G)
 
 
-def test_noalloc_many_points_and_limits(env):
+def _points(seed, n=64):
+    rng = np.random.default_rng(seed)
+    pts = 0.95 * np.sqrt(rng.random(n)) * np.exp(2j * np.pi * rng.random(n))
+    pts[0], pts[1], pts[2] = 0.0, 0.999 * np.exp(0.25j), -0.5   # the centre, near the circle, on an axis
+    return pts
+
+
+@pytest.mark.parametrize("N", [100, 512, 1000, 4096, 5000, 65536])
+def test_noalloc_every_point_against_oracle(env, N):
+    # 64 points; N = 100 (one partial chunk), 1000 and 5000 (ragged last
+    # chunk), 65536 (all 128 chunks of the scratch); two calls in a row with
+    # different points, every value against the oracle
+    torch, afd, lib = env
+    G = W.random_signal(N, 31 + N) + W.szego_sum(N, np.array([0.9 * np.exp(1.0j)]), np.array([1.5]))
+    for call in range(2):
+        pts = _points(N + call)
+        got = _noalloc(torch, lib, G, pts)
+        _close(got, oracle.inner_many(G, pts), G)
+
+
+def test_noalloc_binding_and_device_memory(env):
+    # the Python binding checks its tensors before calling the library; the
+    # calls themselves leave the device's free memory unchanged
     torch, afd, lib = env
     s = W.kernel_sum(item=1)
-    rng = np.random.default_rng(11)
-    pts = 0.95 * np.sqrt(rng.random(64)) * np.exp(2j * np.pi * rng.random(64))
-    first = _noalloc(torch, lib, s.G, pts)
-    again = _noalloc(torch, lib, s.G, pts)
-    assert np.array_equal(first, again)
-    # every point against the existing entry point: a 1-radius plan whose only
-    # grid circle passes through the point selects it when it is the circle's maximum
-    for p in pts[:4]:
-        r = abs(p)
-        j = int(round(np.angle(p) / (2 * np.pi) * s.N)) % s.N
-        on_grid = r * np.exp(2j * np.pi * j / s.N)
-        got = _noalloc(torch, lib, s.G, np.array([on_grid]))[0]
-        plan = afd.afd_plan_create(s.N, np.array([r]), precision=afd.AFD_FP32_GUARDED)
-        res = afd.afd_decompose(plan, s.G, 1)
-        plan.close()
-        if tuple(res["idx"][0]) == (0, j):
-            assert abs(got - res["coeff"][0]) <= COEFF_TOL * abs(res["coeff"][0]) + 1e-13
+    Gd = torch.from_numpy(s.G).cuda()
+    pd = torch.from_numpy(_points(5)).cuda()
+    out = torch.empty_like(pd)
+    afd.afd_inner_products_noalloc(Gd, pd, out)        # first call: set-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        afd.afd_inner_products_noalloc(Gd, pd, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    _close(out.cpu().numpy(), oracle.inner_many(s.G, pd.cpu().numpy()), s.G)
+    bad = [dict(G=Gd.to(torch.complex64)), dict(points=pd[::2]), dict(out=out[:10]),
+           dict(G=Gd.cpu()), dict(points=torch.zeros(65, dtype=torch.complex128, device="cuda"))]
+    for kw in bad:
+        args = {"G": Gd, "points": pd, "out": out, **kw}
+        with pytest.raises(ValueError):
+            afd.afd_inner_products_noalloc(args["G"], args["points"], args["out"])
+
+
+def test_noalloc_limits(env):
+    torch, afd, lib = env
+    s = W.kernel_sum(item=1)
     Gd = torch.from_numpy(s.G).cuda()
     pd = torch.zeros(65, dtype=torch.complex128, device="cuda")
     out = torch.zeros_like(pd)
     assert lib.afd_inner_products_noalloc(Gd.data_ptr(), s.N, pd.data_ptr(), 65, out.data_ptr(), None) == -1
     assert b"n_points" in lib.afd_last_error()
     assert lib.afd_inner_products_noalloc(Gd.data_ptr(), 65537, pd.data_ptr(), 1, out.data_ptr(), None) == -1
+    assert lib.afd_inner_products_noalloc(Gd.data_ptr(), 0, pd.data_ptr(), 1, out.data_ptr(), None) == -1
     host = np.zeros(2, dtype=np.complex128)
     assert lib.afd_inner_products_noalloc(Gd.data_ptr(), s.N, host.ctypes.data, 1, out.data_ptr(), None) == -1
+    assert lib.afd_inner_products_noalloc(None, s.N, pd.data_ptr(), 1, out.data_ptr(), None) == -1
