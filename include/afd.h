@@ -103,8 +103,12 @@ const char* afd_version(void);
  * Creates a plan for signals of N samples and the radial grid radii[0..M-1]
  * (Sec. 3.2, Step 1: the paper precomputes and stores r_s^l and the FFT
  * twiddles; the plan holds them on the device, generated in FP64).
- *   N      a power of two, 8 <= N <= 16384 (FP32 path) or 8192 (FP64 path),
- *          or N = 65536 (FP32 path, single-signal plans only);
+ *   N      a power of two, 8 <= N <= 65536, on either path (the method at every
+ *          N = 2^K, Sec. 3.2 and the N-sweep of Table 9).  One CTA holds a
+ *          transform of up to 16384 points (FP32) or 8192 (FP64); longer ones
+ *          run as 2, 4 or 8 such transforms of decimated outputs, except
+ *          FP32 N = 65536, which takes the two-pass path through HBM
+ *          (single-signal plans only: batches and servers refuse it);
  *          or N = 2^a 3^b 5^c >= 9 that is not a power of two, N <= 12800
  *          (FP32 path) or 6400 (FP64 path): the remark after Table 9
  *          (Sec. 4.2) that the algorithm holds for N = p^K, taken here as
@@ -238,7 +242,8 @@ afd_status afd_plan_get_stream(const afd_plan* plan, void** stream);
  * together (all signals' grid tiles of one N share a launch; the N classes
  * run on parallel streams, and the step sequence is replayed as one CUDA
  * graph when opts->use_graph is set).
- *   N        host array, n_signals sizes (each as for afd_plan_create).
+ *   N        host array, n_signals sizes (each as for afd_plan_create, but not
+ *            the FP32 two-pass size 65536).
  *   radii    host array of M radii shared by all signals.
  *   K_max    steps per signal (>= 1); energy_tol as for afd_decompose.
  * afd_batch_run takes the samples packed signal after signal (signal i starts

@@ -408,9 +408,10 @@ __device__ __forceinline__ double2 update_point(const SlotDev& sd, int m, int s,
   return update_apply(update_coef(sd, m, s, j, r, g), cr, ci);
 }
 
-// FP64 selection: global best of the per-radius maxima; writes the step record.
+// FP64 selection: global best of the per-radius maxima (sub entries per
+// radius: one per sub-transform of a split size); writes the step record.
 template <int THREADS>
-__device__ void select_best_f64(const SlotDev& sd, int k, Best1D* red) {
+__device__ void select_best_f64(const SlotDev& sd, int k, Best1D* red, int sub = 1) {
   const int M = sd.p.M, N = sd.p.N;
   const Top2D* top = reinterpret_cast<const Top2D*>(sd.top2);
   Best1D b;
@@ -423,13 +424,13 @@ __device__ void select_best_f64(const SlotDev& sd, int k, Best1D* red) {
       b.f.y = __ldcg(&top[0].f1.y);
     }
   } else {
-    for (int s = threadIdx.x; s < M; s += THREADS) {
-      const int j = __ldcg(&top[s].j1);
+    for (int e = threadIdx.x; e < M * sub; e += THREADS) {
+      const int j = __ldcg(&top[e].j1);
       if (j == INT_MAX) continue;
       double2 f;
-      f.x = __ldcg(&top[s].f1.x);
-      f.y = __ldcg(&top[s].f1.y);
-      b.insert(__ldcg(&top[s].v1), s * N + j, f);
+      f.x = __ldcg(&top[e].f1.x);
+      f.y = __ldcg(&top[e].f1.y);
+      b.insert(__ldcg(&top[e].v1), (e / sub) * N + j, f);
     }
     group_reduce<THREADS>(b, red);
   }

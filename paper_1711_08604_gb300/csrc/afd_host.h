@@ -72,13 +72,14 @@ struct Tables {
   Tables(const Tables&) = delete;
   Tables& operator=(const Tables&) = delete;
   ~Tables();
-  afd_status build(int N, const double* radii, int M);
+  int prec = 1;      // the precision the tables were built for (they differ for split sizes)
+  afd_status build(int N, const double* radii, int M, int prec);
   // grid of L angles; samples theta[nN] (ascending in [0, 2 pi)) with
   // weights w[nN] (NULL: the trapezoid rule)
   afd_status build_nu(int nN, const double* theta, const double* w, int L, const double* radii, int M);
   int samples() const { return nu ? nN : N; }
   int spectrum() const { return nu ? nLc : N; }
-  static size_t bytes_for(int N, int M);  // device bytes build() allocates
+  static size_t bytes_for(int N, int M, int prec);  // device bytes build() allocates
 };
 
 }  // namespace afd

@@ -14,7 +14,20 @@ constexpr int FP64_THREADS = 128;
 constexpr int FP64_CHUNK = 128;
 constexpr int GUARD_PAR = 4;           // candidates in flight per guard launch
 constexpr int MAX_LOGN_RESIDENT = 14;  // N <= 16384: one CTA holds one FFT
-constexpr int TWO_PASS_LOGN = 16;      // N = 65536: two-pass FFT through HBM (plans only)
+constexpr int TWO_PASS_LOGN = 16;      // N = 65536: two-pass FFT through HBM (FP32 plans only)
+constexpr int MAX_LOGN = 16;           // largest power-of-two size of any path
+// Longest transform one CTA holds on chip: 2^14 points in FP32, 2^13 in FP64.
+inline __host__ __device__ constexpr int resident_logn(int prec) { return prec ? 14 : 13; }
+// Transforms longer than that (FP32 N = 32768; FP64 N = 16384 .. 65536) are
+// split by output index into 2^LS sub-transforms of the resident length: with
+// S = 2^LS, NS = N / S and l = l' + p NS,
+//   F(S j' + h) = sum_{l' < NS} [ w^{h l'} sum_{p < S} f(l' + p NS) exp(2 pi i h p / S) ] w_NS^{j' l'},
+// one decimation-in-frequency step of radix S (the splitting of Theorem 2.1
+// with radix S instead of 2).  Returns LS (0: not split).  FP32 N = 65536
+// takes the two-pass path instead.
+inline __host__ __device__ constexpr int split_log(int logN, int prec) {
+  return (prec && logN == TWO_PASS_LOGN) ? 0 : (logN > resident_logn(prec) ? logN - resident_logn(prec) : 0);
+}
 constexpr int PERSISTENT_MAX_LOGN = 12;  // persistent single-signal kernel up to N = 4096
 constexpr int MIN_LOGN = 3;            // N >= 8
 constexpr int MAX_CAP = 64;            // guard candidates per step, upper bound
@@ -50,7 +63,7 @@ inline __host__ __device__ int mixed_schedule(int N, I* radix) {
 
 // Per (N, radii) tables, owned by a plan, read-only in kernels.
 struct PlanDev {
-  int N, logN, M, B;        // B = FftSchedule::pow_b(logN); the high power table has N / B entries
+  int N, logN, M, B;        // B = FftSchedule::pow_b(logN - ls); the high power table has N / B entries
   const double* radii;      // [M] ascending radii r_s in [0, 1)
   const double2* tw64;      // [N] exp(+2 pi i k / N) in FP64 (also the sample points z_m)
   const float2* st32;       // [FftSchedule::tw_size] FFT stage twiddles, FP32
@@ -79,6 +92,7 @@ struct PlanDev {
   const float* nrN32;       // [M] r_s^N in FP32
   int mix_npass;            // mixed-radix path (N not a power of two): passes and radices
   unsigned char mix_radix[MIXED_MAX_PASSES];
+  int ls;                   // split_log(logN, precision): 2^ls sub-transforms per radius (0: none)
 };
 
 // One greedy step's outcome, written on the device.

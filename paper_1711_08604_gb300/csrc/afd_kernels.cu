@@ -378,6 +378,187 @@ k_forward(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
   for (int e = 0; e < P; ++e) c[fft_out_index<T, LOGN>(t, e)] = v[e];
 }
 
+// -------------------------------------------- split sizes (long transforms) --
+//
+// A transform longer than one CTA holds on chip (split_log(logN, prec) =
+// LS > 0: FP32 N = 32768, FP64 N = 16384 .. 65536) is split by output index
+// into S = 2^LS resident sub-transforms of NS = N / S points.  For the
+// inverse transforms of the grid, CTA (s, h) computes F_s(S j' + h), j' < NS,
+// from the pre-combined input
+//   f_h(l') = w^{h l'} sum_{p < S} f(l' + p NS) exp(2 pi i h p / S),
+//   f(l) = r_s^l c_l / N,
+// (one radix-S decimation-in-frequency step: Theorem 2.1's even/odd splitting
+// with radix S).  r_s^(l' + p NS) = lo[b] hi[q + p R0] for l' = b + q B, with
+// the tables split at B = NS / R0.  The forward transform is split the same
+// way with conjugate twiddles: S CTAs per signal, CTA h writing c_{S k' + h}.
+
+// exp(+2 pi i h p / S) for p < S, from the N-point twiddle table
+template <typename T, int LS>
+__device__ __forceinline__ void split_roots(V2<T>* wp, const V2<T>* __restrict__ twn, int h, int NS) {
+  constexpr int SPL = 1 << LS;
+#pragma unroll
+  for (int p = 0; p < SPL; ++p) wp[p] = __ldg(&twn[((h * p) & (SPL - 1)) * NS]);
+}
+
+template <typename T, int LOGS, int LS>
+__global__ void __launch_bounds__(FftShape<T, LOGS>::TPF)
+k_grid_split(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
+  using S = FftShape<T, LOGS>;
+  constexpr int P = S::P, TPF = S::TPF, SPL = 1 << LS, NS = S::N;
+  constexpr int R0 = S::radix(0), B = FftSchedule::pow_b(LOGS), NB0 = P / R0;
+  static_assert(TPF >= 256 && B * R0 == NS, "one resident sub-transform per CTA");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_last;
+  pdl_launch_dependents();
+  const SlotDev& sd = slots[ids[blockIdx.y]];
+  const int t = threadIdx.x;
+  const int s = (int)(blockIdx.x >> LS), h = (int)(blockIdx.x & (SPL - 1));
+  const bool active = s < sd.p.M;
+  V2<T>* buf = reinterpret_cast<V2<T>*>(smem_raw);
+  const V2<T>* tw;
+  const V2<T>* twn;
+  const T* lo;
+  const T* hi;
+  const V2<T>* c;
+  if constexpr (sizeof(T) == 4) {
+    tw = sd.p.st32; twn = sd.p.tw32n; lo = sd.p.rlo32; hi = sd.p.rhi32; c = sd.c32;
+  } else {
+    tw = sd.p.st64; twn = sd.p.tw64; lo = sd.p.rlo64; hi = sd.p.rhi64; c = sd.c64;
+  }
+  V2<T> v[P];
+  if (active) {
+    // constant tables first, then wait for the spectrum
+    T hq[R0 * SPL], lb[NB0];
+    V2<T> wp[SPL];
+#pragma unroll
+    for (int e = 0; e < R0 * SPL; ++e) hq[e] = __ldg(&hi[(size_t)s * (R0 * SPL) + e]);
+#pragma unroll
+    for (int i = 0; i < NB0; ++i) lb[i] = __ldg(&lo[(size_t)s * B + t + i * TPF]);
+    split_roots<T, LS>(wp, twn, h, NS);
+    pdl_wait();
+    if (ld_done(sd.ctl)) return;
+#pragma unroll
+    for (int i = 0; i < NB0; ++i) {
+      const int b = t + i * TPF;
+#pragma unroll
+      for (int q = 0; q < R0; ++q) {
+        const int l = b + q * B;  // l' < NS
+        V2<T> acc = mk2<T>((T)0, (T)0);
+#pragma unroll
+        for (int p = 0; p < SPL; ++p) {
+          const T rp = lb[i] * hq[q + p * R0];
+          const V2<T> x = c[l + p * NS];
+          acc = cadd<T>(acc, cmul<T>(mk2<T>(x.x * rp, x.y * rp), wp[p]));
+        }
+        v[i * R0 + q] = cmul<T>(acc, __ldg(&twn[h * l]));
+      }
+    }
+  } else {
+    pdl_wait();
+    if (ld_done(sd.ctl)) return;
+#pragma unroll
+    for (int e = 0; e < P; ++e) v[e] = mk2<T>((T)0, (T)0);
+  }
+  fft_run<T, LOGS, +1>(v, t, buf, tw);
+  // objective and the best of this sub-transform's outputs j = S j' + h
+  if constexpr (sizeof(T) == 4) {
+    __shared__ Best2F red[32];
+    Best2F bb;
+    bb.init();
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      const V2<T> x = v[fft_out_slot<T, LOGS>(u)];
+      bb.push_ascending(x.x * x.x + x.y * x.y, SPL * (t + TPF * u) + h);
+    }
+    group_reduce<TPF>(bb, red);
+    if (t == 0 && active) {
+      const float w2 = obj_w32(sd, s);
+      Top2F o;
+      o.v1 = bb.v1 * w2;
+      o.v2 = bb.v2 * w2;
+      o.j1 = bb.j1;
+      o.j2 = bb.j2;
+      reinterpret_cast<Top2F*>(sd.top2)[s * SPL + h] = o;
+      if (o.v1 >= 0.0f && o.v1 <= 3.402823466e38f) atomicMax(&sd.ctl->vmax_bits, __float_as_uint(o.v1));
+      __threadfence();  // read by the signal's last CTA
+    }
+    if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
+    select_candidates_f32<TPF>(sd, sd.ctl->k, SPL);
+  } else {
+    __shared__ Best1D red[32];
+    Best1D bb;
+    bb.init();
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      const V2<T> x = v[fft_out_slot<T, LOGS>(u)];
+      bb.push_ascending(x.x * x.x + x.y * x.y, SPL * (t + TPF * u) + h, x);
+    }
+    group_reduce<TPF>(bb, red);
+    if (t == 0 && active) {
+      const double w = sd.p.w64[s];
+      Top2D o;
+      o.v1 = bb.v * (w * w) * obj_rho64(sd, s);
+      o.j1 = bb.j;
+      o.f1 = bb.f;
+      o.v2 = -1.0;
+      o.j2 = INT_MAX;
+      o.f2 = make_double2(0.0, 0.0);
+      reinterpret_cast<Top2D*>(sd.top2)[s * SPL + h] = o;
+      __threadfence();  // read by the signal's last CTA
+    }
+    if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
+    __syncthreads();
+    select_best_f64<TPF>(sd, sd.ctl->k, red, SPL);
+  }
+}
+
+// c_l / N of a split size: CTA h of a signal computes c_{S k' + h}, k' < NS,
+// from y_h(m') = w^{-h m'} sum_{p < S} G(z_{m' + p NS}) exp(-2 pi i h p / S) / N.
+template <typename T, int LOGS, int LS>
+__global__ void __launch_bounds__(FftShape<T, LOGS>::TPF)
+k_forward_split(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
+  using S = FftShape<T, LOGS>;
+  constexpr int P = S::P, SPL = 1 << LS, NS = S::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_launch_dependents();
+  const SlotDev& sd = slots[ids[blockIdx.y]];
+  const int t = threadIdx.x, h = (int)blockIdx.x;
+  V2<T>* buf = reinterpret_cast<V2<T>*>(smem_raw);
+  const V2<T>* tw;
+  const V2<T>* twn;
+  V2<T>* c;
+  if constexpr (sizeof(T) == 4) {
+    tw = sd.p.st32; twn = sd.p.tw32n; c = sd.c32;
+  } else {
+    tw = sd.p.st64; twn = sd.p.tw64; c = sd.c64;
+  }
+  V2<T> wp[SPL];
+  split_roots<T, LS>(wp, twn, h, NS);
+  pdl_wait();
+  if (ld_done(sd.ctl)) return;
+  V2<T> v[P];
+#pragma unroll
+  for (int e = 0; e < P; ++e) {
+    const int m = fft_in_index<T, LOGS>(t, e);
+    V2<T> acc = mk2<T>((T)0, (T)0);
+#pragma unroll
+    for (int p = 0; p < SPL; ++p) {
+      V2<T> g;
+      if constexpr (sizeof(T) == 4) {
+        g = sd.g32[m + p * NS];
+      } else {
+        const double2 x = sd.G[m + p * NS];
+        g = mk2<T>(x.x * sd.p.inv_n, x.y * sd.p.inv_n);
+      }
+      acc = cadd<T>(acc, cmulc<T>(g, wp[p]));
+    }
+    v[e] = cmulc<T>(acc, __ldg(&twn[h * m]));
+  }
+  fft_run<T, LOGS, -1>(v, t, buf, tw);
+#pragma unroll
+  for (int e = 0; e < P; ++e) c[SPL * fft_out_index<T, LOGS>(t, e) + h] = v[e];
+}
+
 // -------------------------------------------------------- plan K table --
 
 // K[s N + d] = 1 / (1 - r_s w^d), w = exp(2 pi i / N), written as
@@ -1153,6 +1334,34 @@ cudaError_t set_variant_attrs() {
   return e;
 }
 
+template <typename T, int LOGS, int LS>
+cudaError_t split_launch(bool grid, const SlotDev* slots, const int* ids, int n, int Mmax, cudaStream_t st) {
+  const size_t smem = sizeof(V2<T>) * (size_t)FftShape<T, LOGS>::SMEM;
+  const dim3 block(FftShape<T, LOGS>::TPF);
+  if (grid) return launch_pdl(k_grid_split<T, LOGS, LS>, dim3((unsigned)Mmax << LS, n), block, smem, st, slots, ids);
+  return launch_pdl(k_forward_split<T, LOGS, LS>, dim3(1u << LS, n), block, smem, st, slots, ids);
+}
+
+template <typename T, int LOGS, int LS>
+cudaError_t set_split_attrs() {
+  const int smem = (int)(sizeof(V2<T>) * (size_t)FftShape<T, LOGS>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(k_grid_split<T, LOGS, LS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_forward_split<T, LOGS, LS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+// The split sizes: FP32 N = 2^15; FP64 N = 2^14 .. 2^16.
+cudaError_t split_dispatch(bool grid, const SlotDev* slots, const int* ids, int n, int logN, int prec, int Mmax,
+                           cudaStream_t st) {
+  static_assert(split_log(15, 1) == 1 && split_log(14, 0) == 1 && split_log(16, 0) == 3 && split_log(16, 1) == 0,
+                "split sizes");
+  if (prec && logN == 15) return split_launch<float, 14, 1>(grid, slots, ids, n, Mmax, st);
+  if (!prec && logN == 14) return split_launch<double, 13, 1>(grid, slots, ids, n, Mmax, st);
+  if (!prec && logN == 15) return split_launch<double, 13, 2>(grid, slots, ids, n, Mmax, st);
+  if (!prec && logN == 16) return split_launch<double, 13, 3>(grid, slots, ids, n, Mmax, st);
+  return cudaErrorInvalidValue;
+}
+
 template <typename T, int LOGN>
 cudaError_t fwd_launch(const SlotDev* slots, const int* ids, int n, cudaStream_t st) {
   return launch_pdl(k_forward<T, LOGN>, dim3(n), dim3(FftShape<T, LOGN>::TPF), fwd_smem<T, LOGN>(), st,
@@ -1186,6 +1395,10 @@ cudaError_t configure_kernels() {
   AFD_FOR_EACH_LOGN(X)
 #undef X
   if ((e = set_attrs<float, 14>()) != cudaSuccess) return e;
+  if ((e = set_split_attrs<float, 14, 1>()) != cudaSuccess) return e;
+  if ((e = set_split_attrs<double, 13, 1>()) != cudaSuccess) return e;
+  if ((e = set_split_attrs<double, 13, 2>()) != cudaSuccess) return e;
+  if ((e = set_split_attrs<double, 13, 3>()) != cudaSuccess) return e;
   if ((e = mixed_configure()) != cudaSuccess) return e;
   if ((e = nu_configure()) != cudaSuccess) return e;
   return fft2_configure();
@@ -1239,8 +1452,8 @@ cudaError_t launch_grid(const SlotDev* slots, const int* ids, int n, int logN, i
 #undef X
     case 14:
       if (prec) return grid_launch<float, 14>(slots, ids, n, Mmax, st);
-      return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
+      return split_dispatch(true, slots, ids, n, logN, prec, Mmax, st);
+    default: return split_dispatch(true, slots, ids, n, logN, prec, Mmax, st);
   }
 }
 
@@ -1254,8 +1467,8 @@ cudaError_t launch_forward(const SlotDev* slots, const int* ids, int n, int logN
 #undef X
     case 14:
       if (prec) return fwd_launch<float, 14>(slots, ids, n, st);
-      return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
+      return split_dispatch(false, slots, ids, n, logN, prec, 0, st);
+    default: return split_dispatch(false, slots, ids, n, logN, prec, 0, st);
   }
 }
 

@@ -106,11 +106,10 @@ afd_status check_size(int N, int prec, bool allow_two_pass, bool allow_mixed) {
                      allow_mixed ? "N = %d: must be >= 8 and a power of two or a product of powers of 2, 3 and 5"
                                  : "N = %d: must be a power of two >= 8",
                      N);
-  if (allow_two_pass && prec == AFD_FP32_GUARDED && N == (1 << TWO_PASS_LOGN)) return AFD_OK;
-  const int maxlog = prec == AFD_FP32_GUARDED ? MAX_LOGN_RESIDENT : MAX_LOGN_RESIDENT - 1;
-  if (N > (1 << maxlog))
-    return set_error(AFD_ERR_INVALID, "N = %d: largest supported size is %d for this precision", N,
-                     1 << maxlog);
+  if (N > (1 << MAX_LOGN))
+    return set_error(AFD_ERR_INVALID, "N = %d: largest supported power of two is %d", N, 1 << MAX_LOGN);
+  if (!allow_two_pass && prec == AFD_FP32_GUARDED && N == (1 << TWO_PASS_LOGN))
+    return set_error(AFD_ERR_INVALID, "N = %d in FP32 (the two-pass path) needs its own plan", N);
   return AFD_OK;
 }
 
@@ -154,7 +153,7 @@ Tables::~Tables() {
 }
 
 afd_status Tables::build_nu(int nN_, const double* theta, const double* w, int L, const double* r, int M_) {
-  AFD_TRY(build(L, r, M_));
+  AFD_TRY(build(L, r, M_, AFD_FP32_GUARDED));  // non-uniform plans: FP32 path, L <= 8192
   nu = true;
   nN = nN_;
   const double two_pi = 6.283185307179586476925286766559;
@@ -217,28 +216,35 @@ afd_status Tables::build_nu(int nN_, const double* theta, const double* w, int L
 
 // Shape of a plan's tables: the power-table split r^l = lo[l mod B] hi[l div B]
 // (B = N / first radix), the stage-twiddle size of the power-of-two FFTs, and
-// whether the FP32 twiddles w^k of all N points are needed (two-pass and
-// mixed-radix transforms).
+// Shape of a plan's tables.  slog: log2 of the transforms the FFT stage
+// twiddles serve (256-point sub-transforms on the two-pass path, the resident
+// sub-transforms of a split size, else N); B: the split point of the radial
+// powers r^l = lo[l mod B] hi[l div B]; tw32n: whether the FP32 twiddles w^k of
+// all N points are needed (two-pass, split FP32 and mixed-radix transforms).
 struct TableShape {
-  int logN, B, H, tws;
+  int logN, B, H, tws, slog, ls;
   bool two_pass, mixed;
   int mix_npass;
   int mix_radix[MIXED_MAX_PASSES];
-  explicit TableShape(int N) {
+  TableShape(int N, int prec) {
     mixed = !is_pow2(N);
     logN = mixed ? -1 : ilog2(N);
-    two_pass = !mixed && logN > MAX_LOGN_RESIDENT;
+    two_pass = !mixed && prec == AFD_FP32_GUARDED && logN == TWO_PASS_LOGN;
+    ls = mixed || two_pass ? 0 : split_log(logN, prec);
+    slog = two_pass ? 8 : logN - ls;
     mix_npass = mixed ? mixed_schedule(N, mix_radix) : 0;
     if (mixed) B = N / mix_radix[0];
-    else B = two_pass ? 256 : FftSchedule::pow_b(logN);
+    else B = two_pass ? 256 : FftSchedule::pow_b(slog);
     H = N / B;
-    tws = mixed ? 1 : std::max(FftSchedule::tw_size(two_pass ? 8 : logN), 1);
+    tws = mixed ? 1 : std::max(FftSchedule::tw_size(slog), 1);
   }
-  bool tw32n() const { return two_pass || mixed; }
+  bool tw32n() const { return two_pass || mixed || (ls > 0 && prec32); }
+  bool prec32 = false;
 };
 
-size_t Tables::bytes_for(int N, int M) {
-  const TableShape sh(N);
+size_t Tables::bytes_for(int N, int M, int prec) {
+  TableShape sh(N, prec);
+  sh.prec32 = prec == AFD_FP32_GUARDED;
   const int B = sh.B, H = sh.H;
   const size_t tws = (size_t)sh.tws;
   size_t off = 0;
@@ -249,16 +255,18 @@ size_t Tables::bytes_for(int N, int M) {
   return off;
 }
 
-afd_status Tables::build(int N_, const double* r, int M_) {
+afd_status Tables::build(int N_, const double* r, int M_, int prec_) {
     N = N_;
     M = M_;
+    prec = prec_;
     radii.assign(r, r + M);
-    const TableShape sh(N);
+    TableShape sh(N, prec);
+    sh.prec32 = prec == AFD_FP32_GUARDED;
     const int logN = sh.logN;
     const bool two_pass = sh.two_pass;
     // the two-pass path splits r^l at 256 and runs 256-point sub-transforms
     const int B = sh.B, H = sh.H;
-    const int slog = two_pass ? 8 : logN;  // log2 of the transforms the stage twiddles serve
+    const int slog = sh.slog;  // log2 of the transforms the stage twiddles serve
     const int TWS = sh.mixed ? 0 : FftSchedule::tw_size(slog);
     std::vector<double> tw64(2 * (size_t)N), st64(2 * (size_t)std::max(TWS, 1)),
         rlo64((size_t)M * B), rhi64((size_t)M * H);
@@ -338,6 +346,7 @@ afd_status Tables::build(int N_, const double* r, int M_) {
     CUDA_TRY(cudaMemcpy(b + o_rho32, rho32.data(), 4 * (size_t)M, cudaMemcpyHostToDevice));
     dev.N = N;
     dev.logN = logN;
+    dev.ls = sh.ls;
     dev.M = M;
     dev.B = B;
     dev.radii = reinterpret_cast<const double*>(b + o_r);
@@ -455,7 +464,10 @@ struct SlotPool {
     std::vector<size_t> o_c(n), o_g32(n), o_top(n), o_cand(n), o_gp(n), o_ep(n), o_X(n), o_G2(n), o_g32b(n);
     for (int i = 0; i < n; ++i) {
       const int N = tables[i]->samples(), M = tables[i]->M;
-      const bool two_pass = !tables[i]->nu && N == (1 << TWO_PASS_LOGN);
+      const bool two_pass = !tables[i]->nu && prec && N == (1 << TWO_PASS_LOGN);
+      // best pairs per radius: one per pass-2 row block (two-pass), one per
+      // sub-transform (split sizes), else one
+      const size_t per_radius = two_pass ? 16 : (size_t)1 << tables[i]->dev.ls;
       o_c[i] = place((prec ? 8 : 16) * (size_t)tables[i]->spectrum());
       o_g32[i] = place(prec ? 8 * (size_t)N : 0);
       // the persistent kernel alternates two remainder buffers and two FP32 copies
@@ -463,7 +475,7 @@ struct SlotPool {
       o_g32b[i] = place(persistent && prec ? 8 * (size_t)N : 0);
       o_X[i] = place(two_pass ? 8 * (size_t)M * N : 0);
       // two-pass: one best pair per (radius, 16-row block of pass 2)
-      o_top[i] = place((prec ? sizeof(Top2F) : sizeof(Top2D)) * (size_t)M * (two_pass ? 16 : 1));
+      o_top[i] = place((prec ? sizeof(Top2F) : sizeof(Top2D)) * (size_t)M * per_radius);
       o_cand[i] = place(sizeof(int2) * cap);
       // the persistent kernel keeps one partial per 32-sample warp item, and
       // its energy partials for every step
@@ -504,7 +516,8 @@ struct SlotPool {
       d.g32 = prec ? reinterpret_cast<float2*>(b + o_g32[i]) : nullptr;
       d.G2 = persistent ? reinterpret_cast<double2*>(b + o_G2[i]) : nullptr;
       d.g32b = persistent && prec ? reinterpret_cast<float2*>(b + o_g32b[i]) : nullptr;
-      d.X = !tables[i]->nu && tables[i]->N == (1 << TWO_PASS_LOGN) ? reinterpret_cast<float2*>(b + o_X[i]) : nullptr;
+      d.X = !tables[i]->nu && prec && tables[i]->N == (1 << TWO_PASS_LOGN) ? reinterpret_cast<float2*>(b + o_X[i])
+                                                                            : nullptr;
       d.c64 = prec ? nullptr : reinterpret_cast<double2*>(b + o_c[i]);
       d.top2 = b + o_top[i];
       d.cand = reinterpret_cast<int2*>(b + o_cand[i]);
@@ -623,7 +636,7 @@ afd_status enqueue_group(const SlotPool& pool, const SlotPool::Group& g, int K, 
     }
     return AFD_OK;
   }
-  const bool two_pass = g.logN == TWO_PASS_LOGN;
+  const bool two_pass = prec == AFD_FP32_GUARDED && g.logN == TWO_PASS_LOGN;
   const bool mixed = g.logN < 0;
   if (two_pass && (g.count != 1 || pool.n != 1)) return set_error(AFD_ERR_INVALID, "N = 65536 needs its own plan");
   const int per = two_pass ? 2 : 1;  // launches per transform stage
@@ -689,7 +702,7 @@ std::map<std::array<int, 4>, std::pair<int, float>> g_tune_cache;
 
 afd_status autotune(SlotPool& pool, int device, cudaStream_t st) {
   for (auto& g : pool.groups) {
-    if (g.nu || g.logN < 0 || g.logN == TWO_PASS_LOGN || pool.prec != AFD_FP32_GUARDED) continue;
+    if (g.nu || g.logN < 0 || g.logN > MAX_LOGN_RESIDENT || pool.prec != AFD_FP32_GUARDED) continue;
     int n_ok = 0;
     for (int v = 0; v < GRID_VARIANTS; ++v) n_ok += grid_variant_ok(g.logN, pool.prec, v) ? 1 : 0;
     if (n_ok < 2) continue;
@@ -1067,7 +1080,7 @@ afd_status afd_plan_create(afd_plan** out, int N, const double* radii, int M, co
     CUDA_TRY(cudaStreamCreateWithFlags(&p->runner.main, cudaStreamNonBlocking));
     p->own_stream = true;
   }
-  AFD_TRY(p->tables.build(N, radii, M));
+  AFD_TRY(p->tables.build(N, radii, M, o.precision));
   *out = p.release();
   return AFD_OK;
 }
@@ -1277,7 +1290,7 @@ afd_status afd_batch_create(afd_batch** out, int n_signals, const int* N, const 
     auto it = by_n.find(N[i]);
     if (it == by_n.end()) {
       b->tables.emplace_back(new Tables());
-      AFD_TRY(b->tables.back()->build(N[i], radii, M));
+      AFD_TRY(b->tables.back()->build(N[i], radii, M, o.precision));
       it = by_n.emplace(N[i], b->tables.back().get()).first;
     }
     per_signal[i] = it->second;

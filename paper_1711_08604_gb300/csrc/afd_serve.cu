@@ -153,7 +153,8 @@ SlotLayout slot_layout(int N, int M, int K, int prec, int cap) {
   L.G = place(16 * (size_t)N);
   L.g32 = place(prec ? 8 * (size_t)N : 0);
   L.c = place((prec ? 8 : 16) * (size_t)N);
-  L.top2 = place((prec ? sizeof(Top2F) : sizeof(Top2D)) * (size_t)M);
+  // one best pair per radius, or per sub-transform of a split size
+  L.top2 = place((prec ? sizeof(Top2F) : sizeof(Top2D)) * ((size_t)M << split_log(ilog2(N), prec)));
   L.cand = place(sizeof(int2) * cap);
   L.gpart = place(sizeof(double2) * cap * (size_t)chunks_of(N));
   L.epart = place(sizeof(double) * (size_t)chunks_of(N));
@@ -245,7 +246,7 @@ struct afd_server {
     }
     std::unique_ptr<Tables> t(new (std::nothrow) Tables());
     if (!t) return AFD_ERR_NOMEM;
-    AFD_TRY(t->build(r.N, r.radii.data(), (int)r.radii.size()));
+    AFD_TRY(t->build(r.N, r.radii.data(), (int)r.radii.size(), opts.precision));
     if (!arena.charge(t->bytes)) return AFD_ERR_BUDGET;
     *out = t.get();
     plans.emplace(std::move(key), std::move(t));
@@ -325,8 +326,8 @@ struct afd_server {
 
   // One greedy step for every active slot.  Worker thread only.
   afd_status tick() {
-    std::vector<int> fresh[MAX_LOGN_RESIDENT + 1], all[MAX_LOGN_RESIDENT + 1];
-    int Mmax[MAX_LOGN_RESIDENT + 1] = {};
+    std::vector<int> fresh[MAX_LOGN + 1], all[MAX_LOGN + 1];
+    int Mmax[MAX_LOGN + 1] = {};
     int hi = 0;
     for (int i = 0; i < kMaxSlots; ++i) {
       const Slot& s = slots[i];
@@ -337,8 +338,8 @@ struct afd_server {
       Mmax[s.logN] = std::max(Mmax[s.logN], s.tables->M);
     }
     size_t n_ids = 0;
-    size_t off_fresh[MAX_LOGN_RESIDENT + 1], off_all[MAX_LOGN_RESIDENT + 1];
-    for (int l = 0; l <= MAX_LOGN_RESIDENT; ++l) {
+    size_t off_fresh[MAX_LOGN + 1], off_all[MAX_LOGN + 1];
+    for (int l = 0; l <= MAX_LOGN; ++l) {
       off_fresh[l] = n_ids;
       for (int i : fresh[l]) ids_host[n_ids++] = i;
       off_all[l] = n_ids;
@@ -347,7 +348,7 @@ struct afd_server {
     CUDA_TRY(cudaMemcpyAsync(ids_dev, ids_host, sizeof(int) * n_ids, cudaMemcpyHostToDevice, stream));
     const int prec = opts.precision;
     long long launches = 0;
-    for (int l = 0; l <= MAX_LOGN_RESIDENT; ++l) {
+    for (int l = 0; l <= MAX_LOGN; ++l) {
       if (all[l].empty()) continue;
       const int nf = (int)fresh[l].size(), na = (int)all[l].size();
       if (nf) {
@@ -597,7 +598,7 @@ afd_status afd_serve_submit(afd_server* s, int N, const double* radii, int M, co
     return set_error(AFD_ERR_INVALID, "force_a1_zero needs radii[0] == 0");
   const int prec = s->opts.precision, cap = prec == AFD_FP32_GUARDED ? s->opts.guard_cap : 1;
   const size_t need = Arena::class_size(slot_layout(N, M, K_max, prec, cap).total);
-  if (need + Tables::bytes_for(N, M) + s->fixed_bytes > s->arena.budget())
+  if (need + Tables::bytes_for(N, M, prec) + s->fixed_bytes > s->arena.budget())
     return set_error(AFD_ERR_BUDGET, "request needs %zu bytes, more than the budget", need);
   std::unique_ptr<Request> r(new (std::nothrow) Request());
   if (!r) return set_error(AFD_ERR_NOMEM, "host allocation failed");

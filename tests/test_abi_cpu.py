@@ -76,8 +76,8 @@ def test_wait_selftest_checks_arguments_before_any_cuda_call(lib):
     (112, [0.1, 0.2], {}),                # 7 x 16: neither 2^a nor 2^a 3^b 5^c
     (64, [0.2, 0.1], {}),                 # radii not ascending
     (64, [0.1, 1.0], {}),                 # a radius outside [0, 1)
-    (1 << 15, [0.1], {}),                 # above the largest resident size
-    (16384, [0.1], {"precision": 0}),     # above the FP64 path's largest size
+    (1 << 17, [0.1], {}),                 # above the largest size of any path
+    (1 << 17, [0.1], {"precision": 0}),
     (64, [0.1], {"guard_cap": 0}),
     (64, [0.1, 0.2], {"force_a1_zero": True}),  # needs radii[0] == 0
 ])
@@ -103,9 +103,11 @@ def test_nonuniform_plan_arguments_checked_before_any_cuda_call(lib):
 
 @pytest.mark.parametrize("N,prec,valid", [
     (8, 1, True), (4, 1, False),              # smallest size
-    (16384, 1, True), (16384, 0, False),      # largest resident size per precision
-    (8192, 0, True), (32768, 1, False),
-    (65536, 1, True), (65536, 0, False),      # the two-pass size: FP32 path only
+    (16384, 1, True), (8192, 0, True),        # largest resident size per precision
+    (32768, 1, True), (16384, 0, True),       # split into resident sub-transforms
+    (32768, 0, True), (65536, 0, True),
+    (65536, 1, True),                         # the two-pass size (FP32 path)
+    (1 << 17, 1, False), (1 << 17, 0, False), # above every path
     (9, 1, True), (3000, 1, True),            # 2^a 3^b 5^c
     (21, 1, False), (112, 1, False),          # a factor 7
     (12800, 1, True), (13500, 1, False),      # largest mixed-radix sizes: 16 N and
@@ -128,7 +130,8 @@ def test_batch_and_server_arguments_checked_before_any_cuda_call(lib):
     import paper_1711_08604_gb300 as afd
     bad_batches = [([256, 112], [0.1, 0.5], 5),    # a size with a factor 7
                    ([256, 512], [0.5, 0.1], 5),    # radii not ascending
-                   ([256], [0.1], 0)]              # K_max below 1
+                   ([256], [0.1], 0),              # K_max below 1
+                   ([65536], [0.1], 5)]            # the FP32 two-pass size: single-signal plans only
     for N, radii, K in bad_batches:
         with pytest.raises(afd.AfdError) as e:
             afd.afd_batch_create(N, radii, K)

@@ -69,6 +69,26 @@ def test_batch_per_signal_energy_stop(prec):
         assert np.array_equal(res["coeff"][i], full["coeff"][i][:first])
 
 
+@pytest.mark.parametrize("prec,Ns", [(afd.AFD_FP64_PLAIN, (4096, 16384, 32768, 65536)),
+                                     (afd.AFD_FP32_GUARDED, (16384, 32768))])
+def test_batch_with_split_sizes(prec, Ns):
+    # sizes split into resident sub-transforms share launches with other
+    # signals of their N and give the single-signal results bitwise; the
+    # selection of every step against the oracle's FFT-route grid
+    sigs = [W.random_signal(N, 70 + N) for N in Ns for _ in range(2)]
+    radii = W.radii_linear(12)
+    res = afd.afd_decompose_batch(sigs, radii, 3, precision=prec)
+    for i, G in enumerate(sigs):
+        plan = afd.afd_plan_create(G.size, radii, precision=prec)
+        one = afd.afd_decompose(plan, G, 3)
+        plan.close()
+        for key in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(res[key][i], one[key]), (i, key)
+        r = {k: res[k][i] for k in ("a", "coeff", "delta", "idx")}
+        r["steps"] = int(res["steps"][i])
+        assert parity.check(G, radii, r, prec, full_grid="fft")["selection_checked"] == 3
+
+
 def test_batch_reuse_and_counters():
     sigs = small_batch(n=5, Ns=(1024, 2048))
     radii = W.radii_linear(16)

@@ -76,6 +76,41 @@ def test_largest_resident_sizes(prec, N):
     parity.check(G, radii, res, prec)
 
 
+SPLIT = [(afd.AFD_FP32_GUARDED, 32768), (afd.AFD_FP64_PLAIN, 16384), (afd.AFD_FP64_PLAIN, 32768),
+         (afd.AFD_FP64_PLAIN, 65536)]
+
+
+@pytest.mark.parametrize("prec,N", SPLIT)
+def test_split_sizes_full_grid(prec, N):
+    # transforms longer than one CTA holds on chip (2^14 FP32 points, 2^13
+    # FP64), split by output index into 2, 4 or 8 resident sub-transforms: every
+    # grid point of every step against the oracle's FFT-route grid, radii from
+    # 0 (an N-way tie) to 0.999, coefficients and delta against the oracle
+    G = W.random_signal(N, 13 * N) + W.szego_sum(N, np.array([0.95 * np.exp(2.0j), 0.6j]), np.array([1.0, 0.5]))
+    radii = np.array([0.0, 0.3, 0.7, 0.9, 0.99, 0.999])
+    res, _ = run(G, radii, 4, prec)
+    assert res["steps"] == 4
+    assert parity.check(G, radii, res, prec, full_grid="fft")["selection_checked"] == 4
+
+
+@pytest.mark.parametrize("prec,N", SPLIT)
+def test_split_sizes_reproducing_kernel(prec, N):
+    # G = e_b, b on the grid: the split selection finds b (FP64: exactly; FP32:
+    # b or, within the near-tie rule, a neighbouring angle) with |c_1| = 1
+    radii = W.radii_linear(20)
+    j0 = N // 3 + 1  # an index of every residue class mod 8 as N varies
+    b = radii[17] * np.exp(2j * np.pi * j0 / N)
+    G = W.szego_sum(N, np.array([b]), np.array([1.0]))
+    res, _ = run(G, radii, 1, prec)
+    s, j = (int(v) for v in res["idx"][0])
+    if prec == afd.AFD_FP64_PLAIN:
+        assert (s, j) == (17, j0)
+        assert abs(abs(res["coeff"][0]) - 1.0) <= 1e-12
+    else:
+        assert s == 17 and abs(j - j0) <= 4
+        assert abs(res["coeff"][0]) ** 2 >= 1.0 - parity.NEAR_TIE
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_single_radius_and_zero_radius_ties(prec):
     # only r = 0: every angle ties exactly, the lowest index must win
@@ -178,9 +213,9 @@ def test_invalid_arguments():
     with pytest.raises(afd.AfdError):
         afd.afd_plan_create(64, [0.1, 1.0])
     with pytest.raises(afd.AfdError):
-        afd.afd_plan_create(1 << 15, [0.1])
+        afd.afd_plan_create(1 << 17, [0.1])
     with pytest.raises(afd.AfdError):
-        afd.afd_plan_create(16384, [0.1], precision=0)
+        afd.afd_plan_create(1 << 17, [0.1], precision=0)
     with pytest.raises(afd.AfdError):
         afd.afd_plan_create(64, [0.1], guard_cap=0)
     with pytest.raises(afd.AfdError):

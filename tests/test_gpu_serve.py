@@ -86,14 +86,16 @@ def test_poisson_arrivals_parity_and_latency():
 
 
 def test_fp64_server_matches_plan():
-    s = W.kernel_sum(item=6)
-    srv = afd.afd_serve_create(1 << 28, precision=afd.AFD_FP64_PLAIN)
-    i = afd.afd_serve_submit(srv, s.G, s.radii, 10, 0.0)
-    o = afd.afd_serve_wait(srv, i, 60.0)
+    # N = 256 and N = 16384 (two FP64 sub-transforms per radius) in one server
+    reqs = [W.kernel_sum(item=6), W.kernel_sum(item=7, N=16384, M=64, K=6)]
+    srv = afd.afd_serve_create(1 << 30, precision=afd.AFD_FP64_PLAIN)
+    ids = [afd.afd_serve_submit(srv, s.G, s.radii, s.K, 0.0) for s in reqs]
+    outs = [afd.afd_serve_wait(srv, i, 60.0) for i in ids]
     srv.close()
-    one = alone(s.G, s.radii, 10, 0.0, prec=0)
-    for k in ("a", "coeff", "delta", "idx"):
-        assert np.array_equal(o[k], one[k])
+    for s, o in zip(reqs, outs):
+        one = alone(s.G, s.radii, s.K, 0.0, prec=0)
+        for k in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(o[k], one[k])
 
 
 def test_host_side_limits():

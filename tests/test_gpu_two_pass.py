@@ -104,7 +104,8 @@ def test_two_pass_nan_and_limits():
     with pytest.raises(afd.AfdError) as e:
         afd.afd_decompose(plan, G, 2)
     assert e.value.status == -7
-    with pytest.raises(afd.AfdError):
-        afd.afd_plan_create(N, np.array([0.0, 0.5]), precision=afd.AFD_FP64_PLAIN)
+    # the FP32 two-pass path serves single-signal plans only
     with pytest.raises(afd.AfdError):
         afd.afd_decompose_batch([W.random_signal(N, 1)], np.array([0.5]), 2)
+    # the FP64 path takes N = 65536 as eight resident sub-transforms
+    afd.afd_plan_create(N, np.array([0.0, 0.5]), precision=afd.AFD_FP64_PLAIN).close()
