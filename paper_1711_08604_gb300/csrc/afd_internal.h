@@ -200,6 +200,11 @@ cudaError_t nu_configure();
 size_t mixed_smem_bytes(int N, int prec);
 cudaError_t launch_forward(const SlotDev* slots, const int* ids, int n, int logN, int prec,
                            cudaStream_t st);
+// Step records of signals 0..n-1 into caller device arrays on stream st (any
+// pointer may be NULL; the layout of afd_batch_run with K_stride steps per
+// signal); steps_out[i] and E1_out (signal 0) from the control blocks.
+cudaError_t launch_gather(const StepRec* rec, const SlotCtl* ctl, int n, int K_max, int K_stride, double* a,
+                          double* coeff, double* delta, int* idx, int* steps_out, double* E1_out, cudaStream_t st);
 // Fills K[s * N + d] = 1 / (1 - r_s exp(2 pi i d / N)) for a plan.
 cudaError_t launch_kernel_table(const double* radii, int M, int N, double2* K, cudaStream_t st);
 // Shared memory (bytes) the grid kernel needs for this logN and precision.

@@ -559,6 +559,52 @@ k_forward_split(const SlotDev* __restrict__ slots, const int* __restrict__ ids) 
   for (int e = 0; e < P; ++e) c[SPL * fft_out_index<T, LOGS>(t, e) + h] = v[e];
 }
 
+// ------------------------------------------------------- output gather --
+
+// The step records of signal i = blockIdx.x into the caller's device arrays
+// (the layout of afd_batch_run: a, coeff and idx at 2 (i K_stride + k), delta
+// at i (K_stride + 1) + k); any pointer may be NULL.  steps_out[i] and (signal
+// 0) E1_out take the control block's step count and E_1.  The values are the
+// records' own, so they equal what the host-side gather writes.
+__global__ void __launch_bounds__(128)
+k_gather(const StepRec* __restrict__ rec, const SlotCtl* __restrict__ ctl, int K_max, int K_stride,
+         double* a, double* coeff, double* delta, int* idx, int* steps_out, double* E1_out) {
+  const int i = (int)blockIdx.x;
+  const SlotCtl c = ctl[i];
+  const int steps = c.k < K_max ? c.k : K_max;
+  const StepRec* r = rec + (size_t)i * K_max;
+  const size_t b2 = 2 * (size_t)i * K_stride, bd = (size_t)i * (K_stride + 1);
+  if (threadIdx.x == 0) {
+    // delta_0: 1 for a fresh start, E(start) / E_1 for a resumed one
+    if (delta) delta[bd] = (c.E1 > 0.0 && c.Estart != c.E1) ? c.Estart / c.E1 : 1.0;
+    if (steps_out) steps_out[i] = steps;
+    if (E1_out && i == 0) *E1_out = c.E1;
+  }
+  for (int k = threadIdx.x; k < steps; k += blockDim.x) {
+    const StepRec& q = r[k];
+    if (a) {
+      a[b2 + 2 * k] = q.a_re;
+      a[b2 + 2 * k + 1] = q.a_im;
+    }
+    if (coeff) {
+      coeff[b2 + 2 * k] = q.c_re;
+      coeff[b2 + 2 * k + 1] = q.c_im;
+    }
+    if (delta) delta[bd + k + 1] = q.delta;
+    if (idx) {
+      idx[b2 + 2 * k] = q.s;
+      idx[b2 + 2 * k + 1] = q.j;
+    }
+  }
+}
+
+cudaError_t launch_gather(const StepRec* rec, const SlotCtl* ctl, int n, int K_max, int K_stride, double* a,
+                          double* coeff, double* delta, int* idx, int* steps_out, double* E1_out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_gather<<<n, 128, 0, st>>>(rec, ctl, K_max, K_stride, a, coeff, delta, idx, steps_out, E1_out);
+  return cudaGetLastError();
+}
+
 // -------------------------------------------------------- plan K table --
 
 // K[s N + d] = 1 / (1 - r_s w^d), w = exp(2 pi i / N), written as

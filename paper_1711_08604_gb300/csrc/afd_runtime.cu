@@ -929,21 +929,35 @@ struct afd_batch {
 
 namespace {
 
-// Copy `bytes` from host memory `src` to caller memory `dst` (host or device).
-afd_status copy_out(void* dst, const void* src, size_t bytes) {
-  if (!dst || bytes == 0) return AFD_OK;
+// Whether the current device can write p directly (device or managed memory).
+bool device_ptr(const void* p) {
+  if (!p) return false;
   cudaPointerAttributes at{};
-  if (cudaPointerGetAttributes(&at, dst) == cudaSuccess &&
-      (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
-    CUDA_TRY(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
-  } else {
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
-    std::memcpy(dst, src, bytes);
+    return false;
   }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+template <typename T> T* dev_or_null(T* p) { return device_ptr(p) ? p : nullptr; }
+template <typename T> T* host_or_null(T* p) { return device_ptr(p) ? nullptr : p; }
+
+// Device-resident outputs are written by a gather kernel on the call's
+// stream, straight from the step records (no host round trip); host ones are
+// filled from the fetched records afterwards.  Returns whether any was on the
+// device.
+afd_status gather_device_outputs(const SlotPool& pool, int K_stride, double* a_out, double* coeff_out,
+                                 double* delta_out, int* idx_out, int* steps_out, double* E1_out, cudaStream_t st) {
+  double *a = dev_or_null(a_out), *c = dev_or_null(coeff_out), *d = dev_or_null(delta_out),
+         *e = dev_or_null(E1_out);
+  int *ix = dev_or_null(idx_out), *so = dev_or_null(steps_out);
+  if (a || c || d || e || ix || so)
+    CUDA_TRY(launch_gather(pool.rec_dev, pool.ctl_dev, pool.n, pool.K_max, K_stride, a, c, d, ix, so, e, st));
   return AFD_OK;
 }
 
-// Gather the records of signal i (steps = its step count) into caller arrays.
+// Gather the records of signal i (steps = its step count) into caller host
+// arrays (device ones are written by gather_device_outputs).
 afd_status write_outputs(const SlotPool& pool, int i, int K_stride, int steps, double* a_out,
                          double* coeff_out, double* delta_out, int* idx_out) {
   const StepRec* r = pool.rec_host + (size_t)i * pool.K_max;
@@ -962,10 +976,10 @@ afd_status write_outputs(const SlotPool& pool, int i, int K_stride, int steps, d
     ix[2 * k + 1] = r[k].j;
   }
   const size_t base2 = 2 * (size_t)i * K_stride, based = (size_t)i * (K_stride + 1);
-  if (a_out) AFD_TRY(copy_out(a_out + base2, a.data(), 8 * a.size()));
-  if (coeff_out) AFD_TRY(copy_out(coeff_out + base2, c.data(), 8 * c.size()));
-  if (delta_out) AFD_TRY(copy_out(delta_out + based, d.data(), 8 * d.size()));
-  if (idx_out) AFD_TRY(copy_out(idx_out + base2, ix.data(), 4 * ix.size()));
+  if (a_out) std::memcpy(a_out + base2, a.data(), 8 * a.size());
+  if (coeff_out) std::memcpy(coeff_out + base2, c.data(), 8 * c.size());
+  if (delta_out) std::memcpy(delta_out + based, d.data(), 8 * d.size());
+  if (idx_out) std::memcpy(idx_out + base2, ix.data(), 4 * ix.size());
   return AFD_OK;
 }
 
@@ -1171,6 +1185,9 @@ afd_status afd_decompose_from(afd_plan* plan, const double* G, double E1_in, int
   AFD_TRY(pool.upload(energy_tol, st));
   CUDA_TRY(cudaMemcpyAsync(pool.G_dev, G, 16 * (size_t)plan->tables.samples(), cudaMemcpyDefault, st));
   AFD_TRY(plan->runner.run(pool, K_max, plan->opts.use_graph != 0, plan->cnt, &plan->timer));
+  AFD_TRY(gather_device_outputs(pool, K_max, a_out, coeff_out, delta_out, idx_out, steps_done, E1_out, st));
+  if (G_final)
+    CUDA_TRY(cudaMemcpyAsync(G_final, pool.G_dev, 16 * (size_t)plan->tables.samples(), cudaMemcpyDefault, st));
   AFD_TRY(fetch_results(pool, st));
   const int steps = pool.ctl_host[0].k;
   plan->last_steps = steps;
@@ -1181,10 +1198,10 @@ afd_status afd_decompose_from(afd_plan* plan, const double* G, double E1_in, int
       for (int i = 0; i < 7; ++i) plan->phase_sum[i] += (double)(c[8 * k + i + 1] - c[8 * k + i]);
     plan->phase_steps += steps;
   }
-  AFD_TRY(write_outputs(pool, 0, K_max, steps, a_out, coeff_out, delta_out, idx_out));
-  if (steps_done) AFD_TRY(copy_out(steps_done, &steps, sizeof(int)));
-  if (E1_out) AFD_TRY(copy_out(E1_out, &pool.ctl_host[0].E1, sizeof(double)));
-  if (G_final) CUDA_TRY(cudaMemcpy(G_final, pool.G_dev, 16 * (size_t)plan->tables.samples(), cudaMemcpyDefault));
+  AFD_TRY(write_outputs(pool, 0, K_max, steps, host_or_null(a_out), host_or_null(coeff_out),
+                        host_or_null(delta_out), host_or_null(idx_out)));
+  if (int* sd = host_or_null(steps_done)) *sd = steps;
+  if (double* e1 = host_or_null(E1_out)) *e1 = pool.ctl_host[0].E1;
   if (pool.ctl_host[0].err & 2) return set_error(AFD_ERR_NUMERIC, "non-finite objective at step %d", steps);
   return AFD_OK;
 }
@@ -1320,15 +1337,17 @@ afd_status afd_batch_run(afd_batch* b, const double* G_packed, double energy_tol
   }
   b->tuned = true;
   AFD_TRY(b->runner.run(pool, pool.K_max, b->opts.use_graph != 0, b->cnt, nullptr));
+  AFD_TRY(gather_device_outputs(pool, pool.K_max, a_out, coeff_out, delta_out, idx_out, steps_out, nullptr, st));
   AFD_TRY(fetch_results(pool, st));
   bool numeric = false;
-  std::vector<int> steps(pool.n);
+  double *a_h = host_or_null(a_out), *c_h = host_or_null(coeff_out), *d_h = host_or_null(delta_out);
+  int *ix_h = host_or_null(idx_out), *so_h = host_or_null(steps_out);
   for (int i = 0; i < pool.n; ++i) {
-    steps[i] = pool.ctl_host[i].k;
+    const int steps = pool.ctl_host[i].k;
     numeric |= (pool.ctl_host[i].err & 2) != 0;
-    AFD_TRY(write_outputs(pool, i, pool.K_max, steps[i], a_out, coeff_out, delta_out, idx_out));
+    AFD_TRY(write_outputs(pool, i, pool.K_max, steps, a_h, c_h, d_h, ix_h));
+    if (so_h) so_h[i] = steps;
   }
-  if (steps_out) AFD_TRY(copy_out(steps_out, steps.data(), sizeof(int) * steps.size()));
   if (numeric) return set_error(AFD_ERR_NUMERIC, "non-finite objective in at least one signal");
   return AFD_OK;
 }

@@ -204,6 +204,62 @@ def test_device_pointers():
     assert np.array_equal(out["delta"].cpu().numpy(), host["delta"])
 
 
+def test_device_outputs_of_batches_and_resumed_runs():
+    # outputs in device memory are written on the device by a gather kernel;
+    # they must equal the host-output results bitwise, for batches (with
+    # steps_out) and for resumed runs (steps_done, G_final and E_1 as well)
+    import ctypes
+    import torch
+    lib = afd._lib()
+    sigs = [W.kernel_sum(item=i, N=N).G for i, N in enumerate((256, 1024, 256))]
+    radii = W.radii_linear(16)
+    K = 6
+    host = afd.afd_decompose_batch(sigs, radii, K)
+    b = afd.afd_batch_create([g.size for g in sigs], radii, K)
+    dev = {"a": torch.zeros(2 * 3 * K, dtype=torch.float64, device="cuda"),
+           "c": torch.zeros(2 * 3 * K, dtype=torch.float64, device="cuda"),
+           "d": torch.zeros(3 * (K + 1), dtype=torch.float64, device="cuda"),
+           "ix": torch.zeros(2 * 3 * K, dtype=torch.int32, device="cuda"),
+           "st": torch.zeros(3, dtype=torch.int32, device="cuda")}
+    Gp = torch.from_numpy(np.concatenate(sigs)).cuda()
+    st = lib.afd_batch_run(b.handle, Gp.data_ptr(), 0.0, dev["a"].data_ptr(), dev["c"].data_ptr(),
+                           dev["d"].data_ptr(), dev["ix"].data_ptr(), dev["st"].data_ptr())
+    b.close()
+    assert st == 0
+    assert np.array_equal(dev["st"].cpu().numpy(), host["steps"])
+    for i in range(3):
+        n = int(host["steps"][i])
+        a = dev["a"].cpu().numpy()[2 * i * K: 2 * (i * K + n)].view(np.complex128)
+        c = dev["c"].cpu().numpy()[2 * i * K: 2 * (i * K + n)].view(np.complex128)
+        d = dev["d"].cpu().numpy()[i * (K + 1): i * (K + 1) + n + 1]
+        ix = dev["ix"].cpu().numpy()[2 * i * K: 2 * (i * K + n)].reshape(n, 2)
+        assert np.array_equal(a, host["a"][i]) and np.array_equal(c, host["coeff"][i])
+        assert np.array_equal(d, host["delta"][i]) and np.array_equal(ix, host["idx"][i])
+    # resumed single-signal run with every output on the device
+    s = W.tones(item=2, K=10)
+    plan = afd.afd_plan_create(s.N, s.radii)
+    p1 = afd.afd_decompose_from(plan, s.G, 4)
+    ref = afd.afd_decompose_from(plan, p1["G_final"], 6, E1=p1["E1"])
+    o = {"a": torch.zeros(12, dtype=torch.float64, device="cuda"),
+         "c": torch.zeros(12, dtype=torch.float64, device="cuda"),
+         "d": torch.zeros(7, dtype=torch.float64, device="cuda"),
+         "ix": torch.zeros(12, dtype=torch.int32, device="cuda"),
+         "n": torch.zeros(1, dtype=torch.int32, device="cuda"),
+         "gf": torch.zeros(s.N, dtype=torch.complex128, device="cuda"),
+         "e1": torch.zeros(1, dtype=torch.float64, device="cuda")}
+    G1 = torch.from_numpy(p1["G_final"]).cuda()
+    st = lib.afd_decompose_from(plan.handle, G1.data_ptr(), p1["E1"], 6, 0.0, o["a"].data_ptr(), o["c"].data_ptr(),
+                                o["d"].data_ptr(), o["ix"].data_ptr(), o["n"].data_ptr(), o["gf"].data_ptr(),
+                                o["e1"].data_ptr())
+    plan.close()
+    assert st == 0 and int(o["n"].item()) == ref["steps"] == 6
+    assert np.array_equal(o["a"].cpu().numpy().view(np.complex128), ref["a"])
+    assert np.array_equal(o["c"].cpu().numpy().view(np.complex128), ref["coeff"])
+    assert np.array_equal(o["d"].cpu().numpy(), ref["delta"])
+    assert np.array_equal(o["ix"].cpu().numpy().reshape(6, 2), ref["idx"])
+    assert np.array_equal(o["gf"].cpu().numpy(), ref["G_final"]) and o["e1"].item() == ref["E1"]
+
+
 def test_invalid_arguments():
     with pytest.raises(afd.AfdError) as e:
         afd.afd_plan_create(112, [0.1, 0.2])  # 7 * 16: neither 2^a nor 2^a 3^b 5^c
