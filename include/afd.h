@@ -109,11 +109,13 @@ const char* afd_version(void);
  *          run as 2, 4 or 8 such transforms of decimated outputs, except
  *          FP32 N = 65536, which takes the two-pass path through HBM
  *          (single-signal plans only: batches and servers refuse it);
- *          or N = 2^a 3^b 5^c >= 9 that is not a power of two, N <= 12800
- *          (FP32 path) or 6400 (FP64 path): the remark after Table 9
- *          (Sec. 4.2) that the algorithm holds for N = p^K, taken here as
- *          mixed radices 2, 3, 4, 5, 8 and 16.  Not persistent; not served
- *          by afd_serve_* (power-of-two sizes only there).
+ *          or N = 2^a 3^b 5^c 7^d 11^e 13^f >= 9 that is not a power of two
+ *          and has at least two factors, N <= 12800 (FP32 path) or 6400
+ *          (FP64 path): the remark after Table 9 (Sec. 4.2) that the
+ *          algorithm holds for N = p^K with p prime, taken here as mixed
+ *          radices 2, 4, 8, 16 and the primes 3, 5, 7, 11, 13 (so 7^4, 11^3
+ *          and 13^3 among others).  Not persistent; not served by afd_serve_*
+ *          (power-of-two sizes only there).
  *   radii  host array of M ascending values in [0, 1); copied.
  *   M      1 <= M <= 4096.
  *   opts   NULL for defaults.

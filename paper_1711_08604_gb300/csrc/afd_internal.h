@@ -44,10 +44,11 @@ constexpr int BAR_BYTES = 128;
 constexpr int MIXED_MAX_SMEM = 204800;
 
 // Radix schedule of the mixed-radix Stockham transform of length
-// N = 2^a 3^b 5^c: radix-16 passes, one pass of 8, 4 or 2 for the rest of the
-// power of two, then radix-3 and radix-5 passes.  Returns the number of passes
-// written to radix[], or -1 if N has another prime factor or needs more than
-// MIXED_MAX_PASSES passes.
+// N = 2^a 3^b 5^c 7^d 11^e 13^f: radix-16 passes, one pass of 8, 4 or 2 for
+// the rest of the power of two, then one pass per odd prime factor (3, 5, 7,
+// 11, 13, in that order).  Returns the number of passes written to radix[],
+// or -1 if N has another prime factor or needs more than MIXED_MAX_PASSES
+// passes.
 template <typename I>
 inline __host__ __device__ int mixed_schedule(int N, I* radix) {
   if (N < 2) return -1;
@@ -56,8 +57,9 @@ inline __host__ __device__ int mixed_schedule(int N, I* radix) {
   if (n % 8 == 0 && np < MIXED_MAX_PASSES) { radix[np++] = 8; n /= 8; }
   else if (n % 4 == 0 && np < MIXED_MAX_PASSES) { radix[np++] = 4; n /= 4; }
   else if (n % 2 == 0 && np < MIXED_MAX_PASSES) { radix[np++] = 2; n /= 2; }
-  while (n % 3 == 0 && np < MIXED_MAX_PASSES) { radix[np++] = 3; n /= 3; }
-  while (n % 5 == 0 && np < MIXED_MAX_PASSES) { radix[np++] = 5; n /= 5; }
+  for (int p = 3; p <= 13; p += 2) {  // 3, 5, 7, 9 (never divides: 3 is gone), 11, 13
+    while (n % p == 0 && np < MIXED_MAX_PASSES) { radix[np++] = (I)p; n /= p; }
+  }
   return n == 1 ? np : -1;
 }
 

@@ -1,9 +1,11 @@
-// Grid and forward kernels for N = 2^a 3^b 5^c that is not a power of two.
+// Grid and forward kernels for N = 2^a 3^b 5^c 7^d 11^e 13^f that is not a
+// power of two.
 //
 // The paper's fast route (Eq. (rcl), Theorem 2.1, Sec. 3.1) splits the sum
 // over l by the factors of N; the remark after Table 9 (Sec. 4.2) notes that
-// the algorithm stays valid for N = p^K, p prime.  Here the transform is a mixed-radix
-// Stockham FFT with radices 16, 8, 4, 2, 3 and 5 (mixed_schedule): pass p of
+// the algorithm stays valid for N = p^K, p prime.  Here the transform is a
+// mixed-radix Stockham FFT with radices 16, 8, 4, 2 and the odd primes 3, 5,
+// 7, 11, 13 (mixed_schedule): pass p of
 // radix R over sub-transforms of length Ns reads x[b + q N/R] (q < R) for
 // butterfly b, multiplies input q by w^(dir q (b mod Ns) N/(Ns R)) with
 // w = exp(2 pi i / N), does an R-point DFT and writes output q to
@@ -71,10 +73,48 @@ __device__ __forceinline__ void dft5(V2<T>* v) {
   v[4] = csub<T>(A, iP);
 }
 
+// X_k = sum_{q<R} v_q exp(DIR 2 pi i q k / R) for an odd prime R, from the
+// symmetric pairs t_q = v_q + v_{R-q}, d_q = v_q - v_{R-q} (q = 1 .. H,
+// H = (R - 1) / 2):
+//   X_0 = v_0 + sum_q t_q,
+//   X_k, X_{R-k} = v_0 + sum_q t_q cos(2 pi q k / R)  +-  DIR i sum_q d_q sin(2 pi q k / R).
+// rc[m], rs[m] (m = 1 .. H) hold cos and sin of 2 pi m / R; (q k) mod R is a
+// compile-time index once the loops are unrolled.
 template <int R, int DIR, typename T>
-__device__ __forceinline__ void dft_any(V2<T>* v) {
+__device__ __forceinline__ void dft_odd(V2<T>* v, const T* rc, const T* rs) {
+  constexpr int H = (R - 1) / 2;
+  V2<T> t[H + 1], d[H + 1];
+  V2<T> x0 = v[0];
+#pragma unroll
+  for (int q = 1; q <= H; ++q) {
+    t[q] = cadd<T>(v[q], v[R - q]);
+    d[q] = csub<T>(v[q], v[R - q]);
+    x0 = cadd<T>(x0, t[q]);
+  }
+#pragma unroll
+  for (int k = 1; k <= H; ++k) {
+    V2<T> a = v[0], b = mk2<T>((T)0, (T)0);
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+      const int m = (q * k) % R;  // cos and sin of 2 pi m / R from the first half
+      const T c = m <= H ? rc[m] : rc[R - m];
+      const T sn = m <= H ? rs[m] : -rs[R - m];
+      a = mk2<T>(a.x + c * t[q].x, a.y + c * t[q].y);
+      b = mk2<T>(b.x + sn * d[q].x, b.y + sn * d[q].y);
+    }
+    // DIR i b
+    const V2<T> ib = DIR > 0 ? mk2<T>(-b.y, b.x) : mk2<T>(b.y, -b.x);
+    v[k] = cadd<T>(a, ib);
+    v[R - k] = csub<T>(a, ib);
+  }
+  v[0] = x0;
+}
+
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft_any(V2<T>* v, const T* rc, const T* rs) {
   if constexpr (R == 3) dft3<DIR, T>(v);
   else if constexpr (R == 5) dft5<DIR, T>(v);
+  else if constexpr (R == 7 || R == 11 || R == 13) dft_odd<R, DIR, T>(v, rc, rs);
   else dft<R, DIR, T>(v);
 }
 
@@ -84,6 +124,18 @@ __device__ __forceinline__ void dft_any(V2<T>* v) {
 template <typename T, int R, int DIR, bool TWS, class Src, class Dst>
 __device__ __forceinline__ void mx_pass(int N, int Ns, const V2<T>* __restrict__ tw, Src& src, Dst& dst) {
   const int NR = N / R, step = N / (Ns * R);
+  // cos and sin of 2 pi m / R = w^(m N / R), m = 1 .. (R - 1) / 2, for the odd
+  // prime radices that use dft_odd
+  constexpr int H = R > 5 && (R & 1) ? (R - 1) / 2 : 0;
+  T rc[H + 1], rs[H + 1];
+#pragma unroll
+  for (int m = 1; m <= H; ++m) {
+    V2<T> w;
+    if constexpr (TWS) w = tw[m * NR];
+    else w = __ldg(&tw[m * NR]);
+    rc[m] = w.x;
+    rs[m] = w.y;
+  }
   for (int b = threadIdx.x; b < NR; b += MX_THREADS) {
     const int k = b % Ns;
     V2<T> v[R];
@@ -98,7 +150,7 @@ __device__ __forceinline__ void mx_pass(int N, int Ns, const V2<T>* __restrict__
         v[q] = DIR > 0 ? cmul<T>(v[q], w) : cmulc<T>(v[q], w);
       }
     }
-    dft_any<R, DIR, T>(v);
+    dft_any<R, DIR, T>(v, rc, rs);
     const int base = (b - k) * R + k;
 #pragma unroll
     for (int q = 0; q < R; ++q) dst(base + q * Ns, v[q]);
@@ -114,7 +166,10 @@ __device__ __forceinline__ void mx_pass_any(int R, int N, int Ns, const V2<T>* _
     case 4: mx_pass<T, 4, DIR, TWS>(N, Ns, tw, src, dst); break;
     case 2: mx_pass<T, 2, DIR, TWS>(N, Ns, tw, src, dst); break;
     case 3: mx_pass<T, 3, DIR, TWS>(N, Ns, tw, src, dst); break;
-    default: mx_pass<T, 5, DIR, TWS>(N, Ns, tw, src, dst); break;
+    case 5: mx_pass<T, 5, DIR, TWS>(N, Ns, tw, src, dst); break;
+    case 7: mx_pass<T, 7, DIR, TWS>(N, Ns, tw, src, dst); break;
+    case 11: mx_pass<T, 11, DIR, TWS>(N, Ns, tw, src, dst); break;
+    default: mx_pass<T, 13, DIR, TWS>(N, Ns, tw, src, dst); break;
   }
 }
 

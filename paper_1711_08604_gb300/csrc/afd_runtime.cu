@@ -95,7 +95,7 @@ afd_status check_size(int N, int prec, bool allow_two_pass, bool allow_mixed) {
   if (allow_mixed && !is_pow2(N) && N >= (1 << MIN_LOGN)) {
     int radix[MIXED_MAX_PASSES];
     if (mixed_schedule(N, radix) < 2)
-      return set_error(AFD_ERR_INVALID, "N = %d: must be a power of two or a product of powers of 2, 3 and 5", N);
+      return set_error(AFD_ERR_INVALID, "N = %d: must be a power of two or a product of powers of 2, 3, 5, 7, 11 and 13", N);
     if (mixed_smem_bytes(N, prec) > (size_t)MIXED_MAX_SMEM)
       return set_error(AFD_ERR_INVALID, "N = %d: largest mixed-radix size is %d for this precision", N,
                        (int)(MIXED_MAX_SMEM / (prec == AFD_FP32_GUARDED ? 16 : 32)));
@@ -103,7 +103,7 @@ afd_status check_size(int N, int prec, bool allow_two_pass, bool allow_mixed) {
   }
   if (!is_pow2(N) || N < (1 << MIN_LOGN))
     return set_error(AFD_ERR_INVALID,
-                     allow_mixed ? "N = %d: must be >= 8 and a power of two or a product of powers of 2, 3 and 5"
+                     allow_mixed ? "N = %d: must be >= 8 and a power of two or a product of powers of 2, 3, 5, 7, 11 and 13"
                                  : "N = %d: must be a power of two >= 8",
                      N);
   if (N > (1 << MAX_LOGN))

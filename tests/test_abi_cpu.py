@@ -73,7 +73,7 @@ def test_wait_selftest_checks_arguments_before_any_cuda_call(lib):
 
 
 @pytest.mark.parametrize("N,radii,kw", [
-    (112, [0.1, 0.2], {}),                # 7 x 16: neither 2^a nor 2^a 3^b 5^c
+    (272, [0.1, 0.2], {}),                # 17 x 16: a prime factor above 13
     (64, [0.2, 0.1], {}),                 # radii not ascending
     (64, [0.1, 1.0], {}),                 # a radius outside [0, 1)
     (1 << 17, [0.1], {}),                 # above the largest size of any path
@@ -109,7 +109,9 @@ def test_nonuniform_plan_arguments_checked_before_any_cuda_call(lib):
     (65536, 1, True),                         # the two-pass size (FP32 path)
     (1 << 17, 1, False), (1 << 17, 0, False), # above every path
     (9, 1, True), (3000, 1, True),            # 2^a 3^b 5^c
-    (21, 1, False), (112, 1, False),          # a factor 7
+    (21, 1, True), (112, 1, True),            # factors 7: N = p^K sizes (7, 11, 13)
+    (2401, 0, True), (1331, 1, True), (2197, 0, True),
+    (17, 1, False), (272, 1, False), (7, 1, False),  # a factor 17; a single pass
     (12800, 1, True), (13500, 1, False),      # largest mixed-radix sizes: 16 N and
     (6400, 0, True), (6480, 0, False),        # 32 N bytes of shared memory <= 204800
 ])
@@ -128,7 +130,7 @@ def test_size_rules(lib, N, prec, valid):
 
 def test_batch_and_server_arguments_checked_before_any_cuda_call(lib):
     import paper_1711_08604_gb300 as afd
-    bad_batches = [([256, 112], [0.1, 0.5], 5),    # a size with a factor 7
+    bad_batches = [([256, 272], [0.1, 0.5], 5),    # a size with a factor 17
                    ([256, 512], [0.5, 0.1], 5),    # radii not ascending
                    ([256], [0.1], 0),              # K_max below 1
                    ([65536], [0.1], 5)]            # the FP32 two-pass size: single-signal plans only

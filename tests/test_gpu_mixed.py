@@ -1,5 +1,6 @@
-"""N = 2^a 3^b 5^c that is not a power of two: the mixed-radix path against the
-oracle (the remark after Table 9, Sec. 4.2: the algorithm stays valid for N = p^K)."""
+"""N = 2^a 3^b 5^c 7^d 11^e 13^f that is not a power of two: the mixed-radix path
+against the oracle (the remark after Table 9, Sec. 4.2: the algorithm stays valid
+for N = p^K with p prime)."""
 import numpy as np
 import pytest
 
@@ -109,9 +110,48 @@ def test_mixed_resume_is_bitwise(prec):
     assert np.array_equal(p2["G_final"], full["G_final"])
 
 
+# N = p^K for the primes 7, 11 and 13 (the paper's remark), ragged products
+# with 2, 3 and 5, and every odd prime as first, middle and last pass
+PRIME = [49, 14, 26, 77, 91, 143, 343, 105, 616, 1001, 1331, 2197, 2401]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N", PRIME)
+def test_prime_power_sizes_full_grid_parity(prec, N):
+    # every grid point of every step against the oracle's own direct grid
+    G = W.random_signal(N, 13 * N) + W.szego_sum(N, np.array([0.9 * np.exp(1.3j)]), np.array([0.7]))
+    res = run(G, RADII, 5, prec)
+    assert res["steps"] == 5
+    assert parity.check(G, RADII, res, prec)["selection_checked"] == 5
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N", [1331, 2197, 2401])
+def test_prime_power_reproducing_kernel(prec, N):
+    # G = e_b, b on the grid: the first step picks b with |c_1| = 1
+    radii = W.radii_linear(40)
+    j0 = N // 3 + 2
+    b = radii[29] * np.exp(2j * np.pi * j0 / N)
+    G = W.szego_sum(N, np.array([b]), np.array([1.0]))
+    res = run(G, radii, 1, prec)
+    assert tuple(res["idx"][0]) == (29, j0)
+    assert abs(abs(res["coeff"][0]) - 1.0) <= 1e-12
+
+
+def test_prime_power_batch_equals_single_runs():
+    Ns = [2401, 1331, 2197, 1024, 1331, 343]
+    sigs = [W.random_signal(N, 60 + i) for i, N in enumerate(Ns)]
+    radii = W.radii_linear(16)
+    res = afd.afd_decompose_batch(sigs, radii, 4)
+    for i, G in enumerate(sigs):
+        one = run(G, radii, 4, afd.AFD_FP32_GUARDED)
+        for key in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(res[key][i], one[key]), (Ns[i], key)
+
+
 def test_mixed_size_limits():
     r = np.array([0.0, 0.5])
-    for N, prec in [(7 * 128, 1), (11 * 9, 1), (13500, 1), (7200, 0), (6, 1)]:
+    for N, prec in [(17 * 128, 1), (19 * 9, 1), (7, 1), (13500, 1), (7200, 0), (6, 1)]:
         with pytest.raises(afd.AfdError) as e:
             afd.afd_plan_create(N, r, precision=prec)
         assert e.value.status == -1, N

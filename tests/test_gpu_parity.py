@@ -262,7 +262,7 @@ def test_device_outputs_of_batches_and_resumed_runs():
 
 def test_invalid_arguments():
     with pytest.raises(afd.AfdError) as e:
-        afd.afd_plan_create(112, [0.1, 0.2])  # 7 * 16: neither 2^a nor 2^a 3^b 5^c
+        afd.afd_plan_create(272, [0.1, 0.2])  # 17 * 16: a prime factor above 13
     assert e.value.status == -1
     with pytest.raises(afd.AfdError):
         afd.afd_plan_create(64, [0.2, 0.1])
