@@ -193,7 +193,8 @@ __device__ __forceinline__ double2 warp_sum_partials(const double2* part, int co
 // Eq. (formula1): for a = r_s w^j,
 //   <G, e_a>~ = sqrt(1 - r_s^2)/N sum_m G(z_m) K_s[(j - m) mod N],
 // K_s[d] = 1 / (1 - r_s w^d) from the plan.  CTA (c0, p) adds chunk p of the
-// candidates c0, c0 + GUARD_PAR, ...; the last CTA totals each candidate and
+// candidates c0, c0 + par, ... (par = gridDim.x / chunks: the candidates in
+// flight, chosen by launch_guard); the last CTA totals each candidate and
 // picks the largest |.|^2 (ties: lowest flat index s N + j).
 __global__ void __launch_bounds__(FP64_THREADS)
 k_guard(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
@@ -207,13 +208,14 @@ k_guard(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
   if (ld_done(ctl)) return;
   const int N = sd.p.N;
   const int Pg = chunks_of(N);
+  const int par = gridDim.x / Pg;  // candidates in flight (launch_guard)
   const int c0 = blockIdx.x / Pg, p = blockIdx.x % Pg;
   const int n_cand = ctl->n_cand;
   const int m = p * FP64_CHUNK + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double2 g = make_double2(0.0, 0.0);
   if (m < N && c0 < n_cand) g = sd.G[m];
-  for (int c = c0; c < n_cand; c += GUARD_PAR) {
+  for (int c = c0; c < n_cand; c += par) {
     const int2 cj = sd.cand[c];
     double ar = 0.0, ai = 0.0;
     if (m < N) guard_term(sd, cj.x, cj.y, m, g, ar, ai);
@@ -1160,6 +1162,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
     if (clk) clk[8 * k + 4] = clock64();
 
     // ---------------------------------------------------------------- C --
+
     // step k-1 is complete: with a tolerance, its energy, delta and the stop
     // rule (step k ran speculatively so far; nothing of it is recorded before
     // this)
@@ -1565,7 +1568,13 @@ cudaError_t launch_persistent(const SlotDev* slots, int logN, int M, cudaStream_
 
 cudaError_t launch_guard(const SlotDev* slots, const int* ids, int n, int N, int cap, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  dim3 grid((cap < GUARD_PAR ? cap : GUARD_PAR) * chunks_of(N), n);
+  // Candidates in flight per signal: GUARD_PAR for a few signals (the latency
+  // of one signal's step), one when many signals share the launch (most steps
+  // have one candidate, and CTAs whose candidate does not exist still cost a
+  // scheduling slot).  Every chunk's partial sum is the same either way.
+  int par = cap < GUARD_PAR ? cap : GUARD_PAR;
+  if (n >= 8) par = 1;
+  dim3 grid(par * chunks_of(N), n);
   return launch_pdl(k_guard, grid, dim3(FP64_THREADS), 0, st, slots, ids);
 }
 

@@ -89,6 +89,21 @@ def test_batch_with_split_sizes(prec, Ns):
         assert parity.check(G, radii, r, prec, full_grid="fft")["selection_checked"] == 3
 
 
+def test_large_class_equals_single_runs():
+    # twelve signals of one N share each launch (the guard then keeps one
+    # candidate in flight per signal instead of four): the results are the
+    # single-signal ones bitwise
+    sigs = [W.tones(item=20 + i, N=2048, M=40, K=6).G for i in range(12)]
+    radii = W.radii_linear(40)
+    res = afd.afd_decompose_batch(sigs, radii, 6)
+    for i, G in enumerate(sigs):
+        plan = afd.afd_plan_create(G.size, radii)
+        one = afd.afd_decompose(plan, G, 6)
+        plan.close()
+        for key in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(res[key][i], one[key]), (i, key)
+
+
 def test_batch_reuse_and_counters():
     sigs = small_batch(n=5, Ns=(1024, 2048))
     radii = W.radii_linear(16)
