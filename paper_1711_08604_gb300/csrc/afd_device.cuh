@@ -157,22 +157,83 @@ __device__ __forceinline__ void block_best_f(float& v, int& f, float* sv, int* s
     if (better_f(sv[w], sf[w], v, f)) { v = sv[w]; f = sf[w]; }
 }
 
-// Last-CTA detection: returns true in every thread of the CTA that is the
-// last of `target` CTAs to arrive on *counter, and resets the counter.  Every
-// write the last CTA reads must come from thread 0 or be followed by a
-// __threadfence() in the thread that made it.
-__device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned target, int* s_flag) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
+// A set of threads that works and synchronises as one unit: the whole CTA
+// (barrier 0), or a 128-thread quarter of a larger CTA on its own named
+// barrier (1 + quarter), so that one CTA can run four FP64 work items at once.
+// tid: the thread's index within the set.
+struct ThreadSet {
+  int bar, count, tid;
+  __device__ __forceinline__ void sync() const {
+    if (bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(count) : "memory");
+  }
+};
+__device__ __forceinline__ ThreadSet cta_set() { return ThreadSet{0, (int)blockDim.x, (int)threadIdx.x}; }
+__device__ __forceinline__ ThreadSet quarter_set() {
+  return ThreadSet{1 + (int)(threadIdx.x >> 7), 128, (int)(threadIdx.x & 127)};
+}
+
+// Last-work-item detection: returns true in every thread of the set that is
+// the last of `target` items to arrive on *counter, and resets the counter.
+// Every write the last item reads must come from thread 0 of its set or be
+// followed by a __threadfence() in the thread that made it.
+__device__ __forceinline__ bool arrive_last_set(unsigned* counter, unsigned target, int* s_flag, const ThreadSet& ts) {
+  ts.sync();
+  if (ts.tid == 0) {
     __threadfence();
     unsigned prev = atomicAdd(counter, 1u);
     *s_flag = (prev == target - 1u);
     if (*s_flag) *counter = 0u;
   }
-  __syncthreads();
+  ts.sync();
   const bool last = *s_flag != 0;
   if (last) __threadfence();
   return last;
+}
+// The same for the whole CTA (one CTA per work item).
+__device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned target, int* s_flag) {
+  return arrive_last_set(counter, target, s_flag, cta_set());
+}
+
+constexpr long kBarrierLimit = 1L << 22;  // polls before a grid barrier gives up (about a second)
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs are co-resident).  The
+// arrival counter *bar only grows during a launch (the host zeroes it
+// before), so barrier number e of the launch is passed once it reaches
+// nblocks * (e + 1): one reduction per CTA and a poll, no reset.  Thread 0
+// arrives with a release reduction (after the CTA barrier, so it publishes
+// the CTA's writes) and polls with acquire loads, so the others' writes are
+// visible once the count is reached.  Bounded: a CTA that polls
+// kBarrierLimit times sets bit 2 (value 4) of *err, and every CTA that sees
+// the bit leaves.  False in every thread when the kernel must stop.
+__device__ __forceinline__ bool grid_barrier_at(unsigned* bar, int* err, unsigned target, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    for (long it = 1; ld_acquire_gpu(bar) < target; ++it) {
+      if (it > kBarrierLimit) {
+        atomicOr(err, 4);
+        ok = 0;
+        break;
+      }
+      if ((it & 255) == 0 && (*((volatile int*)err) & 4)) {  // another CTA gave up
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+    if (*((volatile int*)err) & 4) ok = 0;
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
 }
 
 // Four doubles read with one 256-bit load through L2 (32-byte aligned).
@@ -316,24 +377,24 @@ __device__ __forceinline__ void guard_term(const SlotDev& sd, int s, int j, int 
   ai = fma(g.x, k.y, g.y * k.x);
 }
 
-// Fixed-order sum over the first FP64_THREADS threads (warps 0..3) of (x, y):
-// a shuffle tree inside each warp, then the warps in order.  Every thread of
-// the CTA must call it; thread 0 gets the total.
-__device__ __forceinline__ double2 sum_fp64_group(double x, double y, double* red) {
+// Fixed-order sum over the first FP64_THREADS threads (warps 0..3) of a
+// thread set of (x, y): a shuffle tree inside each warp, then the warps in
+// order.  Every thread of the set must call it; its thread 0 gets the total.
+__device__ __forceinline__ double2 sum_fp64_set(double x, double y, double* red, const ThreadSet& ts) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     x += __shfl_xor_sync(0xffffffffu, x, off);
     y += __shfl_xor_sync(0xffffffffu, y, off);
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
+  const int lane = ts.tid & 31, warp = ts.tid >> 5;
+  ts.sync();
   if (lane == 0 && warp < FP64_THREADS / 32) {
     red[2 * warp] = x;
     red[2 * warp + 1] = y;
   }
-  __syncthreads();
+  ts.sync();
   double tx = 0.0, ty = 0.0;
-  if (threadIdx.x == 0) {
+  if (ts.tid == 0) {
 #pragma unroll
     for (int w = 0; w < FP64_THREADS / 32; ++w) {
       tx += red[2 * w];
@@ -342,23 +403,27 @@ __device__ __forceinline__ double2 sum_fp64_group(double x, double y, double* re
   }
   return make_double2(tx, ty);
 }
+__device__ __forceinline__ double2 sum_fp64_group(double x, double y, double* red) {
+  return sum_fp64_set(x, y, red, cta_set());
+}
 
-// The same for one component (the energy): the x half of sum_fp64_group,
+// The same for one component (the energy): the x half of sum_fp64_set,
 // bitwise the same total.
-__device__ __forceinline__ double sum_fp64_group1(double x, double* red) {
+__device__ __forceinline__ double sum_fp64_set1(double x, double* red, const ThreadSet& ts) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
+  const int lane = ts.tid & 31, warp = ts.tid >> 5;
+  ts.sync();
   if (lane == 0 && warp < FP64_THREADS / 32) red[warp] = x;
-  __syncthreads();
+  ts.sync();
   double tx = 0.0;
-  if (threadIdx.x == 0) {
+  if (ts.tid == 0) {
 #pragma unroll
     for (int w = 0; w < FP64_THREADS / 32; ++w) tx += red[w];
   }
   return tx;
 }
+__device__ __forceinline__ double sum_fp64_group1(double x, double* red) { return sum_fp64_set1(x, red, cta_set()); }
 
 // Reduced-remainder update of Sec. 2 at z_m for a = r_s w^j and
 // c' = c sqrt(1 - r_s^2):  G_{k+1}(z_m) = (G_k(z_m) u - c') / (z_m - a) with

@@ -36,9 +36,9 @@ inline __host__ __device__ int chunks_of(int N) { return (N + FP64_CHUNK - 1) / 
 // (x mod N) for x in (-N, 2N); N need not be a power of two
 inline __host__ __device__ int wrap_mod(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
 constexpr int MIXED_MAX_PASSES = 24;
-// Grid-barrier counter of the persistent kernel: its own 128-byte line,
-// zeroed before a launch.
-constexpr int BAR_BYTES = 128;
+// Grid-barrier counter of the persistent kernels and their error word: a
+// 128-byte line each, zeroed before a launch.
+constexpr int BAR_BYTES = 256;
 // Largest shared-memory footprint (two ping-pong buffers of N points) of the
 // mixed-radix kernels: N <= 12800 in FP32, N <= 6400 in FP64.
 constexpr int MIXED_MAX_SMEM = 204800;
@@ -167,6 +167,32 @@ __device__ __forceinline__ double obj_rho64(const SlotDev& sd, int s) { return s
 static_assert(sizeof(StepRec) == 80, "StepRec layout");
 static_assert(sizeof(SlotCtl) == 64, "SlotCtl layout");
 static_assert(sizeof(SlotDev) == 392, "SlotDev layout");
+
+// The multi-signal persistent kernel (afd_multi.cu): one N-class of signals
+// (ids[first .. first + count)) and its work split.
+constexpr int MULTI_THREADS = 512;
+constexpr int MULTI_MAX_CLASSES = 16;
+struct MultiClass {
+  int logN, first, count, Mmax;
+  int tiles;    // grid items (radius tiles) per signal
+  int gpar;     // guard: candidates in flight per signal (as launch_guard)
+  int fgroups;  // forward: signals per CTA (transform groups)
+};
+struct MultiArgs {
+  const SlotDev* slots;
+  const int* ids;        // the signals of the steps, grouped by class
+  const int* fresh_ids;  // the signals to initialise first, grouped by class
+  unsigned* bar;         // BAR_BYTES, zeroed before the launch: barrier counter, error word
+  int K;                 // greedy steps
+  int final_forward;     // 1: transform the remainder after the last step too (serving)
+  int n_cls, n_fresh;
+  MultiClass cls[MULTI_MAX_CLASSES], fresh[MULTI_MAX_CLASSES];
+};
+bool multi_size_ok(int logN);  // FP32 powers of two 8 .. 16384
+void multi_class_shape(int logN, int Mmax, int count, int cap, MultiClass* c);  // all but first
+cudaError_t multi_configure();
+// One cooperative launch: the fresh signals' initialisation, then K steps.
+cudaError_t launch_multi(const MultiArgs& a, cudaStream_t st);
 
 // Kernel launchers (afd_kernels.cu).  `ids` lists the slots of one launch, all
 // with the same logN; `n` is their number.  Each returns the launch status.

@@ -29,355 +29,43 @@
 #include "afd_fft.cuh"
 #include "afd_fft2.h"
 #include "afd_internal.h"
+#include "afd_step.cuh"
 
 namespace afd {
 
-// ------------------------------------------------------------ grid kernel --
-
-// PP: points per thread (0: the default of FftShape); CT: the CTA width the
-// transforms are packed up to (several radii per CTA when one transform has
-// fewer threads).  The variants compute bitwise the same values: only which
-// thread computes which butterfly changes.
-template <typename T, int LOGN, int PP = 0, int CT = 256>
-struct GridCfg {
-  using S = FftShape<T, LOGN, PP>;
-  // FP32 packs small transforms into CTAs of CT threads; FP64 keeps one warp
-  // per CTA at most, so that its FP64 work (1/64 of the FP32 rate) spreads
-  // over as many SMs as there are radii
-  static constexpr int CTA = sizeof(T) == 4 ? CT : 32;
-  static constexpr int FPC = S::TPF >= CTA ? 1 : CTA / S::TPF;  // transforms per CTA
-  static constexpr int THREADS = S::TPF * FPC;
-};
+// ------------------------------------------------------------ step kernels --
+// One CTA per work item: the bodies of afd_step.cuh.
 
 template <typename T, int LOGN, int PP = 0, int CT = 256>
 __global__ void __launch_bounds__(GridCfg<T, LOGN, PP, CT>::THREADS)
 k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
-  using S = FftShape<T, LOGN, PP>;
-  using C = GridCfg<T, LOGN, PP, CT>;
-  constexpr int N = S::N, P = S::P, TPF = S::TPF, FPC = C::FPC, THREADS = C::THREADS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_last;
-  pdl_launch_dependents();
-  const SlotDev& sd = slots[ids[blockIdx.y]];
-
-  const int g = threadIdx.x / TPF, t = threadIdx.x % TPF;
-  const int s = blockIdx.x * FPC + g;
-  const int M = sd.p.M;
-  const bool active = s < M;
-  V2<T>* buf = reinterpret_cast<V2<T>*>(smem_raw) + g * S::SMEM;
-
-  // Pass-0 input f(l) = r_s^l c_l / N, read straight from the spectrum.  The
-  // thread's inputs are l = b + q B (q < R0) with B = N / R0, so
-  // r_s^l = lo[b] * hi[q] with one lo value per butterfly.
-  constexpr int R0 = S::radix(0), B = FftSchedule::pow_b(LOGN), NB0 = P / R0;
-  V2<T> v[P];
-  const V2<T>* tw;
-  if constexpr (sizeof(T) == 4) tw = sd.p.st32; else tw = sd.p.st64;
-  if (active) {
-    const T* lo;
-    const T* hi;
-    const V2<T>* c;
-    if constexpr (sizeof(T) == 4) {
-      lo = sd.p.rlo32 + (size_t)s * B;
-      hi = sd.p.rhi32 + (size_t)s * R0;
-      c = sd.c32;
-    } else {
-      lo = sd.p.rlo64 + (size_t)s * B;
-      hi = sd.p.rhi64 + (size_t)s * R0;
-      c = sd.c64;
-    }
-    // the power tables are constant: fetch them before waiting for the
-    // kernel that produced the spectrum
-    T h[R0], lb[NB0];
-#pragma unroll
-    for (int q = 0; q < R0; ++q) h[q] = __ldg(&hi[q]);
-#pragma unroll
-    for (int i = 0; i < NB0; ++i) lb[i] = __ldg(&lo[t + i * TPF]);
-    pdl_wait();
-    if (ld_done(sd.ctl)) return;
-#pragma unroll
-    for (int i = 0; i < NB0; ++i) {
-      const int b = t + i * TPF;
-#pragma unroll
-      for (int q = 0; q < R0; ++q) {
-        const T rp = lb[i] * h[q];
-        const V2<T> x = c[b + q * B];
-        v[i * R0 + q] = mk2<T>(x.x * rp, x.y * rp);
-      }
-    }
-  } else {
-    pdl_wait();
-    if (ld_done(sd.ctl)) return;
-#pragma unroll
-    for (int e = 0; e < P; ++e) v[e] = mk2<T>((T)0, (T)0);
-  }
-
-  // the CTA's transforms synchronise on their own group barriers
-  fft_run<T, LOGN, +1, 0, false, PP, (FPC > 1)>(v, t, buf, tw);
-
-  // Objective and per-radius best, straight from registers.
-  if constexpr (sizeof(T) == 4) {
-    __shared__ Best2F red[32];
-    Best2F b;
-    b.init();
-#pragma unroll
-    for (int u = 0; u < P; ++u) {
-      const V2<T> x = v[fft_out_slot<T, LOGN, PP>(u)];
-      b.push_ascending(x.x * x.x + x.y * x.y, t + TPF * u);
-    }
-    group_reduce<TPF>(b, red);
-    if (t == 0 && active) {
-      const float w2 = obj_w32(sd, s);
-      Top2F o;
-      o.v1 = b.v1 * w2;
-      o.v2 = b.v2 * w2;
-      o.j1 = b.j1;
-      o.j2 = b.j2;
-      reinterpret_cast<Top2F*>(sd.top2)[s] = o;
-      // objectives are >= 0, so their bit patterns order like the values
-      if (o.v1 >= 0.0f && o.v1 <= 3.402823466e38f) atomicMax(&sd.ctl->vmax_bits, __float_as_uint(o.v1));
-      __threadfence();  // read by the signal's last CTA
-    }
-    if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
-    select_candidates_f32<THREADS>(sd, sd.ctl->k);
-  } else {
-    __shared__ Best1D red[32];
-    Best1D b;
-    b.init();
-#pragma unroll
-    for (int u = 0; u < P; ++u) {
-      const V2<T> x = v[fft_out_slot<T, LOGN, PP>(u)];
-      b.push_ascending(x.x * x.x + x.y * x.y, t + TPF * u, x);
-    }
-    group_reduce<TPF>(b, red);
-    if (t == 0 && active) {
-      const double w = sd.p.w64[s];
-      Top2D o;
-      o.v1 = b.v * (w * w) * obj_rho64(sd, s);
-      o.j1 = b.j;
-      o.f1 = b.f;
-      o.v2 = -1.0;
-      o.j2 = INT_MAX;
-      o.f2 = make_double2(0.0, 0.0);
-      reinterpret_cast<Top2D*>(sd.top2)[s] = o;
-      __threadfence();  // read by the signal's last CTA
-    }
-    if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
-    __syncthreads();
-    select_best_f64<THREADS>(sd, sd.ctl->k, red);
-  }
+  grid_body<T, LOGN, PP, CT>(slots, ids, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
-// ----------------------------------------------------------- guard kernel --
-
-// Deterministic sum of `count` partials (double2) by one warp: lane q adds
-// partials q, q + 32, ... in order, then a fixed shuffle tree.  Lane 0 gets
-// the total.
-__device__ __forceinline__ double2 warp_sum_partials(const double2* part, int count) {
-  const int lane = threadIdx.x & 31;
-  double x = 0.0, y = 0.0;
-  for (int q = lane; q < count; q += 32) {
-    const double2 v = __ldcg(&part[q]);
-    x += v.x;
-    y += v.y;
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    x += __shfl_xor_sync(0xffffffffu, x, off);
-    y += __shfl_xor_sync(0xffffffffu, y, off);
-  }
-  return make_double2(x, y);
-}
-
-// FP64 re-evaluation of the FP32 path's candidates by the rectangle rule of
-// Eq. (formula1): for a = r_s w^j,
-//   <G, e_a>~ = sqrt(1 - r_s^2)/N sum_m G(z_m) K_s[(j - m) mod N],
-// K_s[d] = 1 / (1 - r_s w^d) from the plan.  CTA (c0, p) adds chunk p of the
-// candidates c0, c0 + par, ... (par = gridDim.x / chunks: the candidates in
-// flight, chosen by launch_guard); the last CTA totals each candidate and
-// picks the largest |.|^2 (ties: lowest flat index s N + j).
 __global__ void __launch_bounds__(FP64_THREADS)
 k_guard(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
-  __shared__ double red[2 * (FP64_THREADS / 32)];
-  __shared__ double s_re[MAX_CAP], s_im[MAX_CAP];
-  __shared__ int s_last;
+  __shared__ Fp64Smem sm;
   pdl_launch_dependents();
-  const SlotDev& sd = slots[ids[blockIdx.y]];
-  SlotCtl* ctl = sd.ctl;
   pdl_wait();
-  if (ld_done(ctl)) return;
-  const int N = sd.p.N;
-  const int Pg = chunks_of(N);
-  const int par = gridDim.x / Pg;  // candidates in flight (launch_guard)
-  const int c0 = blockIdx.x / Pg, p = blockIdx.x % Pg;
-  const int n_cand = ctl->n_cand;
-  const int m = p * FP64_CHUNK + threadIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double2 g = make_double2(0.0, 0.0);
-  if (m < N && c0 < n_cand) g = sd.G[m];
-  for (int c = c0; c < n_cand; c += par) {
-    const int2 cj = sd.cand[c];
-    double ar = 0.0, ai = 0.0;
-    if (m < N) guard_term(sd, cj.x, cj.y, m, g, ar, ai);
-    const double2 tot = sum_fp64_group(ar, ai, red);
-    if (threadIdx.x == 0) sd.gpart[c * Pg + p] = tot;
-  }
-  if (!arrive_last(&ctl->cnt_guard, gridDim.x, &s_last)) return;
-  for (int c = warp; c < n_cand; c += FP64_THREADS / 32) {
-    const double2 tot = warp_sum_partials(sd.gpart + c * Pg, Pg);
-    if (lane == 0) {
-      const double sc = sd.p.sq64[sd.cand[c].x] / (double)N;
-      s_re[c] = sc * tot.x;
-      s_im[c] = sc * tot.y;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  const int k = ctl->k;
-  StepRec& rec = sd.rec[k];
-  int bs = -1, bj = -1;
-  double bv = -1.0, bre = 0.0, bim = 0.0;
-  for (int c = 0; c < n_cand; ++c) {
-    const int2 cj = sd.cand[c];
-    const double v = (s_re[c] * s_re[c] + s_im[c] * s_im[c]) * obj_rho64(sd, cj.x);
-    const int f = cj.x * N + cj.y, bf = bs * N + bj;
-    if (bs < 0 || v > bv || (v == bv && f < bf)) {
-      bs = cj.x; bj = cj.y; bv = v; bre = s_re[c]; bim = s_im[c];
-    }
-  }
-  if (bs < 0 || !(bv <= 1.79e308)) {
-    rec.s = -1;
-    rec.j = -1;
-    rec.flags |= 2;
-    ctl->err |= 2;
-    ctl->done = 1;
-    return;
-  }
-  const double rr = sd.p.radii[bs];
-  const double2 z = sd.p.tw64[bj];
-  rec.s = bs;
-  rec.j = bj;
-  rec.n_cand = n_cand;
-  rec.a_re = rr * z.x;
-  rec.a_im = rr * z.y;
-  rec.c_re = bre;
-  rec.c_im = bim;
-  rec.obj = bv;
+  guard_body(slots, ids, blockIdx.x, blockIdx.y, gridDim.x, cta_set(), sm);
 }
 
-// ---------------------------------------------------------- update kernel --
-
-// Reduced-remainder update of Sec. 2 at z_m, a = r_s w^j, c' = c sqrt(1-r_s^2):
-//   G_{k+1}(z_m) = (G_k(z_m) u - c') / (z_m - a),   u = 1 - conj(a) z_m = 1 - r_s w^d,
-// d = (m - j) mod N.  Because z_m - a = z_m conj(u), the division is
-// (...) conj(z_m) conj(K_s[d]) with the plan's K_s[d] = 1 / (1 - r_s w^d).
-// Also accumulates the energy and, on the FP32 path, writes G_{k+1}/N in FP32
-// for the next forward FFT.  INIT: energy and FP32 copy of the starting
-// remainder only; E_1 is that energy unless a resumed call supplies it.
 template <bool INIT>
 __global__ void __launch_bounds__(FP64_THREADS)
 k_update(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
-  __shared__ double red[2 * (FP64_THREADS / 32)];
-  __shared__ double s_cp[2];  // c' = c sqrt(1 - r^2), formed once per CTA
-  __shared__ int s_last;
+  __shared__ Fp64Smem sm;
   pdl_launch_dependents();
-  const SlotDev& sd = slots[ids[blockIdx.y]];
-  SlotCtl* ctl = sd.ctl;
   pdl_wait();
-  if (ld_done(ctl)) return;
-  const int N = sd.p.N;
-  const int Pu = chunks_of(N);
-  const int p = blockIdx.x;
-  const int m = p * FP64_CHUNK + threadIdx.x;
-  const int k = ctl->k;
-  if constexpr (!INIT) {
-    // (FP64 instructions cost the same per warp whatever the active lanes)
-    if (threadIdx.x == 0) {
-      const StepRec& rec = sd.rec[k];
-      const double na = sd.p.sq64[rec.s];
-      s_cp[0] = rec.c_re * na;
-      s_cp[1] = rec.c_im * na;
-    }
-    __syncthreads();
-  }
-  double e = 0.0;
-  if (m < N) {
-    double2 g = sd.G[m];
-    if constexpr (!INIT) {
-      const StepRec& rec = sd.rec[k];
-      const int s = rec.s;
-      g = update_point(sd, m, s, rec.j, sd.p.radii[s], s_cp[0], s_cp[1], g);
-      sd.G[m] = g;
-    }
-    e = fma(g.x, g.x, g.y * g.y);
-    // G / N in FP32, converted on the integer pipe: scaling by a power of two
-    // commutes with the rounding
-    if (sd.prec) {
-      const float inv_n = d2f_rn(sd.p.inv_n);
-      sd.g32[m] = make_float2(d2f_rn(g.x) * inv_n, d2f_rn(g.y) * inv_n);
-    }
-  }
-  const double es = sum_fp64_group1(e, red);
-  if (threadIdx.x == 0) sd.epart[p] = es;
-  if (!arrive_last(&ctl->cnt_update, gridDim.x, &s_last)) return;
-  if (threadIdx.x >= 32) return;
-  // energy partials: lane q adds q, q + 32, ... in order, then a fixed tree
-  double E = 0.0;
-  for (int q = threadIdx.x; q < Pu; q += 32) E += __ldcg(&sd.epart[q]);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) E += __shfl_xor_sync(0xffffffffu, E, off);
-  if (threadIdx.x != 0) return;
-  E /= (double)N;
-  if constexpr (INIT) {
-    ctl->Estart = E;
-    ctl->E1 = sd.E1_given > 0.0 ? sd.E1_given : E;
-  } else {
-    StepRec& rec = sd.rec[k];
-    const double delta = ctl->E1 > 0.0 ? E / ctl->E1 : 0.0;
-    rec.energy = E;
-    rec.delta = delta;
-    ctl->k = k + 1;
-    if (k + 1 >= sd.K_max || (sd.tol > 0.0 && delta <= sd.tol)) ctl->done = 1;
-  }
+  update_body<INIT>(slots, ids, blockIdx.x, blockIdx.y, gridDim.x, cta_set(), sm);
 }
 
-// --------------------------------------------------------- forward kernel --
-
-// c_l / N = (1/N) sum_m G(z_m) w^{-ml} (Eq. (term4)); FP32 path from the FP32
-// copy the update wrote, FP64 path from G itself.
 template <typename T, int LOGN>
 __global__ void __launch_bounds__(FftShape<T, LOGN>::TPF)
 k_forward(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
-  using S = FftShape<T, LOGN>;
-  constexpr int P = S::P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_launch_dependents();
-  const SlotDev& sd = slots[ids[blockIdx.x]];
   pdl_wait();
-  if (ld_done(sd.ctl)) return;
-  const int t = threadIdx.x;
-  V2<T>* buf = reinterpret_cast<V2<T>*>(smem_raw);
-  V2<T> v[P];
-  const V2<T>* tw;
-  V2<T>* c;
-  if constexpr (sizeof(T) == 4) {
-#pragma unroll
-    for (int e = 0; e < P; ++e) v[e] = sd.g32[fft_in_index<T, LOGN>(t, e)];
-    tw = sd.p.st32;
-    c = sd.c32;
-  } else {
-    const double inv_n = 1.0 / (double)S::N;
-#pragma unroll
-    for (int e = 0; e < P; ++e) {
-      const double2 g = sd.G[fft_in_index<T, LOGN>(t, e)];
-      v[e] = mk2<T>(g.x * inv_n, g.y * inv_n);
-    }
-    tw = sd.p.st64;
-    c = sd.c64;
-  }
-  fft_run<T, LOGN, -1>(v, t, buf, tw);
-#pragma unroll
-  for (int e = 0; e < P; ++e) c[fft_out_index<T, LOGN>(t, e)] = v[e];
+  forward_body<T, LOGN>(slots, ids, blockIdx.x, threadIdx.x, reinterpret_cast<V2<T>*>(smem_raw));
 }
 
 // -------------------------------------------- split sizes (long transforms) --
@@ -629,47 +317,10 @@ k_kernel_table(const double* __restrict__ radii, int N, double2* __restrict__ K)
 
 // ------------------------------------------------------ persistent kernel --
 
-constexpr long kBarrierLimit = 1L << 22;  // polls before a barrier gives up (about a second)
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Grid-wide barrier of a cooperative launch (all CTAs are co-resident).  The
-// arrival counter only grows during a launch (the host zeroes it before), so
-// barrier number e of the launch is passed once it reaches nblocks * (e + 1):
-// one reduction per CTA and a poll, no reset.  Thread 0 arrives with a
-// release reduction (after the CTA barrier, so it publishes the CTA's writes)
-// and polls with acquire loads, so the others' writes are visible once the
-// count is reached.  Bounded: a CTA that polls kBarrierLimit times flags a
-// timeout (error bit 2), and every CTA that sees the flag leaves.  False in
-// every thread when the kernel must stop.
+// The grid barrier of the persistent kernel: grid_barrier_at (afd_device.cuh)
+// on the slot's counter, with its error word.
 __device__ __forceinline__ bool grid_barrier(const SlotDev& sd, unsigned target, int* s_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    SlotCtl* ctl = sd.ctl;
-    unsigned* bar = sd.bar;
-    int ok = 1;
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
-    for (long it = 1; ld_acquire_gpu(bar) < target; ++it) {
-      if (it > kBarrierLimit) {
-        atomicOr(&ctl->err, 4);
-        ok = 0;
-        break;
-      }
-      if ((it & 255) == 0 && (*((volatile int*)&ctl->err) & 4)) {  // another CTA gave up
-        ok = 0;
-        break;
-      }
-      __nanosleep(20);
-    }
-    if (*((volatile int*)&ctl->err) & 4) ok = 0;
-    *s_ok = ok;
-  }
-  __syncthreads();
-  return *s_ok != 0;
+  return grid_barrier_at(sd.bar, &sd.ctl->err, target, s_ok);
 }
 
 // Self-test of the grid barrier's bound (failure detection without a fault):
@@ -1449,6 +1100,7 @@ cudaError_t configure_kernels() {
   if ((e = set_split_attrs<double, 13, 2>()) != cudaSuccess) return e;
   if ((e = set_split_attrs<double, 13, 3>()) != cudaSuccess) return e;
   if ((e = mixed_configure()) != cudaSuccess) return e;
+  if ((e = multi_configure()) != cudaSuccess) return e;
   if ((e = nu_configure()) != cudaSuccess) return e;
   return fft2_configure();
 }

@@ -415,6 +415,9 @@ struct SlotPool {
   std::vector<Group> groups;
   std::vector<Fft2Maps> maps;       // TMA descriptors of two-pass slots (N = 65536)
   bool persistent = false;          // single FP32 slot: one persistent launch per decomposition
+  bool multi = false;               // batch: all signals in one multi-signal persistent launch
+  unsigned* bar_dev = nullptr;      // grid-barrier counter and error word (BAR_BYTES, in the ctl area)
+  MultiArgs margs{};                // the multi-signal launch's arguments
 
   ~SlotPool() { release(); }
   void release() {
@@ -427,7 +430,8 @@ struct SlotPool {
   }
 
   // tables[i] is the plan of signal i.
-  afd_status build(const std::vector<const Tables*>& tables, int K, const afd_plan_opts& o) {
+  // allow_multi: a batch that may run as one multi-signal persistent launch.
+  afd_status build(const std::vector<const Tables*>& tables, int K, const afd_plan_opts& o, bool allow_multi = false) {
     release();
     n = (int)tables.size();
     K_max = K;
@@ -484,9 +488,9 @@ struct SlotPool {
       o_ep[i] = place(sizeof(double) * parts * (persistent ? (size_t)K_max : 1));
     }
     const size_t o_rec = place(sizeof(StepRec) * (size_t)n * K_max);
-    // control blocks, then (persistent plans) the grid-barrier counters; one
-    // memset per run clears both
-    ctl_bytes = align_up(sizeof(SlotCtl) * (size_t)n) + (persistent ? BAR_BYTES : 0);
+    // control blocks, then the grid-barrier counter and error word of the
+    // persistent kernels; one memset per run clears both
+    ctl_bytes = align_up(sizeof(SlotCtl) * (size_t)n) + BAR_BYTES;
     const size_t o_ctl = place(ctl_bytes);
     const size_t o_slots = place(sizeof(SlotDev) * (size_t)n);
     const size_t o_ids = place(sizeof(int) * (size_t)n);
@@ -525,9 +529,30 @@ struct SlotPool {
       d.epart = reinterpret_cast<double*>(b + o_ep[i]);
       d.rec = rec_dev + (size_t)i * K_max;
       d.ctl = ctl_dev + i;
-      d.bar = persistent ? reinterpret_cast<unsigned*>(b + o_ctl + align_up(sizeof(SlotCtl) * (size_t)n)) : nullptr;
+      d.bar = reinterpret_cast<unsigned*>(b + o_ctl + align_up(sizeof(SlotCtl) * (size_t)n));
     }
     CUDA_TRY(cudaMemcpy(ids_dev, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    bar_dev = reinterpret_cast<unsigned*>(b + o_ctl + align_up(sizeof(SlotCtl) * (size_t)n));
+    // The multi-signal persistent kernel takes a batch when every signal is an
+    // FP32-path power of two it holds on chip.
+    multi = allow_multi && n > 1 && prec == AFD_FP32_GUARDED && (int)groups.size() <= MULTI_MAX_CLASSES;
+    for (const auto& g : groups) multi = multi && !g.nu && g.logN > 0 && multi_size_ok(g.logN);
+    margs = MultiArgs{};
+    if (multi) {
+      margs.slots = slots_dev;
+      margs.ids = ids_dev;
+      margs.fresh_ids = ids_dev;
+      margs.bar = bar_dev;
+      margs.K = K;
+      margs.final_forward = 0;
+      margs.n_cls = margs.n_fresh = (int)groups.size();
+      for (size_t gi = 0; gi < groups.size(); ++gi) {
+        MultiClass& c = margs.cls[gi];
+        multi_class_shape(groups[gi].logN, groups[gi].Mmax, groups[gi].count, cap, &c);
+        c.first = groups[gi].first;
+        margs.fresh[gi] = c;
+      }
+    }
     maps.assign(n, Fft2Maps{});
     for (int i = 0; i < n; ++i) {
       if (!host[i].X) continue;
@@ -701,6 +726,7 @@ std::mutex g_tune_mu;
 std::map<std::array<int, 4>, std::pair<int, float>> g_tune_cache;
 
 afd_status autotune(SlotPool& pool, int device, cudaStream_t st) {
+  if (pool.multi) return AFD_OK;  // the multi-signal kernel has one grid variant per size
   for (auto& g : pool.groups) {
     if (g.nu || g.logN < 0 || g.logN > MAX_LOGN_RESIDENT || pool.prec != AFD_FP32_GUARDED) continue;
     int n_ok = 0;
@@ -827,6 +853,17 @@ struct Runner {
     AFD_TRY(prepare(pool.groups.size()));
     if (timer) timer->used = 0;
     CUDA_TRY(cudaMemsetAsync(pool.ctl_dev, 0, pool.ctl_bytes, main));
+    if (pool.multi) {
+      // every signal of the batch, all K steps: one cooperative launch
+      MultiArgs a = pool.margs;
+      a.K = K;
+      if (timer && timer->on) AFD_TRY(timer->mark(main, -1));
+      CUDA_TRY(launch_multi(a, main));
+      if (timer && timer->on) AFD_TRY(timer->mark(main, 4));
+      cnt.n[4] += 1;
+      cnt.launches += 1;
+      return AFD_OK;
+    }
     if (pool.groups.size() > 1) CUDA_TRY(cudaEventRecord(fork, main));
     for (size_t gi = 0; gi < pool.groups.size(); ++gi) {
       cudaStream_t st = gi == 0 ? main : side[gi - 1];
@@ -1202,6 +1239,7 @@ afd_status afd_decompose_from(afd_plan* plan, const double* G, double E1_in, int
                         host_or_null(delta_out), host_or_null(idx_out)));
   if (int* sd = host_or_null(steps_done)) *sd = steps;
   if (double* e1 = host_or_null(E1_out)) *e1 = pool.ctl_host[0].E1;
+  if (pool.ctl_host[0].err & 4) return set_error(AFD_ERR_TIMEOUT, "a bounded wait on the device ran out at step %d", steps);
   if (pool.ctl_host[0].err & 2) return set_error(AFD_ERR_NUMERIC, "non-finite objective at step %d", steps);
   return AFD_OK;
 }
@@ -1312,8 +1350,11 @@ afd_status afd_batch_create(afd_batch** out, int n_signals, const int* N, const 
     }
     per_signal[i] = it->second;
   }
-  AFD_TRY(b->pool.build(per_signal, K_max, o));
-  b->pool.persistent = false;  // batches use the per-kernel launches
+  // the single-signal persistent kernel is for plans; for a batch the
+  // persistent option picks the multi-signal kernel where it applies
+  afd_plan_opts ob = o;
+  ob.persistent = 0;
+  AFD_TRY(b->pool.build(per_signal, K_max, ob, o.persistent != 0));
   *out = b.release();
   return AFD_OK;
 }
@@ -1339,15 +1380,17 @@ afd_status afd_batch_run(afd_batch* b, const double* G_packed, double energy_tol
   AFD_TRY(b->runner.run(pool, pool.K_max, b->opts.use_graph != 0, b->cnt, nullptr));
   AFD_TRY(gather_device_outputs(pool, pool.K_max, a_out, coeff_out, delta_out, idx_out, steps_out, nullptr, st));
   AFD_TRY(fetch_results(pool, st));
-  bool numeric = false;
+  bool numeric = false, timeout = false;
   double *a_h = host_or_null(a_out), *c_h = host_or_null(coeff_out), *d_h = host_or_null(delta_out);
   int *ix_h = host_or_null(idx_out), *so_h = host_or_null(steps_out);
   for (int i = 0; i < pool.n; ++i) {
     const int steps = pool.ctl_host[i].k;
     numeric |= (pool.ctl_host[i].err & 2) != 0;
+    timeout |= (pool.ctl_host[i].err & 4) != 0;
     AFD_TRY(write_outputs(pool, i, pool.K_max, steps, a_h, c_h, d_h, ix_h));
     if (so_h) so_h[i] = steps;
   }
+  if (timeout) return set_error(AFD_ERR_TIMEOUT, "a bounded wait on the device ran out");
   if (numeric) return set_error(AFD_ERR_NUMERIC, "non-finite objective in at least one signal");
   return AFD_OK;
 }

@@ -207,6 +207,7 @@ struct afd_server {
   SlotDev* slots_dev = nullptr;
   SlotCtl* ctl_dev = nullptr;
   int* ids_dev = nullptr;
+  unsigned* bar_dev = nullptr;      // the multi-signal kernel's barrier counter and error word
   SlotDev* slotdev_host = nullptr;  // pinned
   SlotCtl* ctl_host = nullptr;      // pinned
   int* ids_host = nullptr;          // pinned
@@ -224,6 +225,7 @@ struct afd_server {
     if (slots_dev) cudaFree(slots_dev);
     if (ctl_dev) cudaFree(ctl_dev);
     if (ids_dev) cudaFree(ids_dev);
+    if (bar_dev) cudaFree(bar_dev);
     if (slotdev_host) cudaFreeHost(slotdev_host);
     if (ctl_host) cudaFreeHost(ctl_host);
     if (ids_host) cudaFreeHost(ids_host);
@@ -348,7 +350,36 @@ struct afd_server {
     CUDA_TRY(cudaMemcpyAsync(ids_dev, ids_host, sizeof(int) * n_ids, cudaMemcpyHostToDevice, stream));
     const int prec = opts.precision;
     long long launches = 0;
-    for (int l = 0; l <= MAX_LOGN; ++l) {
+    // FP32 path with every active size on chip: the whole tick (the fresh
+    // requests' initialisation, then one step of every request) is one
+    // multi-signal persistent launch
+    bool multi = prec == AFD_FP32_GUARDED && opts.persistent != 0;
+    for (int l = 0; l <= MAX_LOGN; ++l) multi = multi && (all[l].empty() || multi_size_ok(l));
+    if (multi) {
+      MultiArgs a{};
+      a.slots = slots_dev;
+      a.ids = ids_dev;
+      a.fresh_ids = ids_dev;
+      a.bar = bar_dev;
+      a.K = 1;
+      a.final_forward = 1;
+      for (int l = 0; l <= MAX_LOGN; ++l) {
+        if (!all[l].empty()) {
+          MultiClass& c = a.cls[a.n_cls++];
+          multi_class_shape(l, Mmax[l], (int)all[l].size(), opts.guard_cap, &c);
+          c.first = (int)off_all[l];
+        }
+        if (!fresh[l].empty()) {
+          MultiClass& f = a.fresh[a.n_fresh++];
+          multi_class_shape(l, Mmax[l], (int)fresh[l].size(), opts.guard_cap, &f);
+          f.first = (int)off_fresh[l];
+        }
+      }
+      CUDA_TRY(cudaMemsetAsync(bar_dev, 0, BAR_BYTES, stream));
+      CUDA_TRY(launch_multi(a, stream));
+      launches = 1;
+    }
+    for (int l = 0; !multi && l <= MAX_LOGN; ++l) {
       if (all[l].empty()) continue;
       const int nf = (int)fresh[l].size(), na = (int)all[l].size();
       if (nf) {
@@ -431,7 +462,8 @@ struct afd_server {
     std::vector<int> done;
     size_t need = 0;
     for (int i = 0; i < kMaxSlots; ++i) {
-      if (slots[i].used && ctl_host[i].done) {
+      // (a bounded wait that ran out also ends the request)
+      if (slots[i].used && (ctl_host[i].done || (ctl_host[i].err & 4))) {
         done.push_back(i);
         need += (size_t)ctl_host[i].k;
       }
@@ -464,7 +496,7 @@ struct afd_server {
         Request& r = *it->second;
         r.recs.assign(rec_stage + off, rec_stage + off + k);
         r.steps = k;
-        r.status = (ctl_host[i].err & 2) ? AFD_ERR_NUMERIC : AFD_OK;
+        r.status = (ctl_host[i].err & 4) ? AFD_ERR_TIMEOUT : ((ctl_host[i].err & 2) ? AFD_ERR_NUMERIC : AFD_OK);
         r.state = 2;
         r.t_done = now;
         st.completed += 1;
@@ -573,11 +605,13 @@ afd_status afd_serve_create(afd_server** out, size_t mem_budget_bytes, const afd
   CUDA_TRY(cudaMalloc(&s->slots_dev, sizeof(SlotDev) * kMaxSlots));
   CUDA_TRY(cudaMalloc(&s->ctl_dev, sizeof(SlotCtl) * kMaxSlots));
   CUDA_TRY(cudaMalloc(&s->ids_dev, sizeof(int) * 2 * kMaxSlots));
+  CUDA_TRY(cudaMalloc(&s->bar_dev, BAR_BYTES));
   CUDA_TRY(cudaMallocHost((void**)&s->slotdev_host, sizeof(SlotDev) * kMaxSlots));
   CUDA_TRY(cudaMallocHost((void**)&s->ctl_host, sizeof(SlotCtl) * kMaxSlots));
   CUDA_TRY(cudaMallocHost((void**)&s->ids_host, sizeof(int) * 2 * kMaxSlots));
   CUDA_TRY(cudaMemset(s->ctl_dev, 0, sizeof(SlotCtl) * kMaxSlots));
-  const size_t fixed = sizeof(SlotDev) * kMaxSlots + sizeof(SlotCtl) * kMaxSlots + sizeof(int) * 2 * kMaxSlots;
+  const size_t fixed =
+      sizeof(SlotDev) * kMaxSlots + sizeof(SlotCtl) * kMaxSlots + sizeof(int) * 2 * kMaxSlots + BAR_BYTES;
   if (!s->arena.charge(fixed)) return set_error(AFD_ERR_BUDGET, "budget below the fixed slot tables");
   s->fixed_bytes = fixed;
   afd_server* raw = s.get();

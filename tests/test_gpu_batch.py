@@ -104,6 +104,34 @@ def test_large_class_equals_single_runs():
             assert np.array_equal(res[key][i], one[key]), (i, key)
 
 
+@pytest.mark.parametrize("tol", [0.0, 3e-3])
+def test_multi_signal_launch_equals_stream_path(tol):
+    # every power of two the multi-signal persistent kernel takes (8 .. 16384),
+    # several signals per N-class and a lone one, with and without the stop
+    # rule: one cooperative launch per batch gives bitwise the per-kernel,
+    # per-class sequence (persistent=False) and the single-signal runs
+    Ns = [8, 16, 64, 256, 256, 512, 1024, 2048, 2048, 2048, 4096, 8192, 8192, 16384]
+    sigs = [W.random_signal(N, 90 + i) + W.szego_sum(N, np.array([0.8 * np.exp(0.7j * (i + 1))]), np.array([1.0]))
+            for i, N in enumerate(Ns)]
+    radii = W.radii_linear(21)
+    K = 7
+    multi = afd.afd_batch_create([g.size for g in sigs], radii, K)
+    r1 = afd.afd_batch_run(multi, np.concatenate(sigs), tol)
+    launches = afd.afd_batch_counters(multi)["kernel_launches"]
+    multi.close()
+    assert launches == 1  # the whole batch: one launch
+    r2 = afd.afd_decompose_batch(sigs, radii, K, energy_tol=tol, persistent=False)
+    for i, G in enumerate(sigs):
+        assert r1["steps"][i] == r2["steps"][i]
+        for key in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(r1[key][i], r2[key][i]), (Ns[i], key)
+        plan = afd.afd_plan_create(G.size, radii)
+        one = afd.afd_decompose(plan, G, K, tol)
+        plan.close()
+        for key in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(r1[key][i], one[key]), (Ns[i], key)
+
+
 def test_batch_reuse_and_counters():
     sigs = small_batch(n=5, Ns=(1024, 2048))
     radii = W.radii_linear(16)
@@ -143,26 +171,28 @@ def test_workload3_full_batch_parity():
 def test_grid_variants_are_bitwise_equivalent():
     # the autotuner's candidates (points per thread, CTA width) compute the
     # same values
+    # (on the per-class path, where the variants run)
     sigs = small_batch(n=8, Ns=(256, 1024, 4096, 8192), seed=4)
     radii = W.radii_linear(24)
-    ref = afd.afd_decompose_batch(sigs, radii, 5, autotune=False)
+    ref = afd.afd_decompose_batch(sigs, radii, 5, autotune=False, persistent=False)
     for v in (0, 1, 2):
-        r = afd.afd_decompose_batch(sigs, radii, 5, grid_variant=v)
+        r = afd.afd_decompose_batch(sigs, radii, 5, grid_variant=v, persistent=False)
         for i in range(len(sigs)):
             for key in ("a", "coeff", "delta", "idx"):
                 assert np.array_equal(r[key][i], ref[key][i]), (v, i, key)
 
 
 def test_autotuner_reports_choices_and_keeps_results():
+    # the per-class path (persistent=False) is the one with grid-kernel variants
     sigs = small_batch(n=16, Ns=(1024, 2048, 4096, 8192), seed=6)
     radii = W.radii_linear(50)
-    b = afd.afd_batch_create([g.size for g in sigs], radii, 6)
+    b = afd.afd_batch_create([g.size for g in sigs], radii, 6, persistent=False)
     r = afd.afd_batch_run(b, np.concatenate(sigs))
     tun = afd.afd_batch_tuning(b)
     b.close()
     assert [t["N"] for t in tun] == [1024, 2048, 4096, 8192]
     assert all(t["variant"] in (0, 1, 2) and t["us"] > 0 for t in tun)
-    ref = afd.afd_decompose_batch(sigs, radii, 6, autotune=False)
+    ref = afd.afd_decompose_batch(sigs, radii, 6, autotune=False, persistent=False)
     for i in range(len(sigs)):
         for key in ("a", "coeff", "delta", "idx"):
             assert np.array_equal(r[key][i], ref[key][i]), (i, key)

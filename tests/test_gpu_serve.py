@@ -40,6 +40,7 @@ def test_mix_equals_alone_small_stream():
     srv.close()
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
     assert stats["ticks"] < sum(o["steps"] for o in outs)  # requests shared ticks
+    assert stats["kernel_launches"] == stats["ticks"]  # one multi-signal launch per tick
     for (_, s), o in zip(reqs, outs):
         one = alone(s.G, s.radii, s.K, s.tol)
         assert o["steps"] == one["steps"]
@@ -83,6 +84,25 @@ def test_poisson_arrivals_parity_and_latency():
         assert out["selection_checked"] == o["steps"]
     for (_, s), o in zip(reqs, outs):
         assert o["delta"][-1] <= s.tol or o["steps"] == s.K
+
+
+def test_per_class_launch_server_matches_multi_launch_server():
+    # persistent=False serves each N-class with its own step kernels: the same
+    # results bitwise as the one-launch ticks
+    reqs = W.serving_requests(rate=2000.0, duration=0.05, Ns=(512, 2048, 16384), M=24, K=16, tol=1e-4,
+                              seed_item=11)
+    outs = []
+    for persistent in (True, False):
+        srv = afd.afd_serve_create(1 << 30, persistent=persistent)
+        ids = [afd.afd_serve_submit(srv, s.G, s.radii, s.K, s.tol) for _, s in reqs]
+        outs.append([afd.afd_serve_wait(srv, i, 120.0) for i in ids])
+        st = afd.afd_serve_get_stats(srv)
+        srv.close()
+        assert (st["kernel_launches"] == st["ticks"]) == persistent
+    for a, b in zip(*outs):
+        assert a["steps"] == b["steps"]
+        for k in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(a[k], b[k]), k
 
 
 def test_fp64_server_matches_plan():
