@@ -41,7 +41,7 @@ UNIT = "grid_evals/s"
 N_SIG, M_RAD, K_STEPS = 4096, 200, 50
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
-STEPREC_BYTES, SLOTCTL_BYTES, SLOTDEV_BYTES = 80, 64, 392  # StepRec, SlotCtl, SlotDev
+STEPREC_BYTES, SLOTCTL_BYTES, SLOTDEV_BYTES = 80, 64, 400  # StepRec, SlotCtl, SlotDev
 
 
 def kernel_sources_hash() -> str:

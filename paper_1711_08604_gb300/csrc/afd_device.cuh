@@ -266,12 +266,19 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // entries per radius.  Every thread of the CTA must call it; every thread gets
 // n (candidates kept) and count (points at or above thr).  Deterministic: the
 // same inputs give the same list in any CTA.
+// The candidate list's shared-memory scratch (8 KB): the caller's own, or a
+// buffer of its that is free by then (a grid kernel's transform buffers).
+struct SelectScratch {
+  static constexpr int LIST = 1024;
+  float v[LIST];
+  int f[LIST];
+};
 template <int THREADS>
 __device__ void select_core(const Top2F* top, int M, int N, int sub, float thr, int cap, int2* out, int* n_out,
-                            int* count_out) {
-  constexpr int LIST = 1024;
-  __shared__ float s_v[LIST];
-  __shared__ int s_f[LIST];
+                            int* count_out, SelectScratch& scr) {
+  constexpr int LIST = SelectScratch::LIST;
+  float* s_v = scr.v;
+  int* s_f = scr.f;
   __shared__ int s_count;
   __shared__ float sv[32];
   __shared__ int sf[32];
@@ -338,7 +345,7 @@ __device__ void select_core(const Top2F* top, int M, int N, int sub, float thr, 
 // one (known from the atomicMax each CTA made) becomes a candidate for the
 // FP64 guard, at most cap of them, best first.
 template <int THREADS>
-__device__ void select_candidates_f32(const SlotDev& sd, int k, int sub = 1) {
+__device__ void select_candidates_f32(const SlotDev& sd, int k, int sub, SelectScratch& scr) {
   SlotCtl* ctl = sd.ctl;
   StepRec& rec = sd.rec[k];
   const float vmax = __uint_as_float(__ldcg(&ctl->vmax_bits));
@@ -358,7 +365,7 @@ __device__ void select_candidates_f32(const SlotDev& sd, int k, int sub = 1) {
   const float thr = vmax - vmax * (float)sd.tau;
   int n, count;
   select_core<THREADS>(reinterpret_cast<const Top2F*>(sd.top2), sd.p.M, sd.p.N, sub, thr, sd.cap, sd.cand, &n,
-                       &count);
+                       &count, scr);
   if (threadIdx.x == 0) {
     ctl->n_cand = n;
     if (count > sd.cap) rec.flags = 1;

@@ -369,7 +369,7 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
     Best2F bb;
     bb.init();
 #pragma unroll
-    for (int e = 0; e < 16; ++e) bb.push_ascending(v[e].x * v[e].x + v[e].y * v[e].y, j2 + 256 * (t + 16 * e));
+    for (int e = 0; e < 16; ++e) bb.push_ascending(norm2<float>(v[e]), j2 + 256 * (t + 16 * e));
     // the warp's two transforms, then the CTA's eight warps
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) bb.merge(bb.shfl(off));
@@ -418,7 +418,8 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
     return;
   }
   if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
-  select_candidates_f32<kThreads>(sd, sd.ctl->k, 16);
+  __shared__ SelectScratch scr;
+  select_candidates_f32<kThreads>(sd, sd.ctl->k, 16, scr);
 }
 
 // Self-test of the mbarrier wait's bound (failure detection without a

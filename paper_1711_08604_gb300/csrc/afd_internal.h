@@ -36,9 +36,10 @@ inline __host__ __device__ int chunks_of(int N) { return (N + FP64_CHUNK - 1) / 
 // (x mod N) for x in (-N, 2N); N need not be a power of two
 inline __host__ __device__ int wrap_mod(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
 constexpr int MIXED_MAX_PASSES = 24;
-// Grid-barrier counter of the persistent kernels and their error word: a
-// 128-byte line each, zeroed before a launch.
-constexpr int BAR_BYTES = 256;
+// Grid-barrier counter of the persistent kernels, their error word and the
+// multi-signal kernel's work-item ticket: a 128-byte line each, zeroed before
+// a launch.
+constexpr int BAR_BYTES = 384;
 // Largest shared-memory footprint (two ping-pong buffers of N points) of the
 // mixed-radix kernels: N <= 12800 in FP32, N <= 6400 in FP64.
 constexpr int MIXED_MAX_SMEM = 204800;
@@ -69,6 +70,8 @@ struct PlanDev {
   const double* radii;      // [M] ascending radii r_s in [0, 1)
   const double2* tw64;      // [N] exp(+2 pi i k / N) in FP64 (also the sample points z_m)
   const float2* st32;       // [FftSchedule::tw_size] FFT stage twiddles, FP32
+  const float4* st32p;      // [tw_size / 2] the same, pairs of entries (2j, 2j+1) as
+                            // (re_2j, re_2j+1, im_2j, im_2j+1) for the paired FP32 transforms
   const double2* st64;      // the same in FP64
   const float* rlo32;       // [M * B]        r_s^q,        q = 0..B-1
   const float* rhi32;       // [M * (N / B)]  r_s^(B h),    h = 0..N/B-1
@@ -166,7 +169,7 @@ __device__ __forceinline__ double obj_rho64(const SlotDev& sd, int s) { return s
 // Host-visible layout sizes (the bench reports per-step transfer bytes from them).
 static_assert(sizeof(StepRec) == 80, "StepRec layout");
 static_assert(sizeof(SlotCtl) == 64, "SlotCtl layout");
-static_assert(sizeof(SlotDev) == 392, "SlotDev layout");
+static_assert(sizeof(SlotDev) == 400, "SlotDev layout");
 
 // The multi-signal persistent kernel (afd_multi.cu): one N-class of signals
 // (ids[first .. first + count)) and its work split.
@@ -182,7 +185,7 @@ struct MultiArgs {
   const SlotDev* slots;
   const int* ids;        // the signals of the steps, grouped by class
   const int* fresh_ids;  // the signals to initialise first, grouped by class
-  unsigned* bar;         // BAR_BYTES, zeroed before the launch: barrier counter, error word
+  unsigned* bar;         // BAR_BYTES, zeroed before the launch: barrier counter, error word, ticket
   int K;                 // greedy steps
   int final_forward;     // 1: transform the remainder after the last step too (serving)
   int n_cls, n_fresh;

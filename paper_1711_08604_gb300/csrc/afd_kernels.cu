@@ -37,7 +37,7 @@ namespace afd {
 // One CTA per work item: the bodies of afd_step.cuh.
 
 template <typename T, int LOGN, int PP = 0, int CT = 256>
-__global__ void __launch_bounds__(GridCfg<T, LOGN, PP, CT>::THREADS)
+__global__ void __launch_bounds__(GridCfg<T, LOGN, PP, CT>::THREADS, GridCfg<T, LOGN, PP, CT>::MIN_CTAS)
 k_grid(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
   grid_body<T, LOGN, PP, CT>(slots, ids, blockIdx.x, blockIdx.y, gridDim.x);
 }
@@ -158,7 +158,7 @@ k_grid_split(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
 #pragma unroll
     for (int u = 0; u < P; ++u) {
       const V2<T> x = v[fft_out_slot<T, LOGS>(u)];
-      bb.push_ascending(x.x * x.x + x.y * x.y, SPL * (t + TPF * u) + h);
+      bb.push_ascending(norm2<T>(x), SPL * (t + TPF * u) + h);
     }
     group_reduce<TPF>(bb, red);
     if (t == 0 && active) {
@@ -173,7 +173,8 @@ k_grid_split(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
       __threadfence();  // read by the signal's last CTA
     }
     if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
-    select_candidates_f32<TPF>(sd, sd.ctl->k, SPL);
+    __shared__ SelectScratch scr;
+    select_candidates_f32<TPF>(sd, sd.ctl->k, SPL, scr);
   } else {
     __shared__ Best1D red[32];
     Best1D bb;
@@ -181,7 +182,7 @@ k_grid_split(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
 #pragma unroll
     for (int u = 0; u < P; ++u) {
       const V2<T> x = v[fft_out_slot<T, LOGS>(u)];
-      bb.push_ascending(x.x * x.x + x.y * x.y, SPL * (t + TPF * u) + h, x);
+      bb.push_ascending(norm2<T>(x), SPL * (t + TPF * u) + h, x);
     }
     group_reduce<TPF>(bb, red);
     if (t == 0 && active) {
@@ -372,6 +373,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
   __shared__ float2 s_tw[TWS];  // stage twiddles for the kernel's lifetime
   __shared__ Best2F red2[32];
   __shared__ int2 s_cand[MAX_CAP];
+  __shared__ SelectScratch s_scr;
   __shared__ double s_re[MAX_CAP], s_im[MAX_CAP], s_v[MAX_CAP];
   __shared__ double s_rad[MAX_CAP], s_sq[MAX_CAP];  // radius and sqrt(1 - r^2) of each candidate
   __shared__ double s_scn[MAX_CAP], s_rho[MAX_CAP];  // sqrt(1 - r^2) / N and the objective's factor
@@ -695,7 +697,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
 #pragma unroll
       for (int u = 0; u < P; ++u) {
         const float2 x = v[fft_out_slot<float, LOGN>(u)];
-        b.push_ascending(x.x * x.x + x.y * x.y, t + TPF * u);
+        b.push_ascending(norm2<float>(x), t + TPF * u);
       }
       // (red2 was last read before this tile's spectrum barrier)
       group_reduce<TPF, Best2F, true>(b, red2);
@@ -735,7 +737,7 @@ k_persistent(const SlotDev* __restrict__ slots) {
       if (threadIdx.x == 0) s_cand[0] = make_int2(0, 0);
       __syncthreads();
     } else {
-      select_core<THREADS>(top, M, N, 1, vmax - vmax * tau32, sd.cap, s_cand, &n, &count);
+      select_core<THREADS>(top, M, N, 1, vmax - vmax * tau32, sd.cap, s_cand, &n, &count, s_scr);
     }
     if (cta0 && threadIdx.x == 0) {
       ctl->vmax2[(k + 1) & 1] = 0u;  // the next step's accumulator

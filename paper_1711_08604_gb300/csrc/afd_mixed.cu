@@ -258,7 +258,7 @@ k_grid_mixed(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
         const float2 x = __ldcg(&c[b + q * NR]);
         return make_float2(x.x * rp, x.y * rp);
       };
-      auto last = [&](int i, float2 x) { best.insert(x.x * x.x + x.y * x.y, i); };
+      auto last = [&](int i, float2 x) { best.insert(norm2<float>(x), i); };
       mx_run_staged<float, +1>(sd.p, buf, first, last);
     }
     group_reduce<MX_THREADS>(best, red);
@@ -273,7 +273,8 @@ k_grid_mixed(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
       if (o.v1 >= 0.0f && o.v1 <= 3.402823466e38f) atomicMax(&sd.ctl->vmax_bits, __float_as_uint(o.v1));
     }
     if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
-    select_candidates_f32<MX_THREADS>(sd, sd.ctl->k);
+    __shared__ SelectScratch scr;
+    select_candidates_f32<MX_THREADS>(sd, sd.ctl->k, 1, scr);
   } else {
     __shared__ Best1D red[32];
     Best1D best;
@@ -288,7 +289,7 @@ k_grid_mixed(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
         const double2 x = __ldcg(&c[b + q * NR]);
         return make_double2(x.x * rp, x.y * rp);
       };
-      auto last = [&](int i, double2 x) { best.insert(x.x * x.x + x.y * x.y, i, x); };
+      auto last = [&](int i, double2 x) { best.insert(norm2<double>(x), i, x); };
       mx_run_staged<double, +1>(sd.p, buf, first, last);
     }
     group_reduce<MX_THREADS>(best, red);

@@ -85,13 +85,45 @@ __device__ __forceinline__ void forward_groups_l(const SlotDev* __restrict__ slo
   const SlotDev* sd = sig < count ? &slots[ids[sig]] : nullptr;
   const bool active = g < GF && sd && !ld_done(sd->ctl);
   float2* buf = reinterpret_cast<float2*>(smem_raw) + (g < GF ? g : 0) * S::SMEM;
-  float2 v[P];
+  if constexpr (PP == 32) {
+    // the paired transforms: input pairs (j, j + 1) of the FP32 copy, output
+    // pairs of the spectrum, the values of fft_run lane for lane
+    constexpr int R0 = FftSchedule::radix(L, 0), NPR0 = P / (2 * R0);
+    float2 X[P / 2], Y[P / 2];
+    if constexpr (R0 == 2) {
+      // pass 0 in registers (fftp_r2_pass0)
+      float2 a[32];
 #pragma unroll
-  for (int e = 0; e < P; ++e) v[e] = active ? sd->g32[fft_in_index<float, L, PP>(t, e)] : make_float2(0.f, 0.f);
-  if (g < GF) fft_run<float, L, -1, 0, false, PP, (GF > 1 && TPF > 32)>(v, t, buf, s0.p.st32);
-  if (active) {
+      for (int q = 0; q < 32; ++q) a[q] = active ? sd->g32[fftp_r2_in_index<L>(t, q)] : make_float2(0.f, 0.f);
+      fftp_r2_pass0(a, X, Y);
+    } else {
 #pragma unroll
-    for (int e = 0; e < P; ++e) sd->c32[fft_out_index<float, L, PP>(t, e)] = v[e];
+      for (int i = 0; i < NPR0; ++i) {
+#pragma unroll
+        for (int q = 0; q < R0; ++q) {
+          const float4 x = active ? reinterpret_cast<const float4*>(sd->g32)[fftp_in_index<L>(t, i, 0, q) >> 1]
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+          X[i * R0 + q] = make_float2(x.x, x.z);
+          Y[i * R0 + q] = make_float2(x.y, x.w);
+        }
+      }
+    }
+    if (g < GF) fftp_run<L, -1, (R0 == 2 ? 1 : 0), (GF > 1 && TPF > 32)>(X, Y, t, reinterpret_cast<float*>(buf), s0.p.st32p);
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        reinterpret_cast<float4*>(sd->c32)[fftp_out_index<L>(t, 0, q) >> 1] =
+            make_float4(X[q].x, Y[q].x, X[q].y, Y[q].y);
+    }
+  } else {
+    float2 v[P];
+#pragma unroll
+    for (int e = 0; e < P; ++e) v[e] = active ? sd->g32[fft_in_index<float, L, PP>(t, e)] : make_float2(0.f, 0.f);
+    if (g < GF) fft_run<float, L, -1, 0, false, PP, (GF > 1 && TPF > 32)>(v, t, buf, s0.p.st32);
+    if (active) {
+#pragma unroll
+      for (int e = 0; e < P; ++e) sd->c32[fft_out_index<float, L, PP>(t, e)] = v[e];
+    }
   }
 }
 
@@ -135,10 +167,31 @@ template <int MT>
 __global__ void __launch_bounds__(MT, MT == 256 ? 2 : 1) k_multi(const __grid_constant__ MultiArgs a) {
   constexpr int NW = MT / 32;
   __shared__ Fp64WarpSmem smw[NW];
-  __shared__ int s_ok;
+  __shared__ int s_ok, s_item;
   const int warp = threadIdx.x >> 5;
   int* err = reinterpret_cast<int*>(a.bar + 32);  // its own 128-byte line after the counter
+  unsigned* ticket = a.bar + 64;                  // and the work-item ticket on the next
   unsigned epoch = 0;
+  // Work items go out by ticket, not by a fixed stride: SMs run the same item
+  // at different speeds (a 1.4x spread measured across one launch), so a
+  // fixed share would leave the phase waiting for the slowest.  Every CTA
+  // takes one ticket past a phase's last item, so each phase's tickets start
+  // at base (the same in every CTA) and the next at base + items + gridDim.x.
+  unsigned base = 0;
+  auto each_item = [&](int items, auto&& body) {
+    unsigned next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(ticket, 1u);
+    for (;;) {
+      if (threadIdx.x == 0) s_item = (int)(next - base);
+      __syncthreads();
+      const int item = s_item;
+      if (item >= items) break;
+      if (threadIdx.x == 0) next = atomicAdd(ticket, 1u);  // in flight while the item runs
+      body(item);
+      __syncthreads();  // s_item and the exchange buffers are reused
+    }
+    base += (unsigned)items + gridDim.x;
+  };
   // a phase's end: the grid barrier; on a timeout every signal is flagged and
   // the kernel leaves
   auto barrier = [&]() -> bool {
@@ -151,32 +204,31 @@ __global__ void __launch_bounds__(MT, MT == 256 ? 2 : 1) k_multi(const __grid_co
   auto fp64_phase = [&](int kind, const MultiClass* cls, int n, const int* ids) {
     auto per = [&](const MultiClass& c) { return kind == 0 ? c.gpar * chunks_c(c) : chunks_c(c); };
     const int total = total_items(cls, n, per);
-    for (int item = (int)blockIdx.x * NW + warp; item < total; item += (int)gridDim.x * NW) {
+    each_item((total + NW - 1) / NW, [&](int cta_item) {
+      const int item = cta_item * NW + warp;
       int local = 0;
-      const int c = find_class(cls, n, item, per, &local);
-      if (c < 0) break;
+      const int c = item < total ? find_class(cls, n, item, per, &local) : -1;
+      if (c < 0) return;
       const int pc = per(cls[c]);
       const int* cid = ids + cls[c].first;
       if (kind == 0) guard_warp(a.slots, cid, local % pc, local / pc, pc, smw[warp]);
       else if (kind == 1) update_warp<false>(a.slots, cid, local % pc, local / pc, pc);
       else update_warp<true>(a.slots, cid, local % pc, local / pc, pc);
-    }
+    });
   };
   // forward transforms, a CTA's groups taking consecutive signals of a class
   auto forward_phase = [&](const MultiClass* cls, int n, const int* ids) {
     int total = 0;
     for (int c = 0; c < n; ++c) total += (cls[c].count + cls[c].fgroups - 1) / cls[c].fgroups;
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
-      int base = 0, c = 0;
+    each_item(total, [&](int item) {
+      int first = 0, c = 0;
       for (; c < n; ++c) {
         const int span = (cls[c].count + cls[c].fgroups - 1) / cls[c].fgroups;
-        if (item < base + span) break;
-        base += span;
+        if (item < first + span) break;
+        first += span;
       }
-      if (c >= n) break;
-      forward_groups<MT>(a, cls[c], ids, (item - base) * cls[c].fgroups);
-      __syncthreads();  // the next item reuses the exchange buffers
-    }
+      if (c < n) forward_groups<MT>(a, cls[c], ids, (item - first) * cls[c].fgroups);
+    });
   };
   if (a.n_fresh > 0) {
     fp64_phase(2, a.fresh, a.n_fresh, a.fresh_ids);
@@ -187,14 +239,11 @@ __global__ void __launch_bounds__(MT, MT == 256 ? 2 : 1) k_multi(const __grid_co
   for (int k = 0; k < a.K; ++k) {
     {
       auto per = [](const MultiClass& c) { return c.tiles; };
-      const int total = total_items(a.cls, a.n_cls, per);
-      for (int item = blockIdx.x; item < total; item += gridDim.x) {
+      each_item(total_items(a.cls, a.n_cls, per), [&](int item) {
         int local = 0;
         const int c = find_class(a.cls, a.n_cls, item, per, &local);
-        if (c < 0) break;
-        grid_item<MT>(a, a.cls[c], local / a.cls[c].tiles, local % a.cls[c].tiles);
-        __syncthreads();  // the next item reuses the exchange buffers
-      }
+        if (c >= 0) grid_item<MT>(a, a.cls[c], local / a.cls[c].tiles, local % a.cls[c].tiles);
+      });
     }
     if (!barrier()) return;
     fp64_phase(0, a.cls, a.n_cls, a.ids);

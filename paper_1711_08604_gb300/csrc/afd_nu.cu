@@ -190,7 +190,7 @@ k_grid_nu(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
 #pragma unroll
   for (int u = 0; u < P; ++u) {
     const float2 x = v[fft_out_slot<float, LOGN>(u)];
-    b.push_ascending(x.x * x.x + x.y * x.y, t + TPF * u);
+    b.push_ascending(norm2<float>(x), t + TPF * u);
   }
   group_reduce<TPF>(b, red);
   if (t == 0 && active) {
@@ -205,7 +205,8 @@ k_grid_nu(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
     __threadfence();  // read by the last CTA
   }
   if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
-  select_candidates_f32<THREADS>(sd, sd.ctl->k);
+  __shared__ SelectScratch scr;
+  select_candidates_f32<THREADS>(sd, sd.ctl->k, 1, scr);
 }
 
 // w_m G(z_m) / (1 - a conj(z_m)) in FP64.

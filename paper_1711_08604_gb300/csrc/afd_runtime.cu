@@ -248,7 +248,7 @@ size_t Tables::bytes_for(int N, int M, int prec) {
   const int B = sh.B, H = sh.H;
   const size_t tws = (size_t)sh.tws;
   size_t off = 0;
-  for (size_t b : {sizeof(double) * M, 16 * (size_t)N, 16 * tws, 8 * tws, 8 * (size_t)M * B, 8 * (size_t)M * H,
+  for (size_t b : {sizeof(double) * M, 16 * (size_t)N, 16 * tws, 8 * tws, 8 * tws, 8 * (size_t)M * B, 8 * (size_t)M * H,
                    4 * (size_t)M * B, 4 * (size_t)M * H, 4 * (size_t)M, 8 * (size_t)M, 8 * (size_t)M,
                    8 * (size_t)M, 4 * (size_t)M, 16 * (size_t)M * N, sh.tw32n() ? 8 * ((size_t)N + (sh.two_pass ? 4096 : 0)) : 0})
     off = align_up(off + b);
@@ -323,6 +323,7 @@ afd_status Tables::build(int N_, const double* r, int M_, int prec_) {
     auto place = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
     const size_t o_r = place(sizeof(double) * M), o_tw64 = place(16 * (size_t)N),
                  o_st64 = place(8 * st64.size()), o_st32 = place(4 * st32.size()),
+                 o_st32p = place(4 * st32.size()),
                  o_rlo64 = place(8 * rlo64.size()), o_rhi64 = place(8 * rhi64.size()),
                  o_rlo32 = place(4 * rlo32.size()), o_rhi32 = place(4 * rhi32.size()),
                  o_wsq = place(4 * (size_t)M), o_w64 = place(8 * (size_t)M), o_sq = place(8 * (size_t)M),
@@ -335,6 +336,18 @@ afd_status Tables::build(int N_, const double* r, int M_, int prec_) {
     CUDA_TRY(cudaMemcpy(b + o_tw64, tw64.data(), 16 * (size_t)N, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b + o_st64, st64.data(), 8 * st64.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b + o_st32, st32.data(), 4 * st32.size(), cudaMemcpyHostToDevice));
+    {
+      // entries 2j and 2j + 1 side by side per component (tw_size is even:
+      // every pass after the first has an even ns)
+      std::vector<float> st32p(st32.size(), 0.f);
+      for (size_t j = 0; j + 1 < (size_t)TWS; j += 2) {
+        st32p[2 * j] = st32[2 * j];
+        st32p[2 * j + 1] = st32[2 * j + 2];
+        st32p[2 * j + 2] = st32[2 * j + 1];
+        st32p[2 * j + 3] = st32[2 * j + 3];
+      }
+      CUDA_TRY(cudaMemcpy(b + o_st32p, st32p.data(), 4 * st32p.size(), cudaMemcpyHostToDevice));
+    }
     CUDA_TRY(cudaMemcpy(b + o_rlo64, rlo64.data(), 8 * rlo64.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b + o_rhi64, rhi64.data(), 8 * rhi64.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b + o_rlo32, rlo32.data(), 4 * rlo32.size(), cudaMemcpyHostToDevice));
@@ -353,6 +366,7 @@ afd_status Tables::build(int N_, const double* r, int M_, int prec_) {
     dev.tw64 = reinterpret_cast<const double2*>(b + o_tw64);
     dev.st64 = reinterpret_cast<const double2*>(b + o_st64);
     dev.st32 = reinterpret_cast<const float2*>(b + o_st32);
+    dev.st32p = reinterpret_cast<const float4*>(b + o_st32p);
     dev.rlo64 = reinterpret_cast<const double*>(b + o_rlo64);
     dev.rhi64 = reinterpret_cast<const double*>(b + o_rhi64);
     dev.rlo32 = reinterpret_cast<const float*>(b + o_rlo32);

@@ -33,14 +33,143 @@ struct GridCfg {
   static constexpr int CTA = sizeof(T) == 4 ? CT : 32;
   static constexpr int FPC = S::TPF >= CTA ? 1 : CTA / S::TPF;  // transforms per CTA
   static constexpr int THREADS = S::TPF * FPC;
+  // CTAs per SM the register budget is cut for: the paired FP32 transforms
+  // (32 points per thread) fit three 256-thread CTAs (registers and shared
+  // memory) up to N = 8192; the FP32 variants of 16 points per thread 64
+  // registers per thread; 0: no bound
+  static constexpr int MIN_CTAS = sizeof(T) != 4 ? 0
+                                  : (PP == 32 && THREADS == 256 && LOGN >= 5 && LOGN <= 13) ? 3
+                                  : (S::P <= 16 && THREADS >= 256 ? 65536 / (64 * THREADS) : 0);
 };
+
+// The FP32 grid work item with 32 points per thread on the paired
+// transforms (fftp_run): the arithmetic of grid_body_s lane for lane, so the
+// same objective values, best pairs and selection.
+template <int LOGN, int CT>
+__device__ __forceinline__ void grid_body_p(const SlotDev* __restrict__ slots, const int* __restrict__ ids, int bx,
+                                            int by, int gx) {
+  using S = FftPShape<LOGN>;
+  using C = GridCfg<float, LOGN, 32, CT>;
+  constexpr int TPF = S::TPF, FPC = C::FPC, THREADS = C::THREADS;
+  constexpr int R0 = FftSchedule::radix(LOGN, 0), B = FftSchedule::pow_b(LOGN), NPR0 = S::P / (2 * R0);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_last;
+  __shared__ Best2F red[32];
+  pdl_launch_dependents();
+  const SlotDev& sd = slots[ids[by]];
+
+  const int g = threadIdx.x / TPF, t = threadIdx.x % TPF;
+  const int s = bx * FPC + g;
+  const bool active = s < sd.p.M;
+  float* buf = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + g * FftShape<float, LOGN, 32>::SMEM);
+
+  float2 X[S::P / 2], Y[S::P / 2];
+  constexpr int PASS1 = R0 == 2 ? 1 : 0;  // the first pass that runs in fftp_run
+  if constexpr (R0 == 2) {
+    // Pass 0 in registers (fftp_r2_pass0, formed pair by pair): inputs
+    // l = t + q' N/32, r_s^l = lo[l mod B] hi[l / B]
+    if (active) {
+      const float* lo = sd.p.rlo32 + (size_t)s * B;
+      const float* hi = sd.p.rhi32 + (size_t)s * R0;
+      const float h0 = __ldg(&hi[0]), h1 = __ldg(&hi[1]);
+      float lb[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) lb[q] = __ldg(&lo[fftp_r2_in_index<LOGN>(t, q)]);
+      pdl_wait();
+      if (ld_done(sd.ctl)) return;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float rp0 = lb[q] * h0, rp1 = lb[q] * h1;
+        const float2 x0 = sd.c32[fftp_r2_in_index<LOGN>(t, q)];
+        const float2 x1 = sd.c32[fftp_r2_in_index<LOGN>(t, q + 16)];
+        float2 a[32];
+        a[q] = make_float2(x0.x * rp0, x0.y * rp0);
+        a[q + 16] = make_float2(x1.x * rp1, x1.y * rp1);
+        X[q] = make_float2(a[q].x + a[q + 16].x, a[q].x - a[q + 16].x);
+        Y[q] = make_float2(a[q].y + a[q + 16].y, a[q].y - a[q + 16].y);
+      }
+    } else {
+      pdl_wait();
+      if (ld_done(sd.ctl)) return;
+#pragma unroll
+      for (int e = 0; e < S::P / 2; ++e) X[e] = Y[e] = make_float2(0.f, 0.f);
+    }
+  } else if (active) {
+    // Pass-0 input r_s^l c_l / N for l = 2m + lane + q B, r_s^l = lo[2m + lane] hi[q]
+    const float* lo = sd.p.rlo32 + (size_t)s * B;
+    const float* hi = sd.p.rhi32 + (size_t)s * R0;
+    const float4* c2 = reinterpret_cast<const float4*>(sd.c32);  // spectrum entries (j, j + 1), j even
+    float h[R0];
+    float2 lb[NPR0];
+#pragma unroll
+    for (int q = 0; q < R0; ++q) h[q] = __ldg(&hi[q]);
+#pragma unroll
+    for (int i = 0; i < NPR0; ++i) lb[i] = __ldg(reinterpret_cast<const float2*>(lo + 2 * (t + i * TPF)));
+    pdl_wait();
+    if (ld_done(sd.ctl)) return;
+#pragma unroll
+    for (int i = 0; i < NPR0; ++i) {
+#pragma unroll
+      for (int q = 0; q < R0; ++q) {
+        const float2 rp = mul2(lb[i], dup2(h[q]));
+        const float4 x = c2[(2 * (t + i * TPF) + q * B) >> 1];
+        X[i * R0 + q] = mul2(make_float2(x.x, x.z), rp);
+        Y[i * R0 + q] = mul2(make_float2(x.y, x.w), rp);
+      }
+    }
+  } else {
+    pdl_wait();
+    if (ld_done(sd.ctl)) return;
+#pragma unroll
+    for (int e = 0; e < S::P / 2; ++e) X[e] = Y[e] = make_float2(0.f, 0.f);
+  }
+
+  fftp_run<LOGN, +1, PASS1, (FPC > 1)>(X, Y, t, buf, sd.p.st32p);
+
+  // Objective and per-radius best: outputs 2t + lane + q N / 16 in increasing order
+  Best2F b;
+  b.init();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const float2 o = fma2(X[q], X[q], mul2(Y[q], Y[q]));
+    b.push_ascending(o.x, fftp_out_index<LOGN>(t, 0, q));
+    b.push_ascending(o.y, fftp_out_index<LOGN>(t, 1, q));
+  }
+  group_reduce<TPF>(b, red);
+  if (t == 0 && active) {
+    const float w2 = obj_w32(sd, s);
+    Top2F o;
+    o.v1 = b.v1 * w2;
+    o.v2 = b.v2 * w2;
+    o.j1 = b.j1;
+    o.j2 = b.j2;
+    reinterpret_cast<Top2F*>(sd.top2)[s] = o;
+    if (o.v1 >= 0.0f && o.v1 <= 3.402823466e38f) atomicMax(&sd.ctl->vmax_bits, __float_as_uint(o.v1));
+    __threadfence();  // read by the signal's last CTA
+  }
+  if (!arrive_last(&sd.ctl->cnt_grid, gx, &s_last)) return;
+  // the transform buffers are free (arrive_last ends with a CTA barrier)
+    select_candidates_f32<THREADS>(sd, sd.ctl->k, 1, *reinterpret_cast<SelectScratch*>(smem_raw));
+}
+
+template <typename T, int LOGN, int PP = 0, int CT = 256>
+__device__ __forceinline__ void grid_body_s(const SlotDev* __restrict__ slots, const int* __restrict__ ids, int bx,
+                                            int by, int gx);
 
 // One work item of the grid step: transform tile bx (radii bx FPC ..) of the
 // signal ids[by], whose grid has gx tiles; the signal's last tile also runs
-// the selection.  Every thread of the CTA (THREADS) calls it.
+// the selection.  Every thread of the CTA (THREADS) calls it.  FP32 with 32
+// points per thread runs on the paired transforms, the rest on fft_run.
 template <typename T, int LOGN, int PP = 0, int CT = 256>
 __device__ __forceinline__ void grid_body(const SlotDev* __restrict__ slots, const int* __restrict__ ids, int bx,
                                           int by, int gx) {
+  if constexpr (sizeof(T) == 4 && PP == 32 && LOGN >= 5) grid_body_p<LOGN, CT>(slots, ids, bx, by, gx);
+  else grid_body_s<T, LOGN, PP, CT>(slots, ids, bx, by, gx);
+}
+
+template <typename T, int LOGN, int PP, int CT>
+__device__ __forceinline__ void grid_body_s(const SlotDev* __restrict__ slots, const int* __restrict__ ids, int bx,
+                                            int by, int gx) {
   using S = FftShape<T, LOGN, PP>;
   using C = GridCfg<T, LOGN, PP, CT>;
   constexpr int N = S::N, P = S::P, TPF = S::TPF, FPC = C::FPC, THREADS = C::THREADS;
@@ -112,7 +241,7 @@ __device__ __forceinline__ void grid_body(const SlotDev* __restrict__ slots, con
 #pragma unroll
     for (int u = 0; u < P; ++u) {
       const V2<T> x = v[fft_out_slot<T, LOGN, PP>(u)];
-      b.push_ascending(x.x * x.x + x.y * x.y, t + TPF * u);
+      b.push_ascending(norm2<T>(x), t + TPF * u);
     }
     group_reduce<TPF>(b, red);
     if (t == 0 && active) {
@@ -128,7 +257,8 @@ __device__ __forceinline__ void grid_body(const SlotDev* __restrict__ slots, con
       __threadfence();  // read by the signal's last CTA
     }
     if (!arrive_last(&sd.ctl->cnt_grid, gx, &s_last)) return;
-    select_candidates_f32<THREADS>(sd, sd.ctl->k);
+    // the transform buffers are free (arrive_last ends with a CTA barrier)
+    select_candidates_f32<THREADS>(sd, sd.ctl->k, 1, *reinterpret_cast<SelectScratch*>(smem_raw));
   } else {
     __shared__ Best1D red[32];
     Best1D b;
@@ -136,7 +266,7 @@ __device__ __forceinline__ void grid_body(const SlotDev* __restrict__ slots, con
 #pragma unroll
     for (int u = 0; u < P; ++u) {
       const V2<T> x = v[fft_out_slot<T, LOGN, PP>(u)];
-      b.push_ascending(x.x * x.x + x.y * x.y, t + TPF * u, x);
+      b.push_ascending(norm2<T>(x), t + TPF * u, x);
     }
     group_reduce<TPF>(b, red);
     if (t == 0 && active) {
