@@ -69,11 +69,14 @@ typedef struct afd_plan_opts {
   int use_graph;       /* 1 (default): replay the step sequence as a CUDA graph */
   int persistent;      /* 1 (default): a single-signal FP32-path decomposition with N <= 4096
                           runs as one persistent cooperative kernel (bounded grid barriers
-                          between the phases of a step); a batch, or a serving tick, whose
-                          signals are all FP32-path powers of two up to 16384 runs as one
+                          between the phases of a step), and a serving tick whose signals
+                          are all FP32-path powers of two up to 16384 runs as one
                           multi-signal persistent launch (every N-class in every phase);
-                          0: one launch per kernel per step (per N-class in batches and
-                          ticks).  Results are identical either way. */
+                          2: as 1, and a batch of such signals runs as one multi-signal
+                          persistent launch too (by default a batch keeps one launch per
+                          kernel per N-class and step, replayed as a graph, which measures
+                          faster for batches of 2 to 1024 signals); 0: one launch per
+                          kernel per step everywhere.  Results are identical either way. */
   int renormalise;     /* 1: select by |<G_k, e_a>~|^2 / ||e_a||_N^2, the objective divided by
                           the discrete norm (1 + r^N)/(1 - r^N) of the kernel at a grid point
                           (the continuous norm of Sec. 2 is 1; the discrete one inflates the
@@ -244,12 +247,12 @@ afd_status afd_plan_get_stream(const afd_plan* plan, void** stream);
 
 /*
  * Batched Core AFD: n_signals independent decompositions of uneven N, run
- * together: with opts->persistent (default) and FP32-path powers of two up
- * to 16384, all K steps of every signal in one cooperative persistent launch
- * (all N-classes share each phase; bounded grid barriers between phases);
- * otherwise all signals' grid tiles of one N share a launch and the N
- * classes run on parallel streams.  The launch sequence is replayed as one
- * CUDA graph when opts->use_graph is set.
+ * together: all signals' grid tiles of one N share a launch and the N
+ * classes run on parallel streams, the launch sequence replayed as one CUDA
+ * graph when opts->use_graph is set; with opts->persistent = 2 and FP32-path
+ * powers of two up to 16384, all K steps of every signal in one cooperative
+ * persistent launch instead (all N-classes share each phase; bounded grid
+ * barriers between phases).
  *   N        host array, n_signals sizes (each as for afd_plan_create, but not
  *            the FP32 two-pass size 65536).
  *   radii    host array of M radii shared by all signals.

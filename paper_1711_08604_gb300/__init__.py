@@ -91,8 +91,10 @@ def _opts(opts=None, **kw) -> PlanOpts:
     for k, v in kw.items():
         if k == "stream" and v is not None and not isinstance(v, int):
             v = int(getattr(v, "cuda_stream", v))
-        if k in ("force_a1_zero", "use_graph", "persistent", "renormalise", "autotune"):
+        if k in ("force_a1_zero", "use_graph", "renormalise", "autotune"):
             v = int(bool(v))
+        if k == "persistent":  # False / True / 2 (a batch as one multi-signal launch)
+            v = 2 if (not isinstance(v, bool) and v == 2) else int(bool(v))
         setattr(o, k, v)
     return o
 

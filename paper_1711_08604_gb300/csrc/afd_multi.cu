@@ -34,7 +34,7 @@ namespace afd {
 
 namespace {
 
-// Two builds of the kernel: MT = 256 threads per CTA (two CTAs per SM) for
+// Two builds of the kernel: MT = 256 threads per CTA (three CTAs per SM) for
 // sizes up to 8192, MT = 512 (one per SM) when 16384 is among them.
 // The transforms (grid and forward) use 32 points per thread from N = 32 up
 // and N points below; the grid packs 256 / TPF or 512 / TPF transforms into
@@ -164,9 +164,11 @@ __device__ __forceinline__ int total_items(const MultiClass* cls, int n, Per per
 __device__ __forceinline__ int chunks_c(const MultiClass& c) { return chunks_of(1 << c.logN); }
 
 template <int MT>
-__global__ void __launch_bounds__(MT, MT == 256 ? 2 : 1) k_multi(const __grid_constant__ MultiArgs a) {
+__global__ void __launch_bounds__(MT, MT == 256 ? 3 : 1) k_multi(const __grid_constant__ MultiArgs a) {
   constexpr int NW = MT / 32;
-  __shared__ Fp64WarpSmem smw[NW];
+  // the FP64 items' candidate sums share the dynamic buffer with the transforms
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Fp64WarpSmem* smw = reinterpret_cast<Fp64WarpSmem*>(smem_raw);
   __shared__ int s_ok, s_item;
   const int warp = threadIdx.x >> 5;
   int* err = reinterpret_cast<int*>(a.bar + 32);  // its own 128-byte line after the counter
@@ -317,7 +319,7 @@ void shape_mt(int logN, int Mmax, int count, int cap, MultiClass* c) {
 
 template <int MT>
 cudaError_t launch_mt(const MultiArgs& a, cudaStream_t st) {
-  size_t smem = 0;
+  size_t smem = sizeof(Fp64WarpSmem) * (MT / 32);
   for (int c = 0; c < a.n_cls; ++c) smem = smem_bytes<MT>(a.cls[c].logN) > smem ? smem_bytes<MT>(a.cls[c].logN) : smem;
   for (int c = 0; c < a.n_fresh; ++c)
     smem = smem_bytes<MT>(a.fresh[c].logN) > smem ? smem_bytes<MT>(a.fresh[c].logN) : smem;

@@ -1364,11 +1364,11 @@ afd_status afd_batch_create(afd_batch** out, int n_signals, const int* N, const 
     }
     per_signal[i] = it->second;
   }
-  // the single-signal persistent kernel is for plans; for a batch the
-  // persistent option picks the multi-signal kernel where it applies
+  // the single-signal persistent kernel is for plans; for a batch,
+  // persistent = 2 picks the multi-signal kernel where it applies
   afd_plan_opts ob = o;
   ob.persistent = 0;
-  AFD_TRY(b->pool.build(per_signal, K_max, ob, o.persistent != 0));
+  AFD_TRY(b->pool.build(per_signal, K_max, ob, o.persistent == 2));
   *out = b.release();
   return AFD_OK;
 }

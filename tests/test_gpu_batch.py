@@ -115,7 +115,7 @@ def test_multi_signal_launch_equals_stream_path(tol):
             for i, N in enumerate(Ns)]
     radii = W.radii_linear(21)
     K = 7
-    multi = afd.afd_batch_create([g.size for g in sigs], radii, K)
+    multi = afd.afd_batch_create([g.size for g in sigs], radii, K, persistent=2)
     r1 = afd.afd_batch_run(multi, np.concatenate(sigs), tol)
     launches = afd.afd_batch_counters(multi)["kernel_launches"]
     multi.close()
