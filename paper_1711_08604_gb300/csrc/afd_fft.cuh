@@ -33,13 +33,14 @@ template <typename T> __device__ __forceinline__ V2<T> mk2(T x, T y) { V2<T> r; 
 template <typename T> __device__ __forceinline__ V2<T> cadd(V2<T> a, V2<T> b) { return mk2<T>(a.x + b.x, a.y + b.y); }
 template <typename T> __device__ __forceinline__ V2<T> csub(V2<T> a, V2<T> b) { return mk2<T>(a.x - b.x, a.y - b.y); }
 
-// Products and fused multiply-adds with the rounding fixed in the source (no
-// contraction left to the compiler), so that the paired FP32 path below,
-// which does the same operations two lanes at a time, gives the same bits.
+// FP32 products and fused multiply-adds with the rounding fixed in the
+// source (no contraction left to the compiler), so that the paired FP32 path
+// below, which does the same operations two lanes at a time, gives the same
+// bits.  FP64 has no paired path and keeps the compiler's contraction.
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return a * b; }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return a * b + c; }
 
 // |a|^2 = fma(a.re, a.re, a.im * a.im)
 template <typename T> __device__ __forceinline__ T norm2(V2<T> a) { return fma_rn(a.x, a.x, mul_rn(a.y, a.y)); }
