@@ -158,9 +158,8 @@ __device__ __forceinline__ void block_best_f(float& v, int& f, float* sv, int* s
 }
 
 // A set of threads that works and synchronises as one unit: the whole CTA
-// (barrier 0), or a 128-thread quarter of a larger CTA on its own named
-// barrier (1 + quarter), so that one CTA can run four FP64 work items at once.
-// tid: the thread's index within the set.
+// (barrier 0), or a part of it on its own named barrier (bar > 0, count
+// threads).  tid: the thread's index within the set.
 struct ThreadSet {
   int bar, count, tid;
   __device__ __forceinline__ void sync() const {
@@ -169,9 +168,6 @@ struct ThreadSet {
   }
 };
 __device__ __forceinline__ ThreadSet cta_set() { return ThreadSet{0, (int)blockDim.x, (int)threadIdx.x}; }
-__device__ __forceinline__ ThreadSet quarter_set() {
-  return ThreadSet{1 + (int)(threadIdx.x >> 7), 128, (int)(threadIdx.x & 127)};
-}
 
 // Last-work-item detection: returns true in every thread of the set that is
 // the last of `target` items to arrive on *counter, and resets the counter.
