@@ -310,8 +310,11 @@ afd_status afd_synthesize(int N, const double* a, const double* coeff, int n, in
  * copied at submission).  The worker admits queued requests oldest first into
  * device slots while the memory budget allows (slot buffers and the plan
  * tables of each distinct (N, radii) count against it), then repeatedly runs
- * one greedy step for every admitted request at once (launches grouped by N),
- * retires the requests whose stop rule fired and admits waiting ones, so
+ * a tick for every admitted request at once: with opts->persistent (default)
+ * and FP32-path powers of two up to 16384, four greedy steps in one
+ * multi-signal launch (each request stopping at its own last step);
+ * otherwise one step, launches grouped by N.  After each tick it retires the
+ * requests whose stop rule fired and admits waiting ones, so
  * requests that arrive while others run share the device.  Each request gets
  * the same result as afd_decompose with the server's options would give it
  * alone.

@@ -48,6 +48,11 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr int kMaxSlots = 4096;
+// Greedy steps of every active request per multi-signal launch: the host's
+// per-tick work (the launch, the control-block read, admission and
+// retirement) is paid once per this many steps; a request stops on the
+// device at its own last step, and arrivals wait at most one tick.
+constexpr int kStepsPerTick = 4;
 
 // Device arena: power-of-two size classes (>= 64 KiB) carved from 64 MiB
 // chunks, or a dedicated allocation for larger blocks.  Every byte obtained
@@ -351,8 +356,8 @@ struct afd_server {
     const int prec = opts.precision;
     long long launches = 0;
     // FP32 path with every active size on chip: the whole tick (the fresh
-    // requests' initialisation, then one step of every request) is one
-    // multi-signal persistent launch
+    // requests' initialisation, then kStepsPerTick steps of every request)
+    // is one multi-signal persistent launch
     bool multi = prec == AFD_FP32_GUARDED && opts.persistent != 0;
     for (int l = 0; l <= MAX_LOGN; ++l) multi = multi && (all[l].empty() || multi_size_ok(l));
     if (multi) {
@@ -361,7 +366,7 @@ struct afd_server {
       a.ids = ids_dev;
       a.fresh_ids = ids_dev;
       a.bar = bar_dev;
-      a.K = 1;
+      a.K = kStepsPerTick;
       a.final_forward = 1;
       for (int l = 0; l <= MAX_LOGN; ++l) {
         if (!all[l].empty()) {

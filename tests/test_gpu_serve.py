@@ -149,7 +149,8 @@ def test_budget_admits_in_waves():
     st = afd.afd_serve_get_stats(srv)
     srv.close()
     assert st["completed"] == 12 and st["bytes_reserved"] <= 48 << 20
-    assert st["ticks"] > 8  # more than one wave of 8 steps
+    # more than one wave of 8 steps: a tick runs four steps (one launch)
+    assert st["ticks"] > 2
     for s, o in zip(reqs, outs):
         one = alone(s.G, s.radii, s.K, 0.0)
         assert np.array_equal(o["coeff"], one["coeff"])
