@@ -170,9 +170,11 @@ def test_workload3_full_batch_parity():
 
 def test_grid_variants_are_bitwise_equivalent():
     # the autotuner's candidates (points per thread, CTA width) compute the
-    # same values
-    # (on the per-class path, where the variants run)
-    sigs = small_batch(n=8, Ns=(256, 1024, 4096, 8192), seed=4)
+    # same values (on the per-class path, where the variants run): the paired
+    # 32-points-per-thread transforms against the scalar ones at every first
+    # radix (2: N = 32, 512, 8192, pass 0 in registers; 4: 64, 1024; 8: 128,
+    # 2048; 16: 256, 4096)
+    sigs = small_batch(n=20, Ns=(32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 512), seed=4)
     radii = W.radii_linear(24)
     ref = afd.afd_decompose_batch(sigs, radii, 5, autotune=False, persistent=False)
     for v in (0, 1, 2):
