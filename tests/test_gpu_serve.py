@@ -86,6 +86,27 @@ def test_poisson_arrivals_parity_and_latency():
         assert o["delta"][-1] <= s.tol or o["steps"] == s.K
 
 
+def test_step_limits_inside_a_tick():
+    # a tick runs several steps: requests whose step limit (1, 2, 3, 5, 6) or
+    # stop rule falls inside a tick stop there, with the results they get alone
+    limits = ((1, 0.0), (2, 0.0), (3, 0.0), (5, 0.0), (6, 1e-3))
+    reqs = []
+    for N in (512, 1024, 2048, 4096, 16384):
+        for K, tol in limits:
+            G = W.random_signal(N, 70 + len(reqs)) + W.szego_sum(N, np.array([0.7j, -0.5]), np.array([1.0, 0.3]))
+            reqs.append((G, K, tol))
+    radii = W.radii_linear(20)
+    srv = afd.afd_serve_create(1 << 30)
+    ids = [afd.afd_serve_submit(srv, G, radii, K, tol) for G, K, tol in reqs]
+    outs = [afd.afd_serve_wait(srv, i, 120.0) for i in ids]
+    srv.close()
+    for (G, K, tol), o in zip(reqs, outs):
+        one = alone(G, radii, K, tol)
+        assert o["steps"] == one["steps"] <= K
+        for k in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(o[k], one[k]), (G.size, K, k)
+
+
 def test_per_class_launch_server_matches_multi_launch_server():
     # persistent=False serves each N-class with its own step kernels: the same
     # results bitwise as the one-launch ticks
