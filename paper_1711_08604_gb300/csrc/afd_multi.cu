@@ -21,6 +21,7 @@
 // per transform group); the N-classes share each phase, so no class waits for
 // a launch of its own.  Fresh signals are initialised first (energy and FP32
 // copy, then their transform).
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -333,8 +334,28 @@ cudaError_t launch_mt(const MultiArgs& a, cudaStream_t st) {
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     blocks = per_sm * sms;
   }
+  // No more CTAs than the largest phase has items (a small serving tick
+  // then pays for fewer arrivals at each grid barrier), at most the
+  // co-resident maximum.
+  constexpr int NW = MT / 32;
+  long long need = 1;
+  auto most = [&](const MultiClass* cls, int n) {
+    long long g = 0, gu = 0, up = 0, fw = 0;
+    for (int c = 0; c < n; ++c) {
+      const MultiClass& x = cls[c];
+      const long long ch = chunks_of(1 << x.logN);
+      g += (long long)x.count * x.tiles;
+      gu += ((long long)x.count * x.gpar * ch + NW - 1) / NW;
+      up += ((long long)x.count * ch + NW - 1) / NW;
+      fw += (x.count + x.fgroups - 1) / x.fgroups;
+    }
+    need = std::max({need, g, gu, up, fw});
+  };
+  most(a.cls, a.n_cls);
+  most(a.fresh, a.n_fresh);
+  const int grid = (int)std::min<long long>(blocks, need);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(blocks);
+  cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(MT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
