@@ -317,31 +317,42 @@ k_grid2_pass1(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
 }
 
 // Grid pass 2 (see the file comment): items (s, b) = (i / 16, i mod 16), i =
-// blockIdx.x, + gridDim.x, ...
+// blockIdx.x, + gridDim.x, ...  The warps go through the items on their own,
+// without CTA barriers: each warp waits for the item's slot itself, does its
+// two rows, and the last warp of the CTA to finish an item merges the eight
+// warps' best pairs and refills the slot with the item two ahead (a smem
+// arrival counter per slot; the refill waits for every warp, since no warp
+// can need the slot's next contents before all of them are done with it).
 __global__ void __launch_bounds__(kThreads)
 k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Maps maps) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ alignas(8) uint64_t bars[2];
-  __shared__ float rv1[kThreads / 32], rv2[kThreads / 32];
-  __shared__ int rj1[kThreads / 32], rj2[kThreads / 32];
-  __shared__ int s_last, s_ok;
+  __shared__ float rv1[2][kThreads / 32], rv2[2][kThreads / 32];
+  __shared__ int rj1[2][kThreads / 32], rj2[2][kThreads / 32];
+  __shared__ unsigned s_arrive[2], s_issued[2];
+  __shared__ int s_last, s_fail;
   pdl_launch_dependents();
   const SlotDev& sd = slots[0];
   float2* in = align1024(smem_raw);
   const int g = threadIdx.x >> 4, t = threadIdx.x & 15;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   static_assert(FftSchedule::npass(L8) == 2 && FftSchedule::tw_off(L8, 1) == 0, "fft256_swz: 16 x 16");
   if (threadIdx.x == 0) {
     mbar_init(&bars[0]);
     mbar_init(&bars[1]);
+    s_arrive[0] = s_arrive[1] = 0u;
+    s_issued[0] = s_issued[1] = 0u;
+    s_fail = 0;
   }
   __syncthreads();
   pdl_wait();
   if (ld_done(sd.ctl)) return;
   const int items = 16 * sd.p.M;
-  // thread 0: the TMA load of this CTA's item number i into ring slot i mod 2
+  // the TMA load of this CTA's item number i into ring slot i mod 2 (one thread)
   auto issue = [&](int i) {
     const int item = (int)blockIdx.x + i * (int)gridDim.x;
     if (item >= items) return;
+    ++s_issued[i & 1];
     mbar_expect_tx(&bars[i & 1], kTileBytes);
     tma_load_2d(in + (i & 1) * kTileElems, &maps.xl, 0, (item >> 4) * 256 + 16 * (item & 15), &bars[i & 1]);
   };
@@ -356,7 +367,12 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
     const int s = item >> 4, b = item & 15;
     const int j2 = 16 * b + g;
     float2* tile = in + (i & 1) * kTileElems;
-    if (!cta_wait(&bars[i & 1], (i >> 1) & 1, &s_ok)) break;
+    // every lane polls the slot's barrier (bounded); a warp that gives up, or
+    // sees that another did, leaves the loop
+    if (*((volatile int*)&s_fail) || !mbar_wait_bounded(&bars[i & 1], (i >> 1) & 1)) {
+      if (lane == 0) atomicOr(&s_fail, 1);
+      break;
+    }
     float2 v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = tile[g * 256 + t + 16 * q];  // row j2, l1 = t + 16 q
@@ -364,33 +380,42 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
     fft256_swz<1>(v, t, tile + g * 256, sd.p.st32);
     // the slot's generic writes before the TMA load that refills it
     fence_proxy_async();
-    // best two of the item's 4096 grid points (j = j2 + 256 j1); a thread's
+    // best two of the warp's 512 grid points (j = j2 + 256 j1); a thread's
     // outputs come in increasing j1 = t + 16 e
     Best2F bb;
     bb.init();
 #pragma unroll
     for (int e = 0; e < 16; ++e) bb.push_ascending(norm2<float>(v[e]), j2 + 256 * (t + 16 * e));
-    // the warp's two transforms, then the CTA's eight warps
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) bb.merge(bb.shfl(off));
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned last = 0;
+    __syncwarp();  // the warp's reads and writes of the slot come before its arrival
     if (lane == 0) {
-      rv1[warp] = bb.v1;
-      rv2[warp] = bb.v2;
-      rj1[warp] = bb.j1;
-      rj2[warp] = bb.j2;
+      rv1[i & 1][warp] = bb.v1;
+      rv2[i & 1][warp] = bb.v2;
+      rj1[i & 1][warp] = bb.j1;
+      rj2[i & 1][warp] = bb.j2;
+      __threadfence_block();
+      last = atomicAdd(&s_arrive[i & 1], 1u) == kThreads / 32 - 1;
+      if (last) __threadfence_block();
     }
-    __syncthreads();
-    // every warp is done with the slot: refill it
-    if (threadIdx.x == 0) issue(i + 2);
-    if (warp == 0) {
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      // every warp is done with the slot and has posted its pair: read the
+      // item's eight pairs (their buffer is rewritten for item i + 2, which
+      // the refill lets other warps start), then refill the slot
       Best2F o;
       o.init();
       if (lane < kThreads / 32) {
-        o.v1 = rv1[lane];
-        o.v2 = rv2[lane];
-        o.j1 = rj1[lane];
-        o.j2 = rj2[lane];
+        o.v1 = rv1[i & 1][lane];
+        o.v2 = rv2[i & 1][lane];
+        o.j1 = rj1[i & 1][lane];
+        o.j2 = rj2[i & 1][lane];
+      }
+      __syncwarp();
+      if (lane == 0) {
+        s_arrive[i & 1] = 0u;
+        issue(i + 2);
       }
 #pragma unroll
       for (int off = 4; off > 0; off >>= 1) o.merge(o.shfl(off));
@@ -406,17 +431,21 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
       }
     }
   }
-  if ((int)blockIdx.x + i * (int)gridDim.x < items) {
+  __syncthreads();
+  if (s_fail) {
     // a load did not arrive: flag the signal and leave once the copies this
     // CTA started have landed (bounded)
     if (threadIdx.x == 0) {
       atomicOr(&sd.ctl->err, 4);
       sd.ctl->done = 1;
-      mbar_wait_bounded(&bars[i & 1], (i >> 1) & 1);
-      if ((int)blockIdx.x + (i + 1) * (int)gridDim.x < items) mbar_wait_bounded(&bars[(i + 1) & 1], ((i + 1) >> 1) & 1);
+      // the last load issued into each slot completes that slot's phase
+      // s_issued - 1
+      for (int k = 0; k < 2; ++k)
+        if (s_issued[k]) mbar_wait_bounded(&bars[k], (s_issued[k] - 1) & 1);
     }
     return;
   }
+  __threadfence();  // the Top2F pairs and vmax before the last CTA reads them
   if (!arrive_last(&sd.ctl->cnt_grid, gridDim.x, &s_last)) return;
   __shared__ SelectScratch scr;
   select_candidates_f32<kThreads>(sd, sd.ctl->k, 16, scr);
