@@ -448,7 +448,7 @@ def bench_serve(afd, duration: float = 10.0, fp64_every: int = 25) -> dict:
             "requests": len(reqs), "signals_per_s": served, "grid_evals_per_s": evals / t_all,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
-            "ticks": st["ticks"], "kernel_launches": st["kernel_launches"],
+            "ticks": st["ticks"], "kernel_launches": st["kernel_launches"], "failed": st["failed"],
             "capacity_signals_per_s": capacity,
             "fp64_plain_single_signal_per_s": fp64_rate,
             "capacity_vs_fp64_plain": capacity / fp64_rate,
