@@ -117,8 +117,8 @@ __device__ __forceinline__ void tma_store_2d_async(const CUtensorMap* map, int x
                : "memory");
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
-// At most one of this thread's bulk stores still reading shared memory.
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// None of this thread's bulk stores still reading shared memory.
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // All of this thread's bulk stores complete.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
@@ -293,10 +293,9 @@ k_grid2_pass1(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
   fetch(r0);
   int it = 0;
   for (int s = r0; s < M; s += R, ++it) {
+    // (the store issued from this buffer two radii ago had read it before
+    // the previous radius's last barrier)
     float2* ob = obuf + (it & 1) * (kScratchBytes / 8);
-    // the store issued from this buffer two radii ago has read it
-    if (threadIdx.x == 0) bulk_wait_read1();
-    __syncthreads();
     float2 v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
@@ -310,6 +309,9 @@ k_grid2_pass1(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
 #pragma unroll
     for (int e = 0; e < 16; ++e) ob[swz16(fft_out_index<float, L8>(t, e), g)] = cmul<float>(v[e], tw[e]);
     fence_proxy_async();
+    // the store issued from the other buffer one radius ago has read it (the
+    // next radius transforms there), before the barrier that releases it
+    if (threadIdx.x == 0) bulk_wait_read0();
     __syncthreads();
     if (threadIdx.x == 0) tma_store_2d_async(&maps.xs, 16 * a, s * 256, ob);
   }
