@@ -70,7 +70,9 @@ def _load():
         lib.oracle_energy.restype = ctypes.c_double
         lib.oracle_decompose.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int,
-                                         _dp, _dp, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+                                         _dp, _dp, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
+        lib.oracle_refine.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                      _dp, _dp]
         lib.oracle_kernel_norm2.argtypes = [ctypes.c_int, ctypes.c_double]
         lib.oracle_kernel_norm2.restype = ctypes.c_double
         lib.oracle_nu_inner.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
@@ -125,6 +127,18 @@ def inner_many(G, points) -> np.ndarray:
     return out
 
 
+def refine(G, a0: complex, iters: int) -> tuple:
+    """Off-grid refinement of a point (not in the paper): damped Newton steps
+    on log |<G, e_a>~|^2 over the open disc from a0, at most ``iters`` of
+    them.  Returns (a, <G, e_a>~)."""
+    g = _cvec(G)
+    a = np.zeros(2)
+    c = np.zeros(2)
+    if _load().oracle_refine(g.size, _p(g), float(np.real(a0)), float(np.imag(a0)), int(iters), _p(a), _p(c)) != 0:
+        raise ValueError("oracle_refine: bad arguments")
+    return complex(a[0], a[1]), complex(c[0], c[1])
+
+
 def grid(G, radii) -> np.ndarray:
     """(M, N) complex array of <G, e_{a_{s,j}}>~ over the polar grid, Eq. (term81)."""
     g, r = _cvec(G), _rvec(radii)
@@ -160,7 +174,7 @@ def kernel_norm2(N: int, r: float) -> float:
 
 def decompose(G, radii, K_max: int, energy_tol: float = 0.0, force_a1_zero: bool = False,
               forced_idx=None, compute_grid: bool = True, renormalise: bool = False,
-              keep_steps: bool = False) -> dict:
+              keep_steps: bool = False, offgrid_iters: int = 0) -> dict:
     """Core AFD: K_max greedy steps (or until delta <= energy_tol).
 
     ``renormalise`` selects by |<G_k, e_a>~|^2 / ||e_a||_N^2 (the discrete norm,
@@ -172,6 +186,8 @@ def decompose(G, radii, K_max: int, energy_tol: float = 0.0, force_a1_zero: bool
     skipped; the coefficient then comes from ``inner`` at the forced point.
     ``keep_steps`` adds ``G_steps``: (steps, N) array of G_k at the start of
     every step k (the remainder the step's selection runs on).
+    ``offgrid_iters`` > 0 refines each step's point off the grid (``refine``)
+    before its coefficient and update; ``idx`` keeps the grid starting point.
     """
     g, r = _cvec(G), _rvec(radii)
     K = int(K_max)
@@ -196,7 +212,7 @@ def decompose(G, radii, K_max: int, energy_tol: float = 0.0, force_a1_zero: bool
         g.size, _p(g), r.size, _p(r), K, float(energy_tol), int(bool(force_a1_zero)), int(bool(renormalise)),
         fi.ctypes.data_as(_ip) if fi is not None else None, int(bool(compute_grid)),
         _p(a), _p(c), idx.ctypes.data_as(_ip), own.ctypes.data_as(_ip), _p(objmax), _p(obj2),
-        _p(objused), _p(delta), _p(E), _p(Gf), _p(Gs) if Gs is not None else None)
+        _p(objused), _p(delta), _p(E), _p(Gf), _p(Gs) if Gs is not None else None, int(offgrid_iters))
     if steps < 0:
         raise ValueError("oracle_decompose: bad arguments")
     out = {"steps": steps, "a": a[:steps], "coeff": c[:steps], "idx": idx[:steps],

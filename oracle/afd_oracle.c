@@ -204,6 +204,117 @@ int oracle_update(int N, const double* G, double a_re, double a_im, double c_re,
   return 0;
 }
 
+/*
+ * Off-grid refinement of a selected point (optional; not part of the paper,
+ * whose selection stays on the grid of Sec. 3.2).  The discrete objective
+ * f(a) = |<G, e_a>~|^2 = (1 - |a|^2) |S(a)|^2 / N^2, S(a) = sum_m G(z_m) / (1 - a conj(z_m)),
+ * is maximised over the open disc from the grid point a0 by damped Newton
+ * steps on h = log f = log(1 - |a|^2) + 2 Re log S(a) + const in the real
+ * coordinates (x, y) of a.  With L1 = S'/S and L2 = S''/S - L1^2 (S is
+ * holomorphic, so 2 Re log S is harmonic):
+ *   grad h = (2 Re L1 - 2x/rho, -2 Im L1 - 2y/rho),          rho = 1 - |a|^2,
+ *   h_xx = 2 Re L2 - 2/rho - 4x^2/rho^2,  h_xy = -2 Im L2 - 4xy/rho^2,
+ *   h_yy = -2 Re L2 - 2/rho - 4y^2/rho^2,
+ *   S'(a) = sum G z_bar / (1 - a z_bar)^2,  S''(a) = 2 sum G z_bar^2 / (1 - a z_bar)^3.
+ * Each iteration: stop unless the Hessian is negative definite; a Newton
+ * step shorter than 1e-6 is taken as it is (the quadratic convergence near
+ * the maximum, where f no longer resolves the gain); a longer one, shortened
+ * to at most half the distance to the circle, is tried, then halved up to
+ * three times, and taken at the first try that increases f (none: stop).
+ * Stop after a step shorter than 1e-13.  Returns the refined a and
+ * c = <G, e_a>~ = sqrt(1 - |a|^2) S(a) / N.
+ */
+static void refine_sums(int N, const cplx* g, const cplx* z, cplx a, cplx* S0, cplx* S1, cplx* S2) {
+  cplx s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int m = 0; m < N; ++m) {
+    cplx zb = conj(z[m]);
+    cplx v = 1.0 / (1.0 - a * zb);
+    cplx t = g[m] * v;
+    cplx w = zb * v;
+    s0 += t;
+    s1 += t * w;
+    s2 += 2.0 * t * w * w;
+  }
+  *S0 = s0;
+  *S1 = s1;
+  *S2 = s2;
+}
+
+static double refine_f(cplx a, cplx S) { return (1.0 - creal(a * conj(a))) * creal(S * conj(S)); }
+
+static cplx refine_point(int N, const cplx* g, const cplx* z, cplx a, int iters, cplx* c_out) {
+  cplx S, S1, S2;
+  refine_sums(N, g, z, a, &S, &S1, &S2);
+  double f = refine_f(a, S);
+  for (int it = 0; it < iters; ++it) {
+    if (S == 0.0) break;
+    cplx L1 = S1 / S;
+    cplx L2 = S2 / S - L1 * L1;
+    double x = creal(a), y = cimag(a);
+    double rho = 1.0 - (x * x + y * y);
+    double gx = 2.0 * creal(L1) - 2.0 * x / rho;
+    double gy = -2.0 * cimag(L1) - 2.0 * y / rho;
+    double hxx = 2.0 * creal(L2) - 2.0 / rho - 4.0 * x * x / (rho * rho);
+    double hxy = -2.0 * cimag(L2) - 4.0 * x * y / (rho * rho);
+    double hyy = -2.0 * creal(L2) - 2.0 / rho - 4.0 * y * y / (rho * rho);
+    double det = hxx * hyy - hxy * hxy;
+    if (!(det > 0.0 && hxx < 0.0)) break;
+    double dx = -(hyy * gx - hxy * gy) / det;
+    double dy = -(hxx * gy - hxy * gx) / det;
+    double lim = 0.5 * (1.0 - sqrt(x * x + y * y));
+    double n = sqrt(dx * dx + dy * dy);
+    if (n < 1e-6 && n < lim) {
+      a += dx + I * dy;
+      refine_sums(N, g, z, a, &S, &S1, &S2);
+      f = refine_f(a, S);
+      if (n < 1e-13) break;
+      continue;
+    }
+    if (n > lim) {
+      dx *= lim / n;
+      dy *= lim / n;
+    }
+    int taken = 0;
+    for (int h = 0; h < 4; ++h) {
+      cplx an = a + (dx + I * dy);
+      cplx T, T1, T2;
+      refine_sums(N, g, z, an, &T, &T1, &T2);
+      double fn = refine_f(an, T);
+      if (fn > f) {
+        a = an;
+        S = T;
+        S1 = T1;
+        S2 = T2;
+        f = fn;
+        taken = 1;
+        break;
+      }
+      dx *= 0.5;
+      dy *= 0.5;
+    }
+    if (!taken) break;
+    if (sqrt(dx * dx + dy * dy) < 1e-13) break;
+  }
+  *c_out = sqrt(1.0 - creal(a * conj(a))) * S / (double)N;
+  return a;
+}
+
+int oracle_refine(int N, const double* G, double a_re, double a_im, int iters, double* a_out, double* c_out) {
+  if (N <= 0 || !G || !a_out || !c_out || iters < 0) return -1;
+  cplx a = a_re + I * a_im;
+  if (creal(a * conj(a)) >= 1.0) return -1;
+  cplx* z = make_points(N);
+  if (!z) return -1;
+  cplx c;
+  a = refine_point(N, (const cplx*)G, z, a, iters, &c);
+  free(z);
+  a_out[0] = creal(a);
+  a_out[1] = cimag(a);
+  c_out[0] = creal(c);
+  c_out[1] = cimag(c);
+  return 0;
+}
+
 /* Discrete energy (1/N) sum_m |G(z_m)|^2: the rectangle rule for the norm in
  * the normalised measure dt / 2 pi used by Eq. (formula2). */
 double oracle_energy(int N, const double* G) {
@@ -237,6 +348,9 @@ double oracle_energy(int N, const double* G) {
  *   G_final                     G_{k+1} after the last step (2N doubles);
  *   G_steps                     G_k at the start of every step k = 1..steps
  *                               (2N doubles per step, one after another).
+ * offgrid_iters > 0 refines each step's grid point off the grid
+ * (refine_point) before the coefficient and the update; idx_out then holds
+ * the grid point the refinement started from.
  * Returns the number of steps done (>= 1), or -1 on bad arguments.
  */
 int oracle_decompose(int N, const double* G, int M, const double* radii, int K_max,
@@ -244,7 +358,7 @@ int oracle_decompose(int N, const double* G, int M, const double* radii, int K_m
                      int compute_grid, double* a_out, double* coeff_out, int* idx_out,
                      int* own_idx_out, double* objmax_out, double* obj2_out,
                      double* objused_out, double* delta_out, double* energy_out,
-                     double* G_final, double* G_steps) {
+                     double* G_final, double* G_steps, int offgrid_iters) {
   if (N <= 0 || M <= 0 || K_max <= 0 || !G || !radii) return -1;
   for (int s = 0; s < M; ++s) {
     if (!(radii[s] >= 0.0 && radii[s] < 1.0)) return -1;
@@ -306,6 +420,7 @@ int oracle_decompose(int N, const double* G, int M, const double* radii, int K_m
     cplx c = compute_grid ? A[(long)s_used * N + j_used] : inner_with_table(N, g, z, a);
     double used = creal(c * conj(c));
     if (norm2) used /= norm2[s_used];
+    if (offgrid_iters > 0 && !(k == 0 && force_a1_zero)) a = refine_point(N, g, z, a, offgrid_iters, &c);
 
     if (a_out) { a_out[2 * k] = creal(a); a_out[2 * k + 1] = cimag(a); }
     if (coeff_out) { coeff_out[2 * k] = creal(c); coeff_out[2 * k + 1] = cimag(c); }

@@ -369,3 +369,64 @@ def test_nonuniform_brute_force_argmax():
                 best, arg = v, (s, j)
     d = oracle.nu_decompose(G, theta, w, radii, L, 1)
     assert tuple(d["idx"][0]) == arg and d["objmax"][0] == best
+
+
+# ----------------------------------------------- off-grid refinement (opt-in)
+# The refinement is not in the paper; these pins tie it to closed forms: the
+# reproducing kernel off the grid, the stationarity of the discrete objective
+# (checked by finite differences of the oracle's own inner product, a
+# different code path from the Newton sums), and the exact discrete energy
+# identity at a point off the grid, ||e_a||_N^2 = Re((1 + conj(a)^N) / (1 - conj(a)^N)).
+
+@pytest.mark.parametrize("b", [0.6 * np.exp(2j * np.pi * 0.1234), 0.2 + 0.05j, -0.45 - 0.3j])
+def test_refinement_recovers_an_off_grid_kernel(b):
+    # G = e_b with |b|^N negligible: <G, e_a>~ is maximal at a = b, with
+    # |c| = 1, and the remainder vanishes
+    N = 256
+    G = W.szego_sum(N, np.array([b]), np.array([1.0]))
+    radii = W.radii_linear(20)
+    r = oracle.decompose(G, radii, 2, offgrid_iters=30)
+    assert abs(r["a"][0] - b) < 1e-12
+    assert abs(abs(r["coeff"][0]) - 1.0) < 1e-12
+    assert r["delta"][1] < 1e-20
+    # idx keeps the grid point the refinement started from: the grid argmax
+    r0 = oracle.decompose(G, radii, 1)
+    assert np.array_equal(r["idx"][0], r0["idx"][0])
+
+
+def test_refinement_reaches_a_stationary_point_and_gains():
+    N = 512
+    G = W.random_signal(N, 21) + W.szego_sum(N, np.array([0.7 * np.exp(0.3j)]), np.array([2.0]))
+    radii = W.radii_linear(16)
+    r0 = oracle.decompose(G, radii, 1)
+    a, c = oracle.refine(G, r0["a"][0], 30)
+    f = lambda p: abs(oracle.inner(G, p)) ** 2  # noqa: E731
+    assert f(a) >= f(r0["a"][0])
+    assert abs(c - oracle.inner(G, a)) < 1e-12 * abs(c)
+    h = 1e-5
+    gx = (f(a + h) - f(a - h)) / (2 * h)
+    gy = (f(a + 1j * h) - f(a - 1j * h)) / (2 * h)
+    assert np.hypot(gx, gy) < 1e-6 * f(a)  # a maximum: zero gradient, and
+    for d in (1e-3, 1e-3j, -1e-3, -1e-3j):
+        assert f(a + d) < f(a)                # lower values around it
+
+
+def test_refinement_energy_identity_off_the_grid():
+    N = 64  # small N with radii near 1: the aliasing term matters
+    G = W.random_signal(N, 5)
+    radii = np.array([0.0, 0.5, 0.8, 0.9])
+    r = oracle.decompose(G, radii, 6, offgrid_iters=20)
+    assert r["steps"] == 6
+    E = r["energy"]
+    for k in range(6):
+        a, c = r["a"][k], r["coeff"][k]
+        norm2 = np.real((1 + np.conj(a) ** N) / (1 - np.conj(a) ** N))
+        assert abs(E[k + 1] - (E[k] - 2 * abs(c) ** 2 + abs(c) ** 2 * norm2)) < 1e-12 * E[0]
+
+
+def test_refinement_off_is_the_plain_decomposition():
+    s = W.kernel_sum()
+    r0 = oracle.decompose(s.G, s.radii, 5)
+    r1 = oracle.decompose(s.G, s.radii, 5, offgrid_iters=0)
+    for key in ("a", "coeff", "idx", "delta"):
+        assert np.array_equal(r0[key], r1[key])
