@@ -41,7 +41,7 @@ UNIT = "grid_evals/s"
 N_SIG, M_RAD, K_STEPS = 4096, 200, 50
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
-STEPREC_BYTES, SLOTCTL_BYTES, SLOTDEV_BYTES = 80, 64, 400  # StepRec, SlotCtl, SlotDev
+STEPREC_BYTES, SLOTCTL_BYTES, SLOTDEV_BYTES = 80, 64, 408  # StepRec, SlotCtl, SlotDev
 
 
 def kernel_sources_hash() -> str:
@@ -367,7 +367,8 @@ def bench_single(afd, torch, dev, sig, precision, reps: int = 20, plan=None, gri
 def bench_next(afd, torch, dev, reps: int = 10) -> dict:
     """The NEXT rows, one signal each, FP32 grid + FP64 guard: a mixed-radix
     size (N = 3000 = 2^3 3 5^3), non-uniform samples (3000 jittered angles,
-    L = 1024 grid angles) and the renormalised objective on workload 2."""
+    L = 1024 grid angles), the renormalised objective and the off-grid
+    refinement on workload 2."""
     from paper_1711_08604_gb300 import workloads as W
     fp32 = afd.AFD_FP32_GUARDED
     out = {}
@@ -384,6 +385,14 @@ def bench_next(afd, torch, dev, reps: int = 10) -> dict:
     t = W.tones()
     out["renormalised"] = dict(bench_single(afd, torch, dev, t, fp32, reps=reps, renormalise=True),
                                workload="tones: N=4096, M=200, K=50, renormalised objective")
+    # off-grid refinement of every step's point (not in the paper): time, and
+    # the relative error after K steps against the grid-only decomposition
+    out["offgrid"] = dict(bench_single(afd, torch, dev, t, fp32, reps=reps, offgrid_iters=20),
+                          workload="tones: N=4096, M=200, K=50, points refined off the grid (<= 20 Newton steps)")
+    for key, kw in (("delta_K_offgrid", {"offgrid_iters": 20}), ("delta_K_grid", {})):
+        plan = afd.afd_plan_create(t.N, t.radii, precision=fp32, device=dev.index, **kw)
+        out["offgrid"][key] = float(afd.afd_decompose(plan, t.G, t.K)["delta"][-1])
+        plan.close()
     return out
 
 

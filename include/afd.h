@@ -88,6 +88,13 @@ typedef struct afd_plan_opts {
                           process.  0: the default variant. */
   int grid_variant;    /* -1 (default): as autotune decides; 0..2: use this grid-kernel variant
                           wherever it exists (plans and batches; for tests and profiling) */
+  int offgrid_iters;   /* 0 (default): a_k is the grid point of Step 2 (Sec. 3.2).  n in 1..64:
+                          plans (uniform samples; not with renormalise) refine each step's grid
+                          winner over the open disc by at most n damped Newton steps on the
+                          same discrete objective |<G_k, e_a>~|^2, then take the coefficient and
+                          the update at the refined a_k (not in the paper); the step's idx
+                          stays the grid starting point and flags bit 3 is set.  Batches and
+                          servers reject it.  The persistent kernel is not used. */
 } afd_plan_opts;
 
 typedef struct afd_plan afd_plan;
@@ -202,7 +209,8 @@ afd_status afd_decompose_from(afd_plan* plan, const double* G, double E1_in, int
 /*
  * Diagnostics of the plan's last afd_decompose (host pointers, may be NULL):
  *   n_cand_out  K entries: FP64 guard candidates per step (0 on the FP64 path);
- *   flags_out   K entries: bit 0 the candidate cap ended the list, bit 1 non-finite;
+ *   flags_out   K entries: bit 0 the candidate cap ended the list, bit 1 non-finite,
+ *               bit 3 the point was refined off the grid (offgrid_iters);
  *   obj32_out   K entries: largest grid objective as computed by the grid kernel.
  * K is the number of steps of that call.
  */

@@ -20,7 +20,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("guard_tau", c_double), ("guard_cap", c_int),
                 ("force_a1_zero", c_int), ("device", c_int), ("stream", c_void_p),
                 ("use_graph", c_int), ("persistent", c_int), ("renormalise", c_int),
-                ("autotune", c_int), ("grid_variant", c_int)]
+                ("autotune", c_int), ("grid_variant", c_int), ("offgrid_iters", c_int)]
 
 
 class Result(ctypes.Structure):

@@ -36,6 +36,7 @@ inline __host__ __device__ int chunks_of(int N) { return (N + FP64_CHUNK - 1) / 
 // (x mod N) for x in (-N, 2N); N need not be a power of two
 inline __host__ __device__ int wrap_mod(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
 constexpr int MIXED_MAX_PASSES = 24;
+constexpr int RF_MAX_CTAS = 64;  // CTAs of the off-grid refinement of one signal
 // Grid-barrier counter of the persistent kernels, their error word and the
 // multi-signal kernel's work-item ticket: a 128-byte line each, zeroed before
 // a launch.
@@ -123,7 +124,7 @@ struct SlotCtl {
   double E1;                // initial energy
   unsigned cnt_grid, cnt_guard, cnt_update;  // last-CTA counters
   unsigned vmax_bits;       // FP32 path: bits of the step's largest objective (atomicMax)
-  unsigned bar_count, bar_gen;  // persistent kernel: grid barrier
+  unsigned bar_count, bar_gen;  // bar_gen: grid barriers the off-grid refinement has passed
   unsigned vmax2[2];        // persistent kernel: vmax_bits of even / odd steps
   double Estart;            // energy of the remainder the call started from
 };
@@ -153,6 +154,7 @@ struct SlotDev {
   int2* cand;               // [cap] (s, j)
   double2* gpart;           // [cap * chunks_of(N)] guard partial sums (x4: persistent, per warp)
   double* epart;            // [chunks_of(N)] energy partial sums (persistent: x4 per warp, x K_max steps)
+  double* rfpart;           // off-grid refinement: [2][RF_MAX_CTAS][6] per-CTA sums of a Newton pass
   StepRec* rec;             // [K_max]
   SlotCtl* ctl;
   long long* phase_clk;     // persistent kernel, optional: 8 SM-clock stamps per step (CTA 0)
@@ -169,7 +171,7 @@ __device__ __forceinline__ double obj_rho64(const SlotDev& sd, int s) { return s
 // Host-visible layout sizes (the bench reports per-step transfer bytes from them).
 static_assert(sizeof(StepRec) == 80, "StepRec layout");
 static_assert(sizeof(SlotCtl) == 64, "SlotCtl layout");
-static_assert(sizeof(SlotDev) == 400, "SlotDev layout");
+static_assert(sizeof(SlotDev) == 408, "SlotDev layout");
 
 // The multi-signal persistent kernel (afd_multi.cu): one N-class of signals
 // (ids[first .. first + count)) and its work split.
@@ -216,6 +218,10 @@ cudaError_t launch_selftest_barrier(const SlotDev* slot, unsigned long long* ela
 cudaError_t launch_selftest_mbarrier(SlotCtl* ctl, unsigned long long* elapsed_ns, cudaStream_t st);
 cudaError_t launch_guard(const SlotDev* slots, const int* ids, int n, int N, int cap, cudaStream_t st);
 cudaError_t launch_update(const SlotDev* slots, const int* ids, int n, int N, cudaStream_t st);
+// Off-grid refinement of each signal's step winner (afd_offgrid.cu), then the
+// update at the refined point.
+cudaError_t launch_refine(const SlotDev* slots, const int* ids, int n, int N, int iters, cudaStream_t st);
+cudaError_t launch_update_offgrid(const SlotDev* slots, const int* ids, int n, int N, cudaStream_t st);
 // Mixed-radix path (afd_mixed.cu): N = 2^a 3^b 5^c, not a power of two.
 cudaError_t launch_grid_mixed(const SlotDev* slots, const int* ids, int n, int N, int prec, int Mmax,
                               cudaStream_t st);

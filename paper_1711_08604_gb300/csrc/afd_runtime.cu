@@ -88,6 +88,10 @@ afd_status check_opts(const afd_plan_opts& o) {
     return set_error(AFD_ERR_INVALID, "guard_cap must lie in 1..%d", MAX_CAP);
   if (o.grid_variant < -1 || o.grid_variant >= GRID_VARIANTS)
     return set_error(AFD_ERR_INVALID, "grid_variant must lie in -1..%d", GRID_VARIANTS - 1);
+  if (o.offgrid_iters < 0 || o.offgrid_iters > 64)
+    return set_error(AFD_ERR_INVALID, "offgrid_iters must lie in 0..64");
+  if (o.offgrid_iters && o.renormalise)
+    return set_error(AFD_ERR_INVALID, "offgrid_iters refines the plain objective: not with renormalise");
   return AFD_OK;
 }
 
@@ -429,6 +433,7 @@ struct SlotPool {
   std::vector<Group> groups;
   std::vector<Fft2Maps> maps;       // TMA descriptors of two-pass slots (N = 65536)
   bool persistent = false;          // single FP32 slot: one persistent launch per decomposition
+  int offgrid = 0;                  // off-grid refinement: Newton iterations per step (0: off)
   bool multi = false;               // batch: all signals in one multi-signal persistent launch
   unsigned* bar_dev = nullptr;      // grid-barrier counter and error word (BAR_BYTES, in the ctl area)
   MultiArgs margs{};                // the multi-signal launch's arguments
@@ -450,7 +455,8 @@ struct SlotPool {
     n = (int)tables.size();
     K_max = K;
     prec = o.precision;
-    persistent = o.persistent != 0;
+    offgrid = o.offgrid_iters;
+    persistent = o.persistent != 0 && offgrid == 0;
     cap = prec == AFD_FP32_GUARDED ? o.guard_cap : 1;
     // group by N (stable: signal order within a group)
     std::vector<int> order(n);
@@ -479,7 +485,8 @@ struct SlotPool {
     size_t off = 0;
     auto place = [&](size_t bytes) { size_t o2 = off; off = align_up(off + bytes); return o2; };
     const size_t o_G = place(8 * g_total);
-    std::vector<size_t> o_c(n), o_g32(n), o_top(n), o_cand(n), o_gp(n), o_ep(n), o_X(n), o_G2(n), o_g32b(n);
+    std::vector<size_t> o_c(n), o_g32(n), o_top(n), o_cand(n), o_gp(n), o_ep(n), o_X(n), o_G2(n), o_g32b(n),
+        o_rf(n);
     for (int i = 0; i < n; ++i) {
       const int N = tables[i]->samples(), M = tables[i]->M;
       const bool two_pass = !tables[i]->nu && prec && N == (1 << TWO_PASS_LOGN);
@@ -500,6 +507,7 @@ struct SlotPool {
       const size_t parts = (size_t)chunks_of(N) * (persistent ? FP64_CHUNK / 32 : 1);
       o_gp[i] = place(sizeof(double2) * cap * parts);
       o_ep[i] = place(sizeof(double) * parts * (persistent ? (size_t)K_max : 1));
+      o_rf[i] = place(offgrid ? sizeof(double) * 2 * RF_MAX_CTAS * 6 : 0);
     }
     const size_t o_rec = place(sizeof(StepRec) * (size_t)n * K_max);
     // control blocks, then the grid-barrier counter and error word of the
@@ -540,6 +548,7 @@ struct SlotPool {
       d.top2 = b + o_top[i];
       d.cand = reinterpret_cast<int2*>(b + o_cand[i]);
       d.gpart = reinterpret_cast<double2*>(b + o_gp[i]);
+      d.rfpart = offgrid ? reinterpret_cast<double*>(b + o_rf[i]) : nullptr;
       d.epart = reinterpret_cast<double*>(b + o_ep[i]);
       d.rec = rec_dev + (size_t)i * K_max;
       d.ctl = ctl_dev + i;
@@ -710,10 +719,17 @@ afd_status enqueue_group(const SlotPool& pool, const SlotPool::Group& g, int K, 
       cnt.n[1] += 1;
       cnt.launches += 1;
     }
-    CUDA_TRY(launch_update(slots, ids, g.count, g.N, st));
+    if (pool.offgrid > 0) {
+      // the winner refined off the grid, then the general update
+      CUDA_TRY(launch_refine(slots, ids, g.count, g.N, pool.offgrid, st));
+      CUDA_TRY(launch_update_offgrid(slots, ids, g.count, g.N, st));
+      cnt.launches += 2;
+    } else {
+      CUDA_TRY(launch_update(slots, ids, g.count, g.N, st));
+      cnt.launches += 1;
+    }
     if (t) AFD_TRY(timer->mark(st, 2));
     cnt.n[2] += 1;
-    cnt.launches += 1;
     if (k + 1 < K) {
       CUDA_TRY(forward());
       if (t) AFD_TRY(timer->mark(st, 3));
@@ -1054,6 +1070,7 @@ void afd_plan_opts_default(afd_plan_opts* o) {
   o->renormalise = 0;
   o->autotune = 1;
   o->grid_variant = -1;
+  o->offgrid_iters = 0;
   o->guard_cap = 16;
   o->force_a1_zero = 0;
   o->device = -1;
@@ -1161,8 +1178,9 @@ afd_status afd_plan_create_nonuniform(afd_plan** out, int N, const double* theta
   AFD_TRY(resolve_opts(opts, o));
   if (o.precision != AFD_FP32_GUARDED)
     return set_error(AFD_ERR_INVALID, "non-uniform samples: the FP32-guarded path only");
-  if (o.force_a1_zero || o.renormalise)
-    return set_error(AFD_ERR_INVALID, "non-uniform samples: force_a1_zero and renormalise are not supported");
+  if (o.force_a1_zero || o.renormalise || o.offgrid_iters)
+    return set_error(AFD_ERR_INVALID,
+                     "non-uniform samples: force_a1_zero, renormalise and offgrid_iters are not supported");
   if (N < 1 || N > (1 << 20) || !theta) return set_error(AFD_ERR_INVALID, "need 1 <= N <= 2^20 samples and theta");
   const double two_pi = 6.283185307179586476925286766559;
   for (int m = 0; m < N; ++m) {
@@ -1334,6 +1352,7 @@ afd_status afd_batch_create(afd_batch** out, int n_signals, const int* N, const 
   int dev = 0;
   // every argument is checked before the first CUDA call
   AFD_TRY(resolve_opts(opts, o));
+  if (o.offgrid_iters) return set_error(AFD_ERR_INVALID, "offgrid_iters: plans only");
   AFD_TRY(check_radii(radii, M));
   if (o.force_a1_zero && radii[0] != 0.0)
     return set_error(AFD_ERR_INVALID, "force_a1_zero needs radii[0] == 0");

@@ -593,6 +593,7 @@ afd_status afd_serve_create(afd_server** out, size_t mem_budget_bytes, const afd
   afd_plan_opts o;
   int dev = 0;
   AFD_TRY(normalise_opts(opts, o, dev));
+  if (o.offgrid_iters) return set_error(AFD_ERR_INVALID, "offgrid_iters: plans only");
   DeviceScope scope(dev);
   if (!scope.ok) return set_error(AFD_ERR_CUDA, "cannot make device %d current", dev);
   AFD_TRY(ensure_configured(dev));
