@@ -179,10 +179,10 @@ def afd_decompose(plan: Plan, G, K_max: int, energy_tol: float = 0.0, out: dict 
     """
     gp, keep = _in_ptr(G)
     K = int(K_max)
-    bufs = {"a": np.zeros(2 * K), "coeff": np.zeros(2 * K), "delta": np.zeros(K + 1),
-            "idx": np.zeros(2 * K, dtype=np.int32)}
-    if out:
-        bufs.update(out)
+    out = out or {}
+    bufs = {k: out[k] if k in out else np.zeros(n, dtype=dt)
+            for k, n, dt in (("a", 2 * K, np.float64), ("coeff", 2 * K, np.float64),
+                             ("delta", K + 1, np.float64), ("idx", 2 * K, np.int32))}
     ptrs = {k: (v.data_ptr() if _is_torch(v) else v.ctypes.data) for k, v in bufs.items()}
     steps = ctypes.c_int(0)
     st = _lib().afd_decompose(plan.handle, gp, K, float(energy_tol), ptrs["a"], ptrs["coeff"],

@@ -422,6 +422,8 @@ struct SlotPool {
   size_t ctl_bytes = 0;             // control blocks and barrier counters
   double2* G_dev = nullptr;         // packed remainders
   StepRec* rec_host = nullptr;      // pinned mirrors
+  bool rec_fresh = false;           // rec_host holds the last run's records
+  std::vector<SlotDev> uploaded;    // the descriptors as last copied to slots_dev (empty: none)
   SlotCtl* ctl_host = nullptr;
   struct Group {
     int N, logN, first, count, Mmax;  // logN = -1: mixed-radix N
@@ -446,6 +448,8 @@ struct SlotPool {
     mem = nullptr;
     rec_host = nullptr;
     ctl_host = nullptr;
+    rec_fresh = false;
+    uploaded.clear();
   }
 
   // tables[i] is the plan of signal i.
@@ -585,13 +589,19 @@ struct SlotPool {
     return upload(0.0, nullptr);
   }
 
+  // Copies the descriptors to the device unless they equal what is there:
+  // only build() and this function write slots_dev.
   afd_status upload(double tol, cudaStream_t st) {
     for (auto& d : host) d.tol = tol;
+    if (uploaded.size() == host.size() && std::memcmp(uploaded.data(), host.data(), sizeof(SlotDev) * n) == 0)
+      return AFD_OK;
+    uploaded.clear();
     if (st) {
       CUDA_TRY(cudaMemcpyAsync(slots_dev, host.data(), sizeof(SlotDev) * n, cudaMemcpyHostToDevice, st));
     } else {
       CUDA_TRY(cudaMemcpy(slots_dev, host.data(), sizeof(SlotDev) * n, cudaMemcpyHostToDevice));
     }
+    uploaded = host;
     return AFD_OK;
   }
 };
@@ -1050,12 +1060,25 @@ afd_status write_outputs(const SlotPool& pool, int i, int K_stride, int steps, d
   return AFD_OK;
 }
 
-afd_status fetch_results(SlotPool& pool, cudaStream_t st) {
-  CUDA_TRY(cudaMemcpyAsync(pool.rec_host, pool.rec_dev, sizeof(StepRec) * (size_t)pool.n * pool.K_max,
-                           cudaMemcpyDeviceToHost, st));
+// The control blocks and, with_rec, the step records into the pinned mirrors
+// (callers whose outputs are all on the device need only the control blocks;
+// the records follow on demand, fetch_records).
+afd_status fetch_results(SlotPool& pool, cudaStream_t st, bool with_rec) {
+  pool.rec_fresh = false;
+  if (with_rec)
+    CUDA_TRY(cudaMemcpyAsync(pool.rec_host, pool.rec_dev, sizeof(StepRec) * (size_t)pool.n * pool.K_max,
+                             cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(pool.ctl_host, pool.ctl_dev, sizeof(SlotCtl) * (size_t)pool.n,
                            cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  pool.rec_fresh = with_rec;
+  return AFD_OK;
+}
+afd_status fetch_records(SlotPool& pool) {
+  if (pool.rec_fresh || !pool.rec_host) return AFD_OK;
+  CUDA_TRY(cudaMemcpy(pool.rec_host, pool.rec_dev, sizeof(StepRec) * (size_t)pool.n * pool.K_max,
+                      cudaMemcpyDeviceToHost));
+  pool.rec_fresh = true;
   return AFD_OK;
 }
 
@@ -1257,7 +1280,11 @@ afd_status afd_decompose_from(afd_plan* plan, const double* G, double E1_in, int
   AFD_TRY(gather_device_outputs(pool, K_max, a_out, coeff_out, delta_out, idx_out, steps_done, E1_out, st));
   if (G_final)
     CUDA_TRY(cudaMemcpyAsync(G_final, pool.G_dev, 16 * (size_t)plan->tables.samples(), cudaMemcpyDefault, st));
-  AFD_TRY(fetch_results(pool, st));
+  // (the pointers are classified while the device runs)
+  double *a_h = host_or_null(a_out), *c_h = host_or_null(coeff_out), *d_h = host_or_null(delta_out);
+  double* e1_h = host_or_null(E1_out);
+  int *ix_h = host_or_null(idx_out), *sd_h = host_or_null(steps_done);
+  AFD_TRY(fetch_results(pool, st, a_h || c_h || d_h || ix_h));
   const int steps = pool.ctl_host[0].k;
   plan->last_steps = steps;
   if (stamps && steps > 0) {
@@ -1267,10 +1294,9 @@ afd_status afd_decompose_from(afd_plan* plan, const double* G, double E1_in, int
       for (int i = 0; i < 7; ++i) plan->phase_sum[i] += (double)(c[8 * k + i + 1] - c[8 * k + i]);
     plan->phase_steps += steps;
   }
-  AFD_TRY(write_outputs(pool, 0, K_max, steps, host_or_null(a_out), host_or_null(coeff_out),
-                        host_or_null(delta_out), host_or_null(idx_out)));
-  if (int* sd = host_or_null(steps_done)) *sd = steps;
-  if (double* e1 = host_or_null(E1_out)) *e1 = pool.ctl_host[0].E1;
+  if (a_h || c_h || d_h || ix_h) AFD_TRY(write_outputs(pool, 0, K_max, steps, a_h, c_h, d_h, ix_h));
+  if (sd_h) *sd_h = steps;
+  if (e1_h) *e1_h = pool.ctl_host[0].E1;
   if (pool.ctl_host[0].err & 4) return set_error(AFD_ERR_TIMEOUT, "a bounded wait on the device ran out at step %d", steps);
   if (pool.ctl_host[0].err & 2) return set_error(AFD_ERR_NUMERIC, "non-finite objective at step %d", steps);
   return AFD_OK;
@@ -1284,6 +1310,11 @@ afd_status afd_decompose(afd_plan* plan, const double* G, int K_max, double ener
 
 afd_status afd_plan_last_info(const afd_plan* plan, int* n_cand_out, int* flags_out, double* obj32_out) {
   if (!plan) return set_error(AFD_ERR_INVALID, "plan is NULL");
+  if (!plan->pool.rec_fresh && plan->last_steps > 0) {
+    DeviceScope scope(plan->device);
+    if (!scope.ok) return set_error(AFD_ERR_CUDA, "cannot make device %d current", plan->device);
+    AFD_TRY(fetch_records(const_cast<afd_plan*>(plan)->pool));  // the plan's last call has completed
+  }
   const StepRec* r = plan->pool.rec_host;
   for (int k = 0; k < plan->last_steps && r; ++k) {
     if (n_cand_out) n_cand_out[k] = r[k].n_cand;
@@ -1412,15 +1443,16 @@ afd_status afd_batch_run(afd_batch* b, const double* G_packed, double energy_tol
   b->tuned = true;
   AFD_TRY(b->runner.run(pool, pool.K_max, b->opts.use_graph != 0, b->cnt, nullptr));
   AFD_TRY(gather_device_outputs(pool, pool.K_max, a_out, coeff_out, delta_out, idx_out, steps_out, nullptr, st));
-  AFD_TRY(fetch_results(pool, st));
   bool numeric = false, timeout = false;
   double *a_h = host_or_null(a_out), *c_h = host_or_null(coeff_out), *d_h = host_or_null(delta_out);
   int *ix_h = host_or_null(idx_out), *so_h = host_or_null(steps_out);
+  const bool host_rec = a_h || c_h || d_h || ix_h;
+  AFD_TRY(fetch_results(pool, st, host_rec));
   for (int i = 0; i < pool.n; ++i) {
     const int steps = pool.ctl_host[i].k;
     numeric |= (pool.ctl_host[i].err & 2) != 0;
     timeout |= (pool.ctl_host[i].err & 4) != 0;
-    AFD_TRY(write_outputs(pool, i, pool.K_max, steps, a_h, c_h, d_h, ix_h));
+    if (host_rec) AFD_TRY(write_outputs(pool, i, pool.K_max, steps, a_h, c_h, d_h, ix_h));
     if (so_h) so_h[i] = steps;
   }
   if (timeout) return set_error(AFD_ERR_TIMEOUT, "a bounded wait on the device ran out");

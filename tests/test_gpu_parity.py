@@ -202,6 +202,18 @@ def test_device_pointers():
     assert np.array_equal(out["coeff"].cpu().numpy().view(np.complex128), host["coeff"])
     assert np.array_equal(out["idx"].cpu().numpy().reshape(8, 2), host["idx"])
     assert np.array_equal(out["delta"].cpu().numpy(), host["delta"])
+    # with every output on the device the step records stay there until
+    # afd_plan_last_info asks for them; they are the host-output run's
+    ref = afd.afd_plan_create(s.N, s.radii)
+    afd.afd_decompose(ref, s.G, 8)
+    want = afd.afd_plan_last_info(ref, 8)
+    got = afd.afd_plan_last_info(plan, 8)
+    for k in ("n_cand", "flags", "obj32"):
+        assert np.array_equal(got[k], want[k]), k
+    # a later host-output call on the same plan refreshes the records
+    afd.afd_decompose(plan, s.G, 3)
+    got3 = afd.afd_plan_last_info(plan, 3)
+    assert np.array_equal(got3["obj32"], want["obj32"][:3])
 
 
 def test_device_outputs_of_batches_and_resumed_runs():
