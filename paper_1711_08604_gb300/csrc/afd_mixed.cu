@@ -18,7 +18,9 @@
 //               transform, objective w_s^2 |F_s(j)|^2, the per-radius best
 //               pair(s) and, in the last CTA of the signal, the selection of
 //               Step 2 -- the same contract as k_grid.
-// k_forward_mixed  one CTA per signal: c_l / N = (1/N) sum_m G(z_m) w^{-ml}.
+// k_forward_mixed  one CTA per signal: c_l / N = (1/N) sum_m G(z_m) w^{-ml};
+//               k_forward_mixed_split the same over S CTAs per signal when N
+//               has a factor 2 (mx_split).
 // The FP64 guard and update kernels are shared with the power-of-two path
 // (they index the sample points modulo N).
 #include <climits>
@@ -34,6 +36,17 @@ namespace afd {
 namespace {
 
 constexpr int MX_THREADS = 256;
+
+// CTAs of the split forward transform: the largest power of two dividing N,
+// at most 16, when the remaining N / S points need two or more passes; 1:
+// one CTA per signal.
+__host__ __device__ inline int mx_split(int N) {
+  int S = N & -N;
+  if (S > 16) S = 16;
+  if (S < 2) return 1;
+  int r[MIXED_MAX_PASSES];
+  return mixed_schedule(N / S, r) >= 2 ? S : 1;
+}
 
 // X_k = sum_{q<3} v_q exp(DIR 2 pi i q k / 3)
 template <int DIR, typename T>
@@ -173,20 +186,21 @@ __device__ __forceinline__ void mx_pass_any(int R, int N, int Ns, const V2<T>* _
   }
 }
 
-// The whole transform (at least two passes): first(b, q, N/R0) supplies pass
-// 0's inputs, last(i, value) consumes the natural-order outputs.  buf holds
-// 2 N points.  Every thread of the CTA must call it.
-template <typename T, int DIR, bool TWS, class First, class Last>
-__device__ void mx_run(const PlanDev& p, V2<T>* buf, const V2<T>* __restrict__ tw, First& first, Last& last) {
-  const int N = p.N, np = p.mix_npass;
+// The whole transform of N points with the np radices radix[] (at least two
+// passes): first(b, q, N/R0) supplies pass 0's inputs, last(i, value)
+// consumes the natural-order outputs.  tw: the N twiddles w^k of this
+// length; buf holds 2 N points.  Every thread of the CTA must call it.
+template <typename T, int DIR, bool TWS, class I, class First, class Last>
+__device__ void mx_run_n(int N, int np, const I* radix, V2<T>* buf, const V2<T>* __restrict__ tw, First& first,
+                         Last& last) {
   V2<T>* cur = buf;
   V2<T>* nxt = buf + N;
   auto to_cur = [&](int i, V2<T> x) { cur[i] = x; };
-  mx_pass_any<T, DIR, TWS>(p.mix_radix[0], N, 1, tw, first, to_cur);
-  int Ns = p.mix_radix[0];
+  mx_pass_any<T, DIR, TWS>(radix[0], N, 1, tw, first, to_cur);
+  int Ns = radix[0];
   for (int ps = 1; ps < np; ++ps) {
     __syncthreads();
-    const int R = p.mix_radix[ps];
+    const int R = radix[ps];
     auto from_cur = [&](int b, int q, int NR) { return cur[b + q * NR]; };
     if (ps + 1 < np) {
       auto to_nxt = [&](int i, V2<T> x) { nxt[i] = x; };
@@ -199,6 +213,11 @@ __device__ void mx_run(const PlanDev& p, V2<T>* buf, const V2<T>* __restrict__ t
     }
     Ns *= R;
   }
+}
+// ... of the plan's length N
+template <typename T, int DIR, bool TWS, class First, class Last>
+__device__ void mx_run(const PlanDev& p, V2<T>* buf, const V2<T>* __restrict__ tw, First& first, Last& last) {
+  mx_run_n<T, DIR, TWS>(p.N, p.mix_npass, p.mix_radix, buf, tw, first, last);
 }
 
 template <typename T>
@@ -338,6 +357,62 @@ k_forward_mixed(const SlotDev* __restrict__ slots, const int* __restrict__ ids) 
   }
 }
 
+// The forward transform over S CTAs per signal (S = mx_split(N) > 1): one
+// decimation-in-frequency step of radix S, the splitting of Theorem 2.1 with
+// radix S.  With N' = N / S, l = l' + p N' and j = S j' + h,
+//   c_j = sum_{l' < N'} w_{N'}^{-j' l'} [ w^{-h l'} sum_{p < S} x(l' + p N') e^{-2 pi i h p / S} ],
+// so CTA h forms the bracket for its N' points l' and transforms it with the
+// mixed-radix passes of N' (w_{N'}^k = w^{S k}), writing c_{S j' + h}.
+template <typename T>
+__global__ void __launch_bounds__(MX_THREADS)
+k_forward_mixed_split(const SlotDev* __restrict__ slots, const int* __restrict__ ids) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_launch_dependents();
+  const SlotDev& sd = slots[ids[blockIdx.y]];
+  const int N = sd.p.N, S = (int)gridDim.x, Np = N / S, h = (int)blockIdx.x;
+  int radix[MIXED_MAX_PASSES];
+  const int np = mixed_schedule(Np, radix);
+  V2<T>* buf = reinterpret_cast<V2<T>*>(smem_raw);
+  V2<T>* tws = buf + 2 * Np;
+  const V2<T>* twg = mx_twiddles<T>(sd.p);
+  for (int i = threadIdx.x; i < Np; i += MX_THREADS) tws[i] = __ldg(&twg[(size_t)S * i]);
+  // e^{-2 pi i h p / S} = conj(w^{((h p) mod S) N'}), p < S <= 16
+  V2<T> ws[16];
+#pragma unroll
+  for (int p = 0; p < 16; ++p) {
+    if (p < S) {
+      const V2<T> w = __ldg(&twg[(size_t)((h * p) % S) * Np]);
+      ws[p] = mk2<T>(w.x, -w.y);
+    }
+  }
+  __syncthreads();
+  pdl_wait();
+  if (ld_done(sd.ctl)) return;
+  const T n = (T)N;
+  auto first = [&](int b, int q, int NR) {
+    const int l = b + q * NR;
+    V2<T> acc = mk2<T>((T)0, (T)0);
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+      if (p < S) {
+        V2<T> x;
+        if constexpr (sizeof(T) == 4) {
+          x = __ldcg(&sd.g32[l + p * Np]);  // G / N in FP32, written by the update
+        } else {
+          const double2 g = __ldcg(&sd.G[l + p * Np]);
+          x = make_double2(g.x / n, g.y / n);
+        }
+        acc = cadd<T>(acc, cmul<T>(x, ws[p]));
+      }
+    }
+    return cmulc<T>(acc, __ldg(&twg[h * l]));  // times w^{-h l'}; h l' < N
+  };
+  V2<T>* c;
+  if constexpr (sizeof(T) == 4) c = sd.c32; else c = sd.c64;
+  auto last = [&](int i, V2<T> x) { c[S * i + h] = x; };
+  mx_run_n<T, -1, true>(Np, np, radix, buf, tws, first, last);
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl_mx(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg{};
@@ -378,6 +453,13 @@ cudaError_t launch_grid_mixed(const SlotDev* slots, const int* ids, int n, int N
 
 cudaError_t launch_forward_mixed(const SlotDev* slots, const int* ids, int n, int N, int prec, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  const int S = mx_split(N);
+  if (S > 1) {
+    // two buffers and the twiddles of N / S points
+    const size_t sm = 3 * (size_t)(N / S) * (prec == AFD_FP32_GUARDED ? 8 : 16);
+    if (prec == AFD_FP32_GUARDED) return launch_pdl_mx(k_forward_mixed_split<float>, dim3(S, n), sm, st, slots, ids);
+    return launch_pdl_mx(k_forward_mixed_split<double>, dim3(S, n), sm, st, slots, ids);
+  }
   const size_t smem = mixed_launch_smem(N, prec);
   if (prec == AFD_FP32_GUARDED) return launch_pdl_mx(k_forward_mixed<float>, dim3(n), smem, st, slots, ids);
   return launch_pdl_mx(k_forward_mixed<double>, dim3(n), smem, st, slots, ids);
@@ -391,6 +473,10 @@ cudaError_t mixed_configure() {
   if ((e = cudaFuncSetAttribute(k_grid_mixed<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
     return e;
   if ((e = cudaFuncSetAttribute(k_forward_mixed<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_forward_mixed_split<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_forward_mixed_split<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
     return e;
   return cudaFuncSetAttribute(k_forward_mixed<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
