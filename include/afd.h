@@ -72,7 +72,8 @@ typedef struct afd_plan_opts {
                           between the phases of a step), and a serving tick whose signals
                           are all FP32-path powers of two up to 16384 runs as one
                           multi-signal persistent launch (every N-class in every phase);
-                          2: as 1, and a batch of such signals runs as one multi-signal
+                          2: as 1, and a batch of such signals (mixed-radix sizes too,
+                          unless N = 16384 is among them) runs as one multi-signal
                           persistent launch too (by default a batch keeps one launch per
                           kernel per N-class and step, replayed as a graph, which measures
                           faster for batches of 2 to 1024 signals); 0: one launch per

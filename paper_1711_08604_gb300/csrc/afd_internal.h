@@ -178,7 +178,8 @@ static_assert(sizeof(SlotDev) == 408, "SlotDev layout");
 constexpr int MULTI_THREADS = 512;
 constexpr int MULTI_MAX_CLASSES = 16;
 struct MultiClass {
-  int logN, first, count, Mmax;
+  int logN, first, count, Mmax;  // logN < 0: a mixed-radix size N (256-thread build only)
+  int N;
   int tiles;    // grid items (radius tiles) per signal
   int gpar;     // guard: candidates in flight per signal (as launch_guard)
   int fgroups;  // forward: signals per CTA (transform groups)
@@ -195,6 +196,8 @@ struct MultiArgs {
 };
 bool multi_size_ok(int logN);  // FP32 powers of two 8 .. 16384
 void multi_class_shape(int logN, int Mmax, int count, int cap, MultiClass* c);  // all but first
+// the same for a mixed-radix size N (FP32 path): one radius per grid item
+void multi_class_shape_mixed(int N, int Mmax, int count, int cap, MultiClass* c);
 cudaError_t multi_configure();
 // One cooperative launch: the fresh signals' initialisation, then K steps.
 cudaError_t launch_multi(const MultiArgs& a, cudaStream_t st);

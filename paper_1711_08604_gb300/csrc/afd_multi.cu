@@ -29,6 +29,7 @@
 #include "afd_device.cuh"
 #include "afd_fft.cuh"
 #include "afd_internal.h"
+#include "afd_mixed.cuh"
 #include "afd_step.cuh"
 
 namespace afd {
@@ -58,6 +59,14 @@ __device__ __forceinline__ void grid_item_l(const MultiArgs& a, const MultiClass
 
 template <int MT>
 __device__ void grid_item(const MultiArgs& a, const MultiClass& c, int sig, int tile) {
+  if (c.logN < 0) {
+    // a mixed-radix size: one radius per item, the selection's scratch in
+    // the dynamic buffer once the transform is done
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if constexpr (MT == MX_THREADS)
+      grid_mixed_body<float>(a.slots, a.ids + c.first, tile, sig, c.tiles, reinterpret_cast<SelectScratch*>(smem_raw));
+    return;
+  }
   switch (c.logN) {
 #define X(L) \
   case L: grid_item_l<MT, L>(a, c, sig, tile); break;
@@ -162,7 +171,12 @@ __device__ __forceinline__ int total_items(const MultiClass* cls, int n, Per per
   return t;
 }
 
-__device__ __forceinline__ int chunks_c(const MultiClass& c) { return chunks_of(1 << c.logN); }
+__device__ __forceinline__ int chunks_c(const MultiClass& c) { return chunks_of(c.N); }
+// forward items of a class: groups of fgroups signals, or S items per signal
+// of a mixed-radix size (mx_split)
+__host__ __device__ __forceinline__ int fwd_items(const MultiClass& c) {
+  return c.logN < 0 ? c.count * mx_split(c.N) : (c.count + c.fgroups - 1) / c.fgroups;
+}
 
 template <int MT>
 __global__ void __launch_bounds__(MT, MT == 256 ? 3 : 1) k_multi(const __grid_constant__ MultiArgs a) {
@@ -220,17 +234,28 @@ __global__ void __launch_bounds__(MT, MT == 256 ? 3 : 1) k_multi(const __grid_co
     });
   };
   // forward transforms, a CTA's groups taking consecutive signals of a class
+  // (a mixed-radix size: one item, or one of S split items, per signal)
   auto forward_phase = [&](const MultiClass* cls, int n, const int* ids) {
     int total = 0;
-    for (int c = 0; c < n; ++c) total += (cls[c].count + cls[c].fgroups - 1) / cls[c].fgroups;
+    for (int c = 0; c < n; ++c) total += fwd_items(cls[c]);
     each_item(total, [&](int item) {
       int first = 0, c = 0;
       for (; c < n; ++c) {
-        const int span = (cls[c].count + cls[c].fgroups - 1) / cls[c].fgroups;
+        const int span = fwd_items(cls[c]);
         if (item < first + span) break;
         first += span;
       }
-      if (c < n) forward_groups<MT>(a, cls[c], ids, (item - first) * cls[c].fgroups);
+      if (c >= n) return;
+      const int local = item - first;
+      if (cls[c].logN < 0) {
+        if constexpr (MT == MX_THREADS) {
+          const int S = mx_split(cls[c].N);
+          if (S > 1) forward_mixed_split_body<float>(a.slots, ids + cls[c].first, local % S, local / S, S);
+          else forward_mixed_body<float>(a.slots, ids + cls[c].first, local);
+        }
+        return;
+      }
+      forward_groups<MT>(a, cls[c], ids, local * cls[c].fgroups);
     });
   };
   if (a.n_fresh > 0) {
@@ -310,6 +335,7 @@ void shape_mt(int logN, int Mmax, int count, int cap, MultiClass* c) {
     default: break;
   }
   c->logN = logN;
+  c->N = 1 << logN;
   c->count = count;
   c->Mmax = Mmax;
   c->tiles = (Mmax + fpc - 1) / fpc;
@@ -318,14 +344,32 @@ void shape_mt(int logN, int Mmax, int count, int cap, MultiClass* c) {
   c->fgroups = fg;
 }
 
+// Dynamic shared memory of a class's items: the transforms' buffers, and for
+// a mixed-radix size also the selection's scratch, which the grid item puts
+// there.
+template <int MT>
+size_t class_smem(const MultiClass& c) {
+  if (c.logN >= 0) return smem_bytes<MT>(c.logN);
+  return std::max({mixed_launch_smem(c.N, AFD_FP32_GUARDED), mixed_split_smem(c.N, AFD_FP32_GUARDED),
+                   sizeof(SelectScratch)});
+}
+
 template <int MT>
 cudaError_t launch_mt(const MultiArgs& a, cudaStream_t st) {
   size_t smem = sizeof(Fp64WarpSmem) * (MT / 32);
-  for (int c = 0; c < a.n_cls; ++c) smem = smem_bytes<MT>(a.cls[c].logN) > smem ? smem_bytes<MT>(a.cls[c].logN) : smem;
-  for (int c = 0; c < a.n_fresh; ++c)
-    smem = smem_bytes<MT>(a.fresh[c].logN) > smem ? smem_bytes<MT>(a.fresh[c].logN) : smem;
+  for (int c = 0; c < a.n_cls; ++c) smem = std::max(smem, class_smem<MT>(a.cls[c]));
+  for (int c = 0; c < a.n_fresh; ++c) smem = std::max(smem, class_smem<MT>(a.fresh[c]));
   int& blocks = g_multi_blocks[MT == 512 ? 1 : 0];
-  if (!blocks) {
+  int blocks_big = 0;  // co-resident CTAs at a footprint above max_smem (mixed-radix sizes)
+  if (smem > max_smem<MT>()) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi<MT>, MT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    blocks_big = per_sm * sms;
+  } else if (!blocks) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -343,17 +387,17 @@ cudaError_t launch_mt(const MultiArgs& a, cudaStream_t st) {
     long long g = 0, gu = 0, up = 0, fw = 0;
     for (int c = 0; c < n; ++c) {
       const MultiClass& x = cls[c];
-      const long long ch = chunks_of(1 << x.logN);
+      const long long ch = chunks_of(x.N);
       g += (long long)x.count * x.tiles;
       gu += ((long long)x.count * x.gpar * ch + NW - 1) / NW;
       up += ((long long)x.count * ch + NW - 1) / NW;
-      fw += (x.count + x.fgroups - 1) / x.fgroups;
+      fw += fwd_items(x);
     }
     need = std::max({need, g, gu, up, fw});
   };
   most(a.cls, a.n_cls);
   most(a.fresh, a.n_fresh);
-  const int grid = (int)std::min<long long>(blocks, need);
+  const int grid = (int)std::min<long long>(blocks_big ? blocks_big : blocks, need);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(MT);
@@ -371,6 +415,16 @@ cudaError_t launch_mt(const MultiArgs& a, cudaStream_t st) {
 
 bool multi_size_ok(int logN) { return logN >= 3 && logN <= 14; }
 
+void multi_class_shape_mixed(int N, int Mmax, int count, int cap, MultiClass* c) {
+  c->logN = -1;
+  c->N = N;
+  c->count = count;
+  c->Mmax = Mmax;
+  c->tiles = Mmax;  // one radius per grid item, as k_grid_mixed
+  c->gpar = count >= 8 ? 1 : (cap < GUARD_PAR ? cap : GUARD_PAR);
+  c->fgroups = 1;
+}
+
 void multi_class_shape(int logN, int Mmax, int count, int cap, MultiClass* c) {
   // the split of the 256-thread build; launch_multi takes the 512-thread
   // build (and redoes the split) when a class of N = 16384 is present
@@ -379,7 +433,9 @@ void multi_class_shape(int logN, int Mmax, int count, int cap, MultiClass* c) {
 }
 
 cudaError_t multi_configure() {
-  cudaError_t e = cudaFuncSetAttribute(k_multi<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem<256>());
+  // (the 256-thread build also takes mixed-radix sizes, up to MIXED_MAX_SMEM)
+  cudaError_t e = cudaFuncSetAttribute(k_multi<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)std::max(max_smem<256>(), (size_t)MIXED_MAX_SMEM));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_multi<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem<512>());
 }

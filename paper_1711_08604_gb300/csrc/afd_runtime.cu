@@ -562,8 +562,19 @@ struct SlotPool {
     bar_dev = reinterpret_cast<unsigned*>(b + o_ctl + align_up(sizeof(SlotCtl) * (size_t)n));
     // The multi-signal persistent kernel takes a batch when every signal is an
     // FP32-path power of two it holds on chip.
+    // (Not for a single signal of a mixed-radix size: the kernel's one-warp
+    // FP64 items, made for many signals, run its guard and update at a
+    // quarter of the per-step kernels' width; measured 1.31 against 0.70 ms
+    // at N = 3000.)
     multi = allow_multi && n > 1 && prec == AFD_FP32_GUARDED && (int)groups.size() <= MULTI_MAX_CLASSES;
-    for (const auto& g : groups) multi = multi && !g.nu && g.logN > 0 && multi_size_ok(g.logN);
+    bool any_mixed = false, any_big = false;
+    for (const auto& g : groups) {
+      multi = multi && !g.nu && (g.logN > 0 ? multi_size_ok(g.logN) : g.logN < 0);
+      any_mixed = any_mixed || g.logN < 0;
+      any_big = any_big || g.logN > 13;
+    }
+    // mixed-radix items run in the 256-thread build, which N = 16384 leaves
+    if (any_mixed && any_big) multi = false;
     margs = MultiArgs{};
     if (multi) {
       margs.slots = slots_dev;
@@ -575,7 +586,8 @@ struct SlotPool {
       margs.n_cls = margs.n_fresh = (int)groups.size();
       for (size_t gi = 0; gi < groups.size(); ++gi) {
         MultiClass& c = margs.cls[gi];
-        multi_class_shape(groups[gi].logN, groups[gi].Mmax, groups[gi].count, cap, &c);
+        if (groups[gi].logN < 0) multi_class_shape_mixed(groups[gi].N, groups[gi].Mmax, groups[gi].count, cap, &c);
+        else multi_class_shape(groups[gi].logN, groups[gi].Mmax, groups[gi].count, cap, &c);
         c.first = groups[gi].first;
         margs.fresh[gi] = c;
       }
@@ -1263,7 +1275,7 @@ afd_status afd_decompose_from(afd_plan* plan, const double* G, double E1_in, int
   }
   if (plan->own_stream) AFD_TRY(plan->runner.order_after_default());
   const bool stamps = plan->timer.on && pool.persistent && plan->opts.precision == AFD_FP32_GUARDED &&
-                      !plan->tables.nu && plan->tables.N <= (1 << PERSISTENT_MAX_LOGN);
+                      !plan->tables.nu && is_pow2(plan->tables.N) && plan->tables.N <= (1 << PERSISTENT_MAX_LOGN);
   if (stamps && plan->phase_cap < K_max) {
     if (plan->phase_dev) cudaFree(plan->phase_dev);
     plan->phase_dev = nullptr;

@@ -160,3 +160,32 @@ def test_mixed_size_limits():
         afd.afd_serve_submit(srv, np.ones(1000, complex), r, 2)  # serving: powers of two only
     assert e.value.status == -1
     srv.close()
+
+
+def test_mixed_batch_in_one_persistent_launch():
+    # persistent=2: the batch, mixed-radix classes included (each radius a grid
+    # item, the forward transform split over items for even N), in one launch
+    # of the multi-signal kernel, bitwise equal to the per-step kernels
+    Ns = [729, 1000, 1024, 1500, 96, 4096, 243, 3000]
+    sigs = [W.random_signal(N, 60 + i) for i, N in enumerate(Ns)]
+    radii = W.radii_linear(20)
+    K = 6
+    res = afd.afd_decompose_batch(sigs, radii, K, persistent=2)
+    for i, G in enumerate(sigs):
+        one = run(G, radii, K, afd.AFD_FP32_GUARDED, persistent=False)
+        assert res["steps"][i] == one["steps"]
+        for key in ("a", "coeff", "delta", "idx"):
+            assert np.array_equal(res[key][i], one[key]), (Ns[i], key)
+    # the stop rule inside the launch: a tolerance between deltas 3 and 4 of
+    # one signal stops it after step 4 and leaves the others as they were
+    tol = float(res["delta"][7][4]) * 1.0000001
+    res2 = afd.afd_decompose_batch(sigs, radii, K, energy_tol=tol, persistent=2)
+    for i, G in enumerate(sigs):
+        plan = afd.afd_plan_create(G.size, radii, persistent=False)
+        try:
+            one = afd.afd_decompose(plan, G, K, tol)
+        finally:
+            plan.close()
+        assert res2["steps"][i] == one["steps"]
+        assert np.array_equal(res2["coeff"][i], one["coeff"]), Ns[i]
+    assert res2["steps"][7] <= 4
