@@ -57,13 +57,13 @@ __device__ __forceinline__ void grid_item_l(const MultiArgs& a, const MultiClass
     grid_body<float, L, MGrid<MT, L>::PP, MGrid<MT, L>::CT>(a.slots, a.ids + c.first, tile, sig, c.tiles);
 }
 
-template <int MT>
+template <int MT, bool MIXED>
 __device__ void grid_item(const MultiArgs& a, const MultiClass& c, int sig, int tile) {
-  if (c.logN < 0) {
+  if (MIXED && c.logN < 0) {
     // a mixed-radix size: one radius per item, the selection's scratch in
     // the dynamic buffer once the transform is done
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if constexpr (MT == MX_THREADS)
+    if constexpr (MIXED && MT == MX_THREADS)
       grid_mixed_body<float>(a.slots, a.ids + c.first, tile, sig, c.tiles, reinterpret_cast<SelectScratch*>(smem_raw));
     return;
   }
@@ -178,7 +178,9 @@ __host__ __device__ __forceinline__ int fwd_items(const MultiClass& c) {
   return c.logN < 0 ? c.count * mx_split(c.N) : (c.count + c.fgroups - 1) / c.fgroups;
 }
 
-template <int MT>
+// MIXED: the build that also takes mixed-radix classes (their item bodies
+// are compiled in only there, so the power-of-two build keeps its registers).
+template <int MT, bool MIXED = false>
 __global__ void __launch_bounds__(MT, MT == 256 ? 3 : 1) k_multi(const __grid_constant__ MultiArgs a) {
   constexpr int NW = MT / 32;
   // the FP64 items' candidate sums share the dynamic buffer with the transforms
@@ -247,8 +249,8 @@ __global__ void __launch_bounds__(MT, MT == 256 ? 3 : 1) k_multi(const __grid_co
       }
       if (c >= n) return;
       const int local = item - first;
-      if (cls[c].logN < 0) {
-        if constexpr (MT == MX_THREADS) {
+      if (MIXED && cls[c].logN < 0) {
+        if constexpr (MIXED && MT == MX_THREADS) {
           const int S = mx_split(cls[c].N);
           if (S > 1) forward_mixed_split_body<float>(a.slots, ids + cls[c].first, local % S, local / S, S);
           else forward_mixed_body<float>(a.slots, ids + cls[c].first, local);
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(MT, MT == 256 ? 3 : 1) k_multi(const __grid_co
       each_item(total_items(a.cls, a.n_cls, per), [&](int item) {
         int local = 0;
         const int c = find_class(a.cls, a.n_cls, item, per, &local);
-        if (c >= 0) grid_item<MT>(a, a.cls[c], local / a.cls[c].tiles, local % a.cls[c].tiles);
+        if (c >= 0) grid_item<MT, MIXED>(a, a.cls[c], local / a.cls[c].tiles, local % a.cls[c].tiles);
       });
     }
     if (!barrier()) return;
@@ -359,13 +361,17 @@ cudaError_t launch_mt(const MultiArgs& a, cudaStream_t st) {
   size_t smem = sizeof(Fp64WarpSmem) * (MT / 32);
   for (int c = 0; c < a.n_cls; ++c) smem = std::max(smem, class_smem<MT>(a.cls[c]));
   for (int c = 0; c < a.n_fresh; ++c) smem = std::max(smem, class_smem<MT>(a.fresh[c]));
+  bool mixed = false;
+  for (int c = 0; c < a.n_cls; ++c) mixed = mixed || a.cls[c].logN < 0;
+  // the build with the mixed-radix bodies only when a class needs them
+  void (*kern)(MultiArgs) = (MT == 256 && mixed) ? k_multi<256, true> : k_multi<MT>;
   int& blocks = g_multi_blocks[MT == 512 ? 1 : 0];
-  int blocks_big = 0;  // co-resident CTAs at a footprint above max_smem (mixed-radix sizes)
-  if (smem > max_smem<MT>()) {
+  int blocks_big = 0;  // co-resident CTAs at a footprint above max_smem, or of the mixed build
+  if (smem > max_smem<MT>() || kern != k_multi<MT>) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi<MT>, MT, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     blocks_big = per_sm * sms;
@@ -408,7 +414,7 @@ cudaError_t launch_mt(const MultiArgs& a, cudaStream_t st) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_multi<MT>, a);
+  return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 }  // namespace
@@ -433,9 +439,11 @@ void multi_class_shape(int logN, int Mmax, int count, int cap, MultiClass* c) {
 }
 
 cudaError_t multi_configure() {
-  // (the 256-thread build also takes mixed-radix sizes, up to MIXED_MAX_SMEM)
-  cudaError_t e = cudaFuncSetAttribute(k_multi<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)std::max(max_smem<256>(), (size_t)MIXED_MAX_SMEM));
+  cudaError_t e = cudaFuncSetAttribute(k_multi<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem<256>());
+  if (e != cudaSuccess) return e;
+  // the 256-thread build with mixed-radix sizes, up to MIXED_MAX_SMEM
+  e = cudaFuncSetAttribute(k_multi<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)std::max(max_smem<256>(), (size_t)MIXED_MAX_SMEM));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_multi<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem<512>());
 }
