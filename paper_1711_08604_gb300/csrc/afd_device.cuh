@@ -5,6 +5,7 @@
 #pragma once
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "afd_internal.h"
 
@@ -108,6 +109,29 @@ struct Best1D {
   }
 };
 
+// The best two (value, index) pairs of a whole warp's Best2F, in every lane,
+// by four warp reductions instead of a shuffle tree: the best is the largest
+// v1 (lowest index on ties); the second is the best of the owner lane's
+// (v2, j2) and every other lane's (v1, j1), since a lane's second pair never
+// beats its first.  The values are >= -1 and never NaN (push_ascending and
+// merge keep NaN out), so their order is the float order; indices are
+// distinct.  Bitwise the result of the shuffle-tree merge.
+__device__ __forceinline__ void warp_top2(Best2F& b) {
+  float v1, v2;
+  unsigned j1, j2;
+  asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(v1) : "f"(b.v1));
+  asm volatile("redux.sync.min.u32 %0, %1, 0xffffffff;" : "=r"(j1) : "r"(b.v1 == v1 ? (unsigned)b.j1 : 0xffffffffu));
+  const bool own = (unsigned)b.j1 == j1;
+  const float cv = own ? b.v2 : b.v1;
+  const unsigned cj = (unsigned)(own ? b.j2 : b.j1);
+  asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(v2) : "f"(cv));
+  asm volatile("redux.sync.min.u32 %0, %1, 0xffffffff;" : "=r"(j2) : "r"(cv == v2 ? cj : 0xffffffffu));
+  b.v1 = v1;
+  b.j1 = (int)j1;
+  b.v2 = v2;
+  b.j2 = (int)j2;
+}
+
 // Reduce B over each group of TPF consecutive threads; the group's thread
 // t == 0 ends with the result.  All threads of the CTA must call it.
 // FRESH: red was last read before a CTA barrier the caller has passed since,
@@ -115,8 +139,13 @@ struct Best1D {
 template <int TPF, class B, bool FRESH = false>
 __device__ __forceinline__ void group_reduce(B& b, B* red) {
   constexpr int W = TPF < 32 ? TPF : 32;
+  constexpr bool REDUX = std::is_same<B, Best2F>::value && TPF >= 32;
+  if constexpr (REDUX) {
+    warp_top2(b);
+  } else {
 #pragma unroll
-  for (int off = W / 2; off > 0; off >>= 1) b.merge(b.shfl(off));
+    for (int off = W / 2; off > 0; off >>= 1) b.merge(b.shfl(off));
+  }
   if constexpr (TPF > 32) {
     // the group's warp results, merged by a shuffle tree in its first warp
     // (the best pair of a set of distinct indices does not depend on the
@@ -130,8 +159,12 @@ __device__ __forceinline__ void group_reduce(B& b, B* red) {
       B o;
       if (lane < WPG) o = red[warp + lane];
       else o.init();
+      if constexpr (REDUX) {
+        warp_top2(o);
+      } else {
 #pragma unroll
-      for (int off = WPG / 2; off > 0; off >>= 1) o.merge(o.shfl(off));
+        for (int off = WPG / 2; off > 0; off >>= 1) o.merge(o.shfl(off));
+      }
       if (lane == 0) b = o;
     }
   }
