@@ -388,8 +388,7 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
     bb.init();
 #pragma unroll
     for (int e = 0; e < 16; ++e) bb.push_ascending(norm2<float>(v[e]), j2 + 256 * (t + 16 * e));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) bb.merge(bb.shfl(off));
+    warp_top2(bb);
     unsigned last = 0;
     __syncwarp();  // the warp's reads and writes of the slot come before its arrival
     if (lane == 0) {
@@ -419,8 +418,7 @@ k_grid2_pass2(const SlotDev* __restrict__ slots, const __grid_constant__ Fft2Map
         s_arrive[i & 1] = 0u;
         issue(i + 2);
       }
-#pragma unroll
-      for (int off = 4; off > 0; off >>= 1) o.merge(o.shfl(off));
+      warp_top2(o);  // the eight pairs (the other lanes hold empty ones)
       if (lane == 0) {
         const float w2 = obj_w32(sd, s);
         Top2F r;
