@@ -561,11 +561,10 @@ struct SlotPool {
     CUDA_TRY(cudaMemcpy(ids_dev, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     bar_dev = reinterpret_cast<unsigned*>(b + o_ctl + align_up(sizeof(SlotCtl) * (size_t)n));
     // The multi-signal persistent kernel takes a batch when every signal is an
-    // FP32-path power of two it holds on chip.
-    // (Not for a single signal of a mixed-radix size: the kernel's one-warp
-    // FP64 items, made for many signals, run its guard and update at a
-    // quarter of the per-step kernels' width; measured 1.31 against 0.70 ms
-    // at N = 3000.)
+    // FP32-path power of two it holds on chip or of a mixed-radix size (not
+    // beside N = 16384).  Not a single signal of a mixed-radix size: there the
+    // per-step kernels measured faster (0.70 ms against 0.93-1.31 ms at
+    // N = 3000; the kernel's FP64 items are made for many signals).
     multi = allow_multi && n > 1 && prec == AFD_FP32_GUARDED && (int)groups.size() <= MULTI_MAX_CLASSES;
     bool any_mixed = false, any_big = false;
     for (const auto& g : groups) {
